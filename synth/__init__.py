@@ -1,0 +1,228 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module builds matrices and vectors only.  It holds none of the
+accelerated-Jacobi arithmetic, and both the FP64 oracle and the CUDA library
+take its outputs as plain inputs.  Random numbers come from numpy's PCG64 bit
+generator with an explicit seed.
+
+A CSR matrix is a dict ``{"n", "row_ptr" (int32, n+1), "col" (int32, nnz),
+"val" (float64, nnz)}``.  Column indices ascend within every row.
+
+Workloads (the paper's data sets are not in this container, so these stand in
+for them):
+  * ``poisson2d(N)``: 5-point Dirichlet Laplacian on an N x N grid (diagonal 4,
+    neighbours -1, natural row-major ordering).  Its eigenvalues are known in
+    closed form.
+  * ``poisson3d(N)``: the 7-point analogue (diagonal 6).
+  * ``sdd(n)``: the strictly diagonally dominant matrix of Section 4.1.  It has
+    n on the diagonal and -1 elsewhere, and with b = 1 the exact solution is 1.
+  * ``chung_lu_laplacian``: the weighted Laplacian D - W of a Chung-Lu
+    power-law graph.  It stands in for the SuiteSparse graphs of Section 4.2.
+    Isolated vertices are kept as empty rows.
+  * ``rgg_knn_laplacian``: the Laplacian of a symmetrised k-nearest-neighbour
+    random geometric graph in the unit square, with Gaussian weights.
+"""
+import numpy as np
+
+try:  # the rhs b = Q x* uses a library sparse product; it is input construction only
+    import scipy.sparse as _sp
+except Exception:  # pragma: no cover
+    _sp = None
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def poisson2d(N):
+    """5-point Dirichlet Laplacian on an N x N grid, row r = j*N + i."""
+    n = N * N
+    r = np.arange(n, dtype=np.int64)
+    i = r % N
+    j = r // N
+    offs = [(-N, j > 0), (-1, i > 0), (0, np.ones(n, bool)), (1, i < N - 1), (N, j < N - 1)]
+    return _stencil(n, r, offs, 4.0)
+
+
+def poisson3d(N):
+    """7-point Dirichlet Laplacian on an N^3 grid, row r = (k*N + j)*N + i."""
+    n = N * N * N
+    r = np.arange(n, dtype=np.int64)
+    i = r % N
+    j = (r // N) % N
+    k = r // (N * N)
+    NN = N * N
+    offs = [(-NN, k > 0), (-N, j > 0), (-1, i > 0), (0, np.ones(n, bool)),
+            (1, i < N - 1), (N, j < N - 1), (NN, k < N - 1)]
+    return _stencil(n, r, offs, 6.0)
+
+
+def _stencil(n, r, offs, diag):
+    m = len(offs)
+    mask = np.empty((n, m), dtype=bool)
+    for c, (o, ok) in enumerate(offs):
+        mask[:, c] = ok
+    counts = mask.sum(axis=1)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    nnz = int(row_ptr[-1])
+    cols = np.empty((n, m), dtype=np.int32)
+    vals = np.empty((n, m), dtype=np.float64)
+    for c, (o, ok) in enumerate(offs):
+        cols[:, c] = (r + o).astype(np.int32) if o != 0 else r.astype(np.int32)
+        vals[:, c] = diag if o == 0 else -1.0
+    col = cols[mask]
+    val = vals[mask]
+    assert col.size == nnz
+    return {"n": n, "row_ptr": row_ptr.astype(np.int32), "col": col, "val": val}
+
+
+def sdd(n):
+    """Q = (n + 1) I - 1 1^T: n on the diagonal, -1 off it (Section 4.1)."""
+    row_ptr = (np.arange(n + 1, dtype=np.int64) * n).astype(np.int32)
+    col = np.tile(np.arange(n, dtype=np.int32), n)
+    val = np.full(n * n, -1.0)
+    val[np.arange(n) * n + np.arange(n)] = float(n)
+    return {"n": n, "row_ptr": row_ptr, "col": col, "val": val}
+
+
+def from_edges(n, u, v, w):
+    """Laplacian D - W of an undirected weighted graph with edge list (u, v, w),
+    u != v and no duplicate pairs.  Isolated vertices get empty rows."""
+    u = np.asarray(u, np.int64)
+    v = np.asarray(v, np.int64)
+    w = np.asarray(w, np.float64)
+    deg = np.zeros(n)
+    np.add.at(deg, u, w)
+    np.add.at(deg, v, w)
+    has = deg != 0
+    dr = np.nonzero(has)[0]
+    rows = np.concatenate([u, v, dr])
+    cols = np.concatenate([v, u, dr])
+    vals = np.concatenate([-w, -w, deg[dr]])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    counts = np.bincount(rows, minlength=n)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    if row_ptr[-1] >= 2 ** 31:
+        raise ValueError("nnz exceeds int32 indices")
+    return {"n": n, "row_ptr": row_ptr.astype(np.int32), "col": cols.astype(np.int32),
+            "val": vals}
+
+
+def chung_lu_laplacian(n, mean_degree=16.0, exponent=2.5, seed=3, wlo=0.5, whi=1.5):
+    """Weighted Laplacian of a Chung-Lu graph.
+
+    Expected degrees are w_i proportional to (i + i0)^(-1/(exponent-1)), with
+    mean ``mean_degree``.  The offset i0 is chosen so that w_max = sqrt(sum w).
+    Endpoint pairs are drawn independently in proportion to w.  Self-loops are
+    dropped, and of each duplicate pair the first drawn is kept with its
+    U(wlo, whi) weight.  The sample count is rescaled until the mean degree is
+    within 1 % of ``mean_degree``.
+    """
+    rng = _rng(seed)
+    gamma = 1.0 / (exponent - 1.0)
+    idx = np.arange(n, dtype=np.float64)
+
+    def shape(i0):
+        s = (idx + i0) ** (-gamma)
+        return s * (mean_degree * n / s.sum())
+
+    lo, hi = 0.0, float(n)
+    for _ in range(60):  # bisection on i0 so that w_0 = sqrt(sum w)
+        mid = 0.5 * (lo + hi)
+        w = shape(max(mid, 1e-9))
+        if w[0] > np.sqrt(w.sum()):
+            lo = mid
+        else:
+            hi = mid
+    w = shape(max(hi, 1e-9))
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    target = mean_degree * n / 2.0
+    m = int(round(target))
+    for _ in range(6):
+        a = np.searchsorted(cdf, rng.random(m), side="right")
+        b = np.searchsorted(cdf, rng.random(m), side="right")
+        np.minimum(a, n - 1, out=a)
+        np.minimum(b, n - 1, out=b)
+        wt = rng.uniform(wlo, whi, m)
+        keep = a != b
+        a, b, wt = a[keep], b[keep], wt[keep]
+        key = np.minimum(a, b).astype(np.int64) * n + np.maximum(a, b)
+        _, first = np.unique(key, return_index=True)
+        ne = first.size
+        if abs(ne - target) <= 0.01 * target:
+            break
+        m = int(round(m * target / ne))
+    first.sort()
+    u = np.minimum(a, b)[first]
+    v = np.maximum(a, b)[first]
+    return from_edges(n, u, v, wt[first])
+
+
+def rgg_knn_laplacian(n, k=8, seed=4):
+    """Laplacian of a random geometric graph: n points U[0,1]^2, each joined to
+    its k nearest neighbours (union symmetrisation), weight exp(-d^2/sigma^2)
+    with sigma the median k-th neighbour distance."""
+    from scipy.spatial import cKDTree
+    rng = _rng(seed)
+    P = rng.random((n, 2))
+    dist, nb = cKDTree(P).query(P, k=k + 1)
+    sigma = float(np.median(dist[:, k]))
+    src = np.repeat(np.arange(n), k)
+    dst = nb[:, 1:].reshape(-1)
+    d = dist[:, 1:].reshape(-1)
+    lo = np.minimum(src, dst).astype(np.int64)
+    hi = np.maximum(src, dst).astype(np.int64)
+    key = lo * n + hi
+    _, first = np.unique(key, return_index=True)
+    w = np.exp(-(d[first] ** 2) / sigma ** 2)
+    return from_edges(n, lo[first], hi[first], w)
+
+
+def uniform(n, seed, lo=-1.0, hi=1.0):
+    return _rng(seed).uniform(lo, hi, n)
+
+
+def normal(n, seed):
+    return _rng(seed).standard_normal(n)
+
+
+def rhs(Q, xstar):
+    """b = Q x* (consistent by construction), via a library sparse product."""
+    n = int(Q["n"])
+    A = _sp.csr_matrix((Q["val"], Q["col"], Q["row_ptr"]), shape=(n, n))
+    return A @ np.asarray(xstar, np.float64)
+
+
+def nnz(Q):
+    return int(Q["row_ptr"][-1])
+
+
+def workload(name, seed=None):
+    """The named workloads used by tests and the benchmark: returns (Q, b, xstar)."""
+    if name == "poisson2d_64":
+        Q = poisson2d(64)
+        xs = uniform(Q["n"], 1 if seed is None else seed)
+    elif name == "poisson3d_256":
+        Q = poisson3d(256)
+        xs = normal(Q["n"], 2 if seed is None else seed)
+    elif name.startswith("poisson3d_"):
+        Q = poisson3d(int(name.split("_")[1]))
+        xs = normal(Q["n"], 2 if seed is None else seed)
+    elif name.startswith("poisson2d_"):
+        Q = poisson2d(int(name.split("_")[1]))
+        xs = uniform(Q["n"], 1 if seed is None else seed)
+    elif name.startswith("chunglu_"):
+        n = int(name.split("_")[1])
+        Q = chung_lu_laplacian(n, seed=3 if seed is None else seed)
+        xs = uniform(n, 3 if seed is None else seed + 1000)
+    elif name.startswith("rgg_"):
+        n = int(name.split("_")[1])
+        Q = rgg_knn_laplacian(n, seed=4 if seed is None else seed)
+        xs = uniform(n, 4 if seed is None else seed + 1000)
+    else:
+        raise KeyError(name)
+    return Q, rhs(Q, xs), xs
