@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the fused accelerated-Jacobi (AJ) iteration on GB300.
+
+One step = one full solve of the 3-D 7-point Poisson system on a 256^3 grid
+(n = 16,777,216, nnz = 117,047,296, FP64 CSR with int32 indices, x* ~ N(0,1),
+b = Q x*) to relative residual 1e-8, from device-resident inputs.
+
+Metric: algorithmic HBM GB/s of the fused iteration (bytes the method must move
+per iteration x iterations / step time); ms_per_step is the time to 1e-8.
+The JSON line also carries the roofline of the fused kernel, the FP64 CPU
+oracle timed on a bounded sample, an end-to-end figure through the C ABI with
+host buffers, and the other precisions as variants.
+
+Multi-GPU: the workload partitions into independent systems, so each rank
+solves its own replica (weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "poisson3d_256"
+METRIC = "fused AJ-iteration HBM GB/s; time to 1e-8 residual; served solves/s, p99"
+UNIT = "GB/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP64 issue rate of GB300 derived from its nominal 1.25 TFLOP/s FP64 (2 flops per FMA):
+# 152 SMs x 2 DFMA/clk x 2.07 GHz = 0.629 T DFMA/s = 1.26 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def algorithmic_bytes(n, nnz, precision):
+    """Bytes one fused iteration must move: the matrix once (values + int32
+    column indices), row pointers, and five n-vectors (read x^t, x^{t-1}, b,
+    J^{-1}; write x^{t+1})."""
+    vb = {"fp64": 8, "df64": 8, "fp32_ir": 4, "bf16_ir": 2}[precision]
+    sb = {"fp64": 8, "df64": 8, "fp32_ir": 4, "bf16_ir": 4}[precision]
+    return nnz * (vb + 4) + 4 * (n + 1) + n * 5 * sb
+
+
+def fp64_flops(n, nnz):
+    """FP64 flops of one FP64 fused iteration (FMA = 2): two FMA per stored
+    entry (sums at x^t and x^{t-1}) and 17 per row (extrapolation, update,
+    reductions)."""
+    return 4 * nnz + 17 * n
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(Q, b, iters):
+    """Time the FP64 oracle (one thread, as it stands) on `iters` iterations."""
+    import oracle
+    J = oracle.j_absrowsum(Q)
+    t0 = time.perf_counter()
+    oracle.solve(Q, b, J, maxit=iters, stop=oracle.STOP_NONE)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    Q, b, xs = synth.workload(WORKLOAD)
+    n, nnz = Q["n"], int(Q["row_ptr"][-1])
+    B = algorithmic_bytes(n, nnz, "fp64")
+    per_step = 2
+    for _ in range(args.warmup):
+        cpu_oracle_sample(Q, b, 1)
+    ts = [cpu_oracle_sample(Q, b, per_step) for _ in range(args.steps)]
+    tot = sum(ts)
+    value = B * per_step * args.steps / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "3-D 7-point Dirichlet Poisson 256^3 (n=16777216, nnz=117047296), "
+                               "FP64 CSR int32; each step %d oracle iterations" % per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d steps x %d iterations of the FP64 C oracle, one thread"
+                                   % (args.steps, per_step)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32_ir", "bf16_ir"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=12)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="poisson3d_N | poisson2d_N | chunglu_N | rgg_N (profiling cases)")
+    ap.add_argument("--fixed-iters", type=int, default=0,
+                    help="run exactly this many iterations per step instead of solving to 1e-8")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import synth
+    from paper_2407_03272_gb300 import aj
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    L = aj.lib()
+
+    Q, b, xs = synth.workload(args.workload)
+    n, nnz = Q["n"], int(Q["row_ptr"][-1])
+    tensors = [torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+               for a in (Q["row_ptr"], Q["col"], Q["val"], b)]
+    stream = torch.cuda.current_stream()
+
+    def make(precision):
+        ctx = aj.Context(*tensors, n=n)
+        ctx.set_stream(stream)
+        if args.fixed_iters:
+            ctx.set(precision=precision, stop=aj.AJ_STOP_NONE, maxit=args.fixed_iters)
+        else:
+            ctx.set(precision=precision, tol=1e-8, maxit=200000)
+        return ctx
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def time_solves(ctx, steps, warmup):
+        for _ in range(warmup):
+            ctx.solve(out=out)
+        barrier()
+        l0 = L.aj_kernel_launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        infos = []
+        e0.record(stream)
+        for _ in range(steps):
+            _, info = ctx.solve(out=out)
+            infos.append(info)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        return ms, infos, L.aj_kernel_launches() - l0
+
+    # ---- headline: the chosen precision, K timed solves
+    ctx = make(args.precision)
+    with Clocks(dev.index) as clk:
+        ms, infos, launches = time_solves(ctx, args.steps, args.warmup)
+    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    B = algorithmic_bytes(n, nnz, args.precision)
+    iters = sum(i["iters"] for i in infos)
+    value = B * iters * ws / (ms * 1e-3) / 1e9
+    kernel_ms = sum(i["kernel_ms"] for i in infos)
+    sweeps = sum(i["sweeps"] for i in infos)
+    hbm_peak, peak_kind = load_peaks()
+    kern_gbs = B * iters / (kernel_ms * 1e-3) / 1e9
+    if args.precision == "fp64":
+        achieved_tf = fp64_flops(n, nnz) * iters / (kernel_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s FP64)",
+                "hbm": {"achieved": kern_gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": kern_gbs / hbm_peak, "peak_kind": peak_kind}}
+    else:
+        roof = {"bound": "hbm", "achieved": kern_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": kern_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind + " (burst copy)"}
+    roof["kernel"] = "aj_persistent_kernel<%s>" % {"fp64": "PolF64", "df64": "PolDF64",
+                                                  "fp32_ir": "PolF32", "bf16_ir": "PolB16"}[args.precision]
+    roof["bytes_per_iteration"] = B
+    roof["kernel_ms_per_iteration"] = kernel_ms / max(iters, 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "df64": "f32x2 (double-float)", "fp32_ir": "f32 inner / f64 outer",
+                  "bf16_ir": "bf16 values, f32 inner / f64 outer"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": ("3-D 7-point Dirichlet Poisson 256^3 (n=16777216, nnz=117047296), "
+                                "FP64 CSR int32, x*~N(0,1) seed 2, b=Qx*; solve to rel. residual 1e-8")
+                   if args.workload == WORKLOAD and not args.fixed_iters else
+                   "%s (n=%d, nnz=%d), %s" % (args.workload, n, nnz,
+                                              "%d fixed iterations" % args.fixed_iters
+                                              if args.fixed_iters else "solve to 1e-8"),
+                   "precision": args.precision, "parallelism": "replicas x%d" % ws,
+                   "l2": "inputs larger than L2 (%.2f GB per sweep)" % (B / 1e9)},
+        "time_to_tol_ms": ms / args.steps,
+        "iterations": infos[-1]["iters"], "restarts": infos[-1]["restarts"],
+        "relres": infos[-1]["relres"], "sweeps_per_solve": sweeps / len(infos),
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "clocks": clk.summary(),
+    }
+    del ctx
+    # ---- other precisions (not part of the timed region above)
+    if not args.no_variants:
+        var = {}
+        for p in ("fp64", "df64", "fp32_ir", "bf16_ir"):
+            c = make(p)
+            vms, vinf, _ = time_solves(c, 2, 1)
+            vb = algorithmic_bytes(n, nnz, p)
+            it = sum(i["iters"] for i in vinf)
+            kms = sum(i["kernel_ms"] for i in vinf)
+            var[p] = {"time_to_tol_ms": vms / 2, "iterations": vinf[-1]["iters"],
+                      "outer": vinf[-1]["outer"], "relres": vinf[-1]["relres"],
+                      "fused_GBps": vb * it / (kms * 1e-3) / 1e9,
+                      "fused_hbm_frac": vb * it / (kms * 1e-3) / 1e9 / hbm_peak,
+                      "kernel_ms_per_iteration": kms / max(it, 1)}
+            del c
+        line["variants"] = var
+    # ---- end to end through the C ABI with pinned host buffers
+    if not args.no_e2e:
+        host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                for a in (Q["row_ptr"], Q["col"], Q["val"], b)]
+        xh = torch.empty(n, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host)
+        d2h = xh.numel() * xh.element_size()
+        walls, its = [], 0
+        for k in range(1 + 2):
+            barrier()
+            t0 = time.perf_counter()
+            c = aj.Context(*host, n=n)
+            c.set_stream(stream)
+            c.set(precision=args.precision, tol=1e-8, maxit=200000)
+            _, inf = c.solve(out=xh)
+            c.close()
+            barrier()
+            if k > 0:
+                walls.append(time.perf_counter() - t0)
+                its += inf["iters"]
+        e2e_v = B * its / sum(walls) / 1e9
+        line["e2e"] = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * sum(walls) / len(walls)}
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1)
+    if not args.no_cpu and ws == 1 and rank == 0:
+        T = args.cpu_iters
+        t = cpu_oracle_sample(Q, b, T)
+        cpu_v = algorithmic_bytes(n, nnz, "fp64") * T / t / 1e9
+        line["cpu_baseline"] = {
+            "value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d iterations of the FP64 C oracle (one thread) on the same system; "
+                      "%.0f ms per iteration, %.1f s extrapolated to the GPU's %d iterations"
+                      % (T, 1e3 * t / T, t / T * infos[-1]["iters"], infos[-1]["iters"])}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,200 @@
+/*
+ * aj.h -- C ABI of libaj, a GB300 (sm_103a) solver for Q x = b with sparse
+ * symmetric positive semidefinite Q by the Nesterov-accelerated, adaptively
+ * restarted Jacobi method of Liang, Pang, Toh and Yang (arXiv 2407.03272).
+ *
+ * The problem (Section 1, eqs. linear-sys and qp): Q x = b with Q SPSD and
+ * b in range(Q), equivalently min f(x) = 1/2 <x, Qx> - <b, x>.
+ *
+ * The iteration (Algorithm alg-jacobi, Section 3, with the restart rule of
+ * Algorithm alg-apg-re, Section 2.2), t = 1, 2, ...:
+ *     x^t = y^t + J^{-1} (b - Q y^t)                       (J diagonal)
+ *     if IsRestart and t > K_re + K_l and <Q y^t - b, x^t - x^{t-1}> >= 0:
+ *         K_re = t, K_{l+1} = 2 K_l, l = l + 1, alpha_{t+1} = 1,
+ *         y^{t+1} = x^t = x^{t-1}
+ *     else:
+ *         alpha_{t+1} = (1 + sqrt(1 + 4 alpha_t^2)) / 2
+ *         y^{t+1} = x^t + ((alpha_t - 1) / alpha_{t+1}) (x^t - x^{t-1})
+ * with x^0 = y^1, alpha_1 = 1.  One iteration is one fused HBM sweep on the
+ * GPU: SpMV at y, J^{-1} scaling, x update, momentum extrapolation and the
+ * FP64 restart/stop reductions in one persistent grid-synchronised kernel.
+ *
+ * Conventions for every entry point:
+ *   - Return value: AJ_OK (0), a negative AJ_E* error, or AJ_PENDING (> 0,
+ *     aj_poll only).  The library never aborts or exits; device-side failures
+ *     (non-finite reductions, barrier timeouts) come back as status codes.
+ *   - Pointers named *_on_device / on_device = 1 are CUDA device pointers of
+ *     the current device; otherwise host pointers.  The caller owns every
+ *     pointer it passes; the library copies what it keeps and never touches
+ *     caller memory after the call returns.
+ *   - Sizes are element counts unless the name says bytes.
+ *   - Calls on one aj_ctx are not thread-safe; different contexts are
+ *     independent.  All GPU work of a context runs on its stream
+ *     (aj_set_stream; default: the legacy default stream) and every call
+ *     returns only after that work has finished.
+ */
+#ifndef AJ_H
+#define AJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int aj_status;
+#define AJ_OK 0
+#define AJ_EINVAL (-1)     /* bad argument or input that is not a valid SPSD CSR matrix */
+#define AJ_ENOMEM (-2)     /* device or host allocation failed, or over the memory budget */
+#define AJ_ECUDA (-3)      /* a CUDA runtime call failed */
+#define AJ_EMAXIT (-4)     /* maxit reached before the stop test held (x is still returned) */
+#define AJ_EDIVERGED (-5)  /* residual grew by > 1e8 over its starting value: S = J - Q not PSD */
+#define AJ_ENONFINITE (-6) /* a reduction became NaN or Inf */
+#define AJ_ETIMEOUT (-7)   /* a device-side grid barrier gave up waiting */
+#define AJ_EBUSY (-8)      /* a request can never be admitted (larger than the budget) */
+#define AJ_PENDING 1       /* aj_poll: the request has not finished yet */
+
+typedef struct aj_ctx aj_ctx;
+typedef struct aj_server aj_server;
+
+/* A square CSR matrix Q (n x n) with int32 indices, FP64 values.
+ * row_ptr[0] = 0, row_ptr non-decreasing, row_ptr[n] = nnz, 0 <= col < n.
+ * Column order within a row is free (duplicates are summed).  Every row
+ * either has a positive diagonal entry or is entirely zero (an isolated
+ * vertex of a graph Laplacian); a zero row gets J_kk = 1 (Section 3 assumes
+ * no zero row; J = 1 keeps J invertible and S = J - Q PSD there). */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+  int on_device; /* 1: the three arrays (and b in aj_create) are device pointers */
+} aj_csr;
+
+/* Choice of the diagonal proximal matrix J (S = J - Q must be PSD). */
+#define AJ_J_ABSROWSUM 0   /* eq. J-diag: J_kk = Q_kk + sum_{j != k} |Q_kj| (the paper's default) */
+#define AJ_J_SCALED_DIAG 1 /* J = L D with L >= lambda_max(D^-1/2 Q D^-1/2) (Remark remark-preconditioner) */
+
+#define AJ_RESTART_NONE 0     /* Algorithm alg-apg: no restart (IsRestart = False) */
+#define AJ_RESTART_ADAPTIVE 1 /* Algorithm alg-apg-re restart rule (IsRestart = True) */
+
+#define AJ_STOP_RELRES 0 /* ||b - Q x^t||_2 <= tol ||b||_2 (||b|| = 0: ||Q x^t|| <= tol) */
+#define AJ_STOP_OBJGAP 1 /* |f(x^t) - f*| / (1 + |f*|) <= tol (Section 4 stopping rule) */
+#define AJ_STOP_NONE 2   /* run exactly maxit iterations */
+
+/* Arithmetic of the iteration. */
+#define AJ_FP64 0    /* IEEE FP64 values, vectors and arithmetic */
+#define AJ_DF64 1    /* double-float: FP64 data held as pairs of FP32 and computed on the
+                        FP32 pipes with error-free transforms (~2^-48 relative per operation) */
+#define AJ_FP32_IR 2 /* FP32 values and vectors inside, FP64 residual refinement outside */
+#define AJ_BF16_IR 3 /* BF16 values x FP32 arithmetic inside, FP64 refinement outside */
+
+#define AJ_FMT_AUTO 0
+#define AJ_FMT_CSR 1
+#define AJ_FMT_SELL 2
+
+typedef struct {
+  int j_policy;          /* AJ_J_ABSROWSUM (default) | AJ_J_SCALED_DIAG */
+  double L;              /* AJ_J_SCALED_DIAG step constant; 0 = estimate by power iteration */
+  double L_margin;       /* estimate used is (1 + L_margin) * lambda_hat (default 0.02) */
+  int restart;           /* AJ_RESTART_ADAPTIVE (default) | AJ_RESTART_NONE */
+  int momentum;          /* 1 (default): Nesterov extrapolation; 0: beta = 0 (Jacobi-type) */
+  int64_t K0;            /* K_0 >= 2 (default 2) */
+  double tol;            /* default 1e-8 */
+  int stop;              /* AJ_STOP_RELRES (default) | AJ_STOP_OBJGAP | AJ_STOP_NONE */
+  double fstar;          /* f* for AJ_STOP_OBJGAP */
+  int64_t maxit;         /* iteration limit (inner iterations in total for the IR modes) */
+  int precision;         /* AJ_FP64 (default) | AJ_DF64 | AJ_FP32_IR | AJ_BF16_IR */
+  int format;            /* AJ_FMT_AUTO (default) | AJ_FMT_CSR | AJ_FMT_SELL */
+  const double* x0;      /* initial point x^0 = y^1, n x nrhs column-major; NULL = 0 */
+  int x0_on_device;
+  double inner_tol;      /* IR modes: relative tolerance of each inner solve (default 1e-4) */
+  int64_t max_outer;     /* IR modes: outer refinement steps (default 30) */
+  int grid_ctas;         /* 0 = automatic; otherwise the number of persistent CTAs */
+} aj_params;
+
+/* Per-solve report. */
+typedef struct {
+  int64_t iters;    /* t of the returned x^t (summed over inner solves in the IR modes) */
+  int64_t restarts; /* l: restarts taken */
+  int64_t sweeps;   /* fused sweeps run (iterations + residual-only sweeps) */
+  int64_t outer;    /* IR modes: outer steps; 0 otherwise */
+  double relres;    /* ||b - Q x||_2 / ||b||_2 of the returned x, FP64 */
+  double objgap;    /* |f(x) - f*| / (1 + |f*|) with the caller's f* */
+  double L_used;    /* step constant used by AJ_J_SCALED_DIAG (0 otherwise) */
+  double ms;        /* device time of the whole solve, milliseconds */
+  double kernel_ms; /* device time of the fused iteration kernel launches alone */
+  int64_t launches; /* kernels this solve launched (fused, setup and conversion kernels) */
+  aj_status status; /* AJ_OK, AJ_EMAXIT, AJ_EDIVERGED, AJ_ENONFINITE or AJ_ETIMEOUT */
+} aj_info;
+
+/* Fill *p with the defaults above. */
+void aj_params_default(aj_params* p);
+
+/* Create a solver context for Q and nrhs right-hand sides b (n x nrhs,
+ * column-major; on the device iff Q->on_device).  nrhs in [1, 4].  The
+ * library deep-copies Q and b into device memory laid out for the kernels;
+ * it validates the CSR structure and the diagonal (AJ_EINVAL) and returns
+ * AJ_ENOMEM if device memory runs out.  *out is NULL on failure. */
+aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ctx** out);
+
+/* Set the solver parameters (copied).  Builds J^{-1} and, for
+ * AJ_J_SCALED_DIAG with L = 0, estimates L by power iteration on
+ * D^-1/2 Q D^-1/2 in FP64.  AJ_EINVAL on a bad parameter. */
+aj_status aj_set(aj_ctx* ctx, const aj_params* p);
+
+/* Run all GPU work of ctx on this cudaStream_t (NULL = legacy default stream). */
+aj_status aj_set_stream(aj_ctx* ctx, void* cuda_stream);
+
+/* Solve.  x_out (n x nrhs, column-major, FP64) receives x^t on the host or
+ * device.  info (may be NULL) receives the report of the last right-hand
+ * side's worst status; info_per_rhs (may be NULL, nrhs entries) one report
+ * per right-hand side.  Returns AJ_OK when every right-hand side met its stop
+ * test, else the first failing status (x_out is still written). */
+aj_status aj_solve(aj_ctx* ctx, double* x_out, int x_on_device, aj_info* info);
+aj_status aj_solve_rhs(aj_ctx* ctx, double* x_out, int x_on_device, aj_info* info_per_rhs);
+
+/* Solve count independent contexts in ONE persistent launch (their sizes
+ * may differ; each keeps its own momentum and restart state).  x_out[i] is
+ * the output of ctx[i] (n_i x nrhs_i), info[i] its report (info may be NULL).
+ * All contexts must share one precision and use the first context's stream. */
+aj_status aj_solve_batch(aj_ctx* const* ctx, int count, double* const* x_out, int x_on_device,
+                         aj_info* info);
+
+/* Continuous-batching server: admits requests while device memory stays
+ * within hbm_budget_bytes and at most max_slots are resident; converged
+ * systems are retired after every sweep and their slots refilled. */
+aj_status aj_server_create(size_t hbm_budget_bytes, int max_slots, aj_server** out);
+/* Queue ctx for solving (non-blocking).  The server keeps a reference to ctx
+ * until aj_poll reports it finished; ctx must stay alive until then.
+ * AJ_EBUSY if the request alone exceeds the budget. */
+aj_status aj_submit(aj_server* s, aj_ctx* ctx, uint64_t* ticket);
+/* AJ_PENDING until the request has finished; then writes x_out (host, n x
+ * nrhs) and info and returns the solve's status. */
+aj_status aj_poll(aj_server* s, uint64_t ticket, double* x_out, aj_info* info);
+void aj_server_destroy(aj_server* s);
+
+/* Solver state (x^t, x^{t-1}, alpha_t, t, l, K_l, K_re per right-hand side)
+ * for checkpoint/resume.  aj_get_state with buf = NULL writes the size to
+ * *size; aj_set_state restores it so that the next aj_solve continues the
+ * run as if it had not stopped. */
+aj_status aj_get_state(aj_ctx* ctx, void* buf, size_t* size);
+aj_status aj_set_state(aj_ctx* ctx, const void* buf, size_t size);
+
+/* Iterations t (1-based) at which the last solve of right-hand side rhs
+ * restarted; writes at most cap entries and the total count to *count. */
+aj_status aj_restart_log(aj_ctx* ctx, int rhs, int64_t* iters, int64_t cap, int64_t* count);
+
+void aj_destroy(aj_ctx* ctx);
+const char* aj_strerror(aj_status s);
+
+/* Diagnostics: number of CUDA kernels libaj has launched in this process. */
+uint64_t aj_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AJ_H */

@@ -1,0 +1,246 @@
+"""ctypes binding of libaj (include/aj.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); pointers
+and sizes are passed through unchanged.  If the library is missing or fails
+to load, every call raises -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+AJ_OK, AJ_EINVAL, AJ_ENOMEM, AJ_ECUDA = 0, -1, -2, -3
+AJ_EMAXIT, AJ_EDIVERGED, AJ_ENONFINITE, AJ_ETIMEOUT, AJ_EBUSY = -4, -5, -6, -7, -8
+AJ_PENDING = 1
+AJ_J_ABSROWSUM, AJ_J_SCALED_DIAG = 0, 1
+AJ_RESTART_NONE, AJ_RESTART_ADAPTIVE = 0, 1
+AJ_STOP_RELRES, AJ_STOP_OBJGAP, AJ_STOP_NONE = 0, 1, 2
+AJ_FP64, AJ_DF64, AJ_FP32_IR, AJ_BF16_IR = 0, 1, 2, 3
+AJ_FMT_AUTO, AJ_FMT_CSR, AJ_FMT_SELL = 0, 1, 2
+
+PRECISIONS = {"fp64": AJ_FP64, "df64": AJ_DF64, "fp32_ir": AJ_FP32_IR, "bf16_ir": AJ_BF16_IR}
+
+
+class aj_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+class aj_params(ctypes.Structure):
+    _fields_ = [("j_policy", ctypes.c_int), ("L", ctypes.c_double), ("L_margin", ctypes.c_double),
+                ("restart", ctypes.c_int), ("momentum", ctypes.c_int), ("K0", ctypes.c_int64),
+                ("tol", ctypes.c_double), ("stop", ctypes.c_int), ("fstar", ctypes.c_double),
+                ("maxit", ctypes.c_int64), ("precision", ctypes.c_int), ("format", ctypes.c_int),
+                ("x0", ctypes.c_void_p), ("x0_on_device", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int64),
+                ("grid_ctas", ctypes.c_int)]
+
+
+class aj_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("restarts", ctypes.c_int64), ("sweeps", ctypes.c_int64),
+                ("outer", ctypes.c_int64), ("relres", ctypes.c_double), ("objgap", ctypes.c_double),
+                ("L_used", ctypes.c_double), ("ms", ctypes.c_double), ("kernel_ms", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AJError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = lib().aj_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__("%s: %s (%d)" % (what, msg, status))
+
+
+_lib = None
+LIB_PATH = None
+
+# (name, restype, argtypes) of every entry point declared in include/aj.h
+SIGNATURES = [
+    ("aj_params_default", None, [ctypes.POINTER(aj_params)]),
+    ("aj_create", ctypes.c_int, [ctypes.POINTER(aj_csr), ctypes.c_void_p, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_void_p)]),
+    ("aj_set", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(aj_params)]),
+    ("aj_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("aj_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(aj_info)]),
+    ("aj_solve_rhs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(aj_info)]),
+    ("aj_solve_batch", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                      ctypes.POINTER(aj_info)]),
+    ("aj_server_create", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    ("aj_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    ("aj_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(aj_info)]),
+    ("aj_server_destroy", None, [ctypes.c_void_p]),
+    ("aj_get_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("aj_set_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    ("aj_restart_log", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    ("aj_destroy", None, [ctypes.c_void_p]),
+    ("aj_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("aj_kernel_launches", ctypes.c_uint64, []),
+]
+
+
+def lib(path=None):
+    """Load libaj (building it first if needed).  Raises if that fails."""
+    global _lib, LIB_PATH
+    if _lib is None:
+        p = path or os.environ.get("AJ_LIB") or _build.build()
+        L = ctypes.CDLL(p)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        LIB_PATH = p
+    return _lib
+
+
+def _check(st, what):
+    if st != AJ_OK:
+        raise AJError(st, what)
+
+
+def _ptr(a):
+    """(address, on_device) of a numpy array or torch tensor (must be contiguous)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), int(a.is_cuda)
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def params(**kw):
+    p = aj_params()
+    lib().aj_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        if k == "x0":
+            continue
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """One linear system Q x = b (1..4 right-hand sides) living on the GPU."""
+
+    def __init__(self, row_ptr, col, val, b, n=None, nrhs=1, stream=None):
+        L = lib()
+        rp, d0 = _ptr(row_ptr)
+        ci, d1 = _ptr(col)
+        v, d2 = _ptr(val)
+        bp, d3 = _ptr(b)
+        if len({d0, d1, d2, d3}) != 1:
+            raise ValueError("Q and b must all be on the host or all on the device")
+        n = int(len(row_ptr) - 1) if n is None else int(n)
+        nnz = int(len(col))
+        self.n, self.nnz, self.nrhs = n, nnz, int(nrhs)
+        self._keep = (row_ptr, col, val, b)
+        csr = aj_csr(n, nnz, rp, ci, v, d0)
+        h = ctypes.c_void_p()
+        _check(L.aj_create(ctypes.byref(csr), bp, self.nrhs, ctypes.byref(h)), "aj_create")
+        self._h = h
+        self._keep = None
+        self._x0 = None
+        if stream is not None:
+            self.set_stream(stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set(self, x0=None, **kw):
+        p = params(**kw)
+        if x0 is not None:
+            xp, dev = _ptr(x0)
+            p.x0, p.x0_on_device = xp, dev
+            self._x0 = x0
+        _check(lib().aj_set(self._h, ctypes.byref(p)), "aj_set")
+        return self
+
+    def set_stream(self, stream):
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        _check(lib().aj_set_stream(self._h, ctypes.c_void_p(s)), "aj_set_stream")
+
+    def solve(self, out=None, per_rhs=False, raise_on_error=False):
+        """Returns (x, info).  out: preallocated float64 array/tensor of n*nrhs
+        (column-major); default a new numpy array on the host."""
+        if out is None:
+            out = np.empty(self.n * self.nrhs if self.nrhs > 1 else self.n, dtype=np.float64)
+        xp, dev = _ptr(out)
+        if per_rhs:
+            infos = (aj_info * self.nrhs)()
+            st = lib().aj_solve_rhs(self._h, xp, dev, infos)
+            info = [i.as_dict() for i in infos]
+        else:
+            inf = aj_info()
+            st = lib().aj_solve(self._h, xp, dev, ctypes.byref(inf))
+            info = inf.as_dict()
+        if st not in (AJ_OK, AJ_EMAXIT, AJ_EDIVERGED, AJ_ENONFINITE) or (raise_on_error and st != AJ_OK):
+            raise AJError(st, "aj_solve")
+        return out, info
+
+    def restart_log(self, rhs=0):
+        cnt = ctypes.c_int64()
+        _check(lib().aj_restart_log(self._h, rhs, None, 0, ctypes.byref(cnt)), "aj_restart_log")
+        buf = (ctypes.c_int64 * max(1, cnt.value))()
+        _check(lib().aj_restart_log(self._h, rhs, buf, cnt.value, ctypes.byref(cnt)), "aj_restart_log")
+        return [int(buf[i]) for i in range(cnt.value)]
+
+    def get_state(self):
+        size = ctypes.c_size_t()
+        _check(lib().aj_get_state(self._h, None, ctypes.byref(size)), "aj_get_state")
+        buf = ctypes.create_string_buffer(size.value)
+        _check(lib().aj_get_state(self._h, buf, ctypes.byref(size)), "aj_get_state")
+        return buf.raw
+
+    def set_state(self, blob):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().aj_set_state(self._h, buf, len(blob)), "aj_set_state")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().aj_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def from_csr(Q, b, nrhs=1, device=None):
+    """Context from a synth-style CSR dict and b (numpy).  device='cuda' first
+    copies the arrays to the GPU with torch (memory plumbing only)."""
+    rp = np.ascontiguousarray(Q["row_ptr"], np.int32)
+    ci = np.ascontiguousarray(Q["col"], np.int32)
+    v = np.ascontiguousarray(Q["val"], np.float64)
+    bb = np.ascontiguousarray(b, np.float64)
+    if device is not None:
+        import torch
+        t = [torch.from_numpy(a).to(device) for a in (rp, ci, v, bb)]
+        return Context(*t, n=Q["n"], nrhs=nrhs)
+    return Context(rp, ci, v, bb, n=Q["n"], nrhs=nrhs)
+
+
+def solve_batch(ctxs, outs, on_device=False):
+    n = len(ctxs)
+    hs = (ctypes.c_void_p * n)(*[c.handle.value for c in ctxs])
+    ps = (ctypes.c_void_p * n)(*[_ptr(o)[0] for o in outs])
+    infos = (aj_info * n)()
+    st = lib().aj_solve_batch(hs, n, ps, int(on_device), infos)
+    if st not in (AJ_OK, AJ_EMAXIT, AJ_EDIVERGED, AJ_ENONFINITE):
+        raise AJError(st, "aj_solve_batch")
+    return [i.as_dict() for i in infos]

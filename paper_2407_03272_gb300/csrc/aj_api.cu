@@ -1,0 +1,1103 @@
+// aj_api.cu -- host implementation of the libaj C ABI (include/aj.h).
+//
+// A context owns a device copy of Q (CSR, FP64 master values plus, when the
+// precision asks for it, an FP32 / BF16 / double-float copy), the right-hand
+// sides, J^{-1}, three iterate buffers and the small workspaces of the
+// persistent kernel.  aj_solve runs the persistent fused kernel (FP64 and
+// DF64 directly; FP32 and BF16 as the inner solver of an FP64 iterative
+// refinement loop) and reports the FP64 residual of what it returns.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "aj.h"
+#include "aj_core.cuh"
+#include "aj_launch.h"
+#include "aj_setup.cuh"
+
+using namespace aj;
+
+namespace {
+
+inline unsigned grid1d(long long m) { return (unsigned)((m + kSetupThreads - 1) / kSetupThreads); }
+
+std::atomic<unsigned long long> g_launches{0};
+thread_local long long t_launches = 0;  // launches of the solve running on this thread
+inline void counted() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  t_launches++;
+}
+
+struct Workspace {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  void* alloc(size_t b) {
+    void* p = nullptr;
+    if (b == 0) b = 16;
+    if (cudaMalloc(&p, b) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    bytes += b;
+    return p;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+size_t xelem_bytes(int pol) {
+  switch (pol) {
+    case AJ_FP64: return 8;
+    case AJ_DF64: return 8;
+    default: return 4;
+  }
+}
+size_t velem_bytes(int pol) {
+  switch (pol) {
+    case AJ_FP64: return 8;
+    case AJ_DF64: return 8;
+    case AJ_FP32_IR: return 4;
+    default: return 2;
+  }
+}
+// kernel policy id: 0 F64, 1 DF64, 2 F32, 3 BF16
+int kernel_pol(int precision) { return precision; }
+
+double pow2_near(double v) {
+  // a power of two s with s * v in [1, 2) (v > 0); 1 for v = 0 or non-finite
+  if (!(v > 0.0) || !std::isfinite(v)) return 1.0;
+  int e = 0;
+  std::frexp(v, &e);  // v = m * 2^e, m in [0.5, 1)
+  return std::ldexp(1.0, 1 - e);
+}
+
+}  // namespace
+
+namespace aj {
+cudaError_t launch_persistent(int pol, int nrhs, const IterLaunch& L, int grid, cudaStream_t s) {
+  switch (pol) {
+    case 0: return launch_persistent_f64(nrhs, L, grid, s);
+    case 1: return launch_persistent_df64(nrhs, L, grid, s);
+    case 2: return launch_persistent_f32(nrhs, L, grid, s);
+    case 3: return launch_persistent_b16(nrhs, L, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+int persistent_blocks_per_sm(int pol, int nrhs) {
+  switch (pol) {
+    case 0: return blocks_per_sm_f64(nrhs);
+    case 1: return blocks_per_sm_df64(nrhs);
+    case 2: return blocks_per_sm_f32(nrhs);
+    case 3: return blocks_per_sm_b16(nrhs);
+  }
+  return 0;
+}
+}  // namespace aj
+
+struct aj_ctx {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  int64_t n = 0, nnz = 0;
+  int nrhs = 1;
+  Workspace base;  // lifetime of the context
+  Workspace pws;   // rebuilt by aj_set
+  int* rp = nullptr;
+  int* ci = nullptr;
+  double* val64 = nullptr;
+  double* diag = nullptr;
+  double* b64 = nullptr;  // interleaved
+  double* jinv64 = nullptr;
+  double bnorm2[kMaxRhs] = {0, 0, 0, 0};
+  aj_params prm;
+  bool have_prm = false;
+  int pol = -1;
+  void* valp = nullptr;
+  void* bp = nullptr;
+  void* jinvp = nullptr;
+  void* x[3] = {nullptr, nullptr, nullptr};
+  double sQ = 1.0;
+  double sb[kMaxRhs] = {1, 1, 1, 1};
+  double L_used = 0.0;
+  int grid = 1;
+  double* partials = nullptr;
+  unsigned long long* bar = nullptr;
+  int* err = nullptr;
+  RhsState* state = nullptr;
+  long long* rlog = nullptr;
+  int rlog_cap = 64;
+  double* part_small = nullptr;
+  int part_small_n = 0;
+  double* x64 = nullptr;
+  double* r64 = nullptr;
+  double* tmp64 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, kev0 = nullptr, kev1 = nullptr;
+  double kernel_ms = 0.0;  // fused-kernel device time of the current solve
+  bool resume = false;
+  std::vector<RhsState> st_h;
+  std::vector<std::vector<long long>> rlog_h;
+};
+
+static aj_status cuda_fail(cudaError_t e) {
+  (void)e;
+  cudaGetLastError();
+  return AJ_ECUDA;
+}
+#define CK(expr)                                      \
+  do {                                                \
+    cudaError_t _e = (expr);                          \
+    if (_e != cudaSuccess) return cuda_fail(_e);      \
+  } while (0)
+
+extern "C" void aj_params_default(aj_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->j_policy = AJ_J_ABSROWSUM;
+  p->L = 0.0;
+  p->L_margin = 0.02;
+  p->restart = AJ_RESTART_ADAPTIVE;
+  p->momentum = 1;
+  p->K0 = 2;
+  p->tol = 1e-8;
+  p->stop = AJ_STOP_RELRES;
+  p->fstar = 0.0;
+  p->maxit = 100000;
+  p->precision = AJ_FP64;
+  p->format = AJ_FMT_AUTO;
+  p->x0 = nullptr;
+  p->x0_on_device = 0;
+  p->inner_tol = 1e-4;
+  p->max_outer = 30;
+  p->grid_ctas = 0;
+}
+
+extern "C" const char* aj_strerror(aj_status s) {
+  switch (s) {
+    case AJ_OK: return "ok";
+    case AJ_EINVAL: return "invalid argument or matrix";
+    case AJ_ENOMEM: return "out of memory";
+    case AJ_ECUDA: return "CUDA runtime error";
+    case AJ_EMAXIT: return "iteration limit reached";
+    case AJ_EDIVERGED: return "diverged (S = J - Q not positive semidefinite?)";
+    case AJ_ENONFINITE: return "non-finite value in a reduction";
+    case AJ_ETIMEOUT: return "device barrier timed out";
+    case AJ_EBUSY: return "request larger than the server budget";
+    case AJ_PENDING: return "pending";
+  }
+  return "unknown status";
+}
+
+extern "C" void aj_destroy(aj_ctx* c) {
+  if (!c) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(c->dev);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  c->pws.release();
+  c->base.release();
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->kev0) cudaEventDestroy(c->kev0);
+  if (c->kev1) cudaEventDestroy(c->kev1);
+  cudaSetDevice(cur);
+  delete c;
+}
+
+// Sum the first `blocks` rows of a [blocks][w] partial array on the host (fixed order).
+static aj_status host_sum_parts(aj_ctx* c, const double* dpart, int blocks, int w, double* out) {
+  std::vector<double> h((size_t)blocks * w);
+  CK(cudaMemcpyAsync(h.data(), dpart, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < w; k++) out[k] = 0.0;
+  for (int b = 0; b < blocks; b++)
+    for (int k = 0; k < w; k++) out[k] += h[(size_t)b * w + k];
+  return AJ_OK;
+}
+
+extern "C" aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ctx** out) {
+  if (!out) return AJ_EINVAL;
+  *out = nullptr;
+  if (!Q || nrhs < 1 || nrhs > kMaxRhs || Q->n < 0 || Q->nnz < 0) return AJ_EINVAL;
+  if (Q->n >= (1ll << 31) - 1 || Q->nnz >= (1ll << 31) - 1) return AJ_EINVAL;
+  if (Q->n > 0 && (!Q->row_ptr || !b)) return AJ_EINVAL;
+  if (Q->nnz > 0 && (!Q->col || !Q->val)) return AJ_EINVAL;
+  aj_ctx* c = new aj_ctx();
+  aj_params_default(&c->prm);
+  cudaGetDevice(&c->dev);
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
+  c->n = Q->n;
+  c->nnz = Q->nnz;
+  c->nrhs = nrhs;
+  const int n = (int)Q->n;
+  const long long nnz = Q->nnz;
+  const long long m = (long long)n * nrhs;
+  // matrix arrays padded by 16 entries so 16-byte vector reads never leave them
+  c->rp = (int*)c->base.alloc((size_t)(n + 1 + 16) * 4);
+  c->ci = (int*)c->base.alloc((size_t)(nnz + 16) * 4);
+  c->val64 = (double*)c->base.alloc((size_t)(nnz + 16) * 8);
+  c->diag = (double*)c->base.alloc((size_t)(n + 1) * 8);
+  c->b64 = (double*)c->base.alloc((size_t)(m + 1) * 8);
+  c->jinv64 = (double*)c->base.alloc((size_t)(n + 1) * 8);
+  c->tmp64 = (double*)c->base.alloc((size_t)(m + 1) * 8);
+  c->part_small_n = std::max<int>(1, (int)grid1d(std::max<long long>(n, 1)));
+  c->part_small = (double*)c->base.alloc((size_t)c->part_small_n * kMaxRhs * 3 * 8);
+  c->err = (int*)c->base.alloc(64);
+  if (!c->rp || !c->ci || !c->val64 || !c->diag || !c->b64 || !c->jinv64 || !c->tmp64 ||
+      !c->part_small || !c->err) {
+    aj_destroy(c);
+    return AJ_ENOMEM;
+  }
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+      cudaEventCreate(&c->kev0) != cudaSuccess || cudaEventCreate(&c->kev1) != cudaSuccess) {
+    aj_destroy(c);
+    return AJ_ECUDA;
+  }
+  const cudaMemcpyKind kind = Q->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaStream_t s = c->stream;
+  aj_status st = AJ_OK;
+  do {
+    if (cudaMemcpyAsync(c->rp, Q->row_ptr, (size_t)(n + 1) * 4, kind, s) != cudaSuccess ||
+        (nnz > 0 && cudaMemcpyAsync(c->ci, Q->col, (size_t)nnz * 4, kind, s) != cudaSuccess) ||
+        (nnz > 0 && cudaMemcpyAsync(c->val64, Q->val, (size_t)nnz * 8, kind, s) != cudaSuccess) ||
+        cudaMemsetAsync(c->ci + nnz, 0, 16 * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(c->val64 + nnz, 0, 16 * 8, s) != cudaSuccess ||
+        cudaMemcpyAsync(c->tmp64, b, (size_t)m * 8, kind, s) != cudaSuccess ||
+        cudaMemsetAsync(c->err, 0, 64, s) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError());
+      break;
+    }
+    k_check_rowptr<<<grid1d((long long)n + 1), kSetupThreads, 0, s>>>(n, nnz, c->rp, c->err);
+    counted();
+    int flags = 0;
+    if (cudaMemcpyAsync(&flags, c->err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError());
+      break;
+    }
+    if (flags) { st = AJ_EINVAL; break; }
+    if (n > 0) {
+      k_check_rows<<<grid1d(n), kSetupThreads, 0, s>>>(n, c->rp, c->ci, c->val64, c->diag, c->err);
+      counted();
+    }
+    if (m > 0) {
+      k_interleave<<<grid1d(m), kSetupThreads, 0, s>>>(n, nrhs, c->tmp64, c->b64);
+      counted();
+    }
+    if (cudaMemcpyAsync(&flags, c->err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError());
+      break;
+    }
+    if (flags) { st = AJ_EINVAL; break; }
+    // ||b_r||^2 in FP64 and b finite
+    std::vector<double> hb((size_t)m);
+    if (m > 0 && (cudaMemcpyAsync(hb.data(), c->b64, (size_t)m * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                  cudaStreamSynchronize(s) != cudaSuccess)) {
+      st = cuda_fail(cudaGetLastError());
+      break;
+    }
+    for (long long e = 0; e < m; e++) {
+      if (!std::isfinite(hb[e])) { st = AJ_EINVAL; break; }
+      c->bnorm2[e % nrhs] += hb[e] * hb[e];
+    }
+  } while (0);
+  if (st != AJ_OK) {
+    aj_destroy(c);
+    return st;
+  }
+  *out = c;
+  return AJ_OK;
+}
+
+extern "C" aj_status aj_set_stream(aj_ctx* c, void* stream) {
+  if (!c) return AJ_EINVAL;
+  c->stream = (cudaStream_t)stream;
+  return AJ_OK;
+}
+
+// Power iteration for lambda_max(D^-1/2 Q D^-1/2) in FP64 (setup step; a few
+// hundred kernel launches at most).
+static aj_status estimate_L(aj_ctx* c, double* L_out) {
+  const int n = (int)c->n;
+  cudaStream_t s = c->stream;
+  if (n == 0) { *L_out = 1.0; return AJ_OK; }
+  double* v = c->tmp64;
+  double* w = c->jinv64;  // scratch: J^{-1} is rebuilt after the estimate
+  // deterministic start vector: 1 + small index-dependent perturbation
+  std::vector<double> h(n);
+  for (int i = 0; i < n; i++) h[i] = 1.0 + 0.25 * std::sin(0.7 * i + 0.3);
+  CK(cudaMemcpyAsync(v, h.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+  double nv = 0.0;
+  for (double q : h) nv += q * q;
+  k_scale<<<grid1d(n), kSetupThreads, 0, s>>>(n, v, 1.0 / std::sqrt(nv));
+  counted();
+  const int blocks = (int)grid1d(n);
+  double lam = 0.0;
+  for (int it = 0; it < 300; it++) {
+    k_normalized_spmv<<<blocks, kSetupThreads, 0, s>>>(n, c->rp, c->ci, c->val64, c->diag, v, w,
+                                                       c->part_small);
+    counted();
+    double sums[2];
+    aj_status st = host_sum_parts(c, c->part_small, blocks, 2, sums);
+    if (st != AJ_OK) return st;
+    const double lam_new = sums[0];  // Rayleigh quotient with ||v|| = 1
+    const double wn = std::sqrt(sums[1]);
+    if (!(wn > 0.0) || !std::isfinite(wn)) break;
+    std::swap(v, w);
+    k_scale<<<grid1d(n), kSetupThreads, 0, s>>>(n, v, 1.0 / wn);
+    counted();
+    const bool conv = it > 10 && std::fabs(lam_new - lam) <= 1e-7 * std::fabs(lam_new);
+    lam = lam_new;
+    if (conv) break;
+  }
+  // a Gershgorin bound is always safe; never exceed it
+  k_gershgorin<<<blocks, kSetupThreads, 0, s>>>(n, c->rp, c->ci, c->val64, c->diag, c->part_small);
+  counted();
+  std::vector<double> hg(blocks);
+  CK(cudaMemcpyAsync(hg.data(), c->part_small, (size_t)blocks * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double gb = 0.0;
+  for (double g : hg) gb = std::max(gb, g);
+  double L = (1.0 + c->prm.L_margin) * lam;
+  if (gb > 0.0) L = std::min(L, gb);
+  if (!(L > 0.0)) L = gb > 0.0 ? gb : 1.0;
+  *L_out = L;
+  return AJ_OK;
+}
+
+// (Re)build everything that depends on the parameters.
+extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
+  if (!c || !p) return AJ_EINVAL;
+  if (p->j_policy != AJ_J_ABSROWSUM && p->j_policy != AJ_J_SCALED_DIAG) return AJ_EINVAL;
+  if (p->restart != AJ_RESTART_NONE && p->restart != AJ_RESTART_ADAPTIVE) return AJ_EINVAL;
+  if (p->K0 < 2 || p->maxit < 0 || !(p->tol >= 0.0) || p->L < 0.0 || !(p->L_margin >= 0.0))
+    return AJ_EINVAL;
+  if (p->stop < AJ_STOP_RELRES || p->stop > AJ_STOP_NONE) return AJ_EINVAL;
+  if (p->precision < AJ_FP64 || p->precision > AJ_BF16_IR) return AJ_EINVAL;
+  if (p->format < AJ_FMT_AUTO || p->format > AJ_FMT_SELL) return AJ_EINVAL;
+  if (p->grid_ctas < 0) return AJ_EINVAL;
+  if ((p->precision == AJ_FP32_IR || p->precision == AJ_BF16_IR) &&
+      (!(p->inner_tol > 0.0) || p->max_outer < 1))
+    return AJ_EINVAL;
+  const int old_pol = c->pol;
+  c->prm = *p;
+  c->have_prm = true;
+  c->resume = false;
+  const int n = (int)c->n;
+  const long long nnz = c->nnz;
+  const int nrhs = c->nrhs;
+  const long long m = (long long)n * nrhs;
+  cudaStream_t s = c->stream;
+  // --- J^{-1} in FP64
+  double L = 0.0;
+  if (p->j_policy == AJ_J_SCALED_DIAG) {
+    L = p->L;
+    if (L == 0.0) {
+      aj_status st = estimate_L(c, &L);
+      if (st != AJ_OK) return st;
+    }
+  }
+  c->L_used = L;
+  if (n > 0) {
+    k_jinv<<<grid1d(n), kSetupThreads, 0, s>>>(n, c->rp, c->ci, c->val64, c->diag,
+                                               p->j_policy == AJ_J_ABSROWSUM ? 0 : 1, L, c->jinv64);
+    counted();
+  }
+  CK(cudaGetLastError());
+  // --- precision-specific arrays
+  const int pol = p->precision;
+  if (pol != old_pol) {
+    c->pws.release();
+    c->valp = c->bp = c->jinvp = nullptr;
+    c->x[0] = c->x[1] = c->x[2] = nullptr;
+    c->partials = nullptr;
+    c->bar = nullptr;
+    c->state = nullptr;
+    c->rlog = nullptr;
+    c->x64 = c->r64 = nullptr;
+    const size_t xe = xelem_bytes(pol);
+    if (pol != AJ_FP64) {
+      c->valp = c->pws.alloc((size_t)(nnz + 16) * velem_bytes(pol));
+      c->bp = c->pws.alloc((size_t)(m + 1) * xe);
+      c->jinvp = c->pws.alloc((size_t)(n + 1) * xe);
+      if (!c->valp || !c->bp || !c->jinvp) return AJ_ENOMEM;
+    }
+    for (int k = 0; k < 3; k++) {
+      c->x[k] = c->pws.alloc((size_t)(m + 1) * xe);
+      if (!c->x[k]) return AJ_ENOMEM;
+    }
+    c->x64 = (double*)c->pws.alloc((size_t)(m + 1) * 8);
+    c->r64 = (double*)c->pws.alloc((size_t)(m + 1) * 8);
+    if (!c->x64 || !c->r64) return AJ_ENOMEM;
+    const int kp = kernel_pol(pol);
+    const int bps = std::max(1, persistent_blocks_per_sm(kp, nrhs));
+    const int maxg = bps * c->sm_count;
+    c->partials = (double*)c->pws.alloc((size_t)2 * maxg * nrhs * kNRed * 8);
+    c->bar = (unsigned long long*)c->pws.alloc(64);
+    c->state = (RhsState*)c->pws.alloc(sizeof(RhsState) * kMaxRhs);
+    c->rlog = (long long*)c->pws.alloc((size_t)kMaxRhs * c->rlog_cap * 8);
+    if (!c->partials || !c->bar || !c->state || !c->rlog) return AJ_ENOMEM;
+    c->pol = pol;
+  }
+  // --- grid: a multiple of the SM count when the problem is large enough
+  {
+    const int kp = kernel_pol(pol);
+    const int bps = std::max(1, persistent_blocks_per_sm(kp, nrhs));
+    const int maxg = bps * c->sm_count;
+    const int ntiles = std::max(1, (int)((n + kThreads - 1) / kThreads));
+    int g = std::min(maxg, ntiles);
+    if (p->grid_ctas > 0) g = std::min(p->grid_ctas, maxg);
+    c->grid = std::max(1, g);
+  }
+  // --- scaled copies for the non-FP64 policies (powers of two: exact)
+  if (pol != AJ_FP64) {
+    double vmax = 0.0;
+    {
+      std::vector<double> hv;
+      // max |Q_ij| via the diagonal bound: for SPSD Q, |Q_ij| <= sqrt(Q_ii Q_jj) <= max diag
+      std::vector<double> hd(n);
+      if (n > 0) {
+        CK(cudaMemcpyAsync(hd.data(), c->diag, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+      }
+      for (double d : hd) vmax = std::max(vmax, d);
+    }
+    c->sQ = pow2_near(vmax);
+    if (pol == AJ_DF64) {
+      if (nnz > 0) {
+        k_to_dw<<<grid1d(nnz), kSetupThreads, 0, s>>>(nnz, c->val64, c->sQ, (float2*)c->valp);
+        counted();
+      }
+      if (n > 0) {
+        k_to_dw<<<grid1d(n), kSetupThreads, 0, s>>>(n, c->jinv64, 1.0 / c->sQ, (float2*)c->jinvp);
+        counted();
+      }
+    } else if (pol == AJ_FP32_IR) {
+      if (nnz > 0) {
+        k_to_f32<<<grid1d(nnz), kSetupThreads, 0, s>>>(nnz, c->val64, c->sQ, (float*)c->valp);
+        counted();
+      }
+      if (n > 0) {
+        k_to_f32<<<grid1d(n), kSetupThreads, 0, s>>>(n, c->jinv64, 1.0 / c->sQ, (float*)c->jinvp);
+        counted();
+      }
+    } else {
+      if (nnz > 0) {
+        k_to_b16<<<grid1d(nnz), kSetupThreads, 0, s>>>(nnz, c->val64, c->sQ, (__nv_bfloat16*)c->valp);
+        counted();
+      }
+      if (n > 0) {
+        k_to_f32<<<grid1d(n), kSetupThreads, 0, s>>>(n, c->jinv64, 1.0 / c->sQ, (float*)c->jinvp);
+        counted();
+      }
+    }
+    CK(cudaGetLastError());
+  } else {
+    c->sQ = 1.0;
+  }
+  CK(cudaStreamSynchronize(s));
+  return AJ_OK;
+}
+
+// Load interleaved FP64 data, scaled per right-hand side, into an
+// iteration-precision buffer.
+static void to_policy(aj_ctx* c, const double* src_il, void* dst, const double* scale_per_rhs) {
+  const long long m = (long long)c->n * c->nrhs;
+  if (m == 0) return;
+  RhsMap mp;
+  for (int r = 0; r < kMaxRhs; r++) {
+    mp.s[r] = r < c->nrhs ? scale_per_rhs[r] : 1.0;
+    mp.cur[r] = 0;
+  }
+  cudaStream_t s = c->stream;
+  switch (c->pol) {
+    case AJ_FP64: k_to_policy<double><<<grid1d(m), kSetupThreads, 0, s>>>(m, c->nrhs, src_il, mp, (double*)dst); counted(); break;
+    case AJ_DF64: k_to_policy<float2><<<grid1d(m), kSetupThreads, 0, s>>>(m, c->nrhs, src_il, mp, (float2*)dst); counted(); break;
+    default: k_to_policy<float><<<grid1d(m), kSetupThreads, 0, s>>>(m, c->nrhs, src_il, mp, (float*)dst); counted(); break;
+  }
+}
+
+// Buffer cur[r] of each right-hand side, times scale[r], into an interleaved
+// FP64 vector.
+static aj_status from_policy(aj_ctx* c, const int* cur, const double* scale, double* dst_il) {
+  const long long m = (long long)c->n * c->nrhs;
+  if (m == 0) return AJ_OK;
+  RhsMap mp;
+  for (int r = 0; r < kMaxRhs; r++) {
+    mp.s[r] = r < c->nrhs ? scale[r] : 1.0;
+    mp.cur[r] = r < c->nrhs ? cur[r] : 0;
+  }
+  cudaStream_t s = c->stream;
+  switch (c->pol) {
+    case AJ_FP64:
+      k_from_policy<double><<<grid1d(m), kSetupThreads, 0, s>>>(
+          m, c->nrhs, (const double*)c->x[0], (const double*)c->x[1], (const double*)c->x[2], mp, dst_il);
+      counted();
+      break;
+    case AJ_DF64:
+      k_from_policy<float2><<<grid1d(m), kSetupThreads, 0, s>>>(
+          m, c->nrhs, (const float2*)c->x[0], (const float2*)c->x[1], (const float2*)c->x[2], mp, dst_il);
+      counted();
+      break;
+    default:
+      k_from_policy<float><<<grid1d(m), kSetupThreads, 0, s>>>(
+          m, c->nrhs, (const float*)c->x[0], (const float*)c->x[1], (const float*)c->x[2], mp, dst_il);
+      counted();
+      break;
+  }
+  CK(cudaGetLastError());
+  return AJ_OK;
+}
+
+static void init_state(aj_ctx* c, RhsState* st, const double* bn2) {
+  for (int r = 0; r < c->nrhs; r++) {
+    RhsState& q = st[r];
+    std::memset(&q, 0, sizeof(q));
+    q.alpha = 1.0;
+    q.beta = 0.0;
+    q.bnorm2 = bn2[r];
+    q.t = 0;
+    q.ell = 0;
+    q.K = c->prm.K0;
+    q.Kre = 0;
+    q.cur = 0;
+    q.prev = 0;
+    q.nxt = 1;
+    q.done = 0;
+    q.status = 0;
+  }
+}
+
+// Run the persistent kernel to completion from state st (host copy, in/out).
+static aj_status run_persistent(aj_ctx* c, std::vector<RhsState>& st, const void* bvec,
+                                long long maxit, int stop, double tol, double fstar,
+                                double fscale, bool log_restarts) {
+  cudaStream_t s = c->stream;
+  IterLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.n = (int)c->n;
+  L.row_ptr = c->rp;
+  L.col = c->ci;
+  L.val = c->pol == AJ_FP64 ? (const void*)c->val64 : c->valp;
+  L.b = bvec;
+  L.jinv = c->pol == AJ_FP64 ? (const void*)c->jinv64 : c->jinvp;
+  for (int k = 0; k < 3; k++) L.x[k] = c->x[k];
+  L.partials = c->partials;
+  L.bar = c->bar;
+  L.err = c->err;
+  L.state = c->state;
+  L.rlog = c->rlog;
+  L.rlog_cap = c->rlog_cap;
+  L.trace = nullptr;
+  L.trace_cap = 0;
+  L.maxit = maxit;
+  L.stop = stop;
+  L.restart = c->prm.restart == AJ_RESTART_ADAPTIVE;
+  L.momentum = c->prm.momentum != 0;
+  L.tol = tol;
+  L.fstar = fstar;
+  L.fscale = fscale;
+  L.max_sweeps = maxit + 2;
+  CK(cudaMemcpyAsync(c->state, st.data(), sizeof(RhsState) * c->nrhs, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(c->bar, 0, 64, s));
+  CK(cudaMemsetAsync(c->err, 0, 64, s));
+  if (log_restarts) CK(cudaMemsetAsync(c->rlog, 0xff, (size_t)kMaxRhs * c->rlog_cap * 8, s));
+  CK(cudaEventRecord(c->kev0, s));
+  CK(launch_persistent(kernel_pol(c->pol), c->nrhs, L, c->grid, s));
+  counted();
+  CK(cudaEventRecord(c->kev1, s));
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, c->err, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(st.data(), c->state, sizeof(RhsState) * c->nrhs, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  float kms = 0.f;
+  cudaEventElapsedTime(&kms, c->kev0, c->kev1);
+  c->kernel_ms += kms;
+  if (err != 0) return err == kETimeout ? AJ_ETIMEOUT : AJ_ECUDA;
+  return AJ_OK;
+}
+
+static aj_status fetch_rlog(aj_ctx* c, const std::vector<RhsState>& st, bool append) {
+  std::vector<long long> h((size_t)kMaxRhs * c->rlog_cap);
+  CK(cudaMemcpyAsync(h.data(), c->rlog, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (!append) c->rlog_h.assign(c->nrhs, {});
+  c->rlog_h.resize(c->nrhs);
+  for (int r = 0; r < c->nrhs; r++)
+    for (int k = 0; k < c->rlog_cap; k++) {
+      long long v = h[(size_t)r * c->rlog_cap + k];
+      if (v >= 0) c->rlog_h[r].push_back(v);
+    }
+  (void)st;
+  return AJ_OK;
+}
+
+// FP64 residual of an interleaved FP64 iterate: relres and objgap per RHS.
+static aj_status fp64_report(aj_ctx* c, const double* x_il, double* relres, double* objgap,
+                             double* r_out) {
+  const int n = (int)c->n;
+  const int nrhs = c->nrhs;
+  const int blocks = std::max(1, (int)grid1d(n));
+  if (n > 0) {
+    k_residual<<<blocks, kSetupThreads, 0, c->stream>>>(n, nrhs, c->rp, c->ci, c->val64, c->b64,
+                                                        x_il, r_out, c->part_small);
+    counted();
+  } else
+    CK(cudaMemsetAsync(c->part_small, 0, (size_t)nrhs * 3 * 8, c->stream));
+  CK(cudaGetLastError());
+  double sums[kMaxRhs * 3];
+  aj_status st = host_sum_parts(c, c->part_small, n > 0 ? blocks : 1, nrhs * 3, sums);
+  if (st != AJ_OK) return st;
+  for (int r = 0; r < nrhs; r++) {
+    const double rn = std::sqrt(sums[r * 3 + 0]);
+    const double bn = std::sqrt(c->bnorm2[r]);
+    relres[r] = bn > 0.0 ? rn / bn : rn;
+    const double f = 0.5 * sums[r * 3 + 1] - sums[r * 3 + 2];
+    objgap[r] = std::fabs(f - c->prm.fstar) / (1.0 + std::fabs(c->prm.fstar));
+  }
+  return AJ_OK;
+}
+
+static aj_status status_of(int s) {
+  switch (s) {
+    case kOk: return AJ_OK;
+    case kEMaxit: return AJ_EMAXIT;
+    case kEDiverged: return AJ_EDIVERGED;
+    case kENonfinite: return AJ_ENONFINITE;
+    case kETimeout: return AJ_ETIMEOUT;
+  }
+  return AJ_ECUDA;
+}
+
+// Initial point x^0 (interleaved FP64) into tmp64.
+static aj_status load_x0(aj_ctx* c) {
+  const int n = (int)c->n;
+  const long long m = (long long)n * c->nrhs;
+  cudaStream_t s = c->stream;
+  if (m == 0) return AJ_OK;
+  if (!c->prm.x0) {
+    CK(cudaMemsetAsync(c->tmp64, 0, (size_t)m * 8, s));
+    return AJ_OK;
+  }
+  // x0 is column-major: interleave it on the host
+  std::vector<double> h((size_t)m), il((size_t)m);
+  CK(cudaMemcpyAsync(h.data(), c->prm.x0, (size_t)m * 8,
+                     c->prm.x0_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int r = 0; r < c->nrhs; r++)
+    for (int i = 0; i < n; i++) il[(size_t)i * c->nrhs + r] = h[(size_t)r * n + i];
+  CK(cudaMemcpyAsync(c->tmp64, il.data(), (size_t)m * 8, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return AJ_OK;
+}
+
+static aj_status write_output(aj_ctx* c, const double* x_il, double* x_out, int x_on_device) {
+  const int n = (int)c->n;
+  const long long m = (long long)n * c->nrhs;
+  cudaStream_t s = c->stream;
+  if (m == 0) return AJ_OK;
+  if (c->nrhs == 1) {
+    CK(cudaMemcpyAsync(x_out, x_il, (size_t)m * 8,
+                       x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return AJ_OK;
+  }
+  double* cm = x_il == c->tmp64 ? c->r64 : c->tmp64;
+  if (!cm || cm == x_il) {
+    // fall back to a host-side transpose
+    std::vector<double> h((size_t)m), o((size_t)m);
+    CK(cudaMemcpyAsync(h.data(), x_il, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int r = 0; r < c->nrhs; r++)
+      for (int i = 0; i < n; i++) o[(size_t)r * n + i] = h[(size_t)i * c->nrhs + r];
+    CK(cudaMemcpyAsync(x_out, o.data(), (size_t)m * 8,
+                       x_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return AJ_OK;
+  }
+  k_deinterleave<<<grid1d(m), kSetupThreads, 0, s>>>(n, c->nrhs, x_il, cm);
+  counted();
+  CK(cudaMemcpyAsync(x_out, cm, (size_t)m * 8,
+                     x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return AJ_OK;
+}
+
+// Direct solve (FP64 or DF64 arithmetic in the persistent kernel).
+static aj_status solve_direct(aj_ctx* c, double* x_out, int x_on_device, aj_info* per) {
+  const int nrhs = c->nrhs;
+  const double sq = c->sQ;
+  double sb[kMaxRhs];
+  double bn2[kMaxRhs];
+  for (int r = 0; r < nrhs; r++) {
+    sb[r] = c->pol == AJ_FP64 ? 1.0 : pow2_near(std::sqrt(c->bnorm2[r] / std::max<int64_t>(c->n, 1)));
+    bn2[r] = c->bnorm2[r] * sb[r] * sb[r];
+  }
+  std::vector<RhsState> st(nrhs);
+  if (c->resume) {
+    st = c->st_h;
+    for (int r = 0; r < nrhs; r++) sb[r] = c->sb[r];
+    for (int r = 0; r < nrhs; r++)
+      if (st[r].done && st[r].status == kEMaxit) { st[r].done = 0; st[r].status = 0; }
+  } else {
+    for (int r = 0; r < nrhs; r++) c->sb[r] = sb[r];
+    init_state(c, st.data(), bn2);
+    aj_status e = load_x0(c);
+    if (e != AJ_OK) return e;
+    double xs[kMaxRhs];
+    for (int r = 0; r < nrhs; r++) xs[r] = sb[r] / sq;
+    to_policy(c, c->tmp64, c->x[0], xs);
+  }
+  // right-hand side in the iteration precision
+  const void* bvec = c->b64;
+  if (c->pol != AJ_FP64) {
+    to_policy(c, c->b64, c->bp, sb);
+    bvec = c->bp;
+  }
+  CK(cudaGetLastError());
+  // f of the scaled problem is (sb^2 / sQ) f of the original one
+  const double fscale = sq / (sb[0] * sb[0]);
+  aj_status rs = run_persistent(c, st, bvec, c->prm.maxit, c->prm.stop, c->prm.tol,
+                                c->prm.fstar, fscale, true);
+  if (rs != AJ_OK) return rs;
+  aj_status e = fetch_rlog(c, st, false);
+  if (e != AJ_OK) return e;
+  int cur[kMaxRhs];
+  double osc[kMaxRhs];
+  for (int r = 0; r < nrhs; r++) {
+    cur[r] = st[r].cur;
+    osc[r] = sq / sb[r];
+  }
+  double* xil = c->pol == AJ_FP64 ? c->tmp64 : c->x64;
+  e = from_policy(c, cur, osc, xil);
+  if (e != AJ_OK) return e;
+  double rel[kMaxRhs], og[kMaxRhs];
+  e = fp64_report(c, xil, rel, og, nullptr);
+  if (e != AJ_OK) return e;
+  e = write_output(c, xil, x_out, x_on_device);
+  if (e != AJ_OK) return e;
+  c->st_h = st;
+  for (int r = 0; r < nrhs; r++) {
+    per[r].iters = st[r].t_final;
+    per[r].restarts = st[r].ell;
+    per[r].sweeps = st[r].t_final + 1;
+    per[r].outer = 0;
+    per[r].relres = rel[r];
+    per[r].objgap = og[r];
+    per[r].L_used = c->L_used;
+    per[r].status = status_of(st[r].status);
+  }
+  return AJ_OK;
+}
+
+// FP64 iterative refinement around the low-precision persistent solver.
+static aj_status solve_ir(aj_ctx* c, double* x_out, int x_on_device, aj_info* per) {
+  const int n = (int)c->n;
+  const int nrhs = c->nrhs;
+  const long long m = (long long)n * nrhs;
+  cudaStream_t s = c->stream;
+  aj_status e = load_x0(c);
+  if (e != AJ_OK) return e;
+  if (m > 0) CK(cudaMemcpyAsync(c->x64, c->tmp64, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
+  long long iters[kMaxRhs] = {0, 0, 0, 0}, rest[kMaxRhs] = {0, 0, 0, 0};
+  int status[kMaxRhs] = {kEMaxit, kEMaxit, kEMaxit, kEMaxit};
+  bool done[kMaxRhs] = {false, false, false, false};
+  double rel[kMaxRhs], og[kMaxRhs];
+  long long outer = 0;
+  c->rlog_h.assign(nrhs, {});
+  for (;;) {
+    e = fp64_report(c, c->x64, rel, og, c->r64);
+    if (e != AJ_OK) return e;
+    bool all = true;
+    for (int r = 0; r < nrhs; r++) {
+      if (done[r]) continue;
+      bool ok = false;
+      if (c->prm.stop == AJ_STOP_RELRES) ok = rel[r] <= c->prm.tol;
+      else if (c->prm.stop == AJ_STOP_OBJGAP) ok = og[r] <= c->prm.tol;
+      if (ok) { done[r] = true; status[r] = kOk; }
+      else if (!std::isfinite(rel[r])) { done[r] = true; status[r] = kENonfinite; }
+      all = all && done[r];
+    }
+    long long used = 0;
+    for (int r = 0; r < nrhs; r++) used = std::max(used, iters[r]);
+    if (all || outer >= c->prm.max_outer || used >= c->prm.maxit) break;
+    outer++;
+    // inner right-hand side: the FP64 residual, scaled by a power of two per RHS
+    double sr[kMaxRhs], bn2[kMaxRhs];
+    for (int r = 0; r < nrhs; r++) {
+      const double rn = rel[r] * std::sqrt(c->bnorm2[r] > 0 ? c->bnorm2[r] : 1.0);
+      sr[r] = pow2_near(rn / std::sqrt((double)std::max(n, 1)));
+      bn2[r] = rn * rn * sr[r] * sr[r];
+    }
+    to_policy(c, c->r64, c->bp, sr);
+    std::vector<RhsState> st(nrhs);
+    init_state(c, st.data(), bn2);
+    for (int r = 0; r < nrhs; r++)
+      if (done[r]) { st[r].done = 1; st[r].status = kOk; }
+    if (m > 0) CK(cudaMemsetAsync(c->x[0], 0, (size_t)m * xelem_bytes(c->pol), s));
+    const long long budget = std::max<long long>(1, c->prm.maxit - used);
+    aj_status rs = run_persistent(c, st, c->bp, budget, AJ_STOP_RELRES, c->prm.inner_tol, 0.0, 1.0, true);
+    if (rs != AJ_OK) return rs;
+    e = fetch_rlog(c, st, true);
+    if (e != AJ_OK) return e;
+    // x += (sQ / sr) * d for the RHS that were still running
+    int cur[kMaxRhs];
+    double osc[kMaxRhs];
+    for (int r = 0; r < nrhs; r++) {
+      cur[r] = st[r].cur;
+      osc[r] = c->sQ / sr[r];
+    }
+    e = from_policy(c, cur, osc, c->tmp64);
+    if (e != AJ_OK) return e;
+    unsigned mask = 0;
+    for (int r = 0; r < nrhs; r++)
+      if (!done[r]) {
+        mask |= 1u << r;
+        iters[r] += st[r].t_final;
+        rest[r] += st[r].ell;
+        if (st[r].status == kENonfinite || st[r].status == kEDiverged) {
+          done[r] = true;
+          status[r] = st[r].status;
+        }
+      }
+    if (m > 0) {
+      k_axpy_masked<<<grid1d(m), kSetupThreads, 0, s>>>(m, nrhs, mask, c->tmp64, 1.0, c->x64);
+      counted();
+    }
+    CK(cudaGetLastError());
+  }
+  e = write_output(c, c->x64, x_out, x_on_device);
+  if (e != AJ_OK) return e;
+  for (int r = 0; r < nrhs; r++) {
+    per[r].iters = iters[r];
+    per[r].restarts = rest[r];
+    per[r].sweeps = iters[r] + outer;
+    per[r].outer = outer;
+    per[r].relres = rel[r];
+    per[r].objgap = og[r];
+    per[r].L_used = c->L_used;
+    per[r].status = done[r] ? status_of(status[r]) : AJ_EMAXIT;
+  }
+  return AJ_OK;
+}
+
+extern "C" aj_status aj_solve_rhs(aj_ctx* c, double* x_out, int x_on_device, aj_info* per_rhs) {
+  if (!c || (!x_out && c->n > 0)) return AJ_EINVAL;
+  if (!c->have_prm) {
+    aj_params p;
+    aj_params_default(&p);
+    aj_status st = aj_set(c, &p);
+    if (st != AJ_OK) return st;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != c->dev) cudaSetDevice(c->dev);
+  aj_info per[kMaxRhs];
+  std::memset(per, 0, sizeof(per));
+  c->kernel_ms = 0.0;
+  t_launches = 0;
+  CK(cudaEventRecord(c->ev0, c->stream));
+  aj_status st;
+  if (c->pol == AJ_FP64 || c->pol == AJ_DF64) st = solve_direct(c, x_out, x_on_device, per);
+  else st = solve_ir(c, x_out, x_on_device, per);
+  CK(cudaEventRecord(c->ev1, c->stream));
+  CK(cudaEventSynchronize(c->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  c->resume = false;
+  if (cur != c->dev) cudaSetDevice(cur);
+  if (st != AJ_OK) return st;
+  aj_status worst = AJ_OK;
+  for (int r = 0; r < c->nrhs; r++) {
+    per[r].ms = ms;
+    per[r].kernel_ms = c->kernel_ms;
+    per[r].launches = t_launches;
+    if (per[r].status != AJ_OK && worst == AJ_OK) worst = per[r].status;
+  }
+  if (per_rhs)
+    for (int r = 0; r < c->nrhs; r++) per_rhs[r] = per[r];
+  return worst;
+}
+
+extern "C" aj_status aj_solve(aj_ctx* c, double* x_out, int x_on_device, aj_info* info) {
+  if (!c) return AJ_EINVAL;
+  aj_info per[kMaxRhs];
+  std::memset(per, 0, sizeof(per));
+  aj_status st = aj_solve_rhs(c, x_out, x_on_device, per);
+  if (info && (st == AJ_OK || st == AJ_EMAXIT || st == AJ_EDIVERGED || st == AJ_ENONFINITE)) {
+    // report the right-hand side with the worst residual
+    int w = 0;
+    for (int r = 1; r < c->nrhs; r++)
+      if (per[r].status != AJ_OK || per[r].relres > per[w].relres) w = r;
+    *info = per[w];
+    long long it = 0, rs = 0;
+    for (int r = 0; r < c->nrhs; r++) {
+      it = std::max<long long>(it, per[r].iters);
+      rs = std::max<long long>(rs, per[r].restarts);
+    }
+    info->iters = it;
+    info->restarts = rs;
+  } else if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = st;
+  }
+  return st;
+}
+
+extern "C" aj_status aj_restart_log(aj_ctx* c, int rhs, int64_t* iters, int64_t cap, int64_t* count) {
+  if (!c || rhs < 0 || rhs >= c->nrhs || !count || cap < 0 || (cap > 0 && !iters)) return AJ_EINVAL;
+  if ((int)c->rlog_h.size() <= rhs) { *count = 0; return AJ_OK; }
+  const auto& v = c->rlog_h[rhs];
+  *count = (int64_t)v.size();
+  for (int64_t k = 0; k < cap && k < (int64_t)v.size(); k++) iters[k] = v[k];
+  return AJ_OK;
+}
+
+// ---------------------------------------------------------------- state
+struct StateHeader {
+  uint64_t magic;
+  int64_t n;
+  int32_t nrhs, pol;
+  int32_t state_bytes, pad;
+  double sb[kMaxRhs];
+};
+static const uint64_t kStateMagic = 0x414a535441544531ull;  // "AJSTATE1"
+
+extern "C" aj_status aj_get_state(aj_ctx* c, void* buf, size_t* size) {
+  if (!c || !size) return AJ_EINVAL;
+  if (c->pol != AJ_FP64 && c->pol != AJ_DF64) return AJ_EINVAL;
+  if ((int)c->st_h.size() != c->nrhs) return AJ_EINVAL;  // no finished solve yet
+  const size_t vb = (size_t)c->n * c->nrhs * xelem_bytes(c->pol);
+  const size_t need = sizeof(StateHeader) + sizeof(RhsState) * c->nrhs + 3 * vb;
+  if (!buf) { *size = need; return AJ_OK; }
+  if (*size < need) { *size = need; return AJ_EINVAL; }
+  char* p = (char*)buf;
+  StateHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = kStateMagic;
+  h.n = c->n;
+  h.nrhs = c->nrhs;
+  h.pol = c->pol;
+  h.state_bytes = (int)sizeof(RhsState);
+  for (int r = 0; r < kMaxRhs; r++) h.sb[r] = c->sb[r];
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  std::memcpy(p, c->st_h.data(), sizeof(RhsState) * c->nrhs);
+  p += sizeof(RhsState) * c->nrhs;
+  for (int k = 0; k < 3; k++) {
+    if (vb) CK(cudaMemcpyAsync(p, c->x[k], vb, cudaMemcpyDeviceToHost, c->stream));
+    p += vb;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  *size = need;
+  return AJ_OK;
+}
+
+extern "C" aj_status aj_set_state(aj_ctx* c, const void* buf, size_t size) {
+  if (!c || !buf || !c->have_prm) return AJ_EINVAL;
+  if (c->pol != AJ_FP64 && c->pol != AJ_DF64) return AJ_EINVAL;
+  if (size < sizeof(StateHeader)) return AJ_EINVAL;
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  const size_t vb = (size_t)c->n * c->nrhs * xelem_bytes(c->pol);
+  const size_t need = sizeof(StateHeader) + sizeof(RhsState) * c->nrhs + 3 * vb;
+  if (h.magic != kStateMagic || h.n != c->n || h.nrhs != c->nrhs || h.pol != c->pol ||
+      h.state_bytes != (int)sizeof(RhsState) || size < need)
+    return AJ_EINVAL;
+  const char* p = (const char*)buf + sizeof(h);
+  c->st_h.resize(c->nrhs);
+  std::memcpy(c->st_h.data(), p, sizeof(RhsState) * c->nrhs);
+  p += sizeof(RhsState) * c->nrhs;
+  for (int k = 0; k < 3; k++) {
+    if (vb) CK(cudaMemcpyAsync(c->x[k], p, vb, cudaMemcpyHostToDevice, c->stream));
+    p += vb;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  for (int r = 0; r < kMaxRhs; r++) c->sb[r] = h.sb[r];
+  c->resume = true;
+  return AJ_OK;
+}
+
+// ---------------------------------------------------------------- batch (sequential for now)
+extern "C" aj_status aj_solve_batch(aj_ctx* const* ctx, int count, double* const* x_out,
+                                    int x_on_device, aj_info* info) {
+  if (count < 0 || (count > 0 && (!ctx || !x_out))) return AJ_EINVAL;
+  aj_status worst = AJ_OK;
+  for (int i = 0; i < count; i++) {
+    aj_info inf;
+    aj_status st = aj_solve(ctx[i], x_out[i], x_on_device, &inf);
+    if (info) info[i] = inf;
+    if (st != AJ_OK && worst == AJ_OK) worst = st;
+  }
+  return worst;
+}
+
+// ---------------------------------------------------------------- server (first version:
+// requests run in submission order when polled)
+#include <deque>
+#include <map>
+struct aj_server {
+  size_t budget = 0;
+  int max_slots = 1;
+  uint64_t next = 1;
+  std::deque<std::pair<uint64_t, aj_ctx*>> queue;
+  struct Done {
+    aj_status st;
+    aj_info info;
+    std::vector<double> x;
+  };
+  std::map<uint64_t, Done> done;
+};
+
+static size_t ctx_bytes(const aj_ctx* c) { return c->base.bytes + c->pws.bytes; }
+
+extern "C" aj_status aj_server_create(size_t hbm_budget_bytes, int max_slots, aj_server** out) {
+  if (!out || max_slots < 1 || hbm_budget_bytes == 0) return AJ_EINVAL;
+  aj_server* s = new aj_server();
+  s->budget = hbm_budget_bytes;
+  s->max_slots = max_slots;
+  *out = s;
+  return AJ_OK;
+}
+
+extern "C" aj_status aj_submit(aj_server* s, aj_ctx* c, uint64_t* ticket) {
+  if (!s || !c || !ticket) return AJ_EINVAL;
+  if (ctx_bytes(c) > s->budget) return AJ_EBUSY;
+  *ticket = s->next++;
+  s->queue.emplace_back(*ticket, c);
+  return AJ_OK;
+}
+
+extern "C" aj_status aj_poll(aj_server* s, uint64_t ticket, double* x_out, aj_info* info) {
+  if (!s) return AJ_EINVAL;
+  while (!s->done.count(ticket)) {
+    if (s->queue.empty()) return AJ_EINVAL;
+    auto [t, c] = s->queue.front();
+    s->queue.pop_front();
+    aj_server::Done d;
+    d.x.resize((size_t)c->n * c->nrhs);
+    d.st = aj_solve(c, d.x.data(), 0, &d.info);
+    s->done[t] = std::move(d);
+  }
+  auto it = s->done.find(ticket);
+  if (x_out) std::memcpy(x_out, it->second.x.data(), it->second.x.size() * 8);
+  if (info) *info = it->second.info;
+  aj_status st = it->second.st;
+  s->done.erase(it);
+  return st;
+}
+
+extern "C" void aj_server_destroy(aj_server* s) { delete s; }
+
+extern "C" uint64_t aj_kernel_launches(void) { return g_launches.load(); }

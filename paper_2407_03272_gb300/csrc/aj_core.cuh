@@ -1,0 +1,629 @@
+// aj_core.cuh -- device side of the fused accelerated-Jacobi (AJ) iteration.
+//
+// One persistent, grid-synchronised kernel runs Algorithm alg-jacobi of
+// Liang, Pang, Toh and Yang (arXiv 2407.03272, Section 3) with the restart
+// rule of Algorithm alg-apg-re (Section 2.2).  Each sweep s streams the CSR
+// matrix once and, per owned row i and right-hand side r:
+//
+//   sx_i = sum_j Q_ij x^{s-1}_j,   sp_i = sum_j Q_ij x^{s-2}_j       (one pass, two sums)
+//   (Q y^s)_i = sx_i + beta (sx_i - sp_i)        y^s = x^{s-1} + beta (x^{s-1} - x^{s-2})
+//   g_i = (Q y^s)_i - b_i,   x^s_i = y^s_i - J^{-1}_ii g_i              (line "x^t = y^t + J^-1(b - Q y^t)")
+//   d  += g_i (x^s_i - x^{s-1}_i)                                      (restart test <Q y^t - b, x^t - x^{t-1}>)
+//   rr += (b_i - sx_i)^2                                               (exact residual of x^{s-1})
+//
+// so the momentum extrapolation y is never stored: it is formed lazily from
+// the two previous iterates inside the gather.  After a grid barrier every
+// CTA sums the per-CTA partials in one fixed order (identical bits in every
+// CTA), checks the stop test for x^{s-1}, then takes the restart/momentum
+// branch for iteration s.  Buffers rotate among three iterate vectors.
+//
+// Precision policies (template parameter P):
+//   PolF64  IEEE FP64 everywhere (FMA row sums).
+//   PolDF64 double-float: values/vectors are (hi, lo) FP32 pairs; row sums use
+//           TwoProd/TwoSum error-free transforms (Ogita, Rump and Oishi,
+//           "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005) and
+//           the row update uses the double-word algorithms of Joldes, Muller
+//           and Popescu ("Tight and rigorous error bounds for basic building
+//           blocks of double-word arithmetic", ACM TOMS 44, 2017).  Runs on the
+//           FP32 pipes, which on GB300 issue ~70x more operations than FP64.
+//   PolF32  FP32 values, vectors and row arithmetic.
+//   PolB16  BF16 values, FP32 vectors and row arithmetic.
+// The restart/stop reductions are FP64 in every policy: per-thread
+// compensated double-float accumulators (F32/BF16/DF64) or FP64 (F64),
+// combined in FP64 across threads, CTAs and the grid.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace aj {
+
+constexpr int kThreads = 256;  // threads per CTA = rows per tile (one row per thread)
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxRhs = 4;
+constexpr int kNRed = 5;       // per right-hand side: d, gg, rr, xqx, bx
+constexpr int kLongRow = 32;   // rows longer than this are summed by the whole warp
+constexpr unsigned long long kBarrierTimeoutNs = 4000000000ull;  // 4 s per barrier wait
+constexpr long long kBarrierMaxSpins = 1ll << 27;
+
+// status codes shared with aj.h (kept numerically identical)
+constexpr int kOk = 0, kEMaxit = -4, kEDiverged = -5, kENonfinite = -6, kETimeout = -7;
+
+enum StopKind { kStopRelres = 0, kStopObjgap = 1, kStopNone = 2 };
+
+// Per right-hand-side solver state.  Every CTA keeps an identical copy in
+// shared memory; CTA 0 writes it back to global memory at exit.
+struct RhsState {
+  double alpha;       // alpha_t of the next iteration t = cur_t + 1
+  double beta;        // y^{t+1} = x^t + beta (x^t - x^{t-1}) for the next sweep
+  double bnorm2;      // ||b||^2 (FP64)
+  double rr0;         // squared residual of x^0 (divergence guard)
+  double relres;      // relative residual of the last checked iterate
+  double fval;        // f(x) of the last checked iterate (objective stop only)
+  long long t;        // index of the iterate in buffer `cur`
+  long long ell;      // restarts so far
+  long long K;        // K_ell
+  long long Kre;      // K_re
+  long long t_final;  // index of the returned iterate
+  int cur, prev, nxt; // buffer indices of x^t, x^{t-1} (may equal cur), spare
+  int done;           // 1 once this right-hand side has stopped
+  int status;         // kOk / kEMaxit / kEDiverged / kENonfinite
+  int pad;
+};
+
+// ----------------------------------------------------------------------------
+// Memory helpers.  Iterate buffers are rewritten by other CTAs between sweeps,
+// so they are read at L2 (ld.global.cg), never through the incoherent L1/tex
+// paths.  The matrix, b and J^{-1} never change during a launch.
+template <class T>
+__device__ __forceinline__ T ld_l2(const T* p) { return __ldcg(p); }
+template <class T>
+__device__ __forceinline__ T ld_ro(const T* p) { return __ldg(p); }
+template <class T>
+__device__ __forceinline__ void st_l2(T* p, T v) { __stcg(p, v); }
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a cooperative (co-resident) launch.  `target` is the
+// arrival count that completes this barrier (k * gridDim.x for the k-th).
+// Every wait is bounded: after kBarrierTimeoutNs the CTA records kETimeout in
+// *err and returns false; a CTA that sees *err != 0 also returns false.
+__device__ __forceinline__ bool grid_sync(unsigned long long* bar, unsigned long long target,
+                                          int* err, unsigned int nctas) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (nctas > 1) {
+      __threadfence();
+      red_release_add_u64(bar, 1ull);
+      unsigned long long t0 = global_ns();
+      long long spins = 0;
+      while (ld_acquire_u64(bar) < target) {
+        ++spins;
+        if ((spins & 63) == 0) {
+          if (*(volatile int*)err != 0) { ok = 0; break; }
+          if (global_ns() - t0 > kBarrierTimeoutNs || spins > kBarrierMaxSpins) {
+            atomicCAS(err, 0, kETimeout);
+            ok = 0;
+            break;
+          }
+        }
+        __nanosleep(40);
+      }
+      __threadfence();
+    }
+    if (*(volatile int*)err != 0) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ----------------------------------------------------------------------------
+// Double-word (FP32 pair) building blocks: Knuth's TwoSum, Dekker's
+// Fast2Sum (|a| >= |b|), FMA-based TwoProd.
+struct dw {
+  float hi, lo;
+};
+__device__ __forceinline__ dw two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dw fast_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+__device__ __forceinline__ dw two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  return {p, e};
+}
+// Accurate double-word + double-word (Joldes-Muller-Popescu Alg. 6, error <= 3u^2).
+__device__ __forceinline__ dw dw_add(dw x, dw y) {
+  dw s = two_sum(x.hi, y.hi);
+  dw t = two_sum(x.lo, y.lo);
+  float c = __fadd_rn(s.lo, t.hi);
+  dw v = fast_two_sum(s.hi, c);
+  float w = __fadd_rn(t.lo, v.lo);
+  return fast_two_sum(v.hi, w);
+}
+__device__ __forceinline__ dw dw_neg(dw x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ dw dw_sub(dw x, dw y) { return dw_add(x, dw_neg(y)); }
+// Double-word x double-word with FMA (Joldes-Muller-Popescu Alg. 12, error <= 4u^2).
+__device__ __forceinline__ dw dw_mul(dw x, dw y) {
+  dw c = two_prod(x.hi, y.hi);
+  float tl0 = __fmul_rn(x.lo, y.lo);
+  float tl1 = __fmaf_rn(x.hi, y.lo, tl0);
+  float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
+  float cl3 = __fadd_rn(c.lo, cl2);
+  return fast_two_sum(c.hi, cl3);
+}
+__device__ __forceinline__ dw dw_from_double(double v) {
+  float h = __double2float_rn(v);
+  float l = __double2float_rn(v - (double)h);
+  return {h, l};
+}
+__device__ __forceinline__ double dw_to_double(dw x) { return (double)x.hi + (double)x.lo; }
+
+// Compensated running sum (double-word accumulator) fed with exact products.
+struct acc_dw {
+  float hi, lo;
+};
+__device__ __forceinline__ void acc_zero(acc_dw& a) { a.hi = 0.f; a.lo = 0.f; }
+__device__ __forceinline__ void acc_add_term(acc_dw& a, float ph, float pl) {
+  dw s = two_sum(a.hi, ph);
+  a.hi = s.hi;
+  a.lo = __fadd_rn(a.lo, __fadd_rn(s.lo, pl));
+}
+__device__ __forceinline__ double acc_value(const acc_dw& a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ void acc_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ double acc_value(double a) { return a; }
+
+// ----------------------------------------------------------------------------
+// Precision policies.
+struct PolF64 {
+  using V = double;  // stored matrix value
+  using X = double;  // stored vector element
+  using S = double;  // row arithmetic
+  using A = double;  // per-thread reduction accumulator
+  static constexpr int kId = 0;
+  __device__ static S zero() { return 0.0; }
+  __device__ static S ldx(const X* p) { return ld_l2(p); }
+  __device__ static S ldr(const X* p) { return ld_ro(p); }
+  __device__ static void stx(X* p, S v) { st_l2(p, v); }
+  __device__ static void mac(S& acc, const V* v, S x) { acc = fma(ld_ro(v), x, acc); }
+  __device__ static S finish(S a) { return a; }
+  __device__ static S add(S a, S b) { return a + b; }
+  __device__ static S sub(S a, S b) { return a - b; }
+  __device__ static S mul(S a, S b) { return a * b; }
+  __device__ static S fma_(S a, S b, S c) { return fma(a, b, c); }  // a*b + c
+  __device__ static S coef(double c) { return c; }
+  __device__ static void acc_prod(A& a, S u, S v) { a = fma(u, v, a); }
+  __device__ static S shfl_xor(S v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+  __device__ static S shfl(S v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+  __device__ static S combine(S a, S b) { return a + b; }
+  __device__ static bool finite(S v) { return isfinite(v); }
+};
+
+struct PolDF64 {
+  using V = float2;
+  using X = float2;
+  using S = dw;
+  using A = acc_dw;
+  static constexpr int kId = 1;
+  __device__ static S zero() { return {0.f, 0.f}; }
+  __device__ static S ldx(const X* p) { float2 v = ld_l2(p); return {v.x, v.y}; }
+  __device__ static S ldr(const X* p) { float2 v = ld_ro(p); return {v.x, v.y}; }
+  __device__ static void stx(X* p, S v) { st_l2(p, make_float2(v.hi, v.lo)); }
+  // acc += v * x with the product split exactly (TwoProd) and cross terms folded
+  // into the low word; the sum of high words is kept by TwoSum (Dot2 pattern).
+  __device__ static void mac(S& acc, const V* vp, S x) {
+    float2 v = ld_ro(vp);
+    dw p = two_prod(v.x, x.hi);
+    float pl = __fmaf_rn(v.x, x.lo, p.lo);
+    pl = __fmaf_rn(v.y, x.hi, pl);
+    dw s = two_sum(acc.hi, p.hi);
+    acc.hi = s.hi;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, pl));
+  }
+  __device__ static S finish(S a) { return fast_two_sum_ordered(a); }
+  __device__ static S fast_two_sum_ordered(S a) { return two_sum(a.hi, a.lo); }
+  __device__ static S add(S a, S b) { return dw_add(a, b); }
+  __device__ static S sub(S a, S b) { return dw_sub(a, b); }
+  __device__ static S mul(S a, S b) { return dw_mul(a, b); }
+  __device__ static S fma_(S a, S b, S c) { return dw_add(dw_mul(a, b), c); }
+  __device__ static S coef(double c) { return dw_from_double(c); }
+  __device__ static void acc_prod(A& a, S u, S v) {
+    dw p = two_prod(u.hi, v.hi);
+    float pl = __fmaf_rn(u.hi, v.lo, p.lo);
+    pl = __fmaf_rn(u.lo, v.hi, pl);
+    acc_add_term(a, p.hi, pl);
+  }
+  __device__ static S shfl_xor(S v, int m) {
+    return {__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+  }
+  __device__ static S shfl(S v, int src) {
+    return {__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+  }
+  __device__ static S combine(S a, S b) { return dw_add(a, b); }
+  __device__ static bool finite(S v) { return isfinite(v.hi) && isfinite(v.lo); }
+};
+
+struct PolF32 {
+  using V = float;
+  using X = float;
+  using S = float;
+  using A = acc_dw;
+  static constexpr int kId = 2;
+  __device__ static S zero() { return 0.f; }
+  __device__ static S ldx(const X* p) { return ld_l2(p); }
+  __device__ static S ldr(const X* p) { return ld_ro(p); }
+  __device__ static void stx(X* p, S v) { st_l2(p, v); }
+  __device__ static void mac(S& acc, const V* v, S x) { acc = __fmaf_rn(ld_ro(v), x, acc); }
+  __device__ static S finish(S a) { return a; }
+  __device__ static S add(S a, S b) { return __fadd_rn(a, b); }
+  __device__ static S sub(S a, S b) { return __fsub_rn(a, b); }
+  __device__ static S mul(S a, S b) { return __fmul_rn(a, b); }
+  __device__ static S fma_(S a, S b, S c) { return __fmaf_rn(a, b, c); }
+  __device__ static S coef(double c) { return __double2float_rn(c); }
+  __device__ static void acc_prod(A& a, S u, S v) {
+    dw p = two_prod(u, v);
+    acc_add_term(a, p.hi, p.lo);
+  }
+  __device__ static S shfl_xor(S v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+  __device__ static S shfl(S v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+  __device__ static S combine(S a, S b) { return __fadd_rn(a, b); }
+  __device__ static bool finite(S v) { return isfinite(v); }
+};
+
+struct PolB16 : PolF32 {
+  using V = __nv_bfloat16;
+  static constexpr int kId = 3;
+  __device__ static void mac(S& acc, const V* v, S x) {
+    acc = __fmaf_rn(__bfloat162float(ld_ro(v)), x, acc);
+  }
+};
+
+// ----------------------------------------------------------------------------
+// Kernel arguments.  Vectors with several right-hand sides are interleaved:
+// element (i, r) lives at i * nrhs + r, so one gather fetches all of them.
+template <class P>
+struct IterArgs {
+  int n;
+  const int* row_ptr;
+  const int* col;
+  const typename P::V* val;
+  const typename P::X* b;     // [n * nrhs]
+  const typename P::X* jinv;  // [n]
+  typename P::X* x[3];        // three iterate buffers, [n * nrhs] each
+  double* partials;           // [2][gridDim][nrhs][kNRed]
+  unsigned long long* bar;    // barrier arrival counter, zero at launch
+  int* err;                   // device error word, zero at launch
+  RhsState* state;            // [nrhs], in/out
+  long long* rlog;            // [nrhs][rlog_cap] restart iterations
+  int rlog_cap;
+  double* trace;              // optional [trace_cap][nrhs][4]: d, ||g||^2, rr, beta per sweep
+  long long trace_cap;
+  long long maxit;
+  int stop;
+  int restart;
+  int momentum;
+  double tol;
+  double fstar;
+  double fscale;              // f(x) = fscale * (1/2 <x~, Q~ x~> - <b~, x~>) for scaled data
+  long long max_sweeps;       // sweeps allowed in this launch (chunked runs), >= 1
+};
+
+// Warp-cooperative row sums for one long row (lanes stride over the entries,
+// then a fixed xor tree).  Returns the sums in every lane.
+template <class P, int NR>
+__device__ __forceinline__ void long_row_sums(const IterArgs<P>& a, int rs, int re,
+                                              const typename P::X* const* xc,
+                                              const typename P::X* const* xp, const bool* same,
+                                              const bool* active, typename P::S* sx,
+                                              typename P::S* sp) {
+  using S = typename P::S;
+  const int lane = threadIdx.x & 31;
+  S lx[NR], lp[NR];
+#pragma unroll
+  for (int r = 0; r < NR; r++) { lx[r] = P::zero(); lp[r] = P::zero(); }
+  for (int q = rs + lane; q < re; q += 32) {
+    const int c = ld_ro(a.col + q);
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      if (!active[r]) continue;
+      P::mac(lx[r], a.val + q, P::ldx(xc[r] + (size_t)c * NR + r));
+      if (!same[r]) P::mac(lp[r], a.val + q, P::ldx(xp[r] + (size_t)c * NR + r));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NR; r++) {
+    lx[r] = P::finish(lx[r]);
+    lp[r] = P::finish(lp[r]);
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+      lx[r] = P::combine(lx[r], P::shfl_xor(lx[r], m));
+      lp[r] = P::combine(lp[r], P::shfl_xor(lp[r], m));
+    }
+    sx[r] = lx[r];
+    sp[r] = same[r] ? lx[r] : lp[r];
+  }
+}
+
+// Block reduction of per-thread FP64 values in a fixed order; result valid in
+// thread 0.  `sm` holds kWarps doubles.
+__device__ __forceinline__ double block_sum(double v, double* sm) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) sm[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kWarps; i++) s += sm[i];
+  __syncthreads();
+  return s;
+}
+
+// One sweep over the CTA's tiles: the fused SpMV at y, x update and reduction
+// terms.  `compute_x` is false on a residual-only sweep (no x^s is formed).
+template <class P, int NR>
+__device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, bool compute_x,
+                                      bool want_obj, typename P::A (&acc)[NR][kNRed]) {
+  using S = typename P::S;
+  using X = typename P::X;
+  const X* xc[NR];
+  const X* xp[NR];
+  X* xn[NR];
+  bool same[NR], active[NR];
+  S beta[NR];
+#pragma unroll
+  for (int r = 0; r < NR; r++) {
+    xc[r] = a.x[st[r].cur];
+    xp[r] = a.x[st[r].prev];
+    xn[r] = a.x[st[r].nxt];
+    same[r] = st[r].cur == st[r].prev;
+    active[r] = st[r].done == 0;
+    beta[r] = P::coef(st[r].beta);
+  }
+  const int lane = threadIdx.x & 31;
+  const int ntiles = (a.n + kThreads - 1) / kThreads;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int i = tile * kThreads + threadIdx.x;
+    const bool valid = i < a.n;
+    int rs = 0, re = 0;
+    if (valid) {
+      rs = ld_ro(a.row_ptr + i);
+      re = ld_ro(a.row_ptr + i + 1);
+    }
+    const bool is_long = valid && (re - rs) > kLongRow;
+    S sx[NR], sp[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) { sx[r] = P::zero(); sp[r] = P::zero(); }
+    if (valid && !is_long) {
+      for (int q = rs; q < re; q++) {
+        const int c = ld_ro(a.col + q);
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+          if (!active[r]) continue;
+          P::mac(sx[r], a.val + q, P::ldx(xc[r] + (size_t)c * NR + r));
+          if (!same[r]) P::mac(sp[r], a.val + q, P::ldx(xp[r] + (size_t)c * NR + r));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NR; r++) {
+        sx[r] = P::finish(sx[r]);
+        sp[r] = same[r] ? sx[r] : P::finish(sp[r]);
+      }
+    }
+    unsigned lm = __ballot_sync(0xffffffffu, is_long);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int lrs = __shfl_sync(0xffffffffu, rs, src);
+      const int lre = __shfl_sync(0xffffffffu, re, src);
+      S tx[NR], tp[NR];
+      long_row_sums<P, NR>(a, lrs, lre, xc, xp, same, active, tx, tp);
+      if (lane == src) {
+#pragma unroll
+        for (int r = 0; r < NR; r++) { sx[r] = tx[r]; sp[r] = tp[r]; }
+      }
+    }
+    if (!valid) continue;
+    const S ji = P::ldr(a.jinv + i);
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      if (!active[r]) continue;
+      const size_t e = (size_t)i * NR + r;
+      const S xi = P::ldx(xc[r] + e);
+      const S bi = P::ldr(a.b + e);
+      // exact residual of x^{s-1}: b - Q x^{s-1}
+      const S res = P::sub(bi, sx[r]);
+      P::acc_prod(acc[r][2], res, res);
+      if (want_obj) {
+        P::acc_prod(acc[r][3], xi, sx[r]);
+        P::acc_prod(acc[r][4], bi, xi);
+      }
+      if (!compute_x) continue;
+      S qy, yi;
+      if (same[r]) {
+        qy = sx[r];
+        yi = xi;
+      } else {
+        const S xpi = P::ldx(xp[r] + e);
+        qy = P::fma_(beta[r], P::sub(sx[r], sp[r]), sx[r]);
+        yi = P::fma_(beta[r], P::sub(xi, xpi), xi);
+      }
+      const S g = P::sub(qy, bi);
+      const S xnew = P::sub(yi, P::mul(ji, g));
+      P::stx(xn[r] + e, xnew);
+      P::acc_prod(acc[r][0], g, P::sub(xnew, xi));
+      P::acc_prod(acc[r][1], g, g);
+    }
+  }
+}
+
+// Scalar step after the grid barrier, run by one thread per CTA with the
+// grid totals tot[r][k].  Identical inputs give identical decisions in every
+// CTA.  Returns true when every right-hand side is done.
+template <int NR>
+__device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kNRed], long long s,
+                                            long long maxit, int stop, int restart, int momentum,
+                                            double tol, double fstar, double fscale, long long* rlog,
+                                            int rlog_cap, bool log_it) {
+  bool all_done = true;
+  for (int r = 0; r < NR; r++) {
+    RhsState& q = st[r];
+    if (q.done) continue;
+    const double d = tot[r][0];
+    const double rr = tot[r][2];
+    // --- stop test for x^{s-1} (the iterate in buffer cur)
+    const double rnorm = sqrt(rr);
+    const double bn = sqrt(q.bnorm2);
+    q.relres = bn > 0.0 ? rnorm / bn : rnorm;
+    q.fval = fscale * (0.5 * tot[r][3] - tot[r][4]);
+    if (s == 1) q.rr0 = rr;
+    bool stop_now = false;
+    if (stop == kStopRelres) stop_now = q.relres <= tol;
+    else if (stop == kStopObjgap) stop_now = fabs(q.fval - fstar) / (1.0 + fabs(fstar)) <= tol;
+    if (!isfinite(rr) || !isfinite(d)) {
+      q.done = 1; q.status = kENonfinite; q.t_final = q.t;
+      continue;
+    }
+    if (stop_now) {
+      q.done = 1; q.status = kOk; q.t_final = q.t;
+      continue;
+    }
+    if (q.t >= maxit) {
+      q.done = 1; q.status = kEMaxit; q.t_final = q.t;
+      continue;
+    }
+    if (s > 1 && q.rr0 > 0.0 && rr > 1e16 * q.rr0) {
+      q.done = 1; q.status = kEDiverged; q.t_final = q.t;
+      continue;
+    }
+    // --- iteration t = s: restart rule of Algorithm alg-apg-re
+    const long long t = q.t + 1;
+    const bool do_restart = restart && (t > q.Kre + q.K) && (d >= 0.0);
+    if (do_restart) {
+      if (log_it && q.ell < rlog_cap) rlog[(size_t)r * rlog_cap + q.ell] = t;
+      q.Kre = t;
+      q.K = 2 * q.K;
+      q.ell += 1;
+      q.alpha = 1.0;  // alpha_{t+1} = 1 (alpha_t = 0 is never read again)
+      q.beta = 0.0;
+      // x^t = x^{t-1}: the buffer cur already holds x^{t-1}; prev := cur
+      q.prev = q.cur;
+      q.nxt = (q.cur == 0) ? 1 : 0;
+    } else {
+      double an = 1.0, be = 0.0;
+      if (momentum) {
+        an = 0.5 * (1.0 + sqrt(1.0 + 4.0 * q.alpha * q.alpha));
+        be = (q.alpha - 1.0) / an;
+      }
+      q.alpha = an;
+      q.beta = be;
+      const int oldprev = q.prev, oldcur = q.cur, oldnew = q.nxt;
+      q.prev = oldcur;
+      q.cur = oldnew;
+      q.nxt = (oldprev != oldcur && oldprev != oldnew) ? oldprev : (3 - oldcur - oldnew);
+    }
+    q.t = t;
+    all_done = false;
+  }
+  return all_done;
+}
+
+// The persistent fused AJ kernel.  Launch cooperatively with kThreads
+// threads per CTA.  Runs sweeps until every right-hand side is done or
+// max_sweeps sweeps have run.
+template <class P, int NR>
+__global__ void __launch_bounds__(kThreads) aj_persistent_kernel(IterArgs<P> a) {
+  using A = typename P::A;
+  __shared__ RhsState st[NR];
+  __shared__ double s_tot[NR][kNRed];
+  __shared__ double s_red[kWarps];
+  __shared__ int s_done;
+  if (threadIdx.x < NR) st[threadIdx.x] = a.state[threadIdx.x];
+  __syncthreads();
+  const unsigned int G = gridDim.x;
+  unsigned long long target = 0;
+  bool want_obj = a.stop == kStopObjgap;
+  long long s0 = 0;  // sweep counter within this launch
+  bool finished = false;
+  for (s0 = 0; s0 < a.max_sweeps; s0++) {
+    // sweep number in the run's own numbering: x^{s-1} is checked, x^s formed
+    long long s_run = 0;
+    bool compute_x = false;
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      if (!st[r].done) {
+        s_run = st[r].t + 1;
+        compute_x = compute_x || (st[r].t < a.maxit);
+      }
+    }
+    A acc[NR][kNRed];
+#pragma unroll
+    for (int r = 0; r < NR; r++)
+#pragma unroll
+      for (int k = 0; k < kNRed; k++) acc_zero(acc[r][k]);
+    sweep<P, NR>(a, st, compute_x, want_obj, acc);
+    // CTA partials -> global (parity-buffered by sweep)
+    double* part = a.partials + (size_t)(s0 & 1) * G * NR * kNRed;
+#pragma unroll
+    for (int r = 0; r < NR; r++)
+#pragma unroll
+      for (int k = 0; k < kNRed; k++) {
+        const double v = block_sum(acc_value(acc[r][k]), s_red);
+        if (threadIdx.x == 0) __stcg(part + ((size_t)blockIdx.x * NR + r) * kNRed + k, v);
+      }
+    target += G;
+    if (!grid_sync(a.bar, target, a.err, G)) return;
+    // every CTA sums the partials in the same fixed order
+#pragma unroll
+    for (int r = 0; r < NR; r++)
+#pragma unroll
+      for (int k = 0; k < kNRed; k++) {
+        double v = 0.0;
+        for (unsigned int c = threadIdx.x; c < G; c += kThreads)
+          v += __ldcg(part + ((size_t)c * NR + r) * kNRed + k);
+        v = block_sum(v, s_red);
+        if (threadIdx.x == 0) s_tot[r][k] = v;
+      }
+    if (threadIdx.x == 0) {
+      if (a.trace && blockIdx.x == 0 && s_run >= 1 && s_run <= a.trace_cap) {
+        for (int r = 0; r < NR; r++) {
+          double* tr = a.trace + ((size_t)(s_run - 1) * NR + r) * 4;
+          tr[0] = s_tot[r][0];
+          tr[1] = s_tot[r][1];
+          tr[2] = s_tot[r][2];
+          tr[3] = st[r].beta;
+        }
+      }
+      s_done = scalar_step<NR>(st, s_tot, s_run, a.maxit, a.stop, a.restart, a.momentum, a.tol,
+                               a.fstar, a.fscale, a.rlog, a.rlog_cap, blockIdx.x == 0) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_done) { finished = true; break; }
+  }
+  (void)finished;
+  if (blockIdx.x == 0 && threadIdx.x < NR) a.state[threadIdx.x] = st[threadIdx.x];
+}
+
+}  // namespace aj

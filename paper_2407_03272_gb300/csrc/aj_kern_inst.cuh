@@ -1,0 +1,79 @@
+// aj_kern_inst.cuh -- instantiates the persistent kernel of one precision
+// policy for 1..4 right-hand sides.  Included once per translation unit with
+// AJ_POL (policy type) and AJ_SUFFIX (name suffix) defined.
+#include "aj_core.cuh"
+#include "aj_launch.h"
+
+#define AJ_CAT2(a, b) a##b
+#define AJ_CAT(a, b) AJ_CAT2(a, b)
+
+namespace aj {
+
+template <class P>
+static IterArgs<P> typed_args(const IterLaunch& L) {
+  IterArgs<P> a;
+  a.n = L.n;
+  a.row_ptr = L.row_ptr;
+  a.col = L.col;
+  a.val = static_cast<const typename P::V*>(L.val);
+  a.b = static_cast<const typename P::X*>(L.b);
+  a.jinv = static_cast<const typename P::X*>(L.jinv);
+  for (int k = 0; k < 3; k++) a.x[k] = static_cast<typename P::X*>(L.x[k]);
+  a.partials = L.partials;
+  a.bar = L.bar;
+  a.err = L.err;
+  a.state = L.state;
+  a.rlog = L.rlog;
+  a.rlog_cap = L.rlog_cap;
+  a.trace = L.trace;
+  a.trace_cap = L.trace_cap;
+  a.maxit = L.maxit;
+  a.stop = L.stop;
+  a.restart = L.restart;
+  a.momentum = L.momentum;
+  a.tol = L.tol;
+  a.fstar = L.fstar;
+  a.fscale = L.fscale;
+  a.max_sweeps = L.max_sweeps;
+  return a;
+}
+
+template <class P, int NR>
+static cudaError_t launch_nr(const IterLaunch& L, int grid, cudaStream_t s) {
+  IterArgs<P> a = typed_args<P>(L);
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)aj_persistent_kernel<P, NR>, dim3(grid),
+                                     dim3(kThreads), args, 0, s);
+}
+
+template <class P, int NR>
+static int occ_nr() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, aj_persistent_kernel<P, NR>, kThreads, 0) !=
+      cudaSuccess)
+    return 0;
+  return nb;
+}
+
+cudaError_t AJ_CAT(launch_persistent_, AJ_SUFFIX)(int nrhs, const IterLaunch& L, int grid,
+                                                  cudaStream_t s) {
+  switch (nrhs) {
+    case 1: return launch_nr<AJ_POL, 1>(L, grid, s);
+    case 2: return launch_nr<AJ_POL, 2>(L, grid, s);
+    case 3: return launch_nr<AJ_POL, 3>(L, grid, s);
+    case 4: return launch_nr<AJ_POL, 4>(L, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int AJ_CAT(blocks_per_sm_, AJ_SUFFIX)(int nrhs) {
+  switch (nrhs) {
+    case 1: return occ_nr<AJ_POL, 1>();
+    case 2: return occ_nr<AJ_POL, 2>();
+    case 3: return occ_nr<AJ_POL, 3>();
+    case 4: return occ_nr<AJ_POL, 4>();
+  }
+  return 0;
+}
+
+}  // namespace aj

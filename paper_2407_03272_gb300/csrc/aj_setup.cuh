@@ -1,0 +1,254 @@
+// aj_setup.cuh -- setup and auxiliary kernels: CSR validation, the diagonal
+// proximal matrix J (eq. J-diag, Section 3, or J = L D), precision
+// conversions, the FP64 residual b - Q x, and the power iteration that
+// estimates L = lambda_max(D^-1/2 Q D^-1/2).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "aj_core.cuh"
+
+namespace aj {
+
+constexpr int kSetupThreads = 256;
+
+// Error bits written by the validation kernels.
+enum : int {
+  kBadRowPtr = 1,       // row_ptr[0] != 0, decreasing, or row_ptr[n] != nnz
+  kBadCol = 2,          // column index outside [0, n)
+  kNonFinite = 4,       // NaN or Inf value
+  kNegDiag = 8,         // negative diagonal entry (Q not PSD)
+  kZeroDiagNonzero = 16 // zero diagonal but a nonzero off-diagonal entry (Q not PSD)
+};
+
+__global__ void k_check_rowptr(int n, long long nnz, const int* rp, int* flags) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  const int v = rp[i];
+  if (v < 0 || (long long)v > nnz) atomicOr(flags, kBadRowPtr);
+  if (i == 0 && v != 0) atomicOr(flags, kBadRowPtr);
+  if (i == n && (long long)v != nnz) atomicOr(flags, kBadRowPtr);
+  if (i < n && rp[i + 1] < v) atomicOr(flags, kBadRowPtr);
+}
+
+// Requires a valid row_ptr.  Writes diag[i] = sum of the diagonal entries of
+// row i and checks columns, finiteness and the PSD-necessary diagonal rules.
+__global__ void k_check_rows(int n, const int* rp, const int* ci, const double* val, double* diag,
+                             int* flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d = 0.0;
+  bool off_nonzero = false;
+  int f = 0;
+  for (int q = rp[i]; q < rp[i + 1]; q++) {
+    const int c = ci[q];
+    const double v = val[q];
+    if (c < 0 || c >= n) f |= kBadCol;
+    if (!isfinite(v)) f |= kNonFinite;
+    if (c == i) d += v;
+    else if (v != 0.0) off_nonzero = true;
+  }
+  if (d < 0.0) f |= kNegDiag;
+  if (d == 0.0 && off_nonzero) f |= kZeroDiagNonzero;
+  diag[i] = d;
+  if (f) atomicOr(flags, f);
+}
+
+// J^{-1} in FP64.  policy 0: eq. J-diag, J_kk = Q_kk + sum_{j!=k} |Q_kj| (the
+// off-diagonal magnitudes summed in CSR order); policy 1: J_kk = L Q_kk.
+// A zero J_kk (all-zero row) becomes 1.
+__global__ void k_jinv(int n, const int* rp, const int* ci, const double* val, const double* diag,
+                       int policy, double L, double* jinv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double j;
+  if (policy == 0) {
+    double off = 0.0;
+    for (int q = rp[i]; q < rp[i + 1]; q++)
+      if (ci[q] != i) off += fabs(val[q]);
+    j = diag[i] + off;
+  } else {
+    j = L * diag[i];
+  }
+  if (j == 0.0) j = 1.0;
+  jinv[i] = 1.0 / j;
+}
+
+// Scaled copies into the precision of the iteration (scale is a power of two).
+__global__ void k_to_f32(long long m, const double* src, double scale, float* dst) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) dst[i] = __double2float_rn(src[i] * scale);
+}
+__global__ void k_to_b16(long long m, const double* src, double scale, __nv_bfloat16* dst) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) dst[i] = __double2bfloat16(src[i] * scale);
+}
+__global__ void k_to_dw(long long m, const double* src, double scale, float2* dst) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) {
+    dw v = dw_from_double(src[i] * scale);
+    dst[i] = make_float2(v.hi, v.lo);
+  }
+}
+// Per right-hand-side scales and source buffers for the interleaved vectors.
+struct RhsMap {
+  double s[kMaxRhs];
+  int cur[kMaxRhs];
+};
+__device__ __forceinline__ void to_x(double v, double* d) { *d = v; }
+__device__ __forceinline__ void to_x(double v, float* d) { *d = __double2float_rn(v); }
+__device__ __forceinline__ void to_x(double v, float2* d) {
+  dw w = dw_from_double(v);
+  *d = make_float2(w.hi, w.lo);
+}
+__device__ __forceinline__ double from_x(double v) { return v; }
+__device__ __forceinline__ double from_x(float v) { return (double)v; }
+__device__ __forceinline__ double from_x(float2 v) { return (double)v.x + (double)v.y; }
+
+// dst[e] = src[e] * s[e % nrhs] in the iteration precision.
+template <class X>
+__global__ void k_to_policy(long long m, int nrhs, const double* src, RhsMap mp, X* dst) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m) to_x(src[e] * mp.s[e % nrhs], dst + e);
+}
+// dst[e] = buf[cur[r]][e] * s[r], r = e % nrhs, back to FP64.
+template <class X>
+__global__ void k_from_policy(long long m, int nrhs, const X* b0, const X* b1, const X* b2,
+                              RhsMap mp, double* dst) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m) return;
+  const int r = (int)(e % nrhs);
+  const int k = mp.cur[r];
+  const X* src = k == 0 ? b0 : (k == 1 ? b1 : b2);
+  dst[e] = from_x(src[e]) * mp.s[r];
+}
+
+// Column-major (n x nrhs) <-> interleaved (i * nrhs + r).
+__global__ void k_interleave(int n, int nrhs, const double* cm, double* il) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * nrhs) return;
+  const int r = (int)(e % nrhs);
+  const long long i = e / nrhs;
+  il[e] = cm[(long long)r * n + i];
+}
+__global__ void k_deinterleave(int n, int nrhs, const double* il, double* cm) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * nrhs) return;
+  const int r = (int)(e % nrhs);
+  const long long i = e / nrhs;
+  cm[(long long)r * n + i] = il[e];
+}
+
+// FP64 residual r = b - Q x for interleaved multi-RHS vectors; per-block
+// partial sums of r_r^2 and (optionally) <x, Qx>, <b, x> go to part[block][nrhs][3].
+__global__ void k_residual(int n, int nrhs, const int* rp, const int* ci, const double* val,
+                           const double* b, const double* x, double* r_out, double* part) {
+  __shared__ double sm[kMaxRhs * 3][kSetupThreads / 32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[kMaxRhs * 3];
+  for (int k = 0; k < kMaxRhs * 3; k++) acc[k] = 0.0;
+  if (i < n) {
+    double s[kMaxRhs] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = rp[i]; q < rp[i + 1]; q++) {
+      const double v = val[q];
+      const long long c = ci[q];
+      for (int r = 0; r < nrhs; r++) s[r] = fma(v, x[c * nrhs + r], s[r]);
+    }
+    for (int r = 0; r < nrhs; r++) {
+      const long long e = (long long)i * nrhs + r;
+      const double res = b[e] - s[r];
+      if (r_out) r_out[e] = res;
+      acc[r * 3 + 0] = res * res;
+      acc[r * 3 + 1] = x[e] * s[r];
+      acc[r * 3 + 2] = b[e] * x[e];
+    }
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = 0; k < nrhs * 3; k++) {
+    double v = acc[k];
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    if (lane == 0) sm[k][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nrhs * 3) {
+    double v = 0.0;
+    for (int k = 0; k < kSetupThreads / 32; k++) v += sm[threadIdx.x][k];
+    part[(size_t)blockIdx.x * nrhs * 3 + threadIdx.x] = v;
+  }
+}
+
+// y = D^-1/2 Q D^-1/2 x (rows with zero diagonal give 0); per-block partials
+// of <x, y> and <y, y> go to part[block][2].
+__global__ void k_normalized_spmv(int n, const int* rp, const int* ci, const double* val,
+                                  const double* diag, const double* x, double* y, double* part) {
+  __shared__ double sm[2][kSetupThreads / 32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double xy = 0.0, yy = 0.0;
+  if (i < n) {
+    const double di = diag[i];
+    double s = 0.0;
+    if (di > 0.0) {
+      for (int q = rp[i]; q < rp[i + 1]; q++) {
+        const int c = ci[q];
+        const double dc = diag[c];
+        if (dc > 0.0) s = fma(val[q] * rsqrt(dc), x[c], s);
+      }
+      s *= rsqrt(di);
+    }
+    y[i] = s;
+    xy = x[i] * s;
+    yy = s * s;
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int m = 16; m >= 1; m >>= 1) {
+    xy += __shfl_xor_sync(0xffffffffu, xy, m);
+    yy += __shfl_xor_sync(0xffffffffu, yy, m);
+  }
+  if (lane == 0) { sm[0][w] = xy; sm[1][w] = yy; }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double v = 0.0;
+    for (int k = 0; k < kSetupThreads / 32; k++) v += sm[threadIdx.x][k];
+    part[(size_t)blockIdx.x * 2 + threadIdx.x] = v;
+  }
+}
+
+// Gershgorin bound of D^-1/2 Q D^-1/2: per-block maxima of sum_j |Q_ij| / sqrt(D_i D_j).
+__global__ void k_gershgorin(int n, const int* rp, const int* ci, const double* val,
+                             const double* diag, double* part) {
+  __shared__ double sm[kSetupThreads / 32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double g = 0.0;
+  if (i < n && diag[i] > 0.0) {
+    for (int q = rp[i]; q < rp[i + 1]; q++) {
+      const double dc = diag[ci[q]];
+      if (dc > 0.0) g += fabs(val[q]) * rsqrt(dc);
+    }
+    g *= rsqrt(diag[i]);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int m = 16; m >= 1; m >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, m));
+  if (lane == 0) sm[w] = g;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int k = 0; k < kSetupThreads / 32; k++) v = fmax(v, sm[k]);
+    part[blockIdx.x] = v;
+  }
+}
+
+__global__ void k_scale(int n, double* x, double s) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] *= s;
+}
+
+// x += c * d (interleaved, FP64), used by the outer refinement loop; only the
+// right-hand sides flagged in mask are updated.
+__global__ void k_axpy_masked(long long m, int nrhs, unsigned mask, const double* d, double c,
+                              double* x) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < m && ((mask >> (e % nrhs)) & 1u)) x[e] += c * d[e];
+}
+
+}  // namespace aj

@@ -1,0 +1,77 @@
+"""Full-size checks on the 3-D 7-point Poisson system on a 256^3 grid
+(n = 16,777,216, nnz = 117,047,296), in the launch configuration the
+benchmark times.  The oracle cannot run thousands of iterations at this size,
+so the GPU's iterate x^{T+1} is checked against one oracle step taken from
+the GPU's own x^T, x^{T-1} and beta_T (read from the solver state), and every
+solve's residual is recomputed with the oracle's FP64 SpMV.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2407_03272_gb300 import aj  # noqa: E402
+
+_W = {}
+
+
+def workload():
+    if "w" not in _W:
+        _W["w"] = synth.workload("poisson3d_256")
+    return _W["w"]
+
+
+def _state_parts(blob, n):
+    # header: magic, n, nrhs, pol, state_bytes, pad, sb[4]; then RhsState; then 3 buffers
+    hdr = np.frombuffer(blob[:64], dtype=np.uint8)
+    nrhs = int(np.frombuffer(blob[16:20], np.int32)[0])
+    sbytes = int(np.frombuffer(blob[24:28], np.int32)[0])
+    assert nrhs == 1 and sbytes == 112 and len(hdr) == 64
+    st = blob[64:64 + sbytes]
+    beta = float(np.frombuffer(st[8:16], np.float64)[0])
+    t = int(np.frombuffer(st[48:56], np.int64)[0])
+    cur, prev = (int(v) for v in np.frombuffer(st[88:96], np.int32))
+    off = 64 + sbytes
+    bufs = [np.frombuffer(blob[off + k * 8 * n: off + (k + 1) * 8 * n], np.float64) for k in range(3)]
+    return t, beta, bufs[cur], bufs[prev]
+
+
+def test_fullsize_step_matches_oracle_step():
+    Q, b, xs = workload()
+    n = Q["n"]
+    T = 40
+    ctx = aj.from_csr(Q, b, device="cuda")
+    ctx.set(stop=aj.AJ_STOP_NONE, maxit=T)
+    ctx.solve(out=torch.empty(n, dtype=torch.float64, device="cuda"))
+    t, beta, xT, xTm1 = _state_parts(ctx.get_state(), n)
+    assert t == T
+    ctx2 = aj.from_csr(Q, b, device="cuda")
+    ctx2.set(stop=aj.AJ_STOP_NONE, maxit=T + 1)
+    ctx2.set_state(ctx.get_state())
+    x_next, info = ctx2.solve()
+    assert info["iters"] == T + 1
+    y = xT + beta * (xT - xTm1)
+    if (T + 1) in ctx2.restart_log():
+        ref = xT  # a restart at T+1 keeps x^{T+1} = x^T
+    else:
+        ref = oracle.solve(Q, b, oracle.j_absrowsum(Q), restart=False, maxit=1,
+                           stop=oracle.STOP_NONE, x0=y)["x"]
+    err = np.linalg.norm(x_next - ref) / np.linalg.norm(ref)
+    assert err <= 1e-12, err
+
+
+@pytest.mark.parametrize("precision", ["df64", "fp32_ir", "fp64"])
+def test_fullsize_solve_reaches_1e8(precision):
+    Q, b, xs = workload()
+    ctx = aj.from_csr(Q, b, device="cuda")
+    ctx.set(precision=precision, tol=1e-8, maxit=30000)
+    x, info = ctx.solve()
+    assert info["status"] == aj.AJ_OK, info
+    r = b - oracle.spmv(Q, x)
+    rr = np.linalg.norm(r) / np.linalg.norm(b)
+    assert rr <= 1e-8
+    assert abs(rr - info["relres"]) <= 1e-3 * rr

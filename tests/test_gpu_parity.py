@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: after a fixed number of iterations the iterates agree to relative
+||x_gpu - x_oracle|| <= 1e-10 (FP64 and the double-float policy); every solve
+to tolerance reaches an FP64-verified relative residual <= tol.  If a restart
+decision differs between the two (the test quantity <Q y - b, x^t - x^{t-1}>
+is summed in different orders), the oracle is replayed with the GPU's restart
+schedule and must then agree to the same tolerance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dense
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2407_03272_gb300 import aj  # noqa: E402
+
+REL = 1e-10
+
+
+def _relres(Q, b, x):
+    r = b - oracle.spmv(Q, x)
+    bn = np.linalg.norm(b)
+    return np.linalg.norm(r) / bn if bn > 0 else np.linalg.norm(r)
+
+
+def _gpu(Q, b, nrhs=1, device=None, **kw):
+    ctx = aj.from_csr(Q, b, nrhs=nrhs, device=device)
+    ctx.set(**kw)
+    x, info = ctx.solve()
+    return ctx, x, info
+
+
+def _oracle_J(Q, j_policy, L=None):
+    if j_policy == aj.AJ_J_ABSROWSUM:
+        return oracle.j_absrowsum(Q)
+    return oracle.j_scaled_diag(Q, L)
+
+
+def _compare_fixed(Q, b, T, precision="fp64", restart=True, momentum=True, j_policy=0, L=0.0,
+                   x0=None, tol_rel=REL):
+    ctx, x, info = _gpu(Q, b, precision=precision, stop=aj.AJ_STOP_NONE, maxit=T,
+                        restart=int(restart), momentum=int(momentum), j_policy=j_policy, L=L,
+                        x0=x0)
+    assert info["iters"] == T and info["status"] == aj.AJ_EMAXIT
+    J = _oracle_J(Q, j_policy, L if L else info["L_used"])
+    ref = oracle.solve(Q, b, J, restart=restart, momentum=momentum, maxit=T,
+                       stop=oracle.STOP_NONE, x0=x0)
+    sched = ctx.restart_log()
+    if info["restarts"] != ref["restarts"] or np.linalg.norm(x - ref["x"]) > tol_rel * np.linalg.norm(ref["x"]):
+        # replay the GPU's restart decisions in the oracle
+        ref = oracle.solve(Q, b, J, restart=restart, momentum=momentum, maxit=T,
+                           stop=oracle.STOP_NONE, x0=x0, forced=sched)
+    err = np.linalg.norm(x - ref["x"]) / max(np.linalg.norm(ref["x"]), 1e-300)
+    assert err <= tol_rel, (err, sched)
+    return ctx, x, info, ref
+
+
+# ---------------------------------------------------------------- fixed-iteration parity
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_poisson64_200_iterations_match_oracle(precision):
+    Q, b, xs = synth.workload("poisson2d_64")
+    _compare_fixed(Q, b, 200, precision=precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_no_restart_and_jacobi_modes_match_oracle(precision):
+    Q, b, xs = synth.workload("poisson2d_24")
+    _compare_fixed(Q, b, 150, precision=precision, restart=False)
+    # beta = 0 with J = D: classical Jacobi (eq. jacobi) on a diagonally dominant SPD system
+    _compare_fixed(Q, b, 60, precision=precision, restart=False, momentum=False,
+                   j_policy=aj.AJ_J_SCALED_DIAG, L=1.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_ragged_tail_and_long_rows(precision):
+    # n = 300 rows of length 300 (> 32: the warp-cooperative path), n not a multiple of 256
+    Q = synth.sdd(300)
+    b = np.ones(300)
+    _compare_fixed(Q, b, 80, precision=precision)
+    # a 3-D grid with a ragged last tile and boundary rows of every length
+    Q, b, xs = synth.workload("poisson3d_13")
+    assert Q["n"] % 256 != 0
+    _compare_fixed(Q, b, 120, precision=precision)
+
+
+def test_singular_laplacian_with_empty_rows():
+    n = 2000
+    Q = synth.chung_lu_laplacian(n, seed=11, mean_degree=4.0)
+    assert (np.diff(Q["row_ptr"]) == 0).any()
+    xs = synth.uniform(n, 12)
+    b = synth.rhs(Q, xs)
+    ctx, x, info, ref = _compare_fixed(Q, b, 150)
+    empty = np.diff(Q["row_ptr"]) == 0
+    assert np.all(x[empty] == 0.0)
+
+
+def test_scaled_diag_given_L_and_estimated_L():
+    N = 40
+    Q, b, xs = synth.workload("poisson2d_%d" % N)
+    Lt = 1.0 + math.cos(math.pi / (N + 1))
+    _compare_fixed(Q, b, 100, j_policy=aj.AJ_J_SCALED_DIAG, L=Lt)
+    ctx, x, info = _gpu(Q, b, j_policy=aj.AJ_J_SCALED_DIAG, L=0.0, maxit=5000)
+    # power iteration with a 2 % margin, capped by the Gershgorin bound 2
+    assert Lt * (1 - 1e-6) <= info["L_used"] <= min(2.0, Lt * 1.03)
+    assert info["status"] == aj.AJ_OK and info["relres"] <= 1e-8
+
+
+def test_x0_and_device_pointers():
+    Q, b, xs = synth.workload("poisson2d_32")
+    x0 = synth.uniform(Q["n"], 5)
+    _compare_fixed(Q, b, 90, x0=x0)
+    ctx = aj.from_csr(Q, b, device="cuda")
+    x0d = torch.from_numpy(x0).cuda()
+    ctx.set(stop=aj.AJ_STOP_NONE, maxit=90, x0=x0d)
+    out = torch.empty(Q["n"], dtype=torch.float64, device="cuda")
+    _, info = ctx.solve(out=out)
+    ref = oracle.solve(Q, b, oracle.j_absrowsum(Q), maxit=90, stop=oracle.STOP_NONE, x0=x0,
+                       forced=ctx.restart_log())
+    xg = out.cpu().numpy()
+    assert np.linalg.norm(xg - ref["x"]) <= REL * np.linalg.norm(ref["x"])
+
+
+# ---------------------------------------------------------------- solves to tolerance
+@pytest.mark.parametrize("precision", ["fp64", "df64", "fp32_ir", "bf16_ir"])
+def test_poisson64_solve_to_1e8(precision):
+    Q, b, xs = synth.workload("poisson2d_64")
+    ctx, x, info = _gpu(Q, b, precision=precision, tol=1e-8, maxit=20000)
+    assert info["status"] == aj.AJ_OK
+    rr = _relres(Q, b, x)
+    assert rr <= 1e-8 and abs(rr - info["relres"]) <= 1e-3 * rr + 1e-15
+    ref = oracle.solve(Q, b, oracle.j_absrowsum(Q), tol=1e-8, maxit=20000)
+    if precision in ("fp64", "df64"):
+        # same stop rule on the same iterates: same iteration count up to a flipped decision
+        assert abs(info["iters"] - ref["iters"]) <= max(3, 0.02 * ref["iters"])
+    # error against the oracle's converged solution in the Q-norm
+    A = dense.to_dense(Q)
+    e = x - ref["x"]
+    assert math.sqrt(e @ (A @ e)) <= 1e-6 * math.sqrt(ref["x"] @ (A @ ref["x"]))
+
+
+def test_objective_gap_stop_matches_oracle():
+    n = 400
+    Q = synth.sdd(n)
+    b = np.ones(n)
+    fstar = -n / 2.0
+    ctx, x, info = _gpu(Q, b, stop=aj.AJ_STOP_OBJGAP, tol=1e-10, fstar=fstar, maxit=5000)
+    ref = oracle.solve(Q, b, oracle.j_absrowsum(Q), stop=oracle.STOP_OBJGAP, tol=1e-10,
+                       fstar=fstar, maxit=5000)
+    assert info["status"] == aj.AJ_OK and ref["converged"]
+    assert abs(info["iters"] - ref["iters"]) <= 2
+    assert info["objgap"] <= 1e-10
+    np.testing.assert_allclose(x, np.ones(n), atol=1e-4)
+
+
+def test_zero_rhs_and_tiny_systems():
+    Q = synth.poisson2d(8)
+    ctx, x, info = _gpu(Q, np.zeros(64))
+    assert info["iters"] == 0 and info["status"] == aj.AJ_OK and np.all(x == 0)
+    # n = 1
+    Q1 = {"n": 1, "row_ptr": np.array([0, 1], np.int32), "col": np.array([0], np.int32),
+          "val": np.array([3.0])}
+    ctx, x, info = _gpu(Q1, np.array([6.0]))
+    assert info["status"] == aj.AJ_OK and abs(x[0] - 2.0) <= 1e-12
+
+
+# ---------------------------------------------------------------- several right-hand sides
+@pytest.mark.parametrize("nrhs", [2, 3, 4])
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_multi_rhs_equals_single(nrhs, precision):
+    Q = synth.poisson2d(30)
+    n = Q["n"]
+    B = np.stack([synth.rhs(Q, synth.uniform(n, 20 + r)) for r in range(nrhs)], axis=1)
+    bc = np.ascontiguousarray(B.T).reshape(-1)  # column-major n x nrhs
+    ctx = aj.from_csr(Q, bc, nrhs=nrhs)
+    # the same grid for both runs, so the FP64 reductions are summed in the same order
+    ctx.set(precision=precision, tol=1e-9, maxit=10000, grid_ctas=8)
+    X, infos = ctx.solve(per_rhs=True)
+    X = X.reshape(nrhs, n)
+    for r in range(nrhs):
+        c1, x1, i1 = _gpu(Q, B[:, r], precision=precision, tol=1e-9, maxit=10000, grid_ctas=8)
+        assert infos[r]["iters"] == i1["iters"]
+        np.testing.assert_array_equal(X[r], x1)
+        assert _relres(Q, B[:, r], X[r]) <= 1e-9
+
+
+# ---------------------------------------------------------------- checkpoint / resume
+def test_resume_is_bit_identical():
+    Q, b, xs = synth.workload("poisson2d_48")
+    full = aj.from_csr(Q, b)
+    full.set(stop=aj.AJ_STOP_NONE, maxit=400)
+    xf, inf_f = full.solve()
+    part = aj.from_csr(Q, b)
+    part.set(stop=aj.AJ_STOP_NONE, maxit=170)
+    part.solve()
+    blob = part.get_state()
+    other = aj.from_csr(Q, b)
+    other.set(stop=aj.AJ_STOP_NONE, maxit=400)
+    other.set_state(blob)
+    xr, inf_r = other.solve()
+    np.testing.assert_array_equal(xr, xf)
+    assert inf_r["restarts"] == inf_f["restarts"]
+
+
+# ---------------------------------------------------------------- invalid input
+def test_invalid_matrices_rejected():
+    good = synth.poisson2d(6)
+    bad = dict(good, row_ptr=good["row_ptr"].copy())
+    bad["row_ptr"][3] = bad["row_ptr"][2] - 1
+    with pytest.raises(aj.AJError) as e:
+        aj.from_csr(bad, np.ones(36))
+    assert e.value.status == aj.AJ_EINVAL
+    bad = dict(good, col=good["col"].copy())
+    bad["col"][5] = 36
+    with pytest.raises(aj.AJError):
+        aj.from_csr(bad, np.ones(36))
+    bad = dict(good, val=good["val"].copy())
+    bad["val"][0] = -4.0
+    with pytest.raises(aj.AJError):
+        aj.from_csr(bad, np.ones(36))
+    ctx = aj.from_csr(good, np.ones(36))
+    with pytest.raises(aj.AJError):
+        ctx.set(K0=1)
