@@ -190,6 +190,47 @@ aj_status aj_restart_log(aj_ctx* ctx, int rhs, int64_t* iters, int64_t cap, int6
 void aj_destroy(aj_ctx* ctx);
 const char* aj_strerror(aj_status s);
 
+/* ---- Allocation-free solve.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory, for instance
+ *   - a latency-critical service whose other streams would stall on the
+ *     implicit device synchronisation of cudaMalloc / cudaFree;
+ *   - a process whose device memory is reserved up front by a framework's
+ *     caching allocator, where a foreign cudaMalloc can fail at run time;
+ *   - deployments that fix every device buffer when the library loads.
+ * It runs the same FP64 fused solve as aj_create + aj_set + aj_solve for ONE
+ * right-hand side (same J, restart rule, stop test and kernel), but takes all
+ * of its scratch -- J^{-1}, the three iterate buffers, the per-CTA partial
+ * sums, the grid-barrier counter, the error word and the solver state -- from
+ * one fixed device array inside libaj of about 4.1 MB, sized for
+ * n <= AJ_NOALLOC_MAX_N.  Every GPU that loads libaj holds that array until
+ * the process exits.  The call allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ *   Q       CSR on the current device (Q->on_device must be 1); read only.
+ *   b       n device doubles; read only.
+ *   p       parameters as for aj_set; precision must be AJ_FP64, and
+ *           AJ_J_SCALED_DIAG needs p->L > 0 (no power-iteration estimate);
+ *           p->x0, if given, must be a device pointer (x0_on_device = 1).
+ *   x_out   n device doubles; receives the returned iterate x^t.
+ *   info    may be NULL; iters, restarts, sweeps, relres (FP64 residual of
+ *           x^t from the fused sweep), objgap (AJ_STOP_OBJGAP only, else 0),
+ *           status; ms and kernel_ms are the host wall time of the call.
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream).
+ * Returns as aj_solve; AJ_ENOMEM when n > AJ_NOALLOC_MAX_N (the problem does
+ * not fit the fixed array), AJ_EINVAL for a bad argument or matrix.  The call
+ * returns after its GPU work has finished.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and the kernel's
+ * occupancy; make that first call before any stream capture begins.  Every
+ * call on a device shares the one array, and it keeps the last call's
+ * contents (each call re-initialises what must start at zero): calls whose
+ * GPU work overlaps -- from two host threads, or on two streams -- race on
+ * it and must be serialised by the caller. */
+#define AJ_NOALLOC_MAX_N 131072
+aj_status aj_solve_noalloc(const aj_csr* Q, const double* b, const aj_params* p, double* x_out,
+                           aj_info* info, void* cuda_stream);
+
 /* Diagnostics: number of CUDA kernels libaj has launched in this process. */
 uint64_t aj_kernel_launches(void);
 

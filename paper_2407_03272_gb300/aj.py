@@ -20,6 +20,7 @@ AJ_RESTART_NONE, AJ_RESTART_ADAPTIVE = 0, 1
 AJ_STOP_RELRES, AJ_STOP_OBJGAP, AJ_STOP_NONE = 0, 1, 2
 AJ_FP64, AJ_DF64, AJ_FP32_IR, AJ_BF16_IR = 0, 1, 2, 3
 AJ_FMT_AUTO, AJ_FMT_CSR, AJ_FMT_SELL = 0, 1, 2
+AJ_NOALLOC_MAX_N = 131072
 
 PRECISIONS = {"fp64": AJ_FP64, "df64": AJ_DF64, "fp32_ir": AJ_FP32_IR, "bf16_ir": AJ_BF16_IR}
 
@@ -82,6 +83,8 @@ SIGNATURES = [
     ("aj_destroy", None, [ctypes.c_void_p]),
     ("aj_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("aj_kernel_launches", ctypes.c_uint64, []),
+    ("aj_solve_noalloc", ctypes.c_int, [ctypes.POINTER(aj_csr), ctypes.c_void_p, ctypes.POINTER(aj_params),
+                                        ctypes.c_void_p, ctypes.POINTER(aj_info), ctypes.c_void_p]),
 ]
 
 
@@ -244,3 +247,22 @@ def solve_batch(ctxs, outs, on_device=False):
     if st not in (AJ_OK, AJ_EMAXIT, AJ_EDIVERGED, AJ_ENONFINITE):
         raise AJError(st, "aj_solve_batch")
     return [i.as_dict() for i in infos]
+
+
+def solve_noalloc(row_ptr, col, val, b, x_out, stream=None, **kw):
+    """aj_solve_noalloc on device tensors: the FP64 solve for one right-hand
+    side with the library's fixed scratch array (no device allocation inside
+    the call).  Returns (status, info dict)."""
+    ptrs = [_ptr(a) for a in (row_ptr, col, val, b, x_out)]
+    if not all(dev for _, dev in ptrs):
+        raise ValueError("aj_solve_noalloc takes device arrays only")
+    p = params(**kw)
+    x0 = kw.get("x0")
+    if x0 is not None:
+        p.x0, p.x0_on_device = _ptr(x0)
+    csr = aj_csr(int(len(row_ptr) - 1), int(len(col)), ptrs[0][0], ptrs[1][0], ptrs[2][0], 1)
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    inf = aj_info()
+    st = lib().aj_solve_noalloc(ctypes.byref(csr), ptrs[3][0], ctypes.byref(p), ptrs[4][0],
+                                ctypes.byref(inf), ctypes.c_void_p(s))
+    return st, inf.as_dict()
