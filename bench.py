@@ -35,24 +35,29 @@ UNIT = "GB/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 # FP64 issue rate of GB300 derived from its nominal 1.25 TFLOP/s FP64 (2 flops per FMA):
-# 152 SMs x 2 DFMA/clk x 2.07 GHz = 0.629 T DFMA/s = 1.26 TFLOP/s.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# 152 SMs x 2 FP64 instructions/clk x 2.07 GHz = 0.629 T FP64 instructions/s.
+FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
 
 
-def algorithmic_bytes(n, nnz, precision):
+def algorithmic_bytes(n, nnz, precision, form="stored"):
     """Bytes one fused iteration must move: the matrix once (values + int32
-    column indices), row pointers, and five n-vectors (read x^t, x^{t-1}, b,
-    J^{-1}; write x^{t+1})."""
+    column indices), row pointers, and the n-vectors of the sweep form.
+    lazy: read x^t, x^{t-1} (both gathered, each counted once), b, J^{-1};
+    write x^{t+1} (5 vectors).  stored: the same plus read u^{t-1} = Q x^{t-1}
+    and write u^t = Q x^t (7 vectors)."""
     vb = {"fp64": 8, "df64": 8, "fp32_ir": 4, "bf16_ir": 2}[precision]
     sb = {"fp64": 8, "df64": 8, "fp32_ir": 4, "bf16_ir": 4}[precision]
-    return nnz * (vb + 4) + 4 * (n + 1) + n * 5 * sb
+    kvec = 7 if form == "stored" else 5
+    return nnz * (vb + 4) + 4 * (n + 1) + n * kvec * sb
 
 
-def fp64_flops(n, nnz):
-    """FP64 flops of one FP64 fused iteration (FMA = 2): two FMA per stored
-    entry (sums at x^t and x^{t-1}) and 17 per row (extrapolation, update,
-    reductions)."""
-    return 4 * nnz + 17 * n
+def fp64_ops(n, nnz, form="stored"):
+    """FP64 instructions of one FP64 fused iteration (an FMA counts once):
+    stored form, one FMA per stored entry and 9 per row (g0, rr, two
+    differences, g, y, x update, x difference, d); lazy form, two FMA per
+    stored entry and 11 per row (qy, y, g, x update, differences, d, rr,
+    ||g||^2)."""
+    return (nnz + 9 * n) if form == "stored" else (2 * nnz + 11 * n)
 
 
 def load_peaks():
@@ -174,6 +179,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32_ir", "bf16_ir"])
+    ap.add_argument("--form", default="auto", choices=["auto", "lazy", "stored"],
+                    help="sweep form; auto = stored for fp64, lazy otherwise")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -207,13 +214,21 @@ def main():
                for a in (Q["row_ptr"], Q["col"], Q["val"], b)]
     stream = torch.cuda.current_stream()
 
-    def make(precision):
+    def form_of(precision, form):
+        if form == "auto":
+            return "stored" if precision == "fp64" else "lazy"
+        return form
+
+    SWEEP = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED}
+
+    def make(precision, form):
         ctx = aj.Context(*tensors, n=n)
         ctx.set_stream(stream)
         if args.fixed_iters:
-            ctx.set(precision=precision, stop=aj.AJ_STOP_NONE, maxit=args.fixed_iters)
+            ctx.set(precision=precision, stop=aj.AJ_STOP_NONE, maxit=args.fixed_iters,
+                    sweep_form=SWEEP[form])
         else:
-            ctx.set(precision=precision, tol=1e-8, maxit=200000)
+            ctx.set(precision=precision, tol=1e-8, maxit=200000, sweep_form=SWEEP[form])
         return ctx
 
     def barrier():
@@ -241,14 +256,15 @@ def main():
         return ms, infos, L.aj_kernel_launches() - l0
 
     # ---- headline: the chosen precision, K timed solves
-    ctx = make(args.precision)
+    form = form_of(args.precision, args.form)
+    ctx = make(args.precision, form)
     with Clocks(dev.index) as clk:
         ms, infos, launches = time_solves(ctx, args.steps, args.warmup)
     ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
     if dist is not None:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
     ms = float(ms_t.item())
-    B = algorithmic_bytes(n, nnz, args.precision)
+    B = algorithmic_bytes(n, nnz, args.precision, form)
     iters = sum(i["iters"] for i in infos)
     value = B * iters * ws / (ms * 1e-3) / 1e9
     kernel_ms = sum(i["kernel_ms"] for i in infos)
@@ -256,17 +272,20 @@ def main():
     hbm_peak, peak_kind = load_peaks()
     kern_gbs = B * iters / (kernel_ms * 1e-3) / 1e9
     if args.precision == "fp64":
-        achieved_tf = fp64_flops(n, nnz) * iters / (kernel_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s FP64)",
+        achieved_t = fp64_ops(n, nnz, form) * iters / (kernel_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved_t, "peak": FP64_PEAK_TOPS,
+                "unit": "T FP64 instructions/s",
+                "frac": achieved_t / FP64_PEAK_TOPS, "traffic": None,
+                "peak_kind": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz "
+                             "(nominal 1.25 TFLOP/s FP64 with FMA = 2 flops)",
                 "hbm": {"achieved": kern_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": kern_gbs / hbm_peak, "peak_kind": peak_kind}}
     else:
         roof = {"bound": "hbm", "achieved": kern_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": kern_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind + " (burst copy)"}
-    roof["kernel"] = "aj_persistent_kernel<%s>" % {"fp64": "PolF64", "df64": "PolDF64",
-                                                  "fp32_ir": "PolF32", "bf16_ir": "PolB16"}[args.precision]
+    roof["kernel"] = "aj_persistent_kernel<%s, 1, %s>" % (
+        {"fp64": "PolF64", "df64": "PolDF64", "fp32_ir": "PolF32", "bf16_ir": "PolB16"}[args.precision],
+        "true" if form == "stored" else "false")
     roof["bytes_per_iteration"] = B
     roof["kernel_ms_per_iteration"] = kernel_ms / max(iters, 1)
     line = {
@@ -282,7 +301,8 @@ def main():
                    "%s (n=%d, nnz=%d), %s" % (args.workload, n, nnz,
                                               "%d fixed iterations" % args.fixed_iters
                                               if args.fixed_iters else "solve to 1e-8"),
-                   "precision": args.precision, "parallelism": "replicas x%d" % ws,
+                   "precision": args.precision, "sweep_form": form,
+                   "parallelism": "replicas x%d" % ws,
                    "l2": "inputs larger than L2 (%.2f GB per sweep)" % (B / 1e9)},
         "time_to_tol_ms": ms / args.steps,
         "iterations": infos[-1]["iters"], "restarts": infos[-1]["restarts"],
@@ -296,17 +316,19 @@ def main():
     if not args.no_variants:
         var = {}
         for p in ("fp64", "df64", "fp32_ir", "bf16_ir"):
-            c = make(p)
-            vms, vinf, _ = time_solves(c, 2, 1)
-            vb = algorithmic_bytes(n, nnz, p)
-            it = sum(i["iters"] for i in vinf)
-            kms = sum(i["kernel_ms"] for i in vinf)
-            var[p] = {"time_to_tol_ms": vms / 2, "iterations": vinf[-1]["iters"],
-                      "outer": vinf[-1]["outer"], "relres": vinf[-1]["relres"],
-                      "fused_GBps": vb * it / (kms * 1e-3) / 1e9,
-                      "fused_hbm_frac": vb * it / (kms * 1e-3) / 1e9 / hbm_peak,
-                      "kernel_ms_per_iteration": kms / max(it, 1)}
-            del c
+            for fm in ("stored", "lazy"):
+                c = make(p, fm)
+                vms, vinf, _ = time_solves(c, 2, 1)
+                vb = algorithmic_bytes(n, nnz, p, fm)
+                it = sum(i["iters"] for i in vinf)
+                kms = sum(i["kernel_ms"] for i in vinf)
+                var[p + "/" + fm] = {
+                    "time_to_tol_ms": vms / 2, "iterations": vinf[-1]["iters"],
+                    "outer": vinf[-1]["outer"], "relres": vinf[-1]["relres"],
+                    "fused_GBps": vb * it / (kms * 1e-3) / 1e9,
+                    "fused_hbm_frac": vb * it / (kms * 1e-3) / 1e9 / hbm_peak,
+                    "kernel_ms_per_iteration": kms / max(it, 1)}
+                del c
         line["variants"] = var
     # ---- end to end through the C ABI with pinned host buffers
     if not args.no_e2e:
@@ -321,7 +343,7 @@ def main():
             t0 = time.perf_counter()
             c = aj.Context(*host, n=n)
             c.set_stream(stream)
-            c.set(precision=args.precision, tol=1e-8, maxit=200000)
+            c.set(precision=args.precision, tol=1e-8, maxit=200000, sweep_form=SWEEP[form])
             _, inf = c.solve(out=xh)
             c.close()
             barrier()
@@ -335,7 +357,7 @@ def main():
     if not args.no_cpu and ws == 1 and rank == 0:
         T = args.cpu_iters
         t = cpu_oracle_sample(Q, b, T)
-        cpu_v = algorithmic_bytes(n, nnz, "fp64") * T / t / 1e9
+        cpu_v = B * T / t / 1e9
         line["cpu_baseline"] = {
             "value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d iterations of the FP64 C oracle (one thread) on the same system; "

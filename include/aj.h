@@ -91,6 +91,16 @@ typedef struct {
 #define AJ_FP32_IR 2 /* FP32 values and vectors inside, FP64 residual refinement outside */
 #define AJ_BF16_IR 3 /* BF16 values x FP32 arithmetic inside, FP64 refinement outside */
 
+/* How one fused sweep obtains Q y^t = Q x^{t-1} + beta (Q x^{t-1} - Q x^{t-2}).
+ * Both give the same iterates up to rounding.  LAZY sums both products over
+ * the gathered x^{t-1} and x^{t-2} (two multiply-adds per stored entry, fewer
+ * bytes); STORED keeps u = Q x per row and re-reads u^{t-2} (one multiply-add
+ * per stored entry, two more n-vectors of traffic).  AUTO picks STORED for
+ * AJ_FP64, whose FP64 issue rate binds on GB300, and LAZY otherwise. */
+#define AJ_SWEEP_AUTO 0
+#define AJ_SWEEP_LAZY 1
+#define AJ_SWEEP_STORED 2
+
 #define AJ_FMT_AUTO 0
 #define AJ_FMT_CSR 1
 #define AJ_FMT_SELL 2
@@ -113,6 +123,7 @@ typedef struct {
   double inner_tol;      /* IR modes: relative tolerance of each inner solve (default 1e-4) */
   int64_t max_outer;     /* IR modes: outer refinement steps (default 30) */
   int grid_ctas;         /* 0 = automatic; otherwise the number of persistent CTAs */
+  int sweep_form;        /* AJ_SWEEP_AUTO (default) | AJ_SWEEP_LAZY | AJ_SWEEP_STORED */
 } aj_params;
 
 /* Per-solve report. */
@@ -199,16 +210,18 @@ const char* aj_strerror(aj_status s);
  *   - deployments that fix every device buffer when the library loads.
  * It runs the same FP64 fused solve as aj_create + aj_set + aj_solve for ONE
  * right-hand side (same J, restart rule, stop test and kernel), but takes all
- * of its scratch -- J^{-1}, the three iterate buffers, the per-CTA partial
- * sums, the grid-barrier counter, the error word and the solver state -- from
- * one fixed device array inside libaj of about 4.1 MB, sized for
+ * of its scratch -- J^{-1}, the three iterate buffers, the two Q x buffers of
+ * the stored sweep form, the per-CTA partial sums, the grid-barrier counter,
+ * the error word and the solver state -- from one fixed device array inside
+ * libaj of about 6.1 MB, sized for
  * n <= AJ_NOALLOC_MAX_N.  Every GPU that loads libaj holds that array until
  * the process exits.  The call allocates nothing: no cudaMalloc, cudaFree or
  * allocating library routine.
  *
  *   Q       CSR on the current device (Q->on_device must be 1); read only.
  *   b       n device doubles; read only.
- *   p       parameters as for aj_set; precision must be AJ_FP64, and
+ *   p       parameters as for aj_set; precision must be AJ_FP64 (the sweep
+ *           form is always AJ_SWEEP_STORED, what AUTO picks for FP64), and
  *           AJ_J_SCALED_DIAG needs p->L > 0 (no power-iteration estimate);
  *           p->x0, if given, must be a device pointer (x0_on_device = 1).
  *   x_out   n device doubles; receives the returned iterate x^t.

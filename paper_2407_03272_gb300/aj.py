@@ -20,6 +20,7 @@ AJ_RESTART_NONE, AJ_RESTART_ADAPTIVE = 0, 1
 AJ_STOP_RELRES, AJ_STOP_OBJGAP, AJ_STOP_NONE = 0, 1, 2
 AJ_FP64, AJ_DF64, AJ_FP32_IR, AJ_BF16_IR = 0, 1, 2, 3
 AJ_FMT_AUTO, AJ_FMT_CSR, AJ_FMT_SELL = 0, 1, 2
+AJ_SWEEP_AUTO, AJ_SWEEP_LAZY, AJ_SWEEP_STORED = 0, 1, 2
 AJ_NOALLOC_MAX_N = 131072
 
 PRECISIONS = {"fp64": AJ_FP64, "df64": AJ_DF64, "fp32_ir": AJ_FP32_IR, "bf16_ir": AJ_BF16_IR}
@@ -37,7 +38,7 @@ class aj_params(ctypes.Structure):
                 ("maxit", ctypes.c_int64), ("precision", ctypes.c_int), ("format", ctypes.c_int),
                 ("x0", ctypes.c_void_p), ("x0_on_device", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int64),
-                ("grid_ctas", ctypes.c_int)]
+                ("grid_ctas", ctypes.c_int), ("sweep_form", ctypes.c_int)]
 
 
 class aj_info(ctypes.Structure):

@@ -93,12 +93,12 @@ cudaError_t launch_persistent(int pol, int nrhs, const IterLaunch& L, int grid, 
   }
   return cudaErrorInvalidValue;
 }
-int persistent_blocks_per_sm(int pol, int nrhs) {
+int persistent_blocks_per_sm(int pol, int nrhs, int qx) {
   switch (pol) {
-    case 0: return blocks_per_sm_f64(nrhs);
-    case 1: return blocks_per_sm_df64(nrhs);
-    case 2: return blocks_per_sm_f32(nrhs);
-    case 3: return blocks_per_sm_b16(nrhs);
+    case 0: return blocks_per_sm_f64(nrhs, qx);
+    case 1: return blocks_per_sm_df64(nrhs, qx);
+    case 2: return blocks_per_sm_f32(nrhs, qx);
+    case 3: return blocks_per_sm_b16(nrhs, qx);
   }
   return 0;
 }
@@ -126,6 +126,8 @@ struct aj_ctx {
   void* bp = nullptr;
   void* jinvp = nullptr;
   void* x[3] = {nullptr, nullptr, nullptr};
+  void* u[2] = {nullptr, nullptr};  // Q x^t, Q x^{t-1} (stored sweep form)
+  int qx = 0;                       // sweep form in use: 1 stored, 0 lazy
   double sQ = 1.0;
   double sb[kMaxRhs] = {1, 1, 1, 1};
   double L_used = 0.0;
@@ -179,6 +181,7 @@ extern "C" void aj_params_default(aj_params* p) {
   p->inner_tol = 1e-4;
   p->max_outer = 30;
   p->grid_ctas = 0;
+  p->sweep_form = AJ_SWEEP_AUTO;
 }
 
 extern "C" const char* aj_strerror(aj_status s) {
@@ -387,6 +390,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   if (p->precision < AJ_FP64 || p->precision > AJ_BF16_IR) return AJ_EINVAL;
   if (p->format < AJ_FMT_AUTO || p->format > AJ_FMT_SELL) return AJ_EINVAL;
   if (p->grid_ctas < 0) return AJ_EINVAL;
+  if (p->sweep_form < AJ_SWEEP_AUTO || p->sweep_form > AJ_SWEEP_STORED) return AJ_EINVAL;
   if ((p->precision == AJ_FP32_IR || p->precision == AJ_BF16_IR) &&
       (!(p->inner_tol > 0.0) || p->max_outer < 1))
     return AJ_EINVAL;
@@ -421,6 +425,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     c->pws.release();
     c->valp = c->bp = c->jinvp = nullptr;
     c->x[0] = c->x[1] = c->x[2] = nullptr;
+    c->u[0] = c->u[1] = nullptr;
     c->partials = nullptr;
     c->bar = nullptr;
     c->state = nullptr;
@@ -437,11 +442,16 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
       c->x[k] = c->pws.alloc((size_t)(m + 1) * xe);
       if (!c->x[k]) return AJ_ENOMEM;
     }
+    for (int k = 0; k < 2; k++) {
+      c->u[k] = c->pws.alloc((size_t)(m + 1) * xe);
+      if (!c->u[k]) return AJ_ENOMEM;
+    }
     c->x64 = (double*)c->pws.alloc((size_t)(m + 1) * 8);
     c->r64 = (double*)c->pws.alloc((size_t)(m + 1) * 8);
     if (!c->x64 || !c->r64) return AJ_ENOMEM;
     const int kp = kernel_pol(pol);
-    const int bps = std::max(1, persistent_blocks_per_sm(kp, nrhs));
+    const int bps = std::max({1, persistent_blocks_per_sm(kp, nrhs, 0),
+                              persistent_blocks_per_sm(kp, nrhs, 1)});
     const int maxg = bps * c->sm_count;
     c->partials = (double*)c->pws.alloc((size_t)2 * maxg * nrhs * kNRed * 8);
     c->bar = (unsigned long long*)c->pws.alloc(64);
@@ -450,10 +460,13 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     if (!c->partials || !c->bar || !c->state || !c->rlog) return AJ_ENOMEM;
     c->pol = pol;
   }
-  // --- grid: a multiple of the SM count when the problem is large enough
+  // --- sweep form and grid: a multiple of the SM count when the problem is large enough
+  c->qx = p->sweep_form == AJ_SWEEP_STORED ? 1
+        : p->sweep_form == AJ_SWEEP_LAZY   ? 0
+                                           : (pol == AJ_FP64 ? 1 : 0);
   {
     const int kp = kernel_pol(pol);
-    const int bps = std::max(1, persistent_blocks_per_sm(kp, nrhs));
+    const int bps = std::max(1, persistent_blocks_per_sm(kp, nrhs, c->qx));
     const int maxg = bps * c->sm_count;
     const int ntiles = std::max(1, (int)((n + kThreads - 1) / kThreads));
     int g = std::min(maxg, ntiles);
@@ -593,6 +606,8 @@ static aj_status run_persistent(aj_ctx* c, std::vector<RhsState>& st, const void
   L.b = bvec;
   L.jinv = c->pol == AJ_FP64 ? (const void*)c->jinv64 : c->jinvp;
   for (int k = 0; k < 3; k++) L.x[k] = c->x[k];
+  for (int k = 0; k < 2; k++) L.u[k] = c->u[k];
+  L.qx = c->qx;
   L.partials = c->partials;
   L.bar = c->bar;
   L.err = c->err;
@@ -969,7 +984,7 @@ struct StateHeader {
   uint64_t magic;
   int64_t n;
   int32_t nrhs, pol;
-  int32_t state_bytes, pad;
+  int32_t state_bytes, pad;  // pad: sweep form of the saved run
   double sb[kMaxRhs];
 };
 static const uint64_t kStateMagic = 0x414a535441544531ull;  // "AJSTATE1"
@@ -979,7 +994,7 @@ extern "C" aj_status aj_get_state(aj_ctx* c, void* buf, size_t* size) {
   if (c->pol != AJ_FP64 && c->pol != AJ_DF64) return AJ_EINVAL;
   if ((int)c->st_h.size() != c->nrhs) return AJ_EINVAL;  // no finished solve yet
   const size_t vb = (size_t)c->n * c->nrhs * xelem_bytes(c->pol);
-  const size_t need = sizeof(StateHeader) + sizeof(RhsState) * c->nrhs + 3 * vb;
+  const size_t need = sizeof(StateHeader) + sizeof(RhsState) * c->nrhs + 5 * vb;
   if (!buf) { *size = need; return AJ_OK; }
   if (*size < need) { *size = need; return AJ_EINVAL; }
   char* p = (char*)buf;
@@ -990,13 +1005,15 @@ extern "C" aj_status aj_get_state(aj_ctx* c, void* buf, size_t* size) {
   h.nrhs = c->nrhs;
   h.pol = c->pol;
   h.state_bytes = (int)sizeof(RhsState);
+  h.pad = c->qx;
   for (int r = 0; r < kMaxRhs; r++) h.sb[r] = c->sb[r];
   std::memcpy(p, &h, sizeof(h));
   p += sizeof(h);
   std::memcpy(p, c->st_h.data(), sizeof(RhsState) * c->nrhs);
   p += sizeof(RhsState) * c->nrhs;
-  for (int k = 0; k < 3; k++) {
-    if (vb) CK(cudaMemcpyAsync(p, c->x[k], vb, cudaMemcpyDeviceToHost, c->stream));
+  for (int k = 0; k < 5; k++) {
+    void* src = k < 3 ? c->x[k] : c->u[k - 3];
+    if (vb) CK(cudaMemcpyAsync(p, src, vb, cudaMemcpyDeviceToHost, c->stream));
     p += vb;
   }
   CK(cudaStreamSynchronize(c->stream));
@@ -1011,16 +1028,17 @@ extern "C" aj_status aj_set_state(aj_ctx* c, const void* buf, size_t size) {
   StateHeader h;
   std::memcpy(&h, buf, sizeof(h));
   const size_t vb = (size_t)c->n * c->nrhs * xelem_bytes(c->pol);
-  const size_t need = sizeof(StateHeader) + sizeof(RhsState) * c->nrhs + 3 * vb;
+  const size_t need = sizeof(StateHeader) + sizeof(RhsState) * c->nrhs + 5 * vb;
   if (h.magic != kStateMagic || h.n != c->n || h.nrhs != c->nrhs || h.pol != c->pol ||
-      h.state_bytes != (int)sizeof(RhsState) || size < need)
+      h.state_bytes != (int)sizeof(RhsState) || h.pad != c->qx || size < need)
     return AJ_EINVAL;
   const char* p = (const char*)buf + sizeof(h);
   c->st_h.resize(c->nrhs);
   std::memcpy(c->st_h.data(), p, sizeof(RhsState) * c->nrhs);
   p += sizeof(RhsState) * c->nrhs;
-  for (int k = 0; k < 3; k++) {
-    if (vb) CK(cudaMemcpyAsync(c->x[k], p, vb, cudaMemcpyHostToDevice, c->stream));
+  for (int k = 0; k < 5; k++) {
+    void* dst = k < 3 ? c->x[k] : c->u[k - 3];
+    if (vb) CK(cudaMemcpyAsync(dst, p, vb, cudaMemcpyHostToDevice, c->stream));
     p += vb;
   }
   CK(cudaStreamSynchronize(c->stream));

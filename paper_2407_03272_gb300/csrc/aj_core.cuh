@@ -2,20 +2,25 @@
 //
 // One persistent, grid-synchronised kernel runs Algorithm alg-jacobi of
 // Liang, Pang, Toh and Yang (arXiv 2407.03272, Section 3) with the restart
-// rule of Algorithm alg-apg-re (Section 2.2).  Each sweep s streams the CSR
-// matrix once and, per owned row i and right-hand side r:
+// rule of Algorithm alg-apg-re (Section 2.2).  Each sweep s streams the matrix
+// once and, per owned row i and right-hand side r, forms x^s from
+// y^s = x^{s-1} + beta (x^{s-1} - x^{s-2}) without ever storing y:
 //
-//   sx_i = sum_j Q_ij x^{s-1}_j,   sp_i = sum_j Q_ij x^{s-2}_j       (one pass, two sums)
-//   (Q y^s)_i = sx_i + beta (sx_i - sp_i)        y^s = x^{s-1} + beta (x^{s-1} - x^{s-2})
-//   g_i = (Q y^s)_i - b_i,   x^s_i = y^s_i - J^{-1}_ii g_i              (line "x^t = y^t + J^-1(b - Q y^t)")
+//   (Q y^s)_i = sx_i + beta (sx_i - sp_i),  sx = Q x^{s-1},  sp = Q x^{s-2}
+//   g_i = (Q y^s)_i - b_i,   x^s_i = y^s_i - J^{-1}_ii g_i              (x^t = y^t + J^-1(b - Q y^t))
 //   d  += g_i (x^s_i - x^{s-1}_i)                                      (restart test <Q y^t - b, x^t - x^{t-1}>)
 //   rr += (b_i - sx_i)^2                                               (exact residual of x^{s-1})
 //
-// so the momentum extrapolation y is never stored: it is formed lazily from
-// the two previous iterates inside the gather.  After a grid barrier every
-// CTA sums the per-CTA partials in one fixed order (identical bits in every
-// CTA), checks the stop test for x^{s-1}, then takes the restart/momentum
-// branch for iteration s.  Buffers rotate among three iterate vectors.
+// Two sweep forms give sp:
+//   lazy  (QX = false): sp is a second row sum over the gathered x^{s-2};
+//         two multiply-adds per stored entry, four n-vectors of traffic.
+//   stored (QX = true): u = Q x is written every sweep (u^{s-1} = sx) and
+//         u^{s-2} is read back for own rows only; one multiply-add per stored
+//         entry, two more n-vectors of traffic.  On GB300 FP64 issue is the
+//         binding resource of the FP64 policy, so it uses this form.
+// After a grid barrier every CTA sums the per-CTA partials in one fixed order
+// (identical bits in every CTA), checks the stop test for x^{s-1}, then takes
+// the restart/momentum branch for iteration s.  Buffers rotate by index.
 //
 // Precision policies (template parameter P):
 //   PolF64  IEEE FP64 everywhere (FMA row sums).
@@ -68,7 +73,7 @@ struct RhsState {
   int cur, prev, nxt; // buffer indices of x^t, x^{t-1} (may equal cur), spare
   int done;           // 1 once this right-hand side has stopped
   int status;         // kOk / kEMaxit / kEDiverged / kENonfinite
-  int pad;
+  int uw;             // stored form: u buffer written this sweep (Q x^t); 1 - uw holds Q x^{t-1}
 };
 
 // ----------------------------------------------------------------------------
@@ -207,12 +212,16 @@ struct PolF64 {
   __device__ static S ldx(const X* p) { return ld_l2(p); }
   __device__ static S ldr(const X* p) { return ld_ro(p); }
   __device__ static void stx(X* p, S v) { st_l2(p, v); }
-  __device__ static void mac(S& acc, const V* v, S x) { acc = fma(ld_ro(v), x, acc); }
+  __device__ static V ldv(const V* p) { return ld_ro(p); }
+  __device__ static V vzero() { return 0.0; }
+  __device__ static void macv(S& acc, V v, S x) { acc = fma(v, x, acc); }
+  __device__ static void mac(S& acc, const V* v, S x) { macv(acc, ldv(v), x); }
   __device__ static S finish(S a) { return a; }
   __device__ static S add(S a, S b) { return a + b; }
   __device__ static S sub(S a, S b) { return a - b; }
   __device__ static S mul(S a, S b) { return a * b; }
   __device__ static S fma_(S a, S b, S c) { return fma(a, b, c); }  // a*b + c
+  __device__ static S fnma(S a, S b, S c) { return fma(-a, b, c); }  // c - a*b
   __device__ static S coef(double c) { return c; }
   __device__ static void acc_prod(A& a, S u, S v) { a = fma(u, v, a); }
   __device__ static S shfl_xor(S v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
@@ -231,10 +240,12 @@ struct PolDF64 {
   __device__ static S ldx(const X* p) { float2 v = ld_l2(p); return {v.x, v.y}; }
   __device__ static S ldr(const X* p) { float2 v = ld_ro(p); return {v.x, v.y}; }
   __device__ static void stx(X* p, S v) { st_l2(p, make_float2(v.hi, v.lo)); }
+  __device__ static V ldv(const V* p) { return ld_ro(p); }
+  __device__ static V vzero() { return make_float2(0.f, 0.f); }
+  __device__ static void mac(S& acc, const V* vp, S x) { macv(acc, ldv(vp), x); }
   // acc += v * x with the product split exactly (TwoProd) and cross terms folded
   // into the low word; the sum of high words is kept by TwoSum (Dot2 pattern).
-  __device__ static void mac(S& acc, const V* vp, S x) {
-    float2 v = ld_ro(vp);
+  __device__ static void macv(S& acc, V v, S x) {
     dw p = two_prod(v.x, x.hi);
     float pl = __fmaf_rn(v.x, x.lo, p.lo);
     pl = __fmaf_rn(v.y, x.hi, pl);
@@ -248,6 +259,7 @@ struct PolDF64 {
   __device__ static S sub(S a, S b) { return dw_sub(a, b); }
   __device__ static S mul(S a, S b) { return dw_mul(a, b); }
   __device__ static S fma_(S a, S b, S c) { return dw_add(dw_mul(a, b), c); }
+  __device__ static S fnma(S a, S b, S c) { return dw_sub(c, dw_mul(a, b)); }
   __device__ static S coef(double c) { return dw_from_double(c); }
   __device__ static void acc_prod(A& a, S u, S v) {
     dw p = two_prod(u.hi, v.hi);
@@ -275,12 +287,16 @@ struct PolF32 {
   __device__ static S ldx(const X* p) { return ld_l2(p); }
   __device__ static S ldr(const X* p) { return ld_ro(p); }
   __device__ static void stx(X* p, S v) { st_l2(p, v); }
-  __device__ static void mac(S& acc, const V* v, S x) { acc = __fmaf_rn(ld_ro(v), x, acc); }
+  __device__ static V ldv(const V* p) { return ld_ro(p); }
+  __device__ static V vzero() { return 0.f; }
+  __device__ static void macv(S& acc, V v, S x) { acc = __fmaf_rn(v, x, acc); }
+  __device__ static void mac(S& acc, const V* v, S x) { macv(acc, ldv(v), x); }
   __device__ static S finish(S a) { return a; }
   __device__ static S add(S a, S b) { return __fadd_rn(a, b); }
   __device__ static S sub(S a, S b) { return __fsub_rn(a, b); }
   __device__ static S mul(S a, S b) { return __fmul_rn(a, b); }
   __device__ static S fma_(S a, S b, S c) { return __fmaf_rn(a, b, c); }
+  __device__ static S fnma(S a, S b, S c) { return __fmaf_rn(-a, b, c); }
   __device__ static S coef(double c) { return __double2float_rn(c); }
   __device__ static void acc_prod(A& a, S u, S v) {
     dw p = two_prod(u, v);
@@ -295,9 +311,10 @@ struct PolF32 {
 struct PolB16 : PolF32 {
   using V = __nv_bfloat16;
   static constexpr int kId = 3;
-  __device__ static void mac(S& acc, const V* v, S x) {
-    acc = __fmaf_rn(__bfloat162float(ld_ro(v)), x, acc);
-  }
+  __device__ static V ldv(const V* p) { return ld_ro(p); }
+  __device__ static V vzero() { return __float2bfloat16_rn(0.f); }
+  __device__ static void macv(S& acc, V v, S x) { acc = __fmaf_rn(__bfloat162float(v), x, acc); }
+  __device__ static void mac(S& acc, const V* v, S x) { macv(acc, ldv(v), x); }
 };
 
 // ----------------------------------------------------------------------------
@@ -312,6 +329,7 @@ struct IterArgs {
   const typename P::X* b;     // [n * nrhs]
   const typename P::X* jinv;  // [n]
   typename P::X* x[3];        // three iterate buffers, [n * nrhs] each
+  typename P::X* u[2];        // stored form: Q x^t and Q x^{t-1}, [n * nrhs] each
   double* partials;           // [2][gridDim][nrhs][kNRed]
   unsigned long long* bar;    // barrier arrival counter, zero at launch
   int* err;                   // device error word, zero at launch
@@ -331,8 +349,9 @@ struct IterArgs {
 };
 
 // Warp-cooperative row sums for one long row (lanes stride over the entries,
-// then a fixed xor tree).  Returns the sums in every lane.
-template <class P, int NR>
+// then a fixed xor tree).  Returns the sums in every lane.  The stored form
+// (QX) forms only sx.
+template <class P, int NR, bool QX>
 __device__ __forceinline__ void long_row_sums(const IterArgs<P>& a, int rs, int re,
                                               const typename P::X* const* xc,
                                               const typename P::X* const* xp, const bool* same,
@@ -349,21 +368,28 @@ __device__ __forceinline__ void long_row_sums(const IterArgs<P>& a, int rs, int 
     for (int r = 0; r < NR; r++) {
       if (!active[r]) continue;
       P::mac(lx[r], a.val + q, P::ldx(xc[r] + (size_t)c * NR + r));
-      if (!same[r]) P::mac(lp[r], a.val + q, P::ldx(xp[r] + (size_t)c * NR + r));
+      if (!QX && !same[r]) P::mac(lp[r], a.val + q, P::ldx(xp[r] + (size_t)c * NR + r));
     }
   }
 #pragma unroll
   for (int r = 0; r < NR; r++) {
     lx[r] = P::finish(lx[r]);
-    lp[r] = P::finish(lp[r]);
 #pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-      lx[r] = P::combine(lx[r], P::shfl_xor(lx[r], m));
-      lp[r] = P::combine(lp[r], P::shfl_xor(lp[r], m));
-    }
+    for (int m = 16; m >= 1; m >>= 1) lx[r] = P::combine(lx[r], P::shfl_xor(lx[r], m));
     sx[r] = lx[r];
-    sp[r] = same[r] ? lx[r] : lp[r];
+    if (!QX) {
+      lp[r] = P::finish(lp[r]);
+#pragma unroll
+      for (int m = 16; m >= 1; m >>= 1) lp[r] = P::combine(lp[r], P::shfl_xor(lp[r], m));
+      sp[r] = same[r] ? lx[r] : lp[r];
+    }
   }
+}
+
+// Reduction slots a sweep fills: d and rr always, the objective terms only
+// for the objective-gap stop.
+__device__ __forceinline__ bool slot_used(int k, bool want_obj) {
+  return k == 0 || k == 2 || (want_obj && k >= 3);
 }
 
 // Block reduction of per-thread FP64 values in a fixed order; result valid in
@@ -383,14 +409,31 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
 
 // One sweep over the CTA's tiles: the fused SpMV at y, x update and reduction
 // terms.  `compute_x` is false on a residual-only sweep (no x^s is formed).
-template <class P, int NR>
+// Reduction slots: 0 d, 2 rr, 3 <x, Qx> and 4 <b, x> (objective stop only);
+// slot 1 is unused.
+// Entries per unrolled chunk of a short row: as many gathers in flight as the
+// register budget allows for NR right-hand sides and the sweep form.
+#ifndef AJ_ROW_UNROLL
+#define AJ_ROW_UNROLL 8
+#endif
+__host__ __device__ constexpr int row_unroll(int nr, bool qx) {
+  return nr * (qx ? 1 : 2) * 8 / AJ_ROW_UNROLL >= 8   ? 1
+         : nr * (qx ? 1 : 2) * 8 / AJ_ROW_UNROLL >= 4 ? 2
+         : nr * (qx ? 1 : 2) * 8 / AJ_ROW_UNROLL >= 2 ? 4
+                                                       : 8;
+}
+
+template <class P, int NR, bool QX>
 __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, bool compute_x,
                                       bool want_obj, typename P::A (&acc)[NR][kNRed]) {
   using S = typename P::S;
+  using V = typename P::V;
   using X = typename P::X;
   const X* xc[NR];
   const X* xp[NR];
   X* xn[NR];
+  const X* up[NR];
+  X* uc[NR];
   bool same[NR], active[NR];
   S beta[NR];
 #pragma unroll
@@ -398,6 +441,10 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
     xc[r] = a.x[st[r].cur];
     xp[r] = a.x[st[r].prev];
     xn[r] = a.x[st[r].nxt];
+    if (QX) {
+      uc[r] = a.u[st[r].uw];
+      up[r] = a.u[1 - st[r].uw];
+    }
     same[r] = st[r].cur == st[r].prev;
     active[r] = st[r].done == 0;
     beta[r] = P::coef(st[r].beta);
@@ -417,19 +464,45 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
 #pragma unroll
     for (int r = 0; r < NR; r++) { sx[r] = P::zero(); sp[r] = P::zero(); }
     if (valid && !is_long) {
-      for (int q = rs; q < re; q++) {
-        const int c = ld_ro(a.col + q);
+      // chunks of U entries: every load of a chunk is issued before its
+      // multiply-adds, which then run in ascending entry order
+      constexpr int U = row_unroll(NR, QX);
+      for (int q0 = rs; q0 < re; q0 += U) {
+        int cc[U];
+        V vv[U];
 #pragma unroll
-        for (int r = 0; r < NR; r++) {
-          if (!active[r]) continue;
-          P::mac(sx[r], a.val + q, P::ldx(xc[r] + (size_t)c * NR + r));
-          if (!same[r]) P::mac(sp[r], a.val + q, P::ldx(xp[r] + (size_t)c * NR + r));
+        for (int k = 0; k < U; k++) {
+          const bool in = q0 + k < re;
+          cc[k] = in ? ld_ro(a.col + q0 + k) : 0;
+          vv[k] = in ? P::ldv(a.val + q0 + k) : P::vzero();
+        }
+        S xv[U][NR], pv[U][NR];
+#pragma unroll
+        for (int k = 0; k < U; k++)
+#pragma unroll
+          for (int r = 0; r < NR; r++) {
+            xv[k][r] = P::zero();
+            pv[k][r] = P::zero();
+            if (q0 + k < re && active[r]) {
+              xv[k][r] = P::ldx(xc[r] + (size_t)cc[k] * NR + r);
+              if (!QX && !same[r]) pv[k][r] = P::ldx(xp[r] + (size_t)cc[k] * NR + r);
+            }
+          }
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+          if (q0 + k >= re) break;
+#pragma unroll
+          for (int r = 0; r < NR; r++) {
+            if (!active[r]) continue;
+            P::macv(sx[r], vv[k], xv[k][r]);
+            if (!QX && !same[r]) P::macv(sp[r], vv[k], pv[k][r]);
+          }
         }
       }
 #pragma unroll
       for (int r = 0; r < NR; r++) {
         sx[r] = P::finish(sx[r]);
-        sp[r] = same[r] ? sx[r] : P::finish(sp[r]);
+        if (!QX) sp[r] = same[r] ? sx[r] : P::finish(sp[r]);
       }
     }
     unsigned lm = __ballot_sync(0xffffffffu, is_long);
@@ -439,10 +512,13 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       const int lrs = __shfl_sync(0xffffffffu, rs, src);
       const int lre = __shfl_sync(0xffffffffu, re, src);
       S tx[NR], tp[NR];
-      long_row_sums<P, NR>(a, lrs, lre, xc, xp, same, active, tx, tp);
+      long_row_sums<P, NR, QX>(a, lrs, lre, xc, xp, same, active, tx, tp);
       if (lane == src) {
 #pragma unroll
-        for (int r = 0; r < NR; r++) { sx[r] = tx[r]; sp[r] = tp[r]; }
+        for (int r = 0; r < NR; r++) {
+          sx[r] = tx[r];
+          if (!QX) sp[r] = tp[r];
+        }
       }
     }
     if (!valid) continue;
@@ -453,28 +529,28 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       const size_t e = (size_t)i * NR + r;
       const S xi = P::ldx(xc[r] + e);
       const S bi = P::ldr(a.b + e);
-      // exact residual of x^{s-1}: b - Q x^{s-1}
-      const S res = P::sub(bi, sx[r]);
-      P::acc_prod(acc[r][2], res, res);
+      // g0 = Q x^{s-1} - b: minus the exact residual of x^{s-1}
+      const S g0 = P::sub(sx[r], bi);
+      P::acc_prod(acc[r][2], g0, g0);
       if (want_obj) {
         P::acc_prod(acc[r][3], xi, sx[r]);
         P::acc_prod(acc[r][4], bi, xi);
       }
+      if (QX) P::stx(uc[r] + e, sx[r]);
       if (!compute_x) continue;
-      S qy, yi;
+      S g, yi;
       if (same[r]) {
-        qy = sx[r];
+        g = g0;
         yi = xi;
       } else {
         const S xpi = P::ldx(xp[r] + e);
-        qy = P::fma_(beta[r], P::sub(sx[r], sp[r]), sx[r]);
+        const S spi = QX ? P::ldx(up[r] + e) : sp[r];
+        g = P::fma_(beta[r], P::sub(sx[r], spi), g0);
         yi = P::fma_(beta[r], P::sub(xi, xpi), xi);
       }
-      const S g = P::sub(qy, bi);
-      const S xnew = P::sub(yi, P::mul(ji, g));
+      const S xnew = P::fnma(ji, g, yi);
       P::stx(xn[r] + e, xnew);
       P::acc_prod(acc[r][0], g, P::sub(xnew, xi));
-      P::acc_prod(acc[r][1], g, g);
     }
   }
 }
@@ -544,6 +620,7 @@ __device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kN
       q.cur = oldnew;
       q.nxt = (oldprev != oldcur && oldprev != oldnew) ? oldprev : (3 - oldcur - oldnew);
     }
+    q.uw = 1 - q.uw;
     q.t = t;
     all_done = false;
   }
@@ -553,8 +630,15 @@ __device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kN
 // The persistent fused AJ kernel.  Launch cooperatively with kThreads
 // threads per CTA.  Runs sweeps until every right-hand side is done or
 // max_sweeps sweeps have run.
-template <class P, int NR>
-__global__ void __launch_bounds__(kThreads) aj_persistent_kernel(IterArgs<P> a) {
+// Co-resident CTAs per SM the register allocation must allow.  The sweep is
+// latency bound (gathers from L2, the matrix stream from DRAM), so warps in
+// flight matter more than registers: measured on the 256^3 Poisson system,
+// 4 CTAs/SM beat the compiler's own choice of 2-3 by 1.3-1.7x for one
+// right-hand side.  More right-hand sides need more registers per thread.
+__host__ __device__ constexpr int min_blocks(int nr) { return nr == 1 ? 4 : nr == 2 ? 2 : 1; }
+
+template <class P, int NR, bool QX>
+__global__ void __launch_bounds__(kThreads, min_blocks(NR)) aj_persistent_kernel(IterArgs<P> a) {
   using A = typename P::A;
   __shared__ RhsState st[NR];
   __shared__ double s_tot[NR][kNRed];
@@ -583,13 +667,14 @@ __global__ void __launch_bounds__(kThreads) aj_persistent_kernel(IterArgs<P> a) 
     for (int r = 0; r < NR; r++)
 #pragma unroll
       for (int k = 0; k < kNRed; k++) acc_zero(acc[r][k]);
-    sweep<P, NR>(a, st, compute_x, want_obj, acc);
+    sweep<P, NR, QX>(a, st, compute_x, want_obj, acc);
     // CTA partials -> global (parity-buffered by sweep)
     double* part = a.partials + (size_t)(s0 & 1) * G * NR * kNRed;
 #pragma unroll
     for (int r = 0; r < NR; r++)
 #pragma unroll
       for (int k = 0; k < kNRed; k++) {
+        if (!slot_used(k, want_obj)) continue;
         const double v = block_sum(acc_value(acc[r][k]), s_red);
         if (threadIdx.x == 0) __stcg(part + ((size_t)blockIdx.x * NR + r) * kNRed + k, v);
       }
@@ -600,6 +685,10 @@ __global__ void __launch_bounds__(kThreads) aj_persistent_kernel(IterArgs<P> a) 
     for (int r = 0; r < NR; r++)
 #pragma unroll
       for (int k = 0; k < kNRed; k++) {
+        if (!slot_used(k, want_obj)) {
+          if (threadIdx.x == 0) s_tot[r][k] = 0.0;
+          continue;
+        }
         double v = 0.0;
         for (unsigned int c = threadIdx.x; c < G; c += kThreads)
           v += __ldcg(part + ((size_t)c * NR + r) * kNRed + k);

@@ -19,6 +19,7 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
   a.b = static_cast<const typename P::X*>(L.b);
   a.jinv = static_cast<const typename P::X*>(L.jinv);
   for (int k = 0; k < 3; k++) a.x[k] = static_cast<typename P::X*>(L.x[k]);
+  for (int k = 0; k < 2; k++) a.u[k] = static_cast<typename P::X*>(L.u[k]);
   a.partials = L.partials;
   a.bar = L.bar;
   a.err = L.err;
@@ -42,17 +43,19 @@ template <class P, int NR>
 static cudaError_t launch_nr(const IterLaunch& L, int grid, cudaStream_t s) {
   IterArgs<P> a = typed_args<P>(L);
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)aj_persistent_kernel<P, NR>, dim3(grid),
-                                     dim3(kThreads), args, 0, s);
+  const void* k = L.qx ? (const void*)aj_persistent_kernel<P, NR, true>
+                       : (const void*)aj_persistent_kernel<P, NR, false>;
+  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
 }
 
 template <class P, int NR>
-static int occ_nr() {
+static int occ_nr(int qx) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, aj_persistent_kernel<P, NR>, kThreads, 0) !=
-      cudaSuccess)
-    return 0;
-  return nb;
+  cudaError_t e = qx ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                           &nb, aj_persistent_kernel<P, NR, true>, kThreads, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                           &nb, aj_persistent_kernel<P, NR, false>, kThreads, 0);
+  return e == cudaSuccess ? nb : 0;
 }
 
 cudaError_t AJ_CAT(launch_persistent_, AJ_SUFFIX)(int nrhs, const IterLaunch& L, int grid,
@@ -66,12 +69,12 @@ cudaError_t AJ_CAT(launch_persistent_, AJ_SUFFIX)(int nrhs, const IterLaunch& L,
   return cudaErrorInvalidValue;
 }
 
-int AJ_CAT(blocks_per_sm_, AJ_SUFFIX)(int nrhs) {
+int AJ_CAT(blocks_per_sm_, AJ_SUFFIX)(int nrhs, int qx) {
   switch (nrhs) {
-    case 1: return occ_nr<AJ_POL, 1>();
-    case 2: return occ_nr<AJ_POL, 2>();
-    case 3: return occ_nr<AJ_POL, 3>();
-    case 4: return occ_nr<AJ_POL, 4>();
+    case 1: return occ_nr<AJ_POL, 1>(qx);
+    case 2: return occ_nr<AJ_POL, 2>(qx);
+    case 3: return occ_nr<AJ_POL, 3>(qx);
+    case 4: return occ_nr<AJ_POL, 4>(qx);
   }
   return 0;
 }

@@ -17,6 +17,7 @@ struct IterLaunch {
   const void* b;
   const void* jinv;
   void* x[3];
+  void* u[2];  // stored sweep form only
   double* partials;
   unsigned long long* bar;
   int* err;
@@ -33,21 +34,22 @@ struct IterLaunch {
   double fstar;
   double fscale;
   long long max_sweeps;
+  int qx;  // 1: stored sweep form (u = Q x kept), 0: lazy form (two row sums)
 };
 
 // Cooperative launch of the persistent kernel for precision `pol`
-// (0 F64, 1 DF64, 2 F32, 3 BF16) and nrhs in [1, 4].
+// (0 F64, 1 DF64, 2 F32, 3 BF16), nrhs in [1, 4] and the sweep form L.qx.
 cudaError_t launch_persistent(int pol, int nrhs, const IterLaunch& L, int grid, cudaStream_t s);
 // Co-resident CTAs per SM of that kernel (0 on error).
-int persistent_blocks_per_sm(int pol, int nrhs);
+int persistent_blocks_per_sm(int pol, int nrhs, int qx);
 
 cudaError_t launch_persistent_f64(int nrhs, const IterLaunch& L, int grid, cudaStream_t s);
 cudaError_t launch_persistent_df64(int nrhs, const IterLaunch& L, int grid, cudaStream_t s);
 cudaError_t launch_persistent_f32(int nrhs, const IterLaunch& L, int grid, cudaStream_t s);
 cudaError_t launch_persistent_b16(int nrhs, const IterLaunch& L, int grid, cudaStream_t s);
-int blocks_per_sm_f64(int nrhs);
-int blocks_per_sm_df64(int nrhs);
-int blocks_per_sm_f32(int nrhs);
-int blocks_per_sm_b16(int nrhs);
+int blocks_per_sm_f64(int nrhs, int qx);
+int blocks_per_sm_df64(int nrhs, int qx);
+int blocks_per_sm_f32(int nrhs, int qx);
+int blocks_per_sm_b16(int nrhs, int qx);
 
 }  // namespace aj

@@ -9,8 +9,9 @@
 // run time; embedded or certified deployments that fix every device buffer at
 // load time.  This entry point serves them.  The caller passes the matrix, b
 // and the output on the device; the library supplies J^{-1}, the three iterate
-// buffers, the per-CTA partial sums, the grid-barrier counter, the error word
-// and the solver state from the array below.  Nothing here calls cudaMalloc,
+// buffers, the two Q x buffers of the stored sweep form, the per-CTA partial
+// sums, the grid-barrier counter, the error word and the solver state from the
+// array below.  Nothing here calls cudaMalloc,
 // cudaFree or an allocating library routine.
 //
 // The array is a host-side stand-in in host code: its device address comes
@@ -42,7 +43,8 @@ constexpr size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 constexpr size_t kOffJinv = 0;
 constexpr size_t kOffX0 = align256(kOffJinv + (size_t)kNaMaxN * 8);
 constexpr size_t kVecBytes = align256((size_t)kNaMaxN * 8);
-constexpr size_t kOffPart = kOffX0 + 3 * kVecBytes;
+constexpr size_t kOffU0 = kOffX0 + 3 * kVecBytes;
+constexpr size_t kOffPart = kOffU0 + 2 * kVecBytes;
 constexpr size_t kOffState = align256(kOffPart + (size_t)2 * kNaMaxTiles * kNRed * 8);
 constexpr size_t kOffRlog = align256(kOffState + sizeof(RhsState));
 constexpr size_t kOffBar = align256(kOffRlog + (size_t)kNaRlogCap * 8);
@@ -50,7 +52,7 @@ constexpr size_t kOffErr = kOffBar + 64;
 constexpr size_t kOffFlags = kOffErr + 64;
 constexpr size_t kScratchBytes = align256(kOffFlags + 64);
 
-// The fixed scratch: about 4.1 MB, held by every GPU that loads libaj.
+// The fixed scratch: about 6.1 MB, held by every GPU that loads libaj.
 static __device__ __align__(256) unsigned char g_na_scratch[kScratchBytes];
 
 struct NaDevice {
@@ -171,7 +173,7 @@ aj_status na_setup(NaDevice** out) {
       cudaGetLastError();
       return AJ_ECUDA;
     }
-    const int bps = blocks_per_sm_f64(1);
+    const int bps = blocks_per_sm_f64(1, 1);
     if (bps < 1 || sms < 1) return AJ_ECUDA;
     d.base = (unsigned char*)p;
     d.grid_cap = bps * sms;
@@ -231,6 +233,8 @@ extern "C" aj_status aj_solve_noalloc(const aj_csr* Q, const double* b, const aj
   double* jinv = (double*)(base + kOffJinv);
   double* xb[3];
   for (int k = 0; k < 3; k++) xb[k] = (double*)(base + kOffX0 + k * kVecBytes);
+  double* ub[2];
+  for (int k = 0; k < 2; k++) ub[k] = (double*)(base + kOffU0 + k * kVecBytes);
   double* part = (double*)(base + kOffPart);
   RhsState* st = (RhsState*)(base + kOffState);
   long long* rlog = (long long*)(base + kOffRlog);
@@ -266,6 +270,8 @@ extern "C" aj_status aj_solve_noalloc(const aj_csr* Q, const double* b, const aj
   L.b = b;
   L.jinv = jinv;
   for (int k = 0; k < 3; k++) L.x[k] = xb[k];
+  for (int k = 0; k < 2; k++) L.u[k] = ub[k];
+  L.qx = 1;  // the stored sweep form, as aj_set picks for AJ_FP64
   L.partials = part;
   L.bar = bar;
   L.err = err;

@@ -43,11 +43,14 @@ def _oracle_J(Q, j_policy, L=None):
     return oracle.j_scaled_diag(Q, L)
 
 
+FORMS = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED}
+
+
 def _compare_fixed(Q, b, T, precision="fp64", restart=True, momentum=True, j_policy=0, L=0.0,
-                   x0=None, tol_rel=REL):
+                   x0=None, tol_rel=REL, form="auto"):
     ctx, x, info = _gpu(Q, b, precision=precision, stop=aj.AJ_STOP_NONE, maxit=T,
                         restart=int(restart), momentum=int(momentum), j_policy=j_policy, L=L,
-                        x0=x0)
+                        x0=x0, sweep_form=FORMS.get(form, aj.AJ_SWEEP_AUTO))
     assert info["iters"] == T and info["status"] == aj.AJ_EMAXIT
     J = _oracle_J(Q, j_policy, L if L else info["L_used"])
     ref = oracle.solve(Q, b, J, restart=restart, momentum=momentum, maxit=T,
@@ -63,10 +66,26 @@ def _compare_fixed(Q, b, T, precision="fp64", restart=True, momentum=True, j_pol
 
 
 # ---------------------------------------------------------------- fixed-iteration parity
+@pytest.mark.parametrize("form", ["lazy", "stored"])
 @pytest.mark.parametrize("precision", ["fp64", "df64"])
-def test_poisson64_200_iterations_match_oracle(precision):
+def test_poisson64_200_iterations_match_oracle(precision, form):
     Q, b, xs = synth.workload("poisson2d_64")
-    _compare_fixed(Q, b, 200, precision=precision)
+    _compare_fixed(Q, b, 200, precision=precision, form=form)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64", "fp32_ir", "bf16_ir"])
+def test_lazy_and_stored_forms_agree(precision):
+    # the two sweep forms compute the same iterates up to rounding
+    Q, b, xs = synth.workload("poisson2d_40")
+    T = 150
+    xs_ = {}
+    for form in FORMS:
+        ctx, x, info = _gpu(Q, b, precision=precision, stop=aj.AJ_STOP_NONE, maxit=T,
+                            sweep_form=FORMS[form], restart=0)
+        assert info["iters"] == T
+        xs_[form] = x
+    tol = 1e-12 if precision in ("fp64", "df64") else 1e-4
+    assert np.linalg.norm(xs_["lazy"] - xs_["stored"]) <= tol * np.linalg.norm(xs_["lazy"])
 
 
 @pytest.mark.parametrize("precision", ["fp64", "df64"])
@@ -78,16 +97,17 @@ def test_no_restart_and_jacobi_modes_match_oracle(precision):
                    j_policy=aj.AJ_J_SCALED_DIAG, L=1.0)
 
 
+@pytest.mark.parametrize("form", ["lazy", "stored"])
 @pytest.mark.parametrize("precision", ["fp64", "df64"])
-def test_ragged_tail_and_long_rows(precision):
+def test_ragged_tail_and_long_rows(precision, form):
     # n = 300 rows of length 300 (> 32: the warp-cooperative path), n not a multiple of 256
     Q = synth.sdd(300)
     b = np.ones(300)
-    _compare_fixed(Q, b, 80, precision=precision)
+    _compare_fixed(Q, b, 80, precision=precision, form=form)
     # a 3-D grid with a ragged last tile and boundary rows of every length
     Q, b, xs = synth.workload("poisson3d_13")
     assert Q["n"] % 256 != 0
-    _compare_fixed(Q, b, 120, precision=precision)
+    _compare_fixed(Q, b, 120, precision=precision, form=form)
 
 
 def test_singular_laplacian_with_empty_rows():
@@ -172,7 +192,7 @@ def test_zero_rhs_and_tiny_systems():
 
 # ---------------------------------------------------------------- several right-hand sides
 @pytest.mark.parametrize("nrhs", [2, 3, 4])
-@pytest.mark.parametrize("precision", ["fp64", "df64"])
+@pytest.mark.parametrize("precision", ["fp64", "df64", "fp32_ir"])
 def test_multi_rhs_equals_single(nrhs, precision):
     Q = synth.poisson2d(30)
     n = Q["n"]
@@ -191,17 +211,18 @@ def test_multi_rhs_equals_single(nrhs, precision):
 
 
 # ---------------------------------------------------------------- checkpoint / resume
-def test_resume_is_bit_identical():
+@pytest.mark.parametrize("form", ["lazy", "stored"])
+def test_resume_is_bit_identical(form):
     Q, b, xs = synth.workload("poisson2d_48")
     full = aj.from_csr(Q, b)
-    full.set(stop=aj.AJ_STOP_NONE, maxit=400)
+    full.set(stop=aj.AJ_STOP_NONE, maxit=400, sweep_form=FORMS[form])
     xf, inf_f = full.solve()
     part = aj.from_csr(Q, b)
-    part.set(stop=aj.AJ_STOP_NONE, maxit=170)
+    part.set(stop=aj.AJ_STOP_NONE, maxit=170, sweep_form=FORMS[form])
     part.solve()
     blob = part.get_state()
     other = aj.from_csr(Q, b)
-    other.set(stop=aj.AJ_STOP_NONE, maxit=400)
+    other.set(stop=aj.AJ_STOP_NONE, maxit=400, sweep_form=FORMS[form])
     other.set_state(blob)
     xr, inf_r = other.solve()
     np.testing.assert_array_equal(xr, xf)
