@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -92,6 +93,33 @@ cudaError_t launch_persistent(int pol, int nrhs, const IterLaunch& L, int grid, 
     case 3: return launch_persistent_b16(nrhs, L, grid, s);
   }
   return cudaErrorInvalidValue;
+}
+size_t iter_args_bytes() { return sizeof(IterArgs<PolF64>); }
+void pack_iter_args(int pol, const IterLaunch& L, void* dst) {
+  switch (pol) {
+    case 0: pack_iter_args_f64(L, dst); break;
+    case 1: pack_iter_args_df64(L, dst); break;
+    case 2: pack_iter_args_f32(L, dst); break;
+    case 3: pack_iter_args_b16(L, dst); break;
+  }
+}
+cudaError_t launch_batched(int pol, int nrhs, int qx, const BatchLaunch& B, int grid, cudaStream_t s) {
+  switch (pol) {
+    case 0: return launch_batched_f64(nrhs, qx, B, grid, s);
+    case 1: return launch_batched_df64(nrhs, qx, B, grid, s);
+    case 2: return launch_batched_f32(nrhs, qx, B, grid, s);
+    case 3: return launch_batched_b16(nrhs, qx, B, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+int batched_blocks_per_sm(int pol, int nrhs, int qx) {
+  switch (pol) {
+    case 0: return batched_blocks_per_sm_f64(nrhs, qx);
+    case 1: return batched_blocks_per_sm_df64(nrhs, qx);
+    case 2: return batched_blocks_per_sm_f32(nrhs, qx);
+    case 3: return batched_blocks_per_sm_b16(nrhs, qx);
+  }
+  return 0;
 }
 int persistent_blocks_per_sm(int pol, int nrhs, int qx) {
   switch (pol) {
@@ -593,10 +621,9 @@ static void init_state(aj_ctx* c, RhsState* st, const double* bn2) {
 }
 
 // Run the persistent kernel to completion from state st (host copy, in/out).
-static aj_status run_persistent(aj_ctx* c, std::vector<RhsState>& st, const void* bvec,
-                                long long maxit, int stop, double tol, double fstar,
-                                double fscale, bool log_restarts) {
-  cudaStream_t s = c->stream;
+// Kernel arguments of one context's persistent solve.
+static IterLaunch make_launch(aj_ctx* c, const void* bvec, long long maxit, int stop, double tol,
+                              double fstar, double fscale) {
   IterLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.n = (int)c->n;
@@ -624,10 +651,27 @@ static aj_status run_persistent(aj_ctx* c, std::vector<RhsState>& st, const void
   L.fstar = fstar;
   L.fscale = fscale;
   L.max_sweeps = maxit + 2;
+  return L;
+}
+
+// Upload the state of a run and clear its barrier, error word and restart log.
+static aj_status stage_state(aj_ctx* c, const std::vector<RhsState>& st, bool log_restarts) {
+  cudaStream_t s = c->stream;
   CK(cudaMemcpyAsync(c->state, st.data(), sizeof(RhsState) * c->nrhs, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(c->bar, 0, 64, s));
   CK(cudaMemsetAsync(c->err, 0, 64, s));
   if (log_restarts) CK(cudaMemsetAsync(c->rlog, 0xff, (size_t)kMaxRhs * c->rlog_cap * 8, s));
+  return AJ_OK;
+}
+
+// Run the persistent kernel to completion from state st (host copy, in/out).
+static aj_status run_persistent(aj_ctx* c, std::vector<RhsState>& st, const void* bvec,
+                                long long maxit, int stop, double tol, double fstar,
+                                double fscale, bool log_restarts) {
+  cudaStream_t s = c->stream;
+  IterLaunch L = make_launch(c, bvec, maxit, stop, tol, fstar, fscale);
+  aj_status e = stage_state(c, st, log_restarts);
+  if (e != AJ_OK) return e;
   CK(cudaEventRecord(c->kev0, s));
   CK(launch_persistent(kernel_pol(c->pol), c->nrhs, L, c->grid, s));
   counted();
@@ -640,6 +684,183 @@ static aj_status run_persistent(aj_ctx* c, std::vector<RhsState>& st, const void
   cudaEventElapsedTime(&kms, c->kev0, c->kev1);
   c->kernel_ms += kms;
   if (err != 0) return err == kETimeout ? AJ_ETIMEOUT : AJ_ECUDA;
+  return AJ_OK;
+}
+
+// ---------------------------------------------------------------- batched launches
+// One system of a batched launch: its context, its state (host copy, in/out)
+// and the arguments of its run.
+struct BatchItem {
+  aj_ctx* c;
+  std::vector<RhsState>* st;
+  const void* bvec;
+  long long maxit;
+  int stop;
+  double tol, fstar, fscale;
+};
+
+static int pow2_ceil(long long v) {
+  int p = 1;
+  while (p < v && p < (1 << 30)) p <<= 1;
+  return p;
+}
+
+// CTAs (the gang size) a system gets in a batched launch: one per 8 tiles of
+// 256 rows rounded up to a power of two and at most 64, so that many systems
+// run side by side; a context's own grid_ctas overrides it.  A system's
+// arithmetic depends only on this count, so a batch member with grid_ctas set
+// computes exactly what aj_solve computes with the same grid_ctas.
+static int batch_gang(const aj_ctx* c, int gmax) {
+  if (c->prm.grid_ctas > 0) return std::max(1, std::min(c->prm.grid_ctas, gmax));
+  const long long ntiles = std::max<long long>(1, (c->n + kThreads - 1) / kThreads);
+  return std::max(1, std::min({pow2_ceil((ntiles + 7) / 8), 64, gmax}));
+}
+
+// Solves every item (all of one precision and sweep form) with one batched
+// persistent launch per right-hand-side count.  Gangs of equal size form a
+// class; a class gets CTAs in proportion to its estimated work (stored
+// entries x sqrt(n), the AJ iteration count of 2-D Laplacians growing like
+// the grid side), at least one gang, and at most one gang per system.
+static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, double* kernel_ms) {
+  if (items.empty()) return AJ_OK;
+  aj_ctx* c0 = items[0].c;
+  cudaStream_t s = c0->stream;
+  const int pol = c0->pol, qx = c0->qx;
+  for (auto& it : items) {
+    aj_status e = stage_state(it.c, *it.st, log_restarts);
+    if (e != AJ_OK) return e;
+  }
+  Workspace ws;
+  struct Release {
+    Workspace& w;
+    ~Release() { w.release(); }
+  } release{ws};
+  const size_t abytes = iter_args_bytes();
+  for (int nr = 1; nr <= kMaxRhs; nr++) {
+    std::vector<int> idx;
+    for (int i = 0; i < (int)items.size(); i++)
+      if (items[i].c->nrhs == nr) idx.push_back(i);
+    if (idx.empty()) continue;
+    const int bps = batched_blocks_per_sm(pol, nr, qx);
+    if (bps < 1) return AJ_ECUDA;
+    const int gmax = bps * c0->sm_count;
+    const int m = (int)idx.size();
+    std::vector<int> gsz(m);
+    std::vector<double> cost(m);
+    std::vector<int> sizes;
+    for (int j = 0; j < m; j++) {
+      const aj_ctx* c = items[idx[j]].c;
+      gsz[j] = batch_gang(c, gmax);
+      cost[j] = (double)(c->nnz + c->n) * (1.0 + 0.5 * (nr - 1)) * std::sqrt((double)std::max<int64_t>(c->n, 1));
+      sizes.push_back(gsz[j]);
+    }
+    std::sort(sizes.begin(), sizes.end());
+    sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+    const int ncls = (int)sizes.size();
+    std::vector<std::vector<int>> mem(ncls);
+    std::vector<double> work(ncls, 0.0);
+    double W = 0.0;
+    for (int j = 0; j < m; j++) {
+      const int k = (int)(std::lower_bound(sizes.begin(), sizes.end(), gsz[j]) - sizes.begin());
+      mem[k].push_back(j);
+      work[k] += cost[j];
+      W += cost[j];
+    }
+    for (auto& v : mem)
+      std::stable_sort(v.begin(), v.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<int> kg(ncls);
+    for (int k = 0; k < ncls; k++) {
+      const double share = W > 0 ? work[k] / W : 1.0 / ncls;
+      kg[k] = std::max(1, std::min((int)mem[k].size(), (int)std::floor(share * gmax / sizes[k])));
+    }
+    auto used = [&]() {
+      long long u = 0;
+      for (int k = 0; k < ncls; k++) u += (long long)kg[k] * sizes[k];
+      return u;
+    };
+    while (used() > gmax) {
+      int best = -1;
+      for (int k = 0; k < ncls; k++)
+        if (kg[k] > 1 && (best < 0 || (long long)kg[k] * sizes[k] > (long long)kg[best] * sizes[best])) best = k;
+      if (best < 0) break;
+      kg[best]--;
+    }
+    if (used() > gmax) return AJ_EINVAL;  // more distinct gang sizes than the GPU holds
+    for (;;) {  // hand out what is left to the class with the most work per CTA
+      int best = -1;
+      double bw = 0.0;
+      for (int k = 0; k < ncls; k++) {
+        if (kg[k] >= (int)mem[k].size() || used() + sizes[k] > gmax) continue;
+        const double wpc = work[k] / ((double)kg[k] * sizes[k]);
+        if (best < 0 || wpc > bw) { best = k; bw = wpc; }
+      }
+      if (best < 0) break;
+      kg[best]++;
+    }
+    const int grid = (int)used();
+    std::vector<int> order, cls_begin(ncls + 1, 0);
+    std::vector<int4> cta_gang;
+    int ngang = 0;
+    for (int k = 0; k < ncls; k++) {
+      cls_begin[k] = (int)order.size();
+      for (int j : mem[k]) order.push_back(j);
+      for (int q = 0; q < kg[k]; q++) {
+        const int base = (int)cta_gang.size();
+        for (int r = 0; r < sizes[k]; r++) cta_gang.push_back(make_int4(base, sizes[k], k, ngang));
+        ngang++;
+      }
+    }
+    cls_begin[ncls] = (int)order.size();
+    std::vector<unsigned char> sysh((size_t)m * abytes);
+    for (int j = 0; j < m; j++) {
+      const BatchItem& it = items[idx[j]];
+      IterLaunch L = make_launch(it.c, it.bvec, it.maxit, it.stop, it.tol, it.fstar, it.fscale);
+      pack_iter_args(pol, L, sysh.data() + (size_t)j * abytes);
+    }
+    void* d_sys = ws.alloc(sysh.size());
+    int* d_order = (int*)ws.alloc(order.size() * 4);
+    int* d_cb = (int*)ws.alloc(cls_begin.size() * 4);
+    int* d_head = (int*)ws.alloc((size_t)ncls * 4);
+    int4* d_cg = (int4*)ws.alloc(cta_gang.size() * sizeof(int4));
+    unsigned long long* d_bar = (unsigned long long*)ws.alloc((size_t)ngang * 8);
+    int* d_slot = (int*)ws.alloc((size_t)ngang * 4);
+    double* d_part = (double*)ws.alloc((size_t)grid * 2 * nr * kNRed * 8);
+    int* d_err = (int*)ws.alloc(64);
+    if (!d_sys || !d_order || !d_cb || !d_head || !d_cg || !d_bar || !d_slot || !d_part || !d_err)
+      return AJ_ENOMEM;
+    CK(cudaMemcpyAsync(d_sys, sysh.data(), sysh.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_cb, cls_begin.data(), cls_begin.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_cg, cta_gang.data(), cta_gang.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(d_head, 0, (size_t)ncls * 4, s));
+    CK(cudaMemsetAsync(d_bar, 0, (size_t)ngang * 8, s));
+    CK(cudaMemsetAsync(d_err, 0, 64, s));
+    BatchLaunch B;
+    B.sys = d_sys;
+    B.order = d_order;
+    B.cls_begin = d_cb;
+    B.cls_head = d_head;
+    B.cta_gang = d_cg;
+    B.gang_bar = d_bar;
+    B.gang_slot = d_slot;
+    B.gang_part = d_part;
+    B.err = d_err;
+    CK(cudaEventRecord(c0->kev0, s));
+    CK(launch_batched(pol, nr, qx, B, grid, s));
+    counted();
+    CK(cudaEventRecord(c0->kev1, s));
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, d_err, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float kms = 0.f;
+    cudaEventElapsedTime(&kms, c0->kev0, c0->kev1);
+    if (kernel_ms) *kernel_ms += kms;
+    if (err != 0) return err == kETimeout ? AJ_ETIMEOUT : AJ_ECUDA;
+  }
+  for (auto& it : items)
+    CK(cudaMemcpyAsync(it.st->data(), it.c->state, sizeof(RhsState) * it.c->nrhs,
+                       cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
   return AJ_OK;
 }
 
@@ -749,50 +970,61 @@ static aj_status write_output(aj_ctx* c, const double* x_il, double* x_out, int 
   return AJ_OK;
 }
 
-// Direct solve (FP64 or DF64 arithmetic in the persistent kernel).
-static aj_status solve_direct(aj_ctx* c, double* x_out, int x_on_device, aj_info* per) {
+// Direct solve (FP64 or DF64 arithmetic in the persistent kernel), in three
+// parts so that a batch can run the middle one for many contexts at once.
+struct DirectRun {
+  std::vector<RhsState> st;
+  double sb[kMaxRhs];
+  const void* bvec = nullptr;
+  double fscale = 1.0;
+};
+
+static aj_status direct_prepare(aj_ctx* c, DirectRun& d) {
   const int nrhs = c->nrhs;
   const double sq = c->sQ;
-  double sb[kMaxRhs];
   double bn2[kMaxRhs];
   for (int r = 0; r < nrhs; r++) {
-    sb[r] = c->pol == AJ_FP64 ? 1.0 : pow2_near(std::sqrt(c->bnorm2[r] / std::max<int64_t>(c->n, 1)));
-    bn2[r] = c->bnorm2[r] * sb[r] * sb[r];
+    d.sb[r] = c->pol == AJ_FP64 ? 1.0 : pow2_near(std::sqrt(c->bnorm2[r] / std::max<int64_t>(c->n, 1)));
+    bn2[r] = c->bnorm2[r] * d.sb[r] * d.sb[r];
   }
-  std::vector<RhsState> st(nrhs);
+  d.st.assign(nrhs, RhsState());
   if (c->resume) {
-    st = c->st_h;
-    for (int r = 0; r < nrhs; r++) sb[r] = c->sb[r];
+    d.st = c->st_h;
+    for (int r = 0; r < nrhs; r++) d.sb[r] = c->sb[r];
     for (int r = 0; r < nrhs; r++)
-      if (st[r].done && st[r].status == kEMaxit) { st[r].done = 0; st[r].status = 0; }
+      if (d.st[r].done && d.st[r].status == kEMaxit) { d.st[r].done = 0; d.st[r].status = 0; }
   } else {
-    for (int r = 0; r < nrhs; r++) c->sb[r] = sb[r];
-    init_state(c, st.data(), bn2);
+    for (int r = 0; r < nrhs; r++) c->sb[r] = d.sb[r];
+    init_state(c, d.st.data(), bn2);
     aj_status e = load_x0(c);
     if (e != AJ_OK) return e;
     double xs[kMaxRhs];
-    for (int r = 0; r < nrhs; r++) xs[r] = sb[r] / sq;
+    for (int r = 0; r < nrhs; r++) xs[r] = d.sb[r] / sq;
     to_policy(c, c->tmp64, c->x[0], xs);
   }
   // right-hand side in the iteration precision
-  const void* bvec = c->b64;
+  d.bvec = c->b64;
   if (c->pol != AJ_FP64) {
-    to_policy(c, c->b64, c->bp, sb);
-    bvec = c->bp;
+    to_policy(c, c->b64, c->bp, d.sb);
+    d.bvec = c->bp;
   }
   CK(cudaGetLastError());
   // f of the scaled problem is (sb^2 / sQ) f of the original one
-  const double fscale = sq / (sb[0] * sb[0]);
-  aj_status rs = run_persistent(c, st, bvec, c->prm.maxit, c->prm.stop, c->prm.tol,
-                                c->prm.fstar, fscale, true);
-  if (rs != AJ_OK) return rs;
-  aj_status e = fetch_rlog(c, st, false);
+  d.fscale = sq / (d.sb[0] * d.sb[0]);
+  return AJ_OK;
+}
+
+static aj_status direct_finish(aj_ctx* c, DirectRun& d, double* x_out, int x_on_device,
+                               aj_info* per) {
+  const int nrhs = c->nrhs;
+  const double sq = c->sQ;
+  aj_status e = fetch_rlog(c, d.st, false);
   if (e != AJ_OK) return e;
   int cur[kMaxRhs];
   double osc[kMaxRhs];
   for (int r = 0; r < nrhs; r++) {
-    cur[r] = st[r].cur;
-    osc[r] = sq / sb[r];
+    cur[r] = d.st[r].cur;
+    osc[r] = sq / d.sb[r];
   }
   double* xil = c->pol == AJ_FP64 ? c->tmp64 : c->x64;
   e = from_policy(c, cur, osc, xil);
@@ -802,109 +1034,189 @@ static aj_status solve_direct(aj_ctx* c, double* x_out, int x_on_device, aj_info
   if (e != AJ_OK) return e;
   e = write_output(c, xil, x_out, x_on_device);
   if (e != AJ_OK) return e;
-  c->st_h = st;
+  c->st_h = d.st;
   for (int r = 0; r < nrhs; r++) {
-    per[r].iters = st[r].t_final;
-    per[r].restarts = st[r].ell;
-    per[r].sweeps = st[r].t_final + 1;
+    per[r].iters = d.st[r].t_final;
+    per[r].restarts = d.st[r].ell;
+    per[r].sweeps = d.st[r].t_final + 1;
     per[r].outer = 0;
     per[r].relres = rel[r];
     per[r].objgap = og[r];
     per[r].L_used = c->L_used;
-    per[r].status = status_of(st[r].status);
+    per[r].status = status_of(d.st[r].status);
   }
   return AJ_OK;
 }
 
-// FP64 iterative refinement around the low-precision persistent solver.
-static aj_status solve_ir(aj_ctx* c, double* x_out, int x_on_device, aj_info* per) {
-  const int n = (int)c->n;
-  const int nrhs = c->nrhs;
-  const long long m = (long long)n * nrhs;
-  cudaStream_t s = c->stream;
-  aj_status e = load_x0(c);
+static aj_status solve_direct(aj_ctx* c, double* x_out, int x_on_device, aj_info* per) {
+  DirectRun d;
+  aj_status e = direct_prepare(c, d);
   if (e != AJ_OK) return e;
-  if (m > 0) CK(cudaMemcpyAsync(c->x64, c->tmp64, (size_t)m * 8, cudaMemcpyDeviceToDevice, s));
+  e = run_persistent(c, d.st, d.bvec, c->prm.maxit, c->prm.stop, c->prm.tol, c->prm.fstar,
+                     d.fscale, true);
+  if (e != AJ_OK) return e;
+  return direct_finish(c, d, x_out, x_on_device, per);
+}
+
+// FP64 iterative refinement around the low-precision persistent solver, for
+// one or many contexts: each outer step computes the FP64 residual of every
+// unfinished context, solves Q d = r in the iteration precision (one
+// persistent launch per context, or one batched launch for all of them) and
+// adds d to the FP64 iterate.
+struct IrRun {
   long long iters[kMaxRhs] = {0, 0, 0, 0}, rest[kMaxRhs] = {0, 0, 0, 0};
   int status[kMaxRhs] = {kEMaxit, kEMaxit, kEMaxit, kEMaxit};
   bool done[kMaxRhs] = {false, false, false, false};
-  double rel[kMaxRhs], og[kMaxRhs];
+  double rel[kMaxRhs] = {0, 0, 0, 0}, og[kMaxRhs] = {0, 0, 0, 0}, sr[kMaxRhs] = {1, 1, 1, 1};
   long long outer = 0;
-  c->rlog_h.assign(nrhs, {});
-  for (;;) {
-    e = fp64_report(c, c->x64, rel, og, c->r64);
+  bool finished = false;
+  std::vector<RhsState> st;
+};
+
+static aj_status ir_solve(aj_ctx* const* cs, int count, double* const* x_out, int x_on_device,
+                          aj_info* const* per, bool batched, double* batch_kms) {
+  std::vector<IrRun> R(count);
+  for (int i = 0; i < count; i++) {
+    aj_ctx* c = cs[i];
+    aj_status e = load_x0(c);
     if (e != AJ_OK) return e;
-    bool all = true;
-    for (int r = 0; r < nrhs; r++) {
-      if (done[r]) continue;
-      bool ok = false;
-      if (c->prm.stop == AJ_STOP_RELRES) ok = rel[r] <= c->prm.tol;
-      else if (c->prm.stop == AJ_STOP_OBJGAP) ok = og[r] <= c->prm.tol;
-      if (ok) { done[r] = true; status[r] = kOk; }
-      else if (!std::isfinite(rel[r])) { done[r] = true; status[r] = kENonfinite; }
-      all = all && done[r];
-    }
-    long long used = 0;
-    for (int r = 0; r < nrhs; r++) used = std::max(used, iters[r]);
-    if (all || outer >= c->prm.max_outer || used >= c->prm.maxit) break;
-    outer++;
-    // inner right-hand side: the FP64 residual, scaled by a power of two per RHS
-    double sr[kMaxRhs], bn2[kMaxRhs];
-    for (int r = 0; r < nrhs; r++) {
-      const double rn = rel[r] * std::sqrt(c->bnorm2[r] > 0 ? c->bnorm2[r] : 1.0);
-      sr[r] = pow2_near(rn / std::sqrt((double)std::max(n, 1)));
-      bn2[r] = rn * rn * sr[r] * sr[r];
-    }
-    to_policy(c, c->r64, c->bp, sr);
-    std::vector<RhsState> st(nrhs);
-    init_state(c, st.data(), bn2);
-    for (int r = 0; r < nrhs; r++)
-      if (done[r]) { st[r].done = 1; st[r].status = kOk; }
-    if (m > 0) CK(cudaMemsetAsync(c->x[0], 0, (size_t)m * xelem_bytes(c->pol), s));
-    const long long budget = std::max<long long>(1, c->prm.maxit - used);
-    aj_status rs = run_persistent(c, st, c->bp, budget, AJ_STOP_RELRES, c->prm.inner_tol, 0.0, 1.0, true);
-    if (rs != AJ_OK) return rs;
-    e = fetch_rlog(c, st, true);
-    if (e != AJ_OK) return e;
-    // x += (sQ / sr) * d for the RHS that were still running
-    int cur[kMaxRhs];
-    double osc[kMaxRhs];
-    for (int r = 0; r < nrhs; r++) {
-      cur[r] = st[r].cur;
-      osc[r] = c->sQ / sr[r];
-    }
-    e = from_policy(c, cur, osc, c->tmp64);
-    if (e != AJ_OK) return e;
-    unsigned mask = 0;
-    for (int r = 0; r < nrhs; r++)
-      if (!done[r]) {
-        mask |= 1u << r;
-        iters[r] += st[r].t_final;
-        rest[r] += st[r].ell;
-        if (st[r].status == kENonfinite || st[r].status == kEDiverged) {
-          done[r] = true;
-          status[r] = st[r].status;
-        }
-      }
-    if (m > 0) {
-      k_axpy_masked<<<grid1d(m), kSetupThreads, 0, s>>>(m, nrhs, mask, c->tmp64, 1.0, c->x64);
-      counted();
-    }
-    CK(cudaGetLastError());
+    const long long m = (long long)c->n * c->nrhs;
+    if (m > 0) CK(cudaMemcpyAsync(c->x64, c->tmp64, (size_t)m * 8, cudaMemcpyDeviceToDevice, c->stream));
+    c->rlog_h.assign(c->nrhs, {});
   }
-  e = write_output(c, c->x64, x_out, x_on_device);
-  if (e != AJ_OK) return e;
-  for (int r = 0; r < nrhs; r++) {
-    per[r].iters = iters[r];
-    per[r].restarts = rest[r];
-    per[r].sweeps = iters[r] + outer;
-    per[r].outer = outer;
-    per[r].relres = rel[r];
-    per[r].objgap = og[r];
-    per[r].L_used = c->L_used;
-    per[r].status = done[r] ? status_of(status[r]) : AJ_EMAXIT;
+  for (;;) {
+    std::vector<int> act;
+    for (int i = 0; i < count; i++) {
+      IrRun& q = R[i];
+      if (q.finished) continue;
+      aj_ctx* c = cs[i];
+      aj_status e = fp64_report(c, c->x64, q.rel, q.og, c->r64);
+      if (e != AJ_OK) return e;
+      bool all = true;
+      for (int r = 0; r < c->nrhs; r++) {
+        if (q.done[r]) continue;
+        bool ok = false;
+        if (c->prm.stop == AJ_STOP_RELRES) ok = q.rel[r] <= c->prm.tol;
+        else if (c->prm.stop == AJ_STOP_OBJGAP) ok = q.og[r] <= c->prm.tol;
+        if (ok) { q.done[r] = true; q.status[r] = kOk; }
+        else if (!std::isfinite(q.rel[r])) { q.done[r] = true; q.status[r] = kENonfinite; }
+        all = all && q.done[r];
+      }
+      long long used = 0;
+      for (int r = 0; r < c->nrhs; r++) used = std::max(used, q.iters[r]);
+      if (all || q.outer >= c->prm.max_outer || used >= c->prm.maxit) q.finished = true;
+      else act.push_back(i);
+    }
+    if (act.empty()) break;
+    std::vector<BatchItem> items;
+    for (int i : act) {
+      IrRun& q = R[i];
+      aj_ctx* c = cs[i];
+      const int n = (int)c->n;
+      const long long m = (long long)n * c->nrhs;
+      q.outer++;
+      // inner right-hand side: the FP64 residual, scaled by a power of two per RHS
+      double bn2[kMaxRhs];
+      for (int r = 0; r < c->nrhs; r++) {
+        const double rn = q.rel[r] * std::sqrt(c->bnorm2[r] > 0 ? c->bnorm2[r] : 1.0);
+        q.sr[r] = pow2_near(rn / std::sqrt((double)std::max(n, 1)));
+        bn2[r] = rn * rn * q.sr[r] * q.sr[r];
+      }
+      to_policy(c, c->r64, c->bp, q.sr);
+      q.st.assign(c->nrhs, RhsState());
+      init_state(c, q.st.data(), bn2);
+      for (int r = 0; r < c->nrhs; r++)
+        if (q.done[r]) { q.st[r].done = 1; q.st[r].status = kOk; }
+      if (m > 0) CK(cudaMemsetAsync(c->x[0], 0, (size_t)m * xelem_bytes(c->pol), c->stream));
+      long long used = 0;
+      for (int r = 0; r < c->nrhs; r++) used = std::max(used, q.iters[r]);
+      const long long budget = std::max<long long>(1, c->prm.maxit - used);
+      items.push_back({c, &q.st, c->bp, budget, AJ_STOP_RELRES, c->prm.inner_tol, 0.0, 1.0});
+    }
+    if (batched) {
+      aj_status e = run_batched(items, true, batch_kms);
+      if (e != AJ_OK) return e;
+    } else {
+      for (auto& it : items) {
+        aj_status e = run_persistent(it.c, *it.st, it.bvec, it.maxit, it.stop, it.tol, it.fstar,
+                                     it.fscale, true);
+        if (e != AJ_OK) return e;
+      }
+    }
+    for (int i : act) {
+      IrRun& q = R[i];
+      aj_ctx* c = cs[i];
+      const long long m = (long long)c->n * c->nrhs;
+      aj_status e = fetch_rlog(c, q.st, true);
+      if (e != AJ_OK) return e;
+      // x += (sQ / sr) * d for the RHS that were still running
+      int cur[kMaxRhs];
+      double osc[kMaxRhs];
+      for (int r = 0; r < c->nrhs; r++) {
+        cur[r] = q.st[r].cur;
+        osc[r] = c->sQ / q.sr[r];
+      }
+      e = from_policy(c, cur, osc, c->tmp64);
+      if (e != AJ_OK) return e;
+      unsigned mask = 0;
+      for (int r = 0; r < c->nrhs; r++)
+        if (!q.done[r]) {
+          mask |= 1u << r;
+          q.iters[r] += q.st[r].t_final;
+          q.rest[r] += q.st[r].ell;
+          if (q.st[r].status == kENonfinite || q.st[r].status == kEDiverged) {
+            q.done[r] = true;
+            q.status[r] = q.st[r].status;
+          }
+        }
+      if (m > 0) {
+        k_axpy_masked<<<grid1d(m), kSetupThreads, 0, c->stream>>>(m, c->nrhs, mask, c->tmp64, 1.0, c->x64);
+        counted();
+      }
+      CK(cudaGetLastError());
+    }
+  }
+  for (int i = 0; i < count; i++) {
+    IrRun& q = R[i];
+    aj_ctx* c = cs[i];
+    aj_status e = write_output(c, c->x64, x_out[i], x_on_device);
+    if (e != AJ_OK) return e;
+    for (int r = 0; r < c->nrhs; r++) {
+      aj_info& o = per[i][r];
+      o.iters = q.iters[r];
+      o.restarts = q.rest[r];
+      o.sweeps = q.iters[r] + q.outer;
+      o.outer = q.outer;
+      o.relres = q.rel[r];
+      o.objgap = q.og[r];
+      o.L_used = c->L_used;
+      o.status = q.done[r] ? status_of(q.status[r]) : AJ_EMAXIT;
+    }
   }
   return AJ_OK;
+}
+
+static aj_status solve_ir(aj_ctx* c, double* x_out, int x_on_device, aj_info* per) {
+  aj_ctx* cs[1] = {c};
+  double* xo[1] = {x_out};
+  aj_info* pp[1] = {per};
+  return ir_solve(cs, 1, xo, x_on_device, pp, false, nullptr);
+}
+
+// The report of the right-hand side with the worst residual, with the largest
+// iteration and restart counts over all right-hand sides.
+static void summarize(const aj_info* per, int nrhs, aj_info* out) {
+  int w = 0;
+  for (int r = 1; r < nrhs; r++)
+    if (per[r].status != AJ_OK || per[r].relres > per[w].relres) w = r;
+  *out = per[w];
+  long long it = 0, rs = 0;
+  for (int r = 0; r < nrhs; r++) {
+    it = std::max<long long>(it, per[r].iters);
+    rs = std::max<long long>(rs, per[r].restarts);
+  }
+  out->iters = it;
+  out->restarts = rs;
 }
 
 extern "C" aj_status aj_solve_rhs(aj_ctx* c, double* x_out, int x_on_device, aj_info* per_rhs) {
@@ -951,18 +1263,7 @@ extern "C" aj_status aj_solve(aj_ctx* c, double* x_out, int x_on_device, aj_info
   std::memset(per, 0, sizeof(per));
   aj_status st = aj_solve_rhs(c, x_out, x_on_device, per);
   if (info && (st == AJ_OK || st == AJ_EMAXIT || st == AJ_EDIVERGED || st == AJ_ENONFINITE)) {
-    // report the right-hand side with the worst residual
-    int w = 0;
-    for (int r = 1; r < c->nrhs; r++)
-      if (per[r].status != AJ_OK || per[r].relres > per[w].relres) w = r;
-    *info = per[w];
-    long long it = 0, rs = 0;
-    for (int r = 0; r < c->nrhs; r++) {
-      it = std::max<long long>(it, per[r].iters);
-      rs = std::max<long long>(rs, per[r].restarts);
-    }
-    info->iters = it;
-    info->restarts = rs;
+    summarize(per, c->nrhs, info);
   } else if (info) {
     std::memset(info, 0, sizeof(*info));
     info->status = st;
@@ -1047,16 +1348,80 @@ extern "C" aj_status aj_set_state(aj_ctx* c, const void* buf, size_t size) {
   return AJ_OK;
 }
 
-// ---------------------------------------------------------------- batch (sequential for now)
+// ---------------------------------------------------------------- batch
 extern "C" aj_status aj_solve_batch(aj_ctx* const* ctx, int count, double* const* x_out,
                                     int x_on_device, aj_info* info) {
   if (count < 0 || (count > 0 && (!ctx || !x_out))) return AJ_EINVAL;
+  if (count == 0) return AJ_OK;
+  for (int i = 0; i < count; i++) {
+    if (!ctx[i] || (!x_out[i] && ctx[i]->n > 0)) return AJ_EINVAL;
+    for (int j = 0; j < i; j++)
+      if (ctx[j] == ctx[i]) return AJ_EINVAL;  // a context appears once
+  }
+  for (int i = 0; i < count; i++)
+    if (!ctx[i]->have_prm) {
+      aj_params p;
+      aj_params_default(&p);
+      aj_status st = aj_set(ctx[i], &p);
+      if (st != AJ_OK) return st;
+    }
+  aj_ctx* c0 = ctx[0];
+  for (int i = 1; i < count; i++)
+    if (ctx[i]->dev != c0->dev || ctx[i]->pol != c0->pol || ctx[i]->qx != c0->qx) return AJ_EINVAL;
+  int dev_prev = 0;
+  cudaGetDevice(&dev_prev);
+  if (dev_prev != c0->dev) cudaSetDevice(c0->dev);
+  // every context's GPU work runs on the first context's stream for the batch
+  std::vector<cudaStream_t> saved(count);
+  for (int i = 0; i < count; i++) {
+    saved[i] = ctx[i]->stream;
+    ctx[i]->stream = c0->stream;
+    ctx[i]->kernel_ms = 0.0;
+  }
+  t_launches = 0;
+  std::vector<aj_info> per((size_t)count * kMaxRhs);
+  std::memset(per.data(), 0, per.size() * sizeof(aj_info));
+  double kms = 0.0;
+  aj_status st = AJ_OK;
+  cudaEventRecord(c0->ev0, c0->stream);
+  if (c0->pol == AJ_FP64 || c0->pol == AJ_DF64) {
+    std::vector<DirectRun> d(count);
+    std::vector<BatchItem> items;
+    for (int i = 0; i < count && st == AJ_OK; i++) {
+      st = direct_prepare(ctx[i], d[i]);
+      items.push_back({ctx[i], &d[i].st, d[i].bvec, ctx[i]->prm.maxit, ctx[i]->prm.stop,
+                       ctx[i]->prm.tol, ctx[i]->prm.fstar, d[i].fscale});
+    }
+    if (st == AJ_OK) st = run_batched(items, true, &kms);
+    for (int i = 0; i < count && st == AJ_OK; i++)
+      st = direct_finish(ctx[i], d[i], x_out[i], x_on_device, per.data() + (size_t)i * kMaxRhs);
+  } else {
+    std::vector<aj_info*> pp(count);
+    for (int i = 0; i < count; i++) pp[i] = per.data() + (size_t)i * kMaxRhs;
+    st = ir_solve(ctx, count, x_out, x_on_device, pp.data(), true, &kms);
+  }
+  cudaEventRecord(c0->ev1, c0->stream);
+  cudaEventSynchronize(c0->ev1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c0->ev0, c0->ev1);
+  for (int i = 0; i < count; i++) {
+    ctx[i]->stream = saved[i];
+    ctx[i]->resume = false;
+  }
+  if (dev_prev != c0->dev) cudaSetDevice(dev_prev);
+  if (st != AJ_OK) return st;
   aj_status worst = AJ_OK;
   for (int i = 0; i < count; i++) {
-    aj_info inf;
-    aj_status st = aj_solve(ctx[i], x_out[i], x_on_device, &inf);
-    if (info) info[i] = inf;
-    if (st != AJ_OK && worst == AJ_OK) worst = st;
+    aj_info* pr = per.data() + (size_t)i * kMaxRhs;
+    for (int r = 0; r < ctx[i]->nrhs; r++) {
+      pr[r].ms = ms;
+      pr[r].kernel_ms = kms;
+      pr[r].launches = t_launches;
+    }
+    aj_info sum;
+    summarize(pr, ctx[i]->nrhs, &sum);
+    if (info) info[i] = sum;
+    if (sum.status != AJ_OK && worst == AJ_OK) worst = sum.status;
   }
   return worst;
 }

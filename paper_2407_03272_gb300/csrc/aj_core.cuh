@@ -425,7 +425,8 @@ __host__ __device__ constexpr int row_unroll(int nr, bool qx) {
 
 template <class P, int NR, bool QX>
 __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, bool compute_x,
-                                      bool want_obj, typename P::A (&acc)[NR][kNRed]) {
+                                      bool want_obj, typename P::A (&acc)[NR][kNRed], int cta,
+                                      int ncta) {
   using S = typename P::S;
   using V = typename P::V;
   using X = typename P::X;
@@ -451,7 +452,7 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
   }
   const int lane = threadIdx.x & 31;
   const int ntiles = (a.n + kThreads - 1) / kThreads;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int tile = cta; tile < ntiles; tile += ncta) {
     const int i = tile * kThreads + threadIdx.x;
     const bool valid = i < a.n;
     int rs = 0, re = 0;
@@ -627,9 +628,6 @@ __device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kN
   return all_done;
 }
 
-// The persistent fused AJ kernel.  Launch cooperatively with kThreads
-// threads per CTA.  Runs sweeps until every right-hand side is done or
-// max_sweeps sweeps have run.
 // Co-resident CTAs per SM the register allocation must allow.  The sweep is
 // latency bound (gathers from L2, the matrix stream from DRAM), so warps in
 // flight matter more than registers: measured on the 256^3 Poisson system,
@@ -637,29 +635,35 @@ __device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kN
 // right-hand side.  More right-hand sides need more registers per thread.
 __host__ __device__ constexpr int min_blocks(int nr) { return nr == 1 ? 4 : nr == 2 ? 2 : 1; }
 
+// Shared memory of one solve: per-RHS state, grid totals, reduction scratch.
+template <int NR>
+struct SolveSmem {
+  RhsState st[NR];
+  double tot[NR][kNRed];
+  double red[kWarps];
+  int done;
+};
+
+// Runs sweeps of one system on `ncta` co-resident CTAs (this one is `cta`)
+// until every right-hand side is done or a.max_sweeps sweeps have run.  The
+// state is in sm.st (identical in every CTA).  `target` is the barrier's
+// arrival count so far and `sw` the sweep counter that parity-buffers the
+// partials; both carry over between systems that reuse the same barrier.
+// Returns false when a barrier gave up (error already recorded in *a.err).
 template <class P, int NR, bool QX>
-__global__ void __launch_bounds__(kThreads, min_blocks(NR)) aj_persistent_kernel(IterArgs<P> a) {
+__device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem<NR>& sm, int cta,
+                                          int ncta, unsigned long long& target, long long& sw) {
   using A = typename P::A;
-  __shared__ RhsState st[NR];
-  __shared__ double s_tot[NR][kNRed];
-  __shared__ double s_red[kWarps];
-  __shared__ int s_done;
-  if (threadIdx.x < NR) st[threadIdx.x] = a.state[threadIdx.x];
-  __syncthreads();
-  const unsigned int G = gridDim.x;
-  unsigned long long target = 0;
-  bool want_obj = a.stop == kStopObjgap;
-  long long s0 = 0;  // sweep counter within this launch
-  bool finished = false;
-  for (s0 = 0; s0 < a.max_sweeps; s0++) {
+  const bool want_obj = a.stop == kStopObjgap;
+  for (long long s0 = 0; s0 < a.max_sweeps; s0++, sw++) {
     // sweep number in the run's own numbering: x^{s-1} is checked, x^s formed
     long long s_run = 0;
     bool compute_x = false;
 #pragma unroll
     for (int r = 0; r < NR; r++) {
-      if (!st[r].done) {
-        s_run = st[r].t + 1;
-        compute_x = compute_x || (st[r].t < a.maxit);
+      if (!sm.st[r].done) {
+        s_run = sm.st[r].t + 1;
+        compute_x = compute_x || (sm.st[r].t < a.maxit);
       }
     }
     A acc[NR][kNRed];
@@ -667,52 +671,117 @@ __global__ void __launch_bounds__(kThreads, min_blocks(NR)) aj_persistent_kernel
     for (int r = 0; r < NR; r++)
 #pragma unroll
       for (int k = 0; k < kNRed; k++) acc_zero(acc[r][k]);
-    sweep<P, NR, QX>(a, st, compute_x, want_obj, acc);
+    sweep<P, NR, QX>(a, sm.st, compute_x, want_obj, acc, cta, ncta);
     // CTA partials -> global (parity-buffered by sweep)
-    double* part = a.partials + (size_t)(s0 & 1) * G * NR * kNRed;
+    double* part = a.partials + (size_t)(sw & 1) * ncta * NR * kNRed;
 #pragma unroll
     for (int r = 0; r < NR; r++)
 #pragma unroll
       for (int k = 0; k < kNRed; k++) {
         if (!slot_used(k, want_obj)) continue;
-        const double v = block_sum(acc_value(acc[r][k]), s_red);
-        if (threadIdx.x == 0) __stcg(part + ((size_t)blockIdx.x * NR + r) * kNRed + k, v);
+        const double v = block_sum(acc_value(acc[r][k]), sm.red);
+        if (threadIdx.x == 0) __stcg(part + ((size_t)cta * NR + r) * kNRed + k, v);
       }
-    target += G;
-    if (!grid_sync(a.bar, target, a.err, G)) return;
+    target += (unsigned long long)ncta;
+    if (!grid_sync(a.bar, target, a.err, (unsigned)ncta)) return false;
     // every CTA sums the partials in the same fixed order
 #pragma unroll
     for (int r = 0; r < NR; r++)
 #pragma unroll
       for (int k = 0; k < kNRed; k++) {
         if (!slot_used(k, want_obj)) {
-          if (threadIdx.x == 0) s_tot[r][k] = 0.0;
+          if (threadIdx.x == 0) sm.tot[r][k] = 0.0;
           continue;
         }
         double v = 0.0;
-        for (unsigned int c = threadIdx.x; c < G; c += kThreads)
+        for (int c = threadIdx.x; c < ncta; c += kThreads)
           v += __ldcg(part + ((size_t)c * NR + r) * kNRed + k);
-        v = block_sum(v, s_red);
-        if (threadIdx.x == 0) s_tot[r][k] = v;
+        v = block_sum(v, sm.red);
+        if (threadIdx.x == 0) sm.tot[r][k] = v;
       }
     if (threadIdx.x == 0) {
-      if (a.trace && blockIdx.x == 0 && s_run >= 1 && s_run <= a.trace_cap) {
+      if (a.trace && cta == 0 && s_run >= 1 && s_run <= a.trace_cap) {
         for (int r = 0; r < NR; r++) {
           double* tr = a.trace + ((size_t)(s_run - 1) * NR + r) * 4;
-          tr[0] = s_tot[r][0];
-          tr[1] = s_tot[r][1];
-          tr[2] = s_tot[r][2];
-          tr[3] = st[r].beta;
+          tr[0] = sm.tot[r][0];
+          tr[1] = sm.tot[r][1];
+          tr[2] = sm.tot[r][2];
+          tr[3] = sm.st[r].beta;
         }
       }
-      s_done = scalar_step<NR>(st, s_tot, s_run, a.maxit, a.stop, a.restart, a.momentum, a.tol,
-                               a.fstar, a.fscale, a.rlog, a.rlog_cap, blockIdx.x == 0) ? 1 : 0;
+      sm.done = scalar_step<NR>(sm.st, sm.tot, s_run, a.maxit, a.stop, a.restart, a.momentum,
+                                a.tol, a.fstar, a.fscale, a.rlog, a.rlog_cap, cta == 0)
+                    ? 1
+                    : 0;
     }
     __syncthreads();
-    if (s_done) { finished = true; break; }
+    if (sm.done) {
+      sw++;
+      break;
+    }
   }
-  (void)finished;
-  if (blockIdx.x == 0 && threadIdx.x < NR) a.state[threadIdx.x] = st[threadIdx.x];
+  return true;
+}
+
+// The persistent fused AJ kernel for one system.  Launch cooperatively with
+// kThreads threads per CTA; every CTA of the grid works on the system.
+template <class P, int NR, bool QX>
+__global__ void __launch_bounds__(kThreads, min_blocks(NR)) aj_persistent_kernel(IterArgs<P> a) {
+  __shared__ SolveSmem<NR> sm;
+  if (threadIdx.x < NR) sm.st[threadIdx.x] = a.state[threadIdx.x];
+  __syncthreads();
+  unsigned long long target = 0;
+  long long sw = 0;
+  if (!run_solve<P, NR, QX>(a, sm, blockIdx.x, gridDim.x, target, sw)) return;
+  if (blockIdx.x == 0 && threadIdx.x < NR) a.state[threadIdx.x] = sm.st[threadIdx.x];
+}
+
+// ----------------------------------------------------------------------------
+// Many independent systems in one persistent launch.  The grid is cut into
+// gangs of co-resident CTAs (cta_gang[c] = {first CTA, size, class, gang id});
+// every gang of class k takes systems from the class's queue order[cls_begin[k]
+// .. cls_begin[k+1]) (largest first) through an atomic head, solves each one
+// with its own gang barrier and then takes the next.  Each system keeps its
+// own state, restart log and stop test; its arithmetic depends only on the
+// system and the gang size, not on the other systems in the batch.
+template <class P>
+struct BatchArgs {
+  const IterArgs<P>* sys;       // per system (partials, bar and err are ignored)
+  const int* order;             // system indices grouped by class
+  const int* cls_begin;         // [ncls + 1] offsets into order
+  int* cls_head;                // [ncls] queue heads, zero at launch
+  const int4* cta_gang;         // [grid]
+  unsigned long long* gang_bar; // [ngangs] barrier counters, zero at launch
+  int* gang_slot;               // [ngangs] system handed to the gang
+  double* gang_part;            // [grid][2][NR][kNRed] partials (indexed from the gang's first CTA)
+  int* err;                     // device error word, zero at launch
+};
+
+template <class P, int NR, bool QX>
+__global__ void __launch_bounds__(kThreads, min_blocks(NR)) aj_batched_kernel(BatchArgs<P> b) {
+  __shared__ SolveSmem<NR> sm;
+  const int4 g = b.cta_gang[blockIdx.x];
+  const int base = g.x, size = g.y, cls = g.z, gid = g.w;
+  const int rank = (int)blockIdx.x - base;
+  const int qbeg = b.cls_begin[cls], qlen = b.cls_begin[cls + 1] - qbeg;
+  unsigned long long target = 0;
+  long long sw = 0;
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) __stcg(b.gang_slot + gid, atomicAdd(b.cls_head + cls, 1));
+    target += (unsigned long long)size;
+    if (!grid_sync(b.gang_bar + gid, target, b.err, (unsigned)size)) return;
+    const int k = __ldcg(b.gang_slot + gid);
+    if (k >= qlen) break;
+    IterArgs<P> a = b.sys[b.order[qbeg + k]];
+    a.partials = b.gang_part + (size_t)base * 2 * NR * kNRed;
+    a.bar = b.gang_bar + gid;
+    a.err = b.err;
+    if (threadIdx.x < NR) sm.st[threadIdx.x] = a.state[threadIdx.x];
+    __syncthreads();
+    if (!run_solve<P, NR, QX>(a, sm, rank, size, target, sw)) return;
+    if (rank == 0 && threadIdx.x < NR) a.state[threadIdx.x] = sm.st[threadIdx.x];
+    __syncthreads();
+  }
 }
 
 }  // namespace aj

@@ -1,6 +1,8 @@
 // aj_kern_inst.cuh -- instantiates the persistent kernel of one precision
 // policy for 1..4 right-hand sides.  Included once per translation unit with
 // AJ_POL (policy type) and AJ_SUFFIX (name suffix) defined.
+#include <string.h>
+
 #include "aj_core.cuh"
 #include "aj_launch.h"
 
@@ -40,6 +42,34 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
 }
 
 template <class P, int NR>
+static cudaError_t launch_batched_nr(int qx, const BatchLaunch& B, int grid, cudaStream_t s) {
+  BatchArgs<P> b;
+  b.sys = static_cast<const IterArgs<P>*>(B.sys);
+  b.order = B.order;
+  b.cls_begin = B.cls_begin;
+  b.cls_head = B.cls_head;
+  b.cta_gang = B.cta_gang;
+  b.gang_bar = B.gang_bar;
+  b.gang_slot = B.gang_slot;
+  b.gang_part = B.gang_part;
+  b.err = B.err;
+  void* args[] = {&b};
+  const void* k = qx ? (const void*)aj_batched_kernel<P, NR, true>
+                     : (const void*)aj_batched_kernel<P, NR, false>;
+  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
+}
+
+template <class P, int NR>
+static int occ_batched_nr(int qx) {
+  int nb = 0;
+  cudaError_t e = qx ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                           &nb, aj_batched_kernel<P, NR, true>, kThreads, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                           &nb, aj_batched_kernel<P, NR, false>, kThreads, 0);
+  return e == cudaSuccess ? nb : 0;
+}
+
+template <class P, int NR>
 static cudaError_t launch_nr(const IterLaunch& L, int grid, cudaStream_t s) {
   IterArgs<P> a = typed_args<P>(L);
   void* args[] = {&a};
@@ -75,6 +105,33 @@ int AJ_CAT(blocks_per_sm_, AJ_SUFFIX)(int nrhs, int qx) {
     case 2: return occ_nr<AJ_POL, 2>(qx);
     case 3: return occ_nr<AJ_POL, 3>(qx);
     case 4: return occ_nr<AJ_POL, 4>(qx);
+  }
+  return 0;
+}
+
+void AJ_CAT(pack_iter_args_, AJ_SUFFIX)(const IterLaunch& L, void* dst) {
+  static_assert(sizeof(IterArgs<AJ_POL>) == sizeof(IterArgs<PolF64>), "one packed layout");
+  IterArgs<AJ_POL> a = typed_args<AJ_POL>(L);
+  memcpy(dst, &a, sizeof(a));
+}
+
+cudaError_t AJ_CAT(launch_batched_, AJ_SUFFIX)(int nrhs, int qx, const BatchLaunch& B, int grid,
+                                                cudaStream_t s) {
+  switch (nrhs) {
+    case 1: return launch_batched_nr<AJ_POL, 1>(qx, B, grid, s);
+    case 2: return launch_batched_nr<AJ_POL, 2>(qx, B, grid, s);
+    case 3: return launch_batched_nr<AJ_POL, 3>(qx, B, grid, s);
+    case 4: return launch_batched_nr<AJ_POL, 4>(qx, B, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int AJ_CAT(batched_blocks_per_sm_, AJ_SUFFIX)(int nrhs, int qx) {
+  switch (nrhs) {
+    case 1: return occ_batched_nr<AJ_POL, 1>(qx);
+    case 2: return occ_batched_nr<AJ_POL, 2>(qx);
+    case 3: return occ_batched_nr<AJ_POL, 3>(qx);
+    case 4: return occ_batched_nr<AJ_POL, 4>(qx);
   }
   return 0;
 }

@@ -37,6 +37,28 @@ struct IterLaunch {
   int qx;  // 1: stored sweep form (u = Q x kept), 0: lazy form (two row sums)
 };
 
+// Untyped mirror of BatchArgs<P>: many systems in one persistent launch.
+// `sys` is a device array of per-system kernel arguments packed with
+// pack_iter_args (the layout is the same for every precision policy).
+struct BatchLaunch {
+  const void* sys;
+  const int* order;
+  const int* cls_begin;
+  int* cls_head;
+  const int4* cta_gang;
+  unsigned long long* gang_bar;
+  int* gang_slot;
+  double* gang_part;
+  int* err;
+};
+
+// Size in bytes of one packed per-system argument block, and the packing.
+size_t iter_args_bytes();
+void pack_iter_args(int pol, const IterLaunch& L, void* dst);
+// Cooperative launch of the batched kernel and its co-resident CTAs per SM.
+cudaError_t launch_batched(int pol, int nrhs, int qx, const BatchLaunch& B, int grid, cudaStream_t s);
+int batched_blocks_per_sm(int pol, int nrhs, int qx);
+
 // Cooperative launch of the persistent kernel for precision `pol`
 // (0 F64, 1 DF64, 2 F32, 3 BF16), nrhs in [1, 4] and the sweep form L.qx.
 cudaError_t launch_persistent(int pol, int nrhs, const IterLaunch& L, int grid, cudaStream_t s);
@@ -51,5 +73,16 @@ int blocks_per_sm_f64(int nrhs, int qx);
 int blocks_per_sm_df64(int nrhs, int qx);
 int blocks_per_sm_f32(int nrhs, int qx);
 int blocks_per_sm_b16(int nrhs, int qx);
+
+#define AJ_DECLARE_BATCHED(suf)                                                              \
+  void pack_iter_args_##suf(const IterLaunch& L, void* dst);                                 \
+  cudaError_t launch_batched_##suf(int nrhs, int qx, const BatchLaunch& B, int grid,         \
+                                   cudaStream_t s);                                          \
+  int batched_blocks_per_sm_##suf(int nrhs, int qx);
+AJ_DECLARE_BATCHED(f64)
+AJ_DECLARE_BATCHED(df64)
+AJ_DECLARE_BATCHED(f32)
+AJ_DECLARE_BATCHED(b16)
+#undef AJ_DECLARE_BATCHED
 
 }  // namespace aj
