@@ -174,17 +174,58 @@ aj_status aj_solve_rhs(aj_ctx* ctx, double* x_out, int x_on_device, aj_info* inf
 aj_status aj_solve_batch(aj_ctx* const* ctx, int count, double* const* x_out, int x_on_device,
                          aj_info* info);
 
-/* Continuous-batching server: admits requests while device memory stays
- * within hbm_budget_bytes and at most max_slots are resident; converged
- * systems are retired after every sweep and their slots refilled. */
+/* Continuous-batching server (no counterpart in the paper; it serves many
+ * independent solves of Algorithm alg-jacobi at once).  A host thread runs
+ * rounds: one batched persistent launch over every admitted request, each
+ * running at most a few sweeps (about 1-4 ms of device time per round) from
+ * its device-resident iterate, momentum and restart state.  After a round the
+ * requests that met their stop test (or failed) are retired and queued
+ * requests are admitted, first fit in submission order, while the device
+ * memory of the admitted requests stays within hbm_budget_bytes and at most
+ * max_slots are admitted.  Cutting a solve into rounds does not change its
+ * arithmetic: a request computes exactly what aj_solve computes for the same
+ * system with grid_ctas equal to its gang size (see aj_solve_batch).
+ * The server runs on the device current at creation, on its own stream. */
 aj_status aj_server_create(size_t hbm_budget_bytes, int max_slots, aj_server** out);
-/* Queue ctx for solving (non-blocking).  The server keeps a reference to ctx
- * until aj_poll reports it finished; ctx must stay alive until then.
- * AJ_EBUSY if the request alone exceeds the budget. */
+/* Queue an existing context (its device memory counts against the budget
+ * while admitted).  Non-blocking.  The server uses ctx until aj_poll reports
+ * the request finished; the caller must not touch ctx until then.
+ * AJ_EBUSY if ctx alone exceeds the budget. */
 aj_status aj_submit(aj_server* s, aj_ctx* ctx, uint64_t* ticket);
+/* Queue a solve from the caller's data (Q, b as for aj_create, p as for
+ * aj_set; NULL p = defaults).  The server copies Q, b and p->x0 at once into
+ * host memory of its own; it allocates the device state only when the request
+ * is admitted and frees it when the request retires, so the budget bounds the
+ * device memory the server uses.  AJ_EBUSY if the request alone exceeds the
+ * budget. */
+aj_status aj_submit_csr(aj_server* s, const aj_csr* Q, const double* b, int nrhs,
+                        const aj_params* p, uint64_t* ticket);
 /* AJ_PENDING until the request has finished; then writes x_out (host, n x
- * nrhs) and info and returns the solve's status. */
+ * nrhs column-major; may be NULL) and info (may be NULL; info->ms is the
+ * wall time from submission to completion) and returns the solve's status.
+ * A finished request is reported once; an unknown ticket gives AJ_EINVAL. */
 aj_status aj_poll(aj_server* s, uint64_t ticket, double* x_out, aj_info* info);
+/* Block until the request has finished or timeout_ms has passed (< 0: no
+ * limit).  AJ_OK when it has finished (collect it with aj_poll), AJ_PENDING
+ * on timeout. */
+aj_status aj_server_wait(aj_server* s, uint64_t ticket, double timeout_ms);
+/* Server counters: rounds run, requests admitted and completed, the largest
+ * number admitted at once in a round and the largest admitted device memory
+ * (both show requests sharing the GPU), current use and queue length, and
+ * the device time of all rounds. */
+typedef struct {
+  uint64_t rounds;
+  uint64_t admitted;
+  uint64_t completed;
+  int64_t peak_active;
+  uint64_t peak_bytes;
+  uint64_t in_use_bytes;
+  int64_t queued;
+  double kernel_ms;
+} aj_server_stats;
+aj_status aj_server_get_stats(aj_server* s, aj_server_stats* out);
+/* Stop the server after its current round; unfinished requests are dropped
+ * (contexts submitted with aj_submit get their stream back). */
 void aj_server_destroy(aj_server* s);
 
 /* Solver state (x^t, x^{t-1}, alpha_t, t, l, K_l, K_re per right-hand side)

@@ -51,6 +51,15 @@ class aj_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class aj_server_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("peak_active", ctypes.c_int64), ("peak_bytes", ctypes.c_uint64),
+                ("in_use_bytes", ctypes.c_uint64), ("queued", ctypes.c_int64), ("kernel_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class AJError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -76,6 +85,10 @@ SIGNATURES = [
     ("aj_server_create", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     ("aj_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     ("aj_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(aj_info)]),
+    ("aj_submit_csr", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(aj_csr), ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.POINTER(aj_params), ctypes.POINTER(ctypes.c_uint64)]),
+    ("aj_server_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double]),
+    ("aj_server_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(aj_server_stats)]),
     ("aj_server_destroy", None, [ctypes.c_void_p]),
     ("aj_get_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     ("aj_set_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
@@ -267,3 +280,77 @@ def solve_noalloc(row_ptr, col, val, b, x_out, stream=None, **kw):
     st = lib().aj_solve_noalloc(ctypes.byref(csr), ptrs[3][0], ctypes.byref(p), ptrs[4][0],
                                 ctypes.byref(inf), ctypes.c_void_p(s))
     return st, inf.as_dict()
+
+
+class Server:
+    """Continuous-batching solve server (aj_server_*)."""
+
+    def __init__(self, hbm_budget_bytes, max_slots):
+        h = ctypes.c_void_p()
+        _check(lib().aj_server_create(ctypes.c_size_t(int(hbm_budget_bytes)), int(max_slots),
+                                      ctypes.byref(h)), "aj_server_create")
+        self._h = h
+        self._meta = {}
+
+    def submit(self, ctx):
+        t = ctypes.c_uint64()
+        _check(lib().aj_submit(self._h, ctx.handle, ctypes.byref(t)), "aj_submit")
+        self._meta[t.value] = (ctx.n, ctx.nrhs, ctx)
+        return t.value
+
+    def submit_csr(self, Q, b, nrhs=1, **kw):
+        """Q: synth-style CSR dict (host numpy); b: n*nrhs column-major."""
+        rp = np.ascontiguousarray(Q["row_ptr"], np.int32)
+        ci = np.ascontiguousarray(Q["col"], np.int32)
+        v = np.ascontiguousarray(Q["val"], np.float64)
+        bb = np.ascontiguousarray(b, np.float64)
+        csr = aj_csr(int(Q["n"]), int(ci.size), rp.ctypes.data, ci.ctypes.data, v.ctypes.data, 0)
+        p = params(**kw)
+        x0 = kw.get("x0")
+        if x0 is not None:
+            x0 = np.ascontiguousarray(x0, np.float64)
+            p.x0, p.x0_on_device = x0.ctypes.data, 0
+        t = ctypes.c_uint64()
+        _check(lib().aj_submit_csr(self._h, ctypes.byref(csr), bb.ctypes.data, int(nrhs), ctypes.byref(p),
+                                   ctypes.byref(t)), "aj_submit_csr")
+        self._meta[t.value] = (int(Q["n"]), int(nrhs), None)
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else (status, x, info)."""
+        n, nrhs, _ = self._meta[ticket]
+        x = np.empty(n * nrhs, dtype=np.float64)
+        inf = aj_info()
+        st = lib().aj_poll(self._h, ctypes.c_uint64(ticket), x.ctypes.data, ctypes.byref(inf))
+        if st == AJ_PENDING:
+            return None
+        if st == AJ_EINVAL:
+            raise AJError(st, "aj_poll")
+        del self._meta[ticket]
+        return st, x, inf.as_dict()
+
+    def wait(self, ticket, timeout_ms=-1.0):
+        return lib().aj_server_wait(self._h, ctypes.c_uint64(ticket), float(timeout_ms))
+
+    def result(self, ticket):
+        """Block until the request finishes; (status, x, info)."""
+        st = self.wait(ticket)
+        if st not in (AJ_OK, AJ_PENDING):
+            raise AJError(st, "aj_server_wait")
+        return self.poll(ticket)
+
+    def stats(self):
+        st = aj_server_stats()
+        _check(lib().aj_server_get_stats(self._h, ctypes.byref(st)), "aj_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().aj_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -10,7 +10,12 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <map>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -697,6 +702,7 @@ struct BatchItem {
   long long maxit;
   int stop;
   double tol, fstar, fscale;
+  long long max_sweeps;  // sweeps this launch may run (maxit + 2: to the end)
 };
 
 static int pow2_ceil(long long v) {
@@ -815,6 +821,7 @@ static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, d
     for (int j = 0; j < m; j++) {
       const BatchItem& it = items[idx[j]];
       IterLaunch L = make_launch(it.c, it.bvec, it.maxit, it.stop, it.tol, it.fstar, it.fscale);
+      L.max_sweeps = it.max_sweeps;
       pack_iter_args(pol, L, sysh.data() + (size_t)j * abytes);
     }
     void* d_sys = ws.alloc(sysh.size());
@@ -1062,7 +1069,8 @@ static aj_status solve_direct(aj_ctx* c, double* x_out, int x_on_device, aj_info
 // one or many contexts: each outer step computes the FP64 residual of every
 // unfinished context, solves Q d = r in the iteration precision (one
 // persistent launch per context, or one batched launch for all of them) and
-// adds d to the FP64 iterate.
+// adds d to the FP64 iterate.  The steps are separate functions so that the
+// server can drive one context through them between its rounds.
 struct IrRun {
   long long iters[kMaxRhs] = {0, 0, 0, 0}, rest[kMaxRhs] = {0, 0, 0, 0};
   int status[kMaxRhs] = {kEMaxit, kEMaxit, kEMaxit, kEMaxit};
@@ -1073,66 +1081,129 @@ struct IrRun {
   std::vector<RhsState> st;
 };
 
+// x64 = x^0.
+static aj_status ir_begin(aj_ctx* c, IrRun& q) {
+  aj_status e = load_x0(c);
+  if (e != AJ_OK) return e;
+  const long long m = (long long)c->n * c->nrhs;
+  if (m > 0) CK(cudaMemcpyAsync(c->x64, c->tmp64, (size_t)m * 8, cudaMemcpyDeviceToDevice, c->stream));
+  c->rlog_h.assign(c->nrhs, {});
+  (void)q;
+  return AJ_OK;
+}
+
+// FP64 residual of x64 and the outer stop test; sets q.finished.
+static aj_status ir_check(aj_ctx* c, IrRun& q) {
+  aj_status e = fp64_report(c, c->x64, q.rel, q.og, c->r64);
+  if (e != AJ_OK) return e;
+  bool all = true;
+  for (int r = 0; r < c->nrhs; r++) {
+    if (q.done[r]) continue;
+    bool ok = false;
+    if (c->prm.stop == AJ_STOP_RELRES) ok = q.rel[r] <= c->prm.tol;
+    else if (c->prm.stop == AJ_STOP_OBJGAP) ok = q.og[r] <= c->prm.tol;
+    if (ok) { q.done[r] = true; q.status[r] = kOk; }
+    else if (!std::isfinite(q.rel[r])) { q.done[r] = true; q.status[r] = kENonfinite; }
+    all = all && q.done[r];
+  }
+  long long used = 0;
+  for (int r = 0; r < c->nrhs; r++) used = std::max(used, q.iters[r]);
+  if (all || q.outer >= c->prm.max_outer || used >= c->prm.maxit) q.finished = true;
+  return AJ_OK;
+}
+
+// Inner right-hand side (the residual scaled by a power of two per RHS), the
+// inner state and x = 0; returns the inner run as a batch item.
+static BatchItem ir_inner_setup(aj_ctx* c, IrRun& q) {
+  const int n = (int)c->n;
+  const long long m = (long long)n * c->nrhs;
+  q.outer++;
+  double bn2[kMaxRhs];
+  for (int r = 0; r < c->nrhs; r++) {
+    const double rn = q.rel[r] * std::sqrt(c->bnorm2[r] > 0 ? c->bnorm2[r] : 1.0);
+    q.sr[r] = pow2_near(rn / std::sqrt((double)std::max(n, 1)));
+    bn2[r] = rn * rn * q.sr[r] * q.sr[r];
+  }
+  to_policy(c, c->r64, c->bp, q.sr);
+  q.st.assign(c->nrhs, RhsState());
+  init_state(c, q.st.data(), bn2);
+  for (int r = 0; r < c->nrhs; r++)
+    if (q.done[r]) { q.st[r].done = 1; q.st[r].status = kOk; }
+  if (m > 0) cudaMemsetAsync(c->x[0], 0, (size_t)m * xelem_bytes(c->pol), c->stream);
+  long long used = 0;
+  for (int r = 0; r < c->nrhs; r++) used = std::max(used, q.iters[r]);
+  const long long budget = std::max<long long>(1, c->prm.maxit - used);
+  return BatchItem{c, &q.st, c->bp, budget, AJ_STOP_RELRES, c->prm.inner_tol, 0.0, 1.0, budget + 2};
+}
+
+// x64 += (sQ / sr) d for the right-hand sides that were still running.
+static aj_status ir_inner_finish(aj_ctx* c, IrRun& q) {
+  const long long m = (long long)c->n * c->nrhs;
+  aj_status e = fetch_rlog(c, q.st, true);
+  if (e != AJ_OK) return e;
+  int cur[kMaxRhs];
+  double osc[kMaxRhs];
+  for (int r = 0; r < c->nrhs; r++) {
+    cur[r] = q.st[r].cur;
+    osc[r] = c->sQ / q.sr[r];
+  }
+  e = from_policy(c, cur, osc, c->tmp64);
+  if (e != AJ_OK) return e;
+  unsigned mask = 0;
+  for (int r = 0; r < c->nrhs; r++)
+    if (!q.done[r]) {
+      mask |= 1u << r;
+      q.iters[r] += q.st[r].t_final;
+      q.rest[r] += q.st[r].ell;
+      if (q.st[r].status == kENonfinite || q.st[r].status == kEDiverged) {
+        q.done[r] = true;
+        q.status[r] = q.st[r].status;
+      }
+    }
+  if (m > 0) {
+    k_axpy_masked<<<grid1d(m), kSetupThreads, 0, c->stream>>>(m, c->nrhs, mask, c->tmp64, 1.0, c->x64);
+    counted();
+  }
+  CK(cudaGetLastError());
+  return AJ_OK;
+}
+
+static aj_status ir_end(aj_ctx* c, IrRun& q, double* x_out, int x_on_device, aj_info* per) {
+  aj_status e = write_output(c, c->x64, x_out, x_on_device);
+  if (e != AJ_OK) return e;
+  for (int r = 0; r < c->nrhs; r++) {
+    aj_info& o = per[r];
+    o.iters = q.iters[r];
+    o.restarts = q.rest[r];
+    o.sweeps = q.iters[r] + q.outer;
+    o.outer = q.outer;
+    o.relres = q.rel[r];
+    o.objgap = q.og[r];
+    o.L_used = c->L_used;
+    o.status = q.done[r] ? status_of(q.status[r]) : AJ_EMAXIT;
+  }
+  return AJ_OK;
+}
+
 static aj_status ir_solve(aj_ctx* const* cs, int count, double* const* x_out, int x_on_device,
                           aj_info* const* per, bool batched, double* batch_kms) {
   std::vector<IrRun> R(count);
   for (int i = 0; i < count; i++) {
-    aj_ctx* c = cs[i];
-    aj_status e = load_x0(c);
+    aj_status e = ir_begin(cs[i], R[i]);
     if (e != AJ_OK) return e;
-    const long long m = (long long)c->n * c->nrhs;
-    if (m > 0) CK(cudaMemcpyAsync(c->x64, c->tmp64, (size_t)m * 8, cudaMemcpyDeviceToDevice, c->stream));
-    c->rlog_h.assign(c->nrhs, {});
   }
   for (;;) {
     std::vector<int> act;
     for (int i = 0; i < count; i++) {
-      IrRun& q = R[i];
-      if (q.finished) continue;
-      aj_ctx* c = cs[i];
-      aj_status e = fp64_report(c, c->x64, q.rel, q.og, c->r64);
+      if (R[i].finished) continue;
+      aj_status e = ir_check(cs[i], R[i]);
       if (e != AJ_OK) return e;
-      bool all = true;
-      for (int r = 0; r < c->nrhs; r++) {
-        if (q.done[r]) continue;
-        bool ok = false;
-        if (c->prm.stop == AJ_STOP_RELRES) ok = q.rel[r] <= c->prm.tol;
-        else if (c->prm.stop == AJ_STOP_OBJGAP) ok = q.og[r] <= c->prm.tol;
-        if (ok) { q.done[r] = true; q.status[r] = kOk; }
-        else if (!std::isfinite(q.rel[r])) { q.done[r] = true; q.status[r] = kENonfinite; }
-        all = all && q.done[r];
-      }
-      long long used = 0;
-      for (int r = 0; r < c->nrhs; r++) used = std::max(used, q.iters[r]);
-      if (all || q.outer >= c->prm.max_outer || used >= c->prm.maxit) q.finished = true;
-      else act.push_back(i);
+      if (!R[i].finished) act.push_back(i);
     }
     if (act.empty()) break;
     std::vector<BatchItem> items;
-    for (int i : act) {
-      IrRun& q = R[i];
-      aj_ctx* c = cs[i];
-      const int n = (int)c->n;
-      const long long m = (long long)n * c->nrhs;
-      q.outer++;
-      // inner right-hand side: the FP64 residual, scaled by a power of two per RHS
-      double bn2[kMaxRhs];
-      for (int r = 0; r < c->nrhs; r++) {
-        const double rn = q.rel[r] * std::sqrt(c->bnorm2[r] > 0 ? c->bnorm2[r] : 1.0);
-        q.sr[r] = pow2_near(rn / std::sqrt((double)std::max(n, 1)));
-        bn2[r] = rn * rn * q.sr[r] * q.sr[r];
-      }
-      to_policy(c, c->r64, c->bp, q.sr);
-      q.st.assign(c->nrhs, RhsState());
-      init_state(c, q.st.data(), bn2);
-      for (int r = 0; r < c->nrhs; r++)
-        if (q.done[r]) { q.st[r].done = 1; q.st[r].status = kOk; }
-      if (m > 0) CK(cudaMemsetAsync(c->x[0], 0, (size_t)m * xelem_bytes(c->pol), c->stream));
-      long long used = 0;
-      for (int r = 0; r < c->nrhs; r++) used = std::max(used, q.iters[r]);
-      const long long budget = std::max<long long>(1, c->prm.maxit - used);
-      items.push_back({c, &q.st, c->bp, budget, AJ_STOP_RELRES, c->prm.inner_tol, 0.0, 1.0});
-    }
+    for (int i : act) items.push_back(ir_inner_setup(cs[i], R[i]));
+    CK(cudaGetLastError());
     if (batched) {
       aj_status e = run_batched(items, true, batch_kms);
       if (e != AJ_OK) return e;
@@ -1144,54 +1215,13 @@ static aj_status ir_solve(aj_ctx* const* cs, int count, double* const* x_out, in
       }
     }
     for (int i : act) {
-      IrRun& q = R[i];
-      aj_ctx* c = cs[i];
-      const long long m = (long long)c->n * c->nrhs;
-      aj_status e = fetch_rlog(c, q.st, true);
+      aj_status e = ir_inner_finish(cs[i], R[i]);
       if (e != AJ_OK) return e;
-      // x += (sQ / sr) * d for the RHS that were still running
-      int cur[kMaxRhs];
-      double osc[kMaxRhs];
-      for (int r = 0; r < c->nrhs; r++) {
-        cur[r] = q.st[r].cur;
-        osc[r] = c->sQ / q.sr[r];
-      }
-      e = from_policy(c, cur, osc, c->tmp64);
-      if (e != AJ_OK) return e;
-      unsigned mask = 0;
-      for (int r = 0; r < c->nrhs; r++)
-        if (!q.done[r]) {
-          mask |= 1u << r;
-          q.iters[r] += q.st[r].t_final;
-          q.rest[r] += q.st[r].ell;
-          if (q.st[r].status == kENonfinite || q.st[r].status == kEDiverged) {
-            q.done[r] = true;
-            q.status[r] = q.st[r].status;
-          }
-        }
-      if (m > 0) {
-        k_axpy_masked<<<grid1d(m), kSetupThreads, 0, c->stream>>>(m, c->nrhs, mask, c->tmp64, 1.0, c->x64);
-        counted();
-      }
-      CK(cudaGetLastError());
     }
   }
   for (int i = 0; i < count; i++) {
-    IrRun& q = R[i];
-    aj_ctx* c = cs[i];
-    aj_status e = write_output(c, c->x64, x_out[i], x_on_device);
+    aj_status e = ir_end(cs[i], R[i], x_out[i], x_on_device, per[i]);
     if (e != AJ_OK) return e;
-    for (int r = 0; r < c->nrhs; r++) {
-      aj_info& o = per[i][r];
-      o.iters = q.iters[r];
-      o.restarts = q.rest[r];
-      o.sweeps = q.iters[r] + q.outer;
-      o.outer = q.outer;
-      o.relres = q.rel[r];
-      o.objgap = q.og[r];
-      o.L_used = c->L_used;
-      o.status = q.done[r] ? status_of(q.status[r]) : AJ_EMAXIT;
-    }
   }
   return AJ_OK;
 }
@@ -1390,7 +1420,7 @@ extern "C" aj_status aj_solve_batch(aj_ctx* const* ctx, int count, double* const
     for (int i = 0; i < count && st == AJ_OK; i++) {
       st = direct_prepare(ctx[i], d[i]);
       items.push_back({ctx[i], &d[i].st, d[i].bvec, ctx[i]->prm.maxit, ctx[i]->prm.stop,
-                       ctx[i]->prm.tol, ctx[i]->prm.fstar, d[i].fscale});
+                       ctx[i]->prm.tol, ctx[i]->prm.fstar, d[i].fscale, ctx[i]->prm.maxit + 2});
     }
     if (st == AJ_OK) st = run_batched(items, true, &kms);
     for (int i = 0; i < count && st == AJ_OK; i++)
@@ -1426,61 +1456,372 @@ extern "C" aj_status aj_solve_batch(aj_ctx* const* ctx, int count, double* const
   return worst;
 }
 
-// ---------------------------------------------------------------- server (first version:
-// requests run in submission order when polled)
-#include <deque>
-#include <map>
+// ---------------------------------------------------------------- server
+// Continuous batching.  A host thread runs rounds: one batched launch over
+// every admitted request, each running at most `round_sweeps` sweeps from its
+// resident state.  After a round, finished requests are retired (their device
+// memory freed when the server created it) and queued requests are admitted,
+// first fit, while the device-memory budget and the slot count allow.  The
+// sweep sequence of a request does not depend on where rounds cut it, so its
+// result equals a solo run with the same gang size.
+struct ServerReq {
+  uint64_t ticket = 0;
+  aj_ctx* c = nullptr;
+  bool owned = false;  // created by the server from a host copy (aj_submit_csr)
+  int64_t n = 0, nnz = 0;
+  int nrhs = 1;
+  std::vector<int32_t> rp, ci;
+  std::vector<double> val, b, x0;
+  aj_params prm;
+  size_t bytes = 0;
+  cudaStream_t user_stream = nullptr;
+  std::chrono::steady_clock::time_point t_submit;
+  bool ir = false;
+  DirectRun d;
+  IrRun q;
+  BatchItem item;
+};
+
+struct ServerDone {
+  aj_status st = AJ_OK;
+  aj_info info;
+  std::vector<double> x;
+};
+
 struct aj_server {
   size_t budget = 0;
   int max_slots = 1;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  long long round_sweeps = 32;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<ServerReq*> queue;
+  std::vector<ServerReq*> active;
+  std::map<uint64_t, ServerDone> done;
+  std::map<uint64_t, int> pending;  // tickets submitted and not yet finished
+  size_t in_use = 0;
   uint64_t next = 1;
-  std::deque<std::pair<uint64_t, aj_ctx*>> queue;
-  struct Done {
-    aj_status st;
-    aj_info info;
-    std::vector<double> x;
-  };
-  std::map<uint64_t, Done> done;
+  bool stop = false;
+  std::thread th;
+  aj_server_stats stats;
 };
 
 static size_t ctx_bytes(const aj_ctx* c) { return c->base.bytes + c->pws.bytes; }
 
+// Device bytes a context of this shape allocates (aj_create + aj_set).
+static size_t estimate_bytes(int64_t n, int64_t nnz, int nrhs, int precision) {
+  const size_t m = (size_t)n * nrhs + 1;
+  const size_t xe = xelem_bytes(precision);
+  size_t v = (size_t)(n + 17) * 4 + (size_t)(nnz + 16) * 12 + (size_t)(n + 1) * 16 + m * 16;
+  v += (size_t)(n / kSetupThreads + 2) * kMaxRhs * 3 * 8;
+  if (precision != AJ_FP64) v += (size_t)(nnz + 16) * velem_bytes(precision) + m * xe + (size_t)(n + 1) * xe;
+  v += 5 * m * xe + 2 * m * 8;
+  v += (size_t)2 * 2048 * kMaxRhs * kNRed * 8 + 4096;
+  return v;
+}
+
+static void server_complete(aj_server* s, ServerReq* r, aj_status st, const aj_info* per,
+                            std::vector<double>&& x) {
+  ServerDone dn;
+  dn.st = st;
+  std::memset(&dn.info, 0, sizeof(dn.info));
+  if (per && r->c) summarize(per, r->c->nrhs, &dn.info);
+  dn.info.status = st == AJ_OK ? dn.info.status : st;
+  dn.info.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
+                                                         r->t_submit).count();
+  dn.x = std::move(x);
+  if (r->c) {
+    if (r->owned) aj_destroy(r->c);
+    else r->c->stream = r->user_stream;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->in_use -= std::min(s->in_use, r->bytes);
+  s->pending.erase(r->ticket);
+  s->stats.completed++;
+  s->done[r->ticket] = std::move(dn);
+  delete r;
+  s->cv.notify_all();
+}
+
+// Admission: create the context if the server owns it and start its run.
+static aj_status server_start(aj_server* s, ServerReq* r) {
+  if (r->owned) {
+    aj_csr Q;
+    Q.n = r->n;
+    Q.nnz = r->nnz;
+    Q.row_ptr = r->rp.data();
+    Q.col = r->ci.data();
+    Q.val = r->val.data();
+    Q.on_device = 0;
+    aj_status e = aj_create(&Q, r->b.data(), r->nrhs, &r->c);
+    if (e != AJ_OK) return e;
+    aj_set_stream(r->c, s->stream);
+    aj_params p = r->prm;
+    p.x0 = r->x0.empty() ? nullptr : r->x0.data();
+    p.x0_on_device = 0;
+    e = aj_set(r->c, &p);
+    if (e != AJ_OK) return e;
+    const size_t actual = ctx_bytes(r->c);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->in_use = s->in_use - std::min(s->in_use, r->bytes) + actual;
+    r->bytes = actual;
+  } else {
+    r->user_stream = r->c->stream;
+    r->c->stream = s->stream;
+    if (!r->c->have_prm) {
+      aj_params p;
+      aj_params_default(&p);
+      aj_status e = aj_set(r->c, &p);
+      if (e != AJ_OK) return e;
+    }
+  }
+  aj_ctx* c = r->c;
+  c->resume = false;
+  c->kernel_ms = 0.0;
+  CK(cudaMemsetAsync(c->rlog, 0xff, (size_t)kMaxRhs * c->rlog_cap * 8, s->stream));
+  r->ir = !(c->pol == AJ_FP64 || c->pol == AJ_DF64);
+  if (!r->ir) {
+    aj_status e = direct_prepare(c, r->d);
+    if (e != AJ_OK) return e;
+    r->item = {c, &r->d.st, r->d.bvec, c->prm.maxit, c->prm.stop, c->prm.tol, c->prm.fstar,
+               r->d.fscale, s->round_sweeps};
+  } else {
+    aj_status e = ir_begin(c, r->q);
+    if (e == AJ_OK) e = ir_check(c, r->q);
+    if (e != AJ_OK) return e;
+    if (!r->q.finished) r->item = ir_inner_setup(c, r->q);
+  }
+  CK(cudaGetLastError());
+  return AJ_OK;
+}
+
+// After a round: retire what finished, start the next inner solve of the
+// refinement requests.  Returns true when r is finished (completed).
+static bool server_advance(aj_server* s, ServerReq* r) {
+  aj_ctx* c = r->c;
+  aj_info per[kMaxRhs];
+  std::memset(per, 0, sizeof(per));
+  const size_t m = (size_t)c->n * c->nrhs;
+  std::vector<double> x(m);
+  aj_status e = AJ_OK;
+  if (!r->ir) {
+    for (int k = 0; k < c->nrhs; k++)
+      if (!r->d.st[k].done) return false;
+    e = direct_finish(c, r->d, x.data(), 0, per);
+  } else {
+    if (!r->q.finished) {
+      for (int k = 0; k < c->nrhs; k++)
+        if (!r->q.st[k].done) return false;
+      e = ir_inner_finish(c, r->q);
+      if (e == AJ_OK) e = ir_check(c, r->q);
+      if (e == AJ_OK && !r->q.finished) {
+        cudaMemsetAsync(c->rlog, 0xff, (size_t)kMaxRhs * c->rlog_cap * 8, s->stream);
+        r->item = ir_inner_setup(c, r->q);
+        return false;
+      }
+    }
+    if (e == AJ_OK) e = ir_end(c, r->q, x.data(), 0, per);
+  }
+  aj_status st = e;
+  if (st == AJ_OK)
+    for (int k = 0; k < c->nrhs; k++)
+      if (per[k].status != AJ_OK && st == AJ_OK) st = per[k].status;
+  server_complete(s, r, st, e == AJ_OK ? per : nullptr, std::move(x));
+  return true;
+}
+
+static void server_main(aj_server* s) {
+  cudaSetDevice(s->dev);
+  for (;;) {
+    std::vector<ServerReq*> admit;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->active.empty())
+        s->cv.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+      if (s->stop) break;
+      for (auto it = s->queue.begin(); it != s->queue.end();) {
+        if ((int)(s->active.size() + admit.size()) >= s->max_slots) break;
+        if (s->in_use + (*it)->bytes <= s->budget) {
+          s->in_use += (*it)->bytes;
+          s->stats.admitted++;
+          s->stats.peak_bytes = std::max<uint64_t>(s->stats.peak_bytes, s->in_use);
+          admit.push_back(*it);
+          it = s->queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    for (ServerReq* r : admit) {
+      aj_status e = server_start(s, r);
+      if (e != AJ_OK) server_complete(s, r, e, nullptr, {});
+      else if (r->ir && r->q.finished) server_advance(s, r);
+      else s->active.push_back(r);
+    }
+    if (s->active.empty()) continue;
+    // one round: a batched launch per (precision, sweep form) over every admitted request
+    std::map<std::pair<int, int>, std::vector<BatchItem>> groups;
+    for (ServerReq* r : s->active) {
+      r->item.max_sweeps = s->round_sweeps;
+      groups[{r->c->pol, r->c->qx}].push_back(r->item);
+    }
+    double kms = 0.0;
+    aj_status e = AJ_OK;
+    for (auto& g : groups) {
+      e = run_batched(g.second, false, &kms);
+      if (e != AJ_OK) break;
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->stats.rounds++;
+      s->stats.peak_active = std::max<int64_t>(s->stats.peak_active, (int64_t)s->active.size());
+      s->stats.kernel_ms += kms;
+    }
+    // keep a round between about 1 and 4 ms of device time
+    if (kms < 1.0 && s->round_sweeps < 1024) s->round_sweeps *= 2;
+    else if (kms > 4.0 && s->round_sweeps > 4) s->round_sweeps /= 2;
+    std::vector<ServerReq*> still;
+    for (ServerReq* r : s->active) {
+      if (e != AJ_OK) server_complete(s, r, e, nullptr, {});
+      else if (!server_advance(s, r)) still.push_back(r);
+    }
+    s->active.swap(still);
+  }
+  for (ServerReq* r : s->active) server_complete(s, r, AJ_ECUDA, nullptr, {});
+  s->active.clear();
+}
+
 extern "C" aj_status aj_server_create(size_t hbm_budget_bytes, int max_slots, aj_server** out) {
   if (!out || max_slots < 1 || hbm_budget_bytes == 0) return AJ_EINVAL;
+  *out = nullptr;
   aj_server* s = new aj_server();
   s->budget = hbm_budget_bytes;
   s->max_slots = max_slots;
+  std::memset(&s->stats, 0, sizeof(s->stats));
+  cudaGetDevice(&s->dev);
+  if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return AJ_ECUDA;
+  }
+  s->th = std::thread(server_main, s);
   *out = s;
+  return AJ_OK;
+}
+
+static aj_status server_enqueue(aj_server* s, ServerReq* r, uint64_t* ticket) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  r->ticket = s->next++;
+  r->t_submit = std::chrono::steady_clock::now();
+  s->pending[r->ticket] = 1;
+  s->queue.push_back(r);
+  *ticket = r->ticket;
+  s->cv.notify_all();
   return AJ_OK;
 }
 
 extern "C" aj_status aj_submit(aj_server* s, aj_ctx* c, uint64_t* ticket) {
   if (!s || !c || !ticket) return AJ_EINVAL;
-  if (ctx_bytes(c) > s->budget) return AJ_EBUSY;
-  *ticket = s->next++;
-  s->queue.emplace_back(*ticket, c);
-  return AJ_OK;
+  if (c->dev != s->dev) return AJ_EINVAL;
+  const size_t bytes = ctx_bytes(c);
+  if (bytes > s->budget) return AJ_EBUSY;
+  ServerReq* r = new ServerReq();
+  r->c = c;
+  r->bytes = bytes;
+  return server_enqueue(s, r, ticket);
+}
+
+extern "C" aj_status aj_submit_csr(aj_server* s, const aj_csr* Q, const double* b, int nrhs,
+                                   const aj_params* p, uint64_t* ticket) {
+  if (!s || !Q || !ticket || nrhs < 1 || nrhs > kMaxRhs || Q->n < 0 || Q->nnz < 0) return AJ_EINVAL;
+  if (Q->n >= (1ll << 31) - 1 || Q->nnz >= (1ll << 31) - 1) return AJ_EINVAL;
+  if (Q->n > 0 && (!Q->row_ptr || !b)) return AJ_EINVAL;
+  if (Q->nnz > 0 && (!Q->col || !Q->val)) return AJ_EINVAL;
+  aj_params prm;
+  if (p) prm = *p;
+  else aj_params_default(&prm);
+  if (prm.precision < AJ_FP64 || prm.precision > AJ_BF16_IR) return AJ_EINVAL;
+  const size_t est = estimate_bytes(Q->n, Q->nnz, nrhs, prm.precision);
+  if (est > s->budget) return AJ_EBUSY;
+  ServerReq* r = new ServerReq();
+  r->owned = true;
+  r->n = Q->n;
+  r->nnz = Q->nnz;
+  r->nrhs = nrhs;
+  r->prm = prm;
+  r->bytes = est;
+  const size_t m = (size_t)Q->n * nrhs;
+  r->rp.resize((size_t)Q->n + 1);
+  r->ci.resize((size_t)Q->nnz);
+  r->val.resize((size_t)Q->nnz);
+  r->b.resize(m);
+  const cudaMemcpyKind k = Q->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  bool ok = cudaMemcpy(r->rp.data(), Q->row_ptr, r->rp.size() * 4, k) == cudaSuccess &&
+            (Q->nnz == 0 || (cudaMemcpy(r->ci.data(), Q->col, r->ci.size() * 4, k) == cudaSuccess &&
+                             cudaMemcpy(r->val.data(), Q->val, r->val.size() * 8, k) == cudaSuccess)) &&
+            (m == 0 || cudaMemcpy(r->b.data(), b, m * 8, k) == cudaSuccess);
+  if (ok && prm.x0) {
+    r->x0.resize(m);
+    ok = m == 0 || cudaMemcpy(r->x0.data(), prm.x0, m * 8,
+                              prm.x0_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost) ==
+                       cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    delete r;
+    return AJ_ECUDA;
+  }
+  r->prm.x0 = nullptr;
+  return server_enqueue(s, r, ticket);
 }
 
 extern "C" aj_status aj_poll(aj_server* s, uint64_t ticket, double* x_out, aj_info* info) {
   if (!s) return AJ_EINVAL;
-  while (!s->done.count(ticket)) {
-    if (s->queue.empty()) return AJ_EINVAL;
-    auto [t, c] = s->queue.front();
-    s->queue.pop_front();
-    aj_server::Done d;
-    d.x.resize((size_t)c->n * c->nrhs);
-    d.st = aj_solve(c, d.x.data(), 0, &d.info);
-    s->done[t] = std::move(d);
-  }
+  std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->done.find(ticket);
-  if (x_out) std::memcpy(x_out, it->second.x.data(), it->second.x.size() * 8);
+  if (it == s->done.end()) return s->pending.count(ticket) ? AJ_PENDING : AJ_EINVAL;
+  if (x_out && !it->second.x.empty()) std::memcpy(x_out, it->second.x.data(), it->second.x.size() * 8);
   if (info) *info = it->second.info;
-  aj_status st = it->second.st;
+  const aj_status st = it->second.st;
   s->done.erase(it);
   return st;
 }
 
-extern "C" void aj_server_destroy(aj_server* s) { delete s; }
+extern "C" aj_status aj_server_wait(aj_server* s, uint64_t ticket, double timeout_ms) {
+  if (!s) return AJ_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto ready = [&] { return s->done.count(ticket) || !s->pending.count(ticket); };
+  if (timeout_ms < 0) s->cv.wait(lk, ready);
+  else s->cv.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), ready);
+  if (s->done.count(ticket)) return AJ_OK;
+  return s->pending.count(ticket) ? AJ_PENDING : AJ_EINVAL;
+}
+
+extern "C" aj_status aj_server_get_stats(aj_server* s, aj_server_stats* out) {
+  if (!s || !out) return AJ_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->stats;
+  out->in_use_bytes = s->in_use;
+  out->queued = (int64_t)s->queue.size();
+  return AJ_OK;
+}
+
+extern "C" void aj_server_destroy(aj_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv.notify_all();
+  }
+  if (s->th.joinable()) s->th.join();
+  for (ServerReq* r : s->queue) delete r;
+  s->queue.clear();
+  if (s->stream) {
+    cudaStreamSynchronize(s->stream);
+    cudaStreamDestroy(s->stream);
+  }
+  delete s;
+}
 
 extern "C" uint64_t aj_kernel_launches(void) { return g_launches.load(); }
