@@ -180,7 +180,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32_ir", "bf16_ir"])
     ap.add_argument("--form", default="auto", choices=["auto", "lazy", "stored"],
-                    help="sweep form; auto = stored for fp64, lazy otherwise")
+                    help="sweep form; auto = stored")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -216,7 +216,7 @@ def main():
 
     def form_of(precision, form):
         if form == "auto":
-            return "stored" if precision == "fp64" else "lazy"
+            return "stored"
         return form
 
     SWEEP = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED}

@@ -95,12 +95,21 @@ typedef struct {
  * Both give the same iterates up to rounding.  LAZY sums both products over
  * the gathered x^{t-1} and x^{t-2} (two multiply-adds per stored entry, fewer
  * bytes); STORED keeps u = Q x per row and re-reads u^{t-2} (one multiply-add
- * per stored entry, two more n-vectors of traffic).  AUTO picks STORED for
- * AJ_FP64, whose FP64 issue rate binds on GB300, and LAZY otherwise. */
+ * per stored entry, two more n-vectors of traffic).  AUTO picks STORED: it
+ * halves the FP64 issue (the binding resource of AJ_FP64 on GB300) and the
+ * random gathers of graph matrices, and measured faster in every precision
+ * on the 3-D Poisson and Chung-Lu systems. */
 #define AJ_SWEEP_AUTO 0
 #define AJ_SWEEP_LAZY 1
 #define AJ_SWEEP_STORED 2
 
+/* Storage of Q for the fused sweep.  CSR: one row per thread.  SELL: the
+ * SELL-C-sigma layout (C = 32, rows sorted by length within windows of sigma
+ * rows, each 32-row slice stored column-major so that a warp's loads are
+ * coalesced), with rows longer than sell_lmax summed warp-cooperatively and
+ * rows longer than 4096 entries CTA-cooperatively from CSR.  AUTO keeps CSR for rows of near-uniform length and otherwise times
+ * CSR and SELL candidates for a few sweeps and keeps the fastest (the choice
+ * is cached per matrix shape and precision for the process). */
 #define AJ_FMT_AUTO 0
 #define AJ_FMT_CSR 1
 #define AJ_FMT_SELL 2
@@ -124,6 +133,8 @@ typedef struct {
   int64_t max_outer;     /* IR modes: outer refinement steps (default 30) */
   int grid_ctas;         /* 0 = automatic; otherwise the number of persistent CTAs */
   int sweep_form;        /* AJ_SWEEP_AUTO (default) | AJ_SWEEP_LAZY | AJ_SWEEP_STORED */
+  int sell_sigma;        /* AJ_FMT_SELL: sorting window sigma in rows (0 = 256) */
+  int sell_lmax;         /* AJ_FMT_SELL: rows longer than this go to the warp-per-row bucket (0 = 64) */
 } aj_params;
 
 /* Per-solve report. */
@@ -155,6 +166,11 @@ aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ctx** out);
  * AJ_J_SCALED_DIAG with L = 0, estimates L by power iteration on
  * D^-1/2 Q D^-1/2 in FP64.  AJ_EINVAL on a bad parameter. */
 aj_status aj_set(aj_ctx* ctx, const aj_params* p);
+
+/* The format aj_set chose (AJ_FMT_CSR or AJ_FMT_SELL), its sigma and long-row
+ * threshold (0 for CSR), and the stored SELL entries per stored entry of Q
+ * (padding overhead, 1.0 for CSR). */
+aj_status aj_get_format(aj_ctx* ctx, int* format, int* sigma, int* lmax, double* fill_ratio);
 
 /* Run all GPU work of ctx on this cudaStream_t (NULL = legacy default stream). */
 aj_status aj_set_stream(aj_ctx* ctx, void* cuda_stream);

@@ -38,7 +38,8 @@ class aj_params(ctypes.Structure):
                 ("maxit", ctypes.c_int64), ("precision", ctypes.c_int), ("format", ctypes.c_int),
                 ("x0", ctypes.c_void_p), ("x0_on_device", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int64),
-                ("grid_ctas", ctypes.c_int), ("sweep_form", ctypes.c_int)]
+                ("grid_ctas", ctypes.c_int), ("sweep_form", ctypes.c_int),
+                ("sell_sigma", ctypes.c_int), ("sell_lmax", ctypes.c_int)]
 
 
 class aj_info(ctypes.Structure):
@@ -77,6 +78,8 @@ SIGNATURES = [
                                  ctypes.POINTER(ctypes.c_void_p)]),
     ("aj_set", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(aj_params)]),
     ("aj_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("aj_get_format", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     ("aj_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(aj_info)]),
     ("aj_solve_rhs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(aj_info)]),
     ("aj_solve_batch", ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
@@ -185,6 +188,13 @@ class Context:
             self._x0 = x0
         _check(lib().aj_set(self._h, ctypes.byref(p)), "aj_set")
         return self
+
+    def format(self):
+        """(format, sigma, lmax, fill_ratio) chosen by aj_set."""
+        f, sg, lm, fr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().aj_get_format(self._h, ctypes.byref(f), ctypes.byref(sg), ctypes.byref(lm),
+                                   ctypes.byref(fr)), "aj_get_format")
+        return f.value, sg.value, lm.value, fr.value
 
     def set_stream(self, stream):
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream

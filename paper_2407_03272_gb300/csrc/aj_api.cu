@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -16,6 +17,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -160,6 +162,14 @@ struct aj_ctx {
   void* jinvp = nullptr;
   void* x[3] = {nullptr, nullptr, nullptr};
   void* u[2] = {nullptr, nullptr};  // Q x^t, Q x^{t-1} (stored sweep form)
+  // SELL-C-sigma copy of Q (fmt = 1), rebuilt by aj_set
+  Workspace sws;
+  int fmt = 0, sell_sigma = 0, sell_lmax = 0;
+  double fill = 1.0;
+  int nsell = 0, ntiles_sell = 0, nltiles = 0, nhuge = 0;
+  int *d_perm = nullptr, *d_rlen = nullptr, *d_sptr = nullptr, *d_scol = nullptr;
+  int *d_long = nullptr, *d_ltp = nullptr, *d_huge = nullptr;
+  void* d_sval = nullptr;
   int qx = 0;                       // sweep form in use: 1 stored, 0 lazy
   double sQ = 1.0;
   double sb[kMaxRhs] = {1, 1, 1, 1};
@@ -215,6 +225,8 @@ extern "C" void aj_params_default(aj_params* p) {
   p->max_outer = 30;
   p->grid_ctas = 0;
   p->sweep_form = AJ_SWEEP_AUTO;
+  p->sell_sigma = 0;
+  p->sell_lmax = 0;
 }
 
 extern "C" const char* aj_strerror(aj_status s) {
@@ -240,6 +252,7 @@ extern "C" void aj_destroy(aj_ctx* c) {
   cudaSetDevice(c->dev);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  c->sws.release();
   c->pws.release();
   c->base.release();
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -412,6 +425,8 @@ static aj_status estimate_L(aj_ctx* c, double* L_out) {
   return AJ_OK;
 }
 
+static aj_status choose_format(aj_ctx* c, const aj_params* p);
+
 // (Re)build everything that depends on the parameters.
 extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   if (!c || !p) return AJ_EINVAL;
@@ -424,6 +439,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   if (p->format < AJ_FMT_AUTO || p->format > AJ_FMT_SELL) return AJ_EINVAL;
   if (p->grid_ctas < 0) return AJ_EINVAL;
   if (p->sweep_form < AJ_SWEEP_AUTO || p->sweep_form > AJ_SWEEP_STORED) return AJ_EINVAL;
+  if (p->sell_sigma < 0 || p->sell_lmax < 0) return AJ_EINVAL;
   if ((p->precision == AJ_FP32_IR || p->precision == AJ_BF16_IR) &&
       (!(p->inner_tol > 0.0) || p->max_outer < 1))
     return AJ_EINVAL;
@@ -494,9 +510,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     c->pol = pol;
   }
   // --- sweep form and grid: a multiple of the SM count when the problem is large enough
-  c->qx = p->sweep_form == AJ_SWEEP_STORED ? 1
-        : p->sweep_form == AJ_SWEEP_LAZY   ? 0
-                                           : (pol == AJ_FP64 ? 1 : 0);
+  c->qx = p->sweep_form == AJ_SWEEP_LAZY ? 0 : 1;
   {
     const int kp = kernel_pol(pol);
     const int bps = std::max(1, persistent_blocks_per_sm(kp, nrhs, c->qx));
@@ -553,7 +567,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     c->sQ = 1.0;
   }
   CK(cudaStreamSynchronize(s));
-  return AJ_OK;
+  return choose_format(c, p);
 }
 
 // Load interleaved FP64 data, scaled per right-hand side, into an
@@ -635,6 +649,21 @@ static IterLaunch make_launch(aj_ctx* c, const void* bvec, long long maxit, int 
   L.row_ptr = c->rp;
   L.col = c->ci;
   L.val = c->pol == AJ_FP64 ? (const void*)c->val64 : c->valp;
+  L.fmt = c->fmt;
+  if (c->fmt == 1) {
+    L.nsell = c->nsell;
+    L.ntiles_sell = c->ntiles_sell;
+    L.nltiles = c->nltiles;
+    L.perm = c->d_perm;
+    L.rlen = c->d_rlen;
+    L.sptr = c->d_sptr;
+    L.scol = c->d_scol;
+    L.sval = c->d_sval;
+    L.long_rows = c->d_long;
+    L.ltp = c->d_ltp;
+    L.nhuge = c->nhuge;
+    L.huge_rows = c->d_huge;
+  }
   L.b = bvec;
   L.jinv = c->pol == AJ_FP64 ? (const void*)c->jinv64 : c->jinvp;
   for (int k = 0; k < 3; k++) L.x[k] = c->x[k];
@@ -689,6 +718,217 @@ static aj_status run_persistent(aj_ctx* c, std::vector<RhsState>& st, const void
   cudaEventElapsedTime(&kms, c->kev0, c->kev1);
   c->kernel_ms += kms;
   if (err != 0) return err == kETimeout ? AJ_ETIMEOUT : AJ_ECUDA;
+  return AJ_OK;
+}
+
+// ---------------------------------------------------------------- matrix format
+// SELL-C-sigma (C = 32) from the CSR arrays: rows longer than kHugeRow get a
+// whole CTA each; rows longer than lmax go to the long-row bucket, sorted by
+// length (longest first) and cut into tiles of at most 256 rows and
+// kLongTileEntries entries, summed a warp per row; the others are sorted by
+// length, longest first, within windows of sigma rows and sliced.
+static const long long kLongTileEntries = 32768;
+static const int kHugeRow = 4096;
+
+template <class T>
+static void sell_fill(aj_ctx* c, const void* val) {
+  k_sell_fill<T><<<grid1d(c->nsell), kSetupThreads, 0, c->stream>>>(
+      c->nsell, c->d_perm, c->d_rlen, c->d_sptr, c->rp, c->ci, (const T*)val, c->d_scol, (T*)c->d_sval);
+  counted();
+}
+
+static aj_status build_sell(aj_ctx* c, int sigma, int lmax) {
+  c->sws.release();
+  c->fmt = 0;
+  c->fill = 1.0;
+  const int n = (int)c->n;
+  cudaStream_t s = c->stream;
+  std::vector<int> rp((size_t)n + 1);
+  CK(cudaMemcpyAsync(rp.data(), c->rp, rp.size() * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  auto len = [&](int i) { return rp[i + 1] - rp[i]; };
+  std::vector<int> rows, lng, hug;
+  rows.reserve(n);
+  for (int i = 0; i < n; i++) {
+    const int l = len(i);
+    (l > kHugeRow ? hug : l > lmax ? lng : rows).push_back(i);
+  }
+  std::stable_sort(lng.begin(), lng.end(), [&](int x, int y) { return len(x) > len(y); });
+  for (size_t w0 = 0; w0 < rows.size(); w0 += (size_t)sigma) {
+    auto b = rows.begin() + w0, e = rows.begin() + std::min(rows.size(), w0 + (size_t)sigma);
+    std::stable_sort(b, e, [&](int x, int y) { return len(x) > len(y); });
+  }
+  const int nsell = (int)rows.size();
+  const int nslices = (nsell + 31) / 32;
+  std::vector<int> rlen(nsell), sptr((size_t)nslices + 1);
+  long long tot = 0;
+  for (int sl = 0; sl < nslices; sl++) {
+    int w = 0;
+    for (int p = sl * 32; p < std::min(nsell, sl * 32 + 32); p++) {
+      rlen[p] = len(rows[p]);
+      w = std::max(w, rlen[p]);
+    }
+    sptr[sl] = (int)tot;
+    tot += 32ll * w;
+    if (tot > (1ll << 31) - 64) return AJ_ENOMEM;
+  }
+  sptr[nslices] = (int)tot;
+  std::vector<int> ltp(1, 0);
+  long long acc = 0, long_entries = 0;
+  int cnt = 0;
+  for (int j = 0; j < (int)lng.size(); j++) {
+    const int l = len(lng[j]);
+    if (cnt > 0 && (cnt == kThreads || acc + l > kLongTileEntries)) {
+      ltp.push_back(j);
+      acc = 0;
+      cnt = 0;
+    }
+    acc += l;
+    cnt++;
+    long_entries += l;
+  }
+  if (!lng.empty()) ltp.push_back((int)lng.size());
+  const size_t vb = velem_bytes(c->pol);
+  c->d_perm = (int*)c->sws.alloc(((size_t)nsell + 1) * 4);
+  c->d_rlen = (int*)c->sws.alloc(((size_t)nsell + 1) * 4);
+  c->d_sptr = (int*)c->sws.alloc(sptr.size() * 4);
+  c->d_scol = (int*)c->sws.alloc(((size_t)tot + 32) * 4);
+  c->d_sval = c->sws.alloc(((size_t)tot + 32) * vb);
+  c->d_long = (int*)c->sws.alloc((lng.size() + 1) * 4);
+  c->d_ltp = (int*)c->sws.alloc(ltp.size() * 4);
+  c->d_huge = (int*)c->sws.alloc((hug.size() + 1) * 4);
+  if (!c->d_perm || !c->d_rlen || !c->d_sptr || !c->d_scol || !c->d_sval || !c->d_long || !c->d_ltp ||
+      !c->d_huge) {
+    c->sws.release();
+    return AJ_ENOMEM;
+  }
+  if (nsell) {
+    CK(cudaMemcpyAsync(c->d_perm, rows.data(), (size_t)nsell * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_rlen, rlen.data(), (size_t)nsell * 4, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemcpyAsync(c->d_sptr, sptr.data(), sptr.size() * 4, cudaMemcpyHostToDevice, s));
+  if (!lng.empty()) CK(cudaMemcpyAsync(c->d_long, lng.data(), lng.size() * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->d_ltp, ltp.data(), ltp.size() * 4, cudaMemcpyHostToDevice, s));
+  if (!hug.empty()) CK(cudaMemcpyAsync(c->d_huge, hug.data(), hug.size() * 4, cudaMemcpyHostToDevice, s));
+  for (int h : hug) long_entries += len(h);
+  CK(cudaMemsetAsync(c->d_scol, 0, ((size_t)tot + 32) * 4, s));
+  CK(cudaMemsetAsync(c->d_sval, 0, ((size_t)tot + 32) * vb, s));
+  c->nsell = nsell;
+  c->ntiles_sell = (nsell + kThreads - 1) / kThreads;
+  c->nltiles = (int)ltp.size() - 1;
+  c->nhuge = (int)hug.size();
+  if (nsell) {
+    const void* val = c->pol == AJ_FP64 ? (const void*)c->val64 : c->valp;
+    switch (c->pol) {
+      case AJ_FP64: sell_fill<double>(c, val); break;
+      case AJ_DF64: sell_fill<float2>(c, val); break;
+      case AJ_FP32_IR: sell_fill<float>(c, val); break;
+      default: sell_fill<__nv_bfloat16>(c, val); break;
+    }
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  c->fmt = 1;
+  c->sell_sigma = sigma;
+  c->sell_lmax = lmax;
+  c->fill = c->nnz > 0 ? (double)(tot + long_entries) / (double)c->nnz : 1.0;
+  return AJ_OK;
+}
+
+// Device time per sweep of the current format: a few sweeps from x = 0 with
+// b = 0 (every load and multiply-add still runs).
+static aj_status time_sweeps(aj_ctx* c, double* ms_per_sweep) {
+  const long long m = (long long)c->n * c->nrhs;
+  cudaStream_t s = c->stream;
+  const void* bvec = c->pol == AJ_FP64 ? (const void*)c->tmp64 : c->bp;
+  CK(cudaMemsetAsync((void*)bvec, 0, (size_t)(m + 1) * xelem_bytes(c->pol), s));
+  double best = 1e300;
+  for (int rep = 0; rep < 2; rep++) {
+    CK(cudaMemsetAsync(c->x[0], 0, (size_t)(m + 1) * xelem_bytes(c->pol), s));
+    std::vector<RhsState> st(c->nrhs);
+    double one[kMaxRhs] = {1, 1, 1, 1};
+    init_state(c, st.data(), one);
+    const double k0 = c->kernel_ms;
+    const long long T = 8;
+    aj_status e = run_persistent(c, st, bvec, T, AJ_STOP_NONE, 0.0, 0.0, 1.0, false);
+    if (e != AJ_OK) return e;
+    best = std::min(best, (c->kernel_ms - k0) / (double)(T + 1));
+  }
+  *ms_per_sweep = best;
+  return AJ_OK;
+}
+
+struct TuneKey {
+  int64_t n, nnz, sumsq, maxlen;
+  int pol, nrhs, qx;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(n, nnz, sumsq, maxlen, pol, nrhs, qx) <
+           std::tie(o.n, o.nnz, o.sumsq, o.maxlen, o.pol, o.nrhs, o.qx);
+  }
+};
+static std::map<TuneKey, std::array<int, 3>> g_tune;  // -> {fmt, sigma, lmax}
+static std::mutex g_tune_mu;
+
+static aj_status choose_format(aj_ctx* c, const aj_params* p) {
+  const int sig = p->sell_sigma > 0 ? p->sell_sigma : 256;
+  const int lmx = p->sell_lmax > 0 ? p->sell_lmax : 64;
+  if (p->format == AJ_FMT_SELL) return build_sell(c, sig, lmx);
+  c->sws.release();
+  c->fmt = 0;
+  c->fill = 1.0;
+  if (p->format == AJ_FMT_CSR) return AJ_OK;
+  // AUTO: CSR unless the rows are long-tailed and the system is large
+  const int n = (int)c->n;
+  if (n < 65536) return AJ_OK;
+  std::vector<int> rp((size_t)n + 1);
+  CK(cudaMemcpyAsync(rp.data(), c->rp, rp.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  int64_t sumsq = 0, maxlen = 0;
+  for (int i = 0; i < n; i++) {
+    const int64_t l = rp[i + 1] - rp[i];
+    sumsq += l * l;
+    maxlen = std::max(maxlen, l);
+  }
+  const double mean = (double)c->nnz / n;
+  if (maxlen <= 2.0 * mean + 8.0) return AJ_OK;
+  const TuneKey key{c->n, c->nnz, sumsq, maxlen, c->pol, c->nrhs, c->qx};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      if (it->second[0] == 1) return build_sell(c, it->second[1], it->second[2]);
+      return AJ_OK;
+    }
+  }
+  const std::array<int, 3> cand[] = {{0, 0, 0}, {1, 256, 64}, {1, 4096, 64}, {1, 256, 256}};
+  std::array<int, 3> best = cand[0];
+  double best_ms = 1e300;
+  for (const auto& k : cand) {
+    aj_status e = k[0] ? build_sell(c, k[1], k[2]) : AJ_OK;
+    if (k[0] == 0) { c->sws.release(); c->fmt = 0; c->fill = 1.0; }
+    if (e != AJ_OK) continue;
+    double ms = 0.0;
+    e = time_sweeps(c, &ms);
+    if (e != AJ_OK) return e;
+    if (ms < best_ms) { best_ms = ms; best = k; }
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+  }
+  if (best[0] == 1) return build_sell(c, best[1], best[2]);
+  c->sws.release();
+  c->fmt = 0;
+  c->fill = 1.0;
+  return AJ_OK;
+}
+
+extern "C" aj_status aj_get_format(aj_ctx* c, int* format, int* sigma, int* lmax, double* fill_ratio) {
+  if (!c) return AJ_EINVAL;
+  if (format) *format = c->fmt ? AJ_FMT_SELL : AJ_FMT_CSR;
+  if (sigma) *sigma = c->fmt ? c->sell_sigma : 0;
+  if (lmax) *lmax = c->fmt ? c->sell_lmax : 0;
+  if (fill_ratio) *fill_ratio = c->fill;
   return AJ_OK;
 }
 

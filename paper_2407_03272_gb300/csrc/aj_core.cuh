@@ -320,12 +320,37 @@ struct PolB16 : PolF32 {
 // ----------------------------------------------------------------------------
 // Kernel arguments.  Vectors with several right-hand sides are interleaved:
 // element (i, r) lives at i * nrhs + r, so one gather fetches all of them.
+//
+// Matrix formats.  CSR: tile k is rows 256k .. 256k+255, one row per thread.
+// SELL-C-sigma (C = 32): the rows without the long ones are sorted by length
+// (longest first) within windows of sigma rows; position p of that order holds
+// row perm[p], and slice p / 32 stores its 32 rows column-major, entry k of
+// position p at sptr[p / 32] + 32 k + p % 32, so the lanes of a warp read
+// consecutive words.  Entries keep their CSR order, so a row sums in the same
+// order in both formats.  Tiles past the SELL ones hold the long rows
+// (long_rows, longest first, at most 256 and a bounded number of entries per
+// tile, dealt round-robin over the warps), each summed by a whole warp from
+// the CSR arrays; the last tiles hold one huge row each, summed by the whole
+// CTA.
 template <class P>
 struct IterArgs {
   int n;
   const int* row_ptr;
   const int* col;
   const typename P::V* val;
+  int fmt;                    // 0 CSR, 1 SELL
+  int nsell;                  // SELL: rows in the sliced part
+  int ntiles_sell;            // SELL: tiles of the sliced part
+  int nltiles;                // SELL: tiles of long rows
+  const int* perm;            // SELL: [nsell] row at each position
+  const int* rlen;            // SELL: [nsell] entries of the row at each position
+  const int* sptr;            // SELL: [nsell / 32 + 1] slice offsets (entries)
+  const int* scol;            // SELL: sliced column indices
+  const typename P::V* sval;  // SELL: sliced values
+  const int* long_rows;       // SELL: rows summed by a whole warp
+  const int* ltp;             // SELL: [nltiles + 1] long tile k = long_rows[ltp[k] .. ltp[k+1])
+  int nhuge;                  // SELL: rows summed by a whole CTA, one per tile
+  const int* huge_rows;       // SELL: [nhuge]
   const typename P::X* b;     // [n * nrhs]
   const typename P::X* jinv;  // [n]
   typename P::X* x[3];        // three iterate buffers, [n * nrhs] each
@@ -348,6 +373,51 @@ struct IterArgs {
   long long max_sweeps;       // sweeps allowed in this launch (chunked runs), >= 1
 };
 
+// Partial row sums over entries q0, q0 + step, ... < re (CSR arrays), U of
+// them loaded before their multiply-adds, which run in entry order.
+template <class P, int NR, bool QX>
+__device__ __forceinline__ void row_sums_strided(const IterArgs<P>& a, int q0, int re, int step,
+                                                 const typename P::X* const* xc,
+                                                 const typename P::X* const* xp, const bool* same,
+                                                 const bool* active, typename P::S* lx,
+                                                 typename P::S* lp) {
+  using S = typename P::S;
+  using V = typename P::V;
+  constexpr int U = NR * (QX ? 1 : 2) >= 4 ? 2 : 4;
+  for (int q = q0; q < re; q += U * step) {
+    int cc[U];
+    V vv[U];
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+      const bool in = q + k * step < re;
+      cc[k] = in ? ld_ro(a.col + q + k * step) : 0;
+      vv[k] = in ? P::ldv(a.val + q + k * step) : P::vzero();
+    }
+    S xv[U][NR], pv[U][NR];
+#pragma unroll
+    for (int k = 0; k < U; k++)
+#pragma unroll
+      for (int r = 0; r < NR; r++) {
+        xv[k][r] = P::zero();
+        pv[k][r] = P::zero();
+        if (q + k * step < re && active[r]) {
+          xv[k][r] = P::ldx(xc[r] + (size_t)cc[k] * NR + r);
+          if (!QX && !same[r]) pv[k][r] = P::ldx(xp[r] + (size_t)cc[k] * NR + r);
+        }
+      }
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+      if (q + k * step >= re) break;
+#pragma unroll
+      for (int r = 0; r < NR; r++) {
+        if (!active[r]) continue;
+        P::macv(lx[r], vv[k], xv[k][r]);
+        if (!QX && !same[r]) P::macv(lp[r], vv[k], pv[k][r]);
+      }
+    }
+  }
+}
+
 // Warp-cooperative row sums for one long row (lanes stride over the entries,
 // then a fixed xor tree).  Returns the sums in every lane.  The stored form
 // (QX) forms only sx.
@@ -362,15 +432,7 @@ __device__ __forceinline__ void long_row_sums(const IterArgs<P>& a, int rs, int 
   S lx[NR], lp[NR];
 #pragma unroll
   for (int r = 0; r < NR; r++) { lx[r] = P::zero(); lp[r] = P::zero(); }
-  for (int q = rs + lane; q < re; q += 32) {
-    const int c = ld_ro(a.col + q);
-#pragma unroll
-    for (int r = 0; r < NR; r++) {
-      if (!active[r]) continue;
-      P::mac(lx[r], a.val + q, P::ldx(xc[r] + (size_t)c * NR + r));
-      if (!QX && !same[r]) P::mac(lp[r], a.val + q, P::ldx(xp[r] + (size_t)c * NR + r));
-    }
-  }
+  row_sums_strided<P, NR, QX>(a, rs + lane, re, 32, xc, xp, same, active, lx, lp);
 #pragma unroll
   for (int r = 0; r < NR; r++) {
     lx[r] = P::finish(lx[r]);
@@ -384,6 +446,52 @@ __device__ __forceinline__ void long_row_sums(const IterArgs<P>& a, int rs, int 
       sp[r] = same[r] ? lx[r] : lp[r];
     }
   }
+}
+
+// CTA-cooperative row sums for one huge row: threads stride over the
+// entries, then a fixed xor tree per warp and the warps in order.  Results
+// valid in thread 0.  Every thread of the CTA must call it.
+template <class P, int NR, bool QX>
+__device__ __forceinline__ void cta_row_sums(const IterArgs<P>& a, int rs, int re,
+                                             const typename P::X* const* xc,
+                                             const typename P::X* const* xp, const bool* same,
+                                             const bool* active, typename P::S* sx,
+                                             typename P::S* sp) {
+  using S = typename P::S;
+  __shared__ S red[2][NR][kWarps];
+  S lx[NR], lp[NR];
+#pragma unroll
+  for (int r = 0; r < NR; r++) { lx[r] = P::zero(); lp[r] = P::zero(); }
+  row_sums_strided<P, NR, QX>(a, rs + threadIdx.x, re, kThreads, xc, xp, same, active, lx, lp);
+  const int w = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < NR; r++) {
+    lx[r] = P::finish(lx[r]);
+    lp[r] = P::finish(lp[r]);
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+      lx[r] = P::combine(lx[r], P::shfl_xor(lx[r], m));
+      if (!QX) lp[r] = P::combine(lp[r], P::shfl_xor(lp[r], m));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[0][r][w] = lx[r];
+      red[1][r][w] = lp[r];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      S tx = red[0][r][0], tp = red[1][r][0];
+      for (int k = 1; k < kWarps; k++) {
+        tx = P::combine(tx, red[0][r][k]);
+        if (!QX) tp = P::combine(tp, red[1][r][k]);
+      }
+      sx[r] = tx;
+      sp[r] = (QX || same[r]) ? tx : tp;
+    }
+  }
+  __syncthreads();
 }
 
 // Reduction slots a sweep fills: d and rr always, the objective terms only
@@ -423,7 +531,9 @@ __host__ __device__ constexpr int row_unroll(int nr, bool qx) {
                                                        : 8;
 }
 
-template <class P, int NR, bool QX>
+// ANY: the kernel handles both formats (runtime a.fmt); otherwise CSR only,
+// which keeps the SELL code and its registers out of the CSR kernel.
+template <class P, int NR, bool QX, bool ANY>
 __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, bool compute_x,
                                       bool want_obj, typename P::A (&acc)[NR][kNRed], int cta,
                                       int ncta) {
@@ -451,31 +561,75 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
     beta[r] = P::coef(st[r].beta);
   }
   const int lane = threadIdx.x & 31;
-  const int ntiles = (a.n + kThreads - 1) / kThreads;
+  const bool sell = ANY && a.fmt != 0;
+  const int ntiles = sell ? a.ntiles_sell + a.nltiles + a.nhuge : (a.n + kThreads - 1) / kThreads;
   for (int tile = cta; tile < ntiles; tile += ncta) {
-    const int i = tile * kThreads + threadIdx.x;
-    const bool valid = i < a.n;
-    int rs = 0, re = 0;
-    if (valid) {
+    // this thread's row i, its entries colp[k * stride], valp[k * stride]
+    // (k < cnt) and, for long rows, its CSR range rs .. re
+    int i, rs = 0, re = 0, cnt = 0, stride = 1;
+    bool valid, is_long, huge = false;
+    const int* colp = a.col;
+    const V* valp = a.val;
+    if (!sell) {
+      i = tile * kThreads + threadIdx.x;
+      valid = i < a.n;
+      if (valid) {
+        rs = ld_ro(a.row_ptr + i);
+        re = ld_ro(a.row_ptr + i + 1);
+      }
+      is_long = valid && (re - rs) > kLongRow;
+      cnt = re - rs;
+      colp += rs;
+      valp += rs;
+    } else if (tile < a.ntiles_sell) {
+      const int pos = tile * kThreads + threadIdx.x;
+      valid = pos < a.nsell;
+      i = valid ? ld_ro(a.perm + pos) : 0;
+      if (valid) {
+        cnt = ld_ro(a.rlen + pos);
+        const int base = ld_ro(a.sptr + (pos >> 5)) + (pos & 31);
+        colp = a.scol + base;
+        valp = a.sval + base;
+        stride = 32;
+      }
+      is_long = false;
+    } else if (tile < a.ntiles_sell + a.nltiles) {
+      // long rows dealt round-robin over the warps: row j of the tile goes to
+      // warp j % 8, lane j / 8
+      const int lt = tile - a.ntiles_sell;
+      const int pos = ld_ro(a.ltp + lt) + (threadIdx.x & 31) * kWarps + (threadIdx.x >> 5);
+      valid = pos < ld_ro(a.ltp + lt + 1);
+      i = valid ? ld_ro(a.long_rows + pos) : 0;
+      if (valid) {
+        rs = ld_ro(a.row_ptr + i);
+        re = ld_ro(a.row_ptr + i + 1);
+      }
+      is_long = valid;
+    } else {
+      i = ld_ro(a.huge_rows + (tile - a.ntiles_sell - a.nltiles));
       rs = ld_ro(a.row_ptr + i);
       re = ld_ro(a.row_ptr + i + 1);
+      huge = true;
+      is_long = false;
+      valid = threadIdx.x == 0;  // thread 0 owns the row's update
     }
-    const bool is_long = valid && (re - rs) > kLongRow;
     S sx[NR], sp[NR];
 #pragma unroll
     for (int r = 0; r < NR; r++) { sx[r] = P::zero(); sp[r] = P::zero(); }
-    if (valid && !is_long) {
+    if (ANY && huge) {
+      cta_row_sums<P, NR, QX>(a, rs, re, xc, xp, same, active, sx, sp);
+    } else if (valid && !is_long) {
       // chunks of U entries: every load of a chunk is issued before its
       // multiply-adds, which then run in ascending entry order
       constexpr int U = row_unroll(NR, QX);
-      for (int q0 = rs; q0 < re; q0 += U) {
+      for (int q0 = 0; q0 < cnt; q0 += U) {
         int cc[U];
         V vv[U];
 #pragma unroll
         for (int k = 0; k < U; k++) {
-          const bool in = q0 + k < re;
-          cc[k] = in ? ld_ro(a.col + q0 + k) : 0;
-          vv[k] = in ? P::ldv(a.val + q0 + k) : P::vzero();
+          const bool in = q0 + k < cnt;
+          cc[k] = in ? ld_ro(colp + (q0 + k) * stride) : 0;
+          vv[k] = in ? P::ldv(valp + (q0 + k) * stride) : P::vzero();
         }
         S xv[U][NR], pv[U][NR];
 #pragma unroll
@@ -484,14 +638,14 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
           for (int r = 0; r < NR; r++) {
             xv[k][r] = P::zero();
             pv[k][r] = P::zero();
-            if (q0 + k < re && active[r]) {
+            if (q0 + k < cnt && active[r]) {
               xv[k][r] = P::ldx(xc[r] + (size_t)cc[k] * NR + r);
               if (!QX && !same[r]) pv[k][r] = P::ldx(xp[r] + (size_t)cc[k] * NR + r);
             }
           }
 #pragma unroll
         for (int k = 0; k < U; k++) {
-          if (q0 + k >= re) break;
+          if (q0 + k >= cnt) break;
 #pragma unroll
           for (int r = 0; r < NR; r++) {
             if (!active[r]) continue;
@@ -650,7 +804,7 @@ struct SolveSmem {
 // arrival count so far and `sw` the sweep counter that parity-buffers the
 // partials; both carry over between systems that reuse the same barrier.
 // Returns false when a barrier gave up (error already recorded in *a.err).
-template <class P, int NR, bool QX>
+template <class P, int NR, bool QX, bool ANY>
 __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem<NR>& sm, int cta,
                                           int ncta, unsigned long long& target, long long& sw) {
   using A = typename P::A;
@@ -671,7 +825,7 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem<NR>& s
     for (int r = 0; r < NR; r++)
 #pragma unroll
       for (int k = 0; k < kNRed; k++) acc_zero(acc[r][k]);
-    sweep<P, NR, QX>(a, sm.st, compute_x, want_obj, acc, cta, ncta);
+    sweep<P, NR, QX, ANY>(a, sm.st, compute_x, want_obj, acc, cta, ncta);
     // CTA partials -> global (parity-buffered by sweep)
     double* part = a.partials + (size_t)(sw & 1) * ncta * NR * kNRed;
 #pragma unroll
@@ -724,15 +878,16 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem<NR>& s
 }
 
 // The persistent fused AJ kernel for one system.  Launch cooperatively with
-// kThreads threads per CTA; every CTA of the grid works on the system.
-template <class P, int NR, bool QX>
+// kThreads threads per CTA; every CTA of the grid works on the system.  ANY
+// selects the instantiation that also reads the SELL-C-sigma format.
+template <class P, int NR, bool QX, bool ANY>
 __global__ void __launch_bounds__(kThreads, min_blocks(NR)) aj_persistent_kernel(IterArgs<P> a) {
   __shared__ SolveSmem<NR> sm;
   if (threadIdx.x < NR) sm.st[threadIdx.x] = a.state[threadIdx.x];
   __syncthreads();
   unsigned long long target = 0;
   long long sw = 0;
-  if (!run_solve<P, NR, QX>(a, sm, blockIdx.x, gridDim.x, target, sw)) return;
+  if (!run_solve<P, NR, QX, ANY>(a, sm, blockIdx.x, gridDim.x, target, sw)) return;
   if (blockIdx.x == 0 && threadIdx.x < NR) a.state[threadIdx.x] = sm.st[threadIdx.x];
 }
 
@@ -778,7 +933,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(NR)) aj_batched_kernel(Ba
     a.err = b.err;
     if (threadIdx.x < NR) sm.st[threadIdx.x] = a.state[threadIdx.x];
     __syncthreads();
-    if (!run_solve<P, NR, QX>(a, sm, rank, size, target, sw)) return;
+    if (!run_solve<P, NR, QX, true>(a, sm, rank, size, target, sw)) return;
     if (rank == 0 && threadIdx.x < NR) a.state[threadIdx.x] = sm.st[threadIdx.x];
     __syncthreads();
   }

@@ -3,6 +3,8 @@
 // AJ_POL (policy type) and AJ_SUFFIX (name suffix) defined.
 #include <string.h>
 
+#include <algorithm>
+
 #include "aj_core.cuh"
 #include "aj_launch.h"
 
@@ -18,6 +20,19 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
   a.row_ptr = L.row_ptr;
   a.col = L.col;
   a.val = static_cast<const typename P::V*>(L.val);
+  a.fmt = L.fmt;
+  a.nsell = L.nsell;
+  a.ntiles_sell = L.ntiles_sell;
+  a.nltiles = L.nltiles;
+  a.perm = L.perm;
+  a.rlen = L.rlen;
+  a.sptr = L.sptr;
+  a.scol = L.scol;
+  a.sval = static_cast<const typename P::V*>(L.sval);
+  a.long_rows = L.long_rows;
+  a.ltp = L.ltp;
+  a.nhuge = L.nhuge;
+  a.huge_rows = L.huge_rows;
   a.b = static_cast<const typename P::X*>(L.b);
   a.jinv = static_cast<const typename P::X*>(L.jinv);
   for (int k = 0; k < 3; k++) a.x[k] = static_cast<typename P::X*>(L.x[k]);
@@ -73,19 +88,27 @@ template <class P, int NR>
 static cudaError_t launch_nr(const IterLaunch& L, int grid, cudaStream_t s) {
   IterArgs<P> a = typed_args<P>(L);
   void* args[] = {&a};
-  const void* k = L.qx ? (const void*)aj_persistent_kernel<P, NR, true>
-                       : (const void*)aj_persistent_kernel<P, NR, false>;
+  const void* k = L.fmt ? (L.qx ? (const void*)aj_persistent_kernel<P, NR, true, true>
+                                : (const void*)aj_persistent_kernel<P, NR, false, true>)
+                       : (L.qx ? (const void*)aj_persistent_kernel<P, NR, true, false>
+                               : (const void*)aj_persistent_kernel<P, NR, false, false>);
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
 }
 
+template <class K>
+static int occ_of(K k) {
+  int nb = 0;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, 0) == cudaSuccess ? nb : 0;
+}
+
+// Co-resident CTAs of the persistent kernel: the smaller of its CSR-only and
+// any-format instantiations, so that a grid sized by it fits either.
 template <class P, int NR>
 static int occ_nr(int qx) {
-  int nb = 0;
-  cudaError_t e = qx ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                           &nb, aj_persistent_kernel<P, NR, true>, kThreads, 0)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                           &nb, aj_persistent_kernel<P, NR, false>, kThreads, 0);
-  return e == cudaSuccess ? nb : 0;
+  return qx ? std::min(occ_of(aj_persistent_kernel<P, NR, true, false>),
+                       occ_of(aj_persistent_kernel<P, NR, true, true>))
+            : std::min(occ_of(aj_persistent_kernel<P, NR, false, false>),
+                       occ_of(aj_persistent_kernel<P, NR, false, true>));
 }
 
 cudaError_t AJ_CAT(launch_persistent_, AJ_SUFFIX)(int nrhs, const IterLaunch& L, int grid,

@@ -14,6 +14,19 @@ struct IterLaunch {
   const int* row_ptr;
   const int* col;
   const void* val;
+  int fmt;  // 0 CSR, 1 SELL-C-sigma (fields below)
+  int nsell;
+  int ntiles_sell;
+  int nltiles;
+  const int* perm;
+  const int* rlen;
+  const int* sptr;
+  const int* scol;
+  const void* sval;
+  const int* long_rows;
+  const int* ltp;
+  int nhuge;
+  const int* huge_rows;
   const void* b;
   const void* jinv;
   void* x[3];
