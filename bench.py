@@ -172,6 +172,167 @@ def run_reference(args):
     return 0
 
 
+def _events(torch, stream):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    return e0, e1
+
+
+def bench_graph(aj, torch, dev, stream, hbm_peak, n):
+    """Singular weighted Chung-Lu graph Laplacian (mean degree 16, exponent 2.5,
+    weights U(0.5, 1.5)), b = Q x* in range(Q): FP32-value refinement and the
+    plain FP64 path, format chosen by the autotuner, each solved to 1e-8."""
+    import synth
+    t0 = time.perf_counter()
+    Q, b, _ = synth.workload("chunglu_%d" % n)
+    gen_s = time.perf_counter() - t0
+    nnz = int(Q["row_ptr"][-1])
+    tens = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (Q["row_ptr"], Q["col"], Q["val"], b)]
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    res = {"workload": "Chung-Lu weighted graph Laplacian n=%d nnz=%d (mean degree 16, exponent 2.5, "
+                       "U(0.5,1.5) weights, isolated vertices kept), b=Qx*, x*~U(-1,1) seed 3" % (n, nnz),
+           "generate_s": gen_s}
+    for prec in ("fp32_ir", "fp64"):
+        ctx = aj.Context(*tens, n=n)
+        ctx.set_stream(stream)
+        t1 = time.perf_counter()
+        ctx.set(precision=prec, tol=1e-8, maxit=200000)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t1
+        fmt = ctx.format()
+        ctx.solve(out=out)
+        e0, e1 = _events(torch, stream)
+        e0.record(stream)
+        _, info = ctx.solve(out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        B = algorithmic_bytes(n, nnz, prec)
+        gbs = B * info["iters"] / (info["kernel_ms"] * 1e-3) / 1e9
+        res[prec] = {"time_to_tol_ms": ms, "iterations": info["iters"], "outer": info["outer"],
+                     "relres": info["relres"], "status": info["status"],
+                     "format": {"kind": "SELL-32-sigma" if fmt[0] == aj.AJ_FMT_SELL else "CSR",
+                                "sigma": fmt[1], "long_row_threshold": fmt[2], "fill_ratio": fmt[3]},
+                     "setup_incl_autotune_s": setup_s,
+                     "fused_GBps": gbs, "fused_hbm_frac": gbs / hbm_peak,
+                     "kernel_ms_per_iteration": info["kernel_ms"] / max(info["iters"], 1)}
+        ctx.close()
+    res["fp32_ir_speedup_vs_fp64"] = res["fp64"]["time_to_tol_ms"] / res["fp32_ir"]["time_to_tol_ms"]
+    return res
+
+
+def bench_batched(aj, torch, dev, stream, count, pool):
+    """Independent systems in one persistent launch per right-hand-side count
+    (aj_solve_batch), against the same systems solved one after another."""
+    import synth
+    t0 = time.perf_counter()
+    systems, mats = synth.batch_mix(count, seed=4, pool=pool)
+    gen_s = time.perf_counter() - t0
+    dmats = [[torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (Q["row_ptr"], Q["col"], Q["val"])]
+             for Q in mats]
+    bs = [torch.from_numpy(synth.mix_rhs(mats[j], seeds)).to(dev) for j, _, seeds in systems]
+    outs = [torch.empty(mats[j]["n"] * nrhs, dtype=torch.float64, device=dev) for j, nrhs, _ in systems]
+
+    def build(prec):
+        cs = []
+        for (j, nrhs, _), b in zip(systems, bs):
+            c = aj.Context(*dmats[j], b, n=mats[j]["n"], nrhs=nrhs)
+            c.set_stream(stream)
+            c.set(precision=prec, tol=1e-8, maxit=200000)
+            cs.append(c)
+        return cs
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch, stream)
+        w0 = time.perf_counter()
+        e0.record(stream)
+        infos = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), 1e3 * (time.perf_counter() - w0), infos
+
+    res = {"workload": "%d independent systems: half 2-D Poisson (side log-uniform 32..1024), half k-NN "
+                       "(k=8) random-geometric-graph Laplacians (n log-uniform 1e3..5e5), 1-4 RHS each, "
+                       "matrices from a pool of %d, b=Qx* per system; tol 1e-8" % (count, pool),
+           "systems": count, "rows_total": int(sum(mats[j]["n"] * 1 for j, _, _ in systems)),
+           "rhs_total": int(sum(nr for _, nr, _ in systems)), "generate_s": gen_s}
+    for prec in ("fp32_ir", "fp64"):
+        cs = build(prec)
+        aj.solve_batch(cs[:4], outs[:4], on_device=True)  # warm-up
+        ms, wall, infos = timed(lambda: aj.solve_batch(cs, outs, on_device=True))
+        ok = sum(1 for i in infos if i["status"] == aj.AJ_OK)
+        byt = sum(algorithmic_bytes(mats[j]["n"], int(mats[j]["row_ptr"][-1]), prec) * i["iters"]
+                  for (j, _, _), i in zip(systems, infos))
+        res["batched_" + prec] = {"makespan_ms": ms, "wall_ms": wall, "systems_per_s": count / (ms * 1e-3),
+                                  "ok": ok, "max_relres": max(i["relres"] for i in infos),
+                                  "approx_GBps": byt / (ms * 1e-3) / 1e9,
+                                  "iterations_total": int(sum(i["iters"] for i in infos))}
+        if prec == "fp64":
+            def serial():
+                return [c.solve(out=o)[1] for c, o in zip(cs, outs)]
+            ms_s, wall_s, inf_s = timed(serial)
+            res["serial_fp64"] = {"makespan_ms": ms_s, "wall_ms": wall_s, "systems_per_s": count / (ms_s * 1e-3),
+                                  "ok": sum(1 for i in inf_s if i["status"] == aj.AJ_OK),
+                                  "max_relres": max(i["relres"] for i in inf_s)}
+        for c in cs:
+            c.close()
+    res["batched_fp32_ir_speedup_vs_serial_fp64"] = (res["serial_fp64"]["makespan_ms"]
+                                                     / res["batched_fp32_ir"]["makespan_ms"])
+    return res
+
+
+def bench_served(aj, torch, count, pool, rate, budget_gb):
+    """Continuous-batching server under Poisson arrivals: the offered rate,
+    then 0.8x the capacity measured there.  Latency = submission to result."""
+    import synth
+    t0 = time.perf_counter()
+    systems, mats = synth.served_mix(2 * count, seed=5, pool=pool)
+    bs = [synth.mix_rhs(mats[j], seeds) for j, _, seeds in systems]
+    gen_s = time.perf_counter() - t0
+    srv = aj.Server(int(budget_gb * 1e9), max_slots=512)
+
+    def run(reqs, r, seed):
+        gaps = np.random.default_rng(seed).exponential(1.0 / r, len(reqs))
+        arr = np.cumsum(gaps)
+        tickets = []
+        w0 = time.perf_counter()
+        for k, (j, nrhs, _) in reqs:
+            d = w0 + arr[len(tickets)] - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append(srv.submit_csr(mats[j], bs[k], nrhs=nrhs, precision="fp32_ir", tol=1e-8,
+                                          maxit=200000))
+        lat, rel, ok = [], [], 0
+        for t in tickets:
+            st, _, info = srv.result(t)
+            ok += st == aj.AJ_OK
+            lat.append(info["ms"])
+            rel.append(info["relres"])
+        wall = time.perf_counter() - w0
+        lat = np.array(lat)
+        return {"offered_per_s": r, "requests": len(reqs), "ok": ok, "solves_per_s": len(reqs) / wall,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_relres": float(max(rel)), "wall_s": wall}
+
+    reqs = list(enumerate(systems))
+    # warm-up: a few requests
+    for t in [srv.submit_csr(mats[j], bs[k], nrhs=nr, precision="fp32_ir", tol=1e-8) for k, (j, nr, _) in reqs[:4]]:
+        srv.result(t)
+    sat = run(reqs[:count], rate, 51)
+    sub_rate = 0.8 * sat["solves_per_s"]
+    sub = run(reqs[count:], sub_rate, 52)
+    st = srv.stats()
+    srv.close()
+    return {"workload": "Poisson arrivals; requests: 80%% the batched mix, 20%% 3-D Poisson (side 64..192), "
+                        "1-4 RHS, FP32 values + FP64 refinement to 1e-8, %.0f GB budget, matrices from a "
+                        "pool of %d" % (budget_gb, pool),
+            "generate_s": gen_s, "at_offered_rate": sat, "at_0.8x_capacity": sub,
+            "overloaded_at_offered_rate": sat["solves_per_s"] < 0.95 * rate,
+            "server": {"rounds": st["rounds"], "peak_active": st["peak_active"],
+                       "peak_GB": st["peak_bytes"] / 1e9, "kernel_ms": st["kernel_ms"]}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -187,6 +348,13 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=12)
     ap.add_argument("--workload", default=WORKLOAD,
                     help="poisson3d_N | poisson2d_N | chunglu_N | rgg_N (profiling cases)")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--graph-n", type=int, default=8388608)
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--served-count", type=int, default=300)
+    ap.add_argument("--served-rate", type=float, default=2000.0)
     ap.add_argument("--fixed-iters", type=int, default=0,
                     help="run exactly this many iterations per step instead of solving to 1e-8")
     args = ap.parse_args()
@@ -353,6 +521,14 @@ def main():
         e2e_v = B * its / sum(walls) / 1e9
         line["e2e"] = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * sum(walls) / len(walls)}
+    # ---- the graph, batched and served workloads (untimed by the headline)
+    if rank == 0 and not args.fixed_iters:
+        if not args.no_graph:
+            line["graph"] = bench_graph(aj, torch, dev, stream, hbm_peak, args.graph_n)
+        if not args.no_batched:
+            line["batched"] = bench_batched(aj, torch, dev, stream, args.batch_count, 48)
+        if not args.no_served:
+            line["served"] = bench_served(aj, torch, args.served_count, 48, args.served_rate, 120.0)
     # ---- CPU oracle on a bounded sample (rank 0, N = 1)
     if not args.no_cpu and ws == 1 and rank == 0:
         T = args.cpu_iters

@@ -110,21 +110,21 @@ void pack_iter_args(int pol, const IterLaunch& L, void* dst) {
     case 3: pack_iter_args_b16(L, dst); break;
   }
 }
-cudaError_t launch_batched(int pol, int nrhs, int qx, const BatchLaunch& B, int grid, cudaStream_t s) {
+cudaError_t launch_batched(int pol, int qx, const BatchLaunch& B, int grid, cudaStream_t s) {
   switch (pol) {
-    case 0: return launch_batched_f64(nrhs, qx, B, grid, s);
-    case 1: return launch_batched_df64(nrhs, qx, B, grid, s);
-    case 2: return launch_batched_f32(nrhs, qx, B, grid, s);
-    case 3: return launch_batched_b16(nrhs, qx, B, grid, s);
+    case 0: return launch_batched_f64(qx, B, grid, s);
+    case 1: return launch_batched_df64(qx, B, grid, s);
+    case 2: return launch_batched_f32(qx, B, grid, s);
+    case 3: return launch_batched_b16(qx, B, grid, s);
   }
   return cudaErrorInvalidValue;
 }
-int batched_blocks_per_sm(int pol, int nrhs, int qx) {
+int batched_blocks_per_sm(int pol, int qx) {
   switch (pol) {
-    case 0: return batched_blocks_per_sm_f64(nrhs, qx);
-    case 1: return batched_blocks_per_sm_df64(nrhs, qx);
-    case 2: return batched_blocks_per_sm_f32(nrhs, qx);
-    case 3: return batched_blocks_per_sm_b16(nrhs, qx);
+    case 0: return batched_blocks_per_sm_f64(qx);
+    case 1: return batched_blocks_per_sm_df64(qx);
+    case 2: return batched_blocks_per_sm_f32(qx);
+    case 3: return batched_blocks_per_sm_b16(qx);
   }
   return 0;
 }
@@ -515,7 +515,8 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     const int kp = kernel_pol(pol);
     const int bps = std::max(1, persistent_blocks_per_sm(kp, nrhs, c->qx));
     const int maxg = bps * c->sm_count;
-    const int ntiles = std::max(1, (int)((n + kThreads - 1) / kThreads));
+    const int rpt = kThreads >> lanes_log2(nrhs);  // rows per tile
+    const int ntiles = std::max(1, (int)((n + rpt - 1) / rpt));
     int g = std::min(maxg, ntiles);
     if (p->grid_ctas > 0) g = std::min(p->grid_ctas, maxg);
     c->grid = std::max(1, g);
@@ -646,6 +647,7 @@ static IterLaunch make_launch(aj_ctx* c, const void* bvec, long long maxit, int 
   IterLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.n = (int)c->n;
+  L.nrhs = c->nrhs;
   L.row_ptr = c->rp;
   L.col = c->ci;
   L.val = c->pol == AJ_FP64 ? (const void*)c->val64 : c->valp;
@@ -742,6 +744,7 @@ static aj_status build_sell(aj_ctx* c, int sigma, int lmax) {
   c->fmt = 0;
   c->fill = 1.0;
   const int n = (int)c->n;
+  const int rpt = kThreads >> lanes_log2(c->nrhs);  // rows per tile
   cudaStream_t s = c->stream;
   std::vector<int> rp((size_t)n + 1);
   CK(cudaMemcpyAsync(rp.data(), c->rp, rp.size() * 4, cudaMemcpyDeviceToHost, s));
@@ -778,7 +781,7 @@ static aj_status build_sell(aj_ctx* c, int sigma, int lmax) {
   int cnt = 0;
   for (int j = 0; j < (int)lng.size(); j++) {
     const int l = len(lng[j]);
-    if (cnt > 0 && (cnt == kThreads || acc + l > kLongTileEntries)) {
+    if (cnt > 0 && (cnt == rpt || acc + l > kLongTileEntries)) {
       ltp.push_back(j);
       acc = 0;
       cnt = 0;
@@ -814,7 +817,7 @@ static aj_status build_sell(aj_ctx* c, int sigma, int lmax) {
   CK(cudaMemsetAsync(c->d_scol, 0, ((size_t)tot + 32) * 4, s));
   CK(cudaMemsetAsync(c->d_sval, 0, ((size_t)tot + 32) * vb, s));
   c->nsell = nsell;
-  c->ntiles_sell = (nsell + kThreads - 1) / kThreads;
+  c->ntiles_sell = (nsell + rpt - 1) / rpt;
   c->nltiles = (int)ltp.size() - 1;
   c->nhuge = (int)hug.size();
   if (nsell) {
@@ -958,12 +961,13 @@ static int pow2_ceil(long long v) {
 // computes exactly what aj_solve computes with the same grid_ctas.
 static int batch_gang(const aj_ctx* c, int gmax) {
   if (c->prm.grid_ctas > 0) return std::max(1, std::min(c->prm.grid_ctas, gmax));
-  const long long ntiles = std::max<long long>(1, (c->n + kThreads - 1) / kThreads);
+  const long long rpt = kThreads >> lanes_log2(c->nrhs);
+  const long long ntiles = std::max<long long>(1, (c->n + rpt - 1) / rpt);
   return std::max(1, std::min({pow2_ceil((ntiles + 7) / 8), 64, gmax}));
 }
 
-// Solves every item (all of one precision and sweep form) with one batched
-// persistent launch per right-hand-side count.  Gangs of equal size form a
+// Solves every item (all of one precision and sweep form, any right-hand-side
+// counts) with one batched persistent launch.  Gangs of equal size form a
 // class; a class gets CTAs in proportion to its estimated work (stored
 // entries x sqrt(n), the AJ iteration count of 2-D Laplacians growing like
 // the grid side), at least one gang, and at most one gang per system.
@@ -982,12 +986,10 @@ static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, d
     ~Release() { w.release(); }
   } release{ws};
   const size_t abytes = iter_args_bytes();
-  for (int nr = 1; nr <= kMaxRhs; nr++) {
+  {
     std::vector<int> idx;
-    for (int i = 0; i < (int)items.size(); i++)
-      if (items[i].c->nrhs == nr) idx.push_back(i);
-    if (idx.empty()) continue;
-    const int bps = batched_blocks_per_sm(pol, nr, qx);
+    for (int i = 0; i < (int)items.size(); i++) idx.push_back(i);
+    const int bps = batched_blocks_per_sm(pol, qx);
     if (bps < 1) return AJ_ECUDA;
     const int gmax = bps * c0->sm_count;
     const int m = (int)idx.size();
@@ -997,7 +999,7 @@ static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, d
     for (int j = 0; j < m; j++) {
       const aj_ctx* c = items[idx[j]].c;
       gsz[j] = batch_gang(c, gmax);
-      cost[j] = (double)(c->nnz + c->n) * (1.0 + 0.5 * (nr - 1)) * std::sqrt((double)std::max<int64_t>(c->n, 1));
+      cost[j] = (double)(c->nnz + c->n) * (1.0 + 0.5 * (c->nrhs - 1)) * std::sqrt((double)std::max<int64_t>(c->n, 1));
       sizes.push_back(gsz[j]);
     }
     std::sort(sizes.begin(), sizes.end());
@@ -1071,7 +1073,7 @@ static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, d
     int4* d_cg = (int4*)ws.alloc(cta_gang.size() * sizeof(int4));
     unsigned long long* d_bar = (unsigned long long*)ws.alloc((size_t)ngang * 8);
     int* d_slot = (int*)ws.alloc((size_t)ngang * 4);
-    double* d_part = (double*)ws.alloc((size_t)grid * 2 * nr * kNRed * 8);
+    double* d_part = (double*)ws.alloc((size_t)grid * 2 * kMaxRhs * kNRed * 8);
     int* d_err = (int*)ws.alloc(64);
     if (!d_sys || !d_order || !d_cb || !d_head || !d_cg || !d_bar || !d_slot || !d_part || !d_err)
       return AJ_ENOMEM;
@@ -1093,7 +1095,7 @@ static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, d
     B.gang_part = d_part;
     B.err = d_err;
     CK(cudaEventRecord(c0->kev0, s));
-    CK(launch_batched(pol, nr, qx, B, grid, s));
+    CK(launch_batched(pol, qx, B, grid, s));
     counted();
     CK(cudaEventRecord(c0->kev1, s));
     int err = 0;

@@ -319,22 +319,32 @@ struct PolB16 : PolF32 {
 
 // ----------------------------------------------------------------------------
 // Kernel arguments.  Vectors with several right-hand sides are interleaved:
-// element (i, r) lives at i * nrhs + r, so one gather fetches all of them.
+// element (i, r) lives at i * nrhs + r.
 //
-// Matrix formats.  CSR: tile k is rows 256k .. 256k+255, one row per thread.
-// SELL-C-sigma (C = 32): the rows without the long ones are sorted by length
-// (longest first) within windows of sigma rows; position p of that order holds
-// row perm[p], and slice p / 32 stores its 32 rows column-major, entry k of
-// position p at sptr[p / 32] + 32 k + p % 32, so the lanes of a warp read
-// consecutive words.  Entries keep their CSR order, so a row sums in the same
-// order in both formats.  Tiles past the SELL ones hold the long rows
-// (long_rows, longest first, at most 256 and a bounded number of entries per
-// tile, dealt round-robin over the warps), each summed by a whole warp from
-// the CSR arrays; the last tiles hold one huge row each, summed by the whole
-// CTA.
+// Lanes per row.  A system with nrhs right-hand sides gives each matrix row
+// 2^lgr adjacent lanes of a warp (lgr = 0, 1, 2 for nrhs = 1, 2, 3-4); lane r
+// of a row owns right-hand side r (with nrhs = 3 the fourth lane idles).  The
+// lanes of a row read the same matrix entries (one broadcast access) and
+// gather x[col * nrhs + r], adjacent words of one sector.  Every lane carries
+// the state of one right-hand side only, so a thread needs the registers of a
+// one-RHS sweep whatever nrhs is, and a tile holds 256 >> lgr rows.
+//
+// Matrix formats.  CSR: tile k is rows k*T .. k*T + T-1 (T = 256 >> lgr), one
+// row per lane group.  SELL-C-sigma (C = 32): the rows without the long ones
+// are sorted by length (longest first) within windows of sigma rows; position
+// p of that order holds row perm[p], and slice p / 32 stores its 32 rows
+// column-major, entry k of position p at sptr[p / 32] + 32 k + p % 32, so
+// consecutive positions read consecutive words.  Entries keep their CSR
+// order, so a row sums in the same order in both formats.  Tiles past the SELL
+// ones hold the long rows (long_rows, longest first, at most T and a bounded
+// number of entries per tile, dealt round-robin over the warps), each summed
+// by a whole warp from the CSR arrays; the last tiles hold one huge row each,
+// summed by the whole CTA.
 template <class P>
 struct IterArgs {
   int n;
+  int nrhs;                   // right-hand sides, 1..4
+  int lgr;                    // log2 of the lanes per row (0, 1 or 2)
   const int* row_ptr;
   const int* col;
   const typename P::V* val;
@@ -373,17 +383,32 @@ struct IterArgs {
   long long max_sweeps;       // sweeps allowed in this launch (chunked runs), >= 1
 };
 
-// Partial row sums over entries q0, q0 + step, ... < re (CSR arrays), U of
-// them loaded before their multiply-adds, which run in entry order.
-template <class P, int NR, bool QX>
-__device__ __forceinline__ void row_sums_strided(const IterArgs<P>& a, int q0, int re, int step,
-                                                 const typename P::X* const* xc,
-                                                 const typename P::X* const* xp, const bool* same,
-                                                 const bool* active, typename P::S* lx,
-                                                 typename P::S* lp) {
+// log2 of the lanes per row for nrhs right-hand sides.
+__host__ __device__ constexpr int lanes_log2(int nrhs) { return nrhs <= 1 ? 0 : nrhs == 2 ? 1 : 2; }
+
+// Iterate buffer k (0..2) and stored-product buffer k (0..1), chosen by
+// selects so that no argument array is indexed at run time.
+template <class P>
+__device__ __forceinline__ typename P::X* xbuf(const IterArgs<P>& a, int k) {
+  return k == 0 ? a.x[0] : k == 1 ? a.x[1] : a.x[2];
+}
+template <class P>
+__device__ __forceinline__ typename P::X* ubuf(const IterArgs<P>& a, int k) {
+  return k == 0 ? a.u[0] : a.u[1];
+}
+
+// Partial row sums over entries q0, q0 + step, ... < re (CSR arrays) for
+// right-hand side r of an nr-RHS system, U entries loaded before their
+// multiply-adds, which run in entry order.  lx sums against x^{s-1} (buffer
+// xc); lp against x^{s-2} (buffer xp) when `two` (lazy form, the two differ).
+template <class P, bool QX>
+__device__ __forceinline__ void row_sums_strided(const IterArgs<P>& a, int nr, int r,
+                                                 const typename P::X* xc, const typename P::X* xp,
+                                                 bool two, int q0, int re, int step,
+                                                 typename P::S& lx, typename P::S& lp) {
   using S = typename P::S;
   using V = typename P::V;
-  constexpr int U = NR * (QX ? 1 : 2) >= 4 ? 2 : 4;
+  constexpr int U = 4;
   for (int q = q0; q < re; q += U * step) {
     int cc[U];
     V vv[U];
@@ -393,104 +418,84 @@ __device__ __forceinline__ void row_sums_strided(const IterArgs<P>& a, int q0, i
       cc[k] = in ? ld_ro(a.col + q + k * step) : 0;
       vv[k] = in ? P::ldv(a.val + q + k * step) : P::vzero();
     }
-    S xv[U][NR], pv[U][NR];
+    S xv[U], pv[U];
 #pragma unroll
-    for (int k = 0; k < U; k++)
-#pragma unroll
-      for (int r = 0; r < NR; r++) {
-        xv[k][r] = P::zero();
-        pv[k][r] = P::zero();
-        if (q + k * step < re && active[r]) {
-          xv[k][r] = P::ldx(xc[r] + (size_t)cc[k] * NR + r);
-          if (!QX && !same[r]) pv[k][r] = P::ldx(xp[r] + (size_t)cc[k] * NR + r);
-        }
+    for (int k = 0; k < U; k++) {
+      xv[k] = P::zero();
+      pv[k] = P::zero();
+      if (q + k * step < re) {
+        xv[k] = P::ldx(xc + (size_t)cc[k] * nr + r);
+        if (two) pv[k] = P::ldx(xp + (size_t)cc[k] * nr + r);
       }
+    }
 #pragma unroll
     for (int k = 0; k < U; k++) {
       if (q + k * step >= re) break;
-#pragma unroll
-      for (int r = 0; r < NR; r++) {
-        if (!active[r]) continue;
-        P::macv(lx[r], vv[k], xv[k][r]);
-        if (!QX && !same[r]) P::macv(lp[r], vv[k], pv[k][r]);
-      }
+      P::macv(lx, vv[k], xv[k]);
+      if (two) P::macv(lp, vv[k], pv[k]);
     }
   }
 }
 
-// Warp-cooperative row sums for one long row (lanes stride over the entries,
-// then a fixed xor tree).  Returns the sums in every lane.  The stored form
-// (QX) forms only sx.
-template <class P, int NR, bool QX>
-__device__ __forceinline__ void long_row_sums(const IterArgs<P>& a, int rs, int re,
-                                              const typename P::X* const* xc,
-                                              const typename P::X* const* xp, const bool* same,
-                                              const bool* active, typename P::S* sx,
-                                              typename P::S* sp) {
+// Warp-cooperative row sums of one long row for right-hand side r (lanes
+// stride over the entries, then a fixed xor tree).  Returns the sums in every
+// lane; sp equals sx when the stored form or x^{s-1} = x^{s-2} needs no
+// second sum.  Every lane of the warp must call it.
+template <class P, bool QX>
+__device__ __forceinline__ void long_row_sums(const IterArgs<P>& a, const RhsState& q, int nr, int r,
+                                              int rs, int re, typename P::S& sx, typename P::S& sp) {
   using S = typename P::S;
   const int lane = threadIdx.x & 31;
-  S lx[NR], lp[NR];
+  const bool two = !QX && q.cur != q.prev;
+  S lx = P::zero(), lp = P::zero();
+  if (!q.done)
+    row_sums_strided<P, QX>(a, nr, r, xbuf(a, q.cur), xbuf(a, q.prev), two, rs + lane, re, 32, lx, lp);
+  lx = P::finish(lx);
 #pragma unroll
-  for (int r = 0; r < NR; r++) { lx[r] = P::zero(); lp[r] = P::zero(); }
-  row_sums_strided<P, NR, QX>(a, rs + lane, re, 32, xc, xp, same, active, lx, lp);
+  for (int m = 16; m >= 1; m >>= 1) lx = P::combine(lx, P::shfl_xor(lx, m));
+  sx = lx;
+  sp = lx;
+  if (two) {
+    lp = P::finish(lp);
 #pragma unroll
-  for (int r = 0; r < NR; r++) {
-    lx[r] = P::finish(lx[r]);
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) lx[r] = P::combine(lx[r], P::shfl_xor(lx[r], m));
-    sx[r] = lx[r];
-    if (!QX) {
-      lp[r] = P::finish(lp[r]);
-#pragma unroll
-      for (int m = 16; m >= 1; m >>= 1) lp[r] = P::combine(lp[r], P::shfl_xor(lp[r], m));
-      sp[r] = same[r] ? lx[r] : lp[r];
-    }
+    for (int m = 16; m >= 1; m >>= 1) lp = P::combine(lp, P::shfl_xor(lp, m));
+    sp = lp;
   }
 }
 
-// CTA-cooperative row sums for one huge row: threads stride over the
-// entries, then a fixed xor tree per warp and the warps in order.  Results
-// valid in thread 0.  Every thread of the CTA must call it.
-template <class P, int NR, bool QX>
-__device__ __forceinline__ void cta_row_sums(const IterArgs<P>& a, int rs, int re,
-                                             const typename P::X* const* xc,
-                                             const typename P::X* const* xp, const bool* same,
-                                             const bool* active, typename P::S* sx,
-                                             typename P::S* sp) {
+// CTA-cooperative row sums of one huge row for right-hand side r: threads
+// stride over the entries, then a fixed xor tree per warp and the warps in
+// order.  Results valid in every thread.  Every thread of the CTA must call it.
+template <class P, bool QX>
+__device__ __forceinline__ void cta_row_sums(const IterArgs<P>& a, const RhsState& q, int nr, int r,
+                                             int rs, int re, typename P::S& sx, typename P::S& sp) {
   using S = typename P::S;
-  __shared__ S red[2][NR][kWarps];
-  S lx[NR], lp[NR];
-#pragma unroll
-  for (int r = 0; r < NR; r++) { lx[r] = P::zero(); lp[r] = P::zero(); }
-  row_sums_strided<P, NR, QX>(a, rs + threadIdx.x, re, kThreads, xc, xp, same, active, lx, lp);
+  __shared__ S red[2][kWarps];
+  const bool two = !QX && q.cur != q.prev;
+  S lx = P::zero(), lp = P::zero();
+  if (!q.done)
+    row_sums_strided<P, QX>(a, nr, r, xbuf(a, q.cur), xbuf(a, q.prev), two, rs + threadIdx.x, re,
+                            kThreads, lx, lp);
   const int w = threadIdx.x >> 5;
+  lx = P::finish(lx);
+  lp = P::finish(lp);
 #pragma unroll
-  for (int r = 0; r < NR; r++) {
-    lx[r] = P::finish(lx[r]);
-    lp[r] = P::finish(lp[r]);
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-      lx[r] = P::combine(lx[r], P::shfl_xor(lx[r], m));
-      if (!QX) lp[r] = P::combine(lp[r], P::shfl_xor(lp[r], m));
-    }
-    if ((threadIdx.x & 31) == 0) {
-      red[0][r][w] = lx[r];
-      red[1][r][w] = lp[r];
-    }
+  for (int m = 16; m >= 1; m >>= 1) {
+    lx = P::combine(lx, P::shfl_xor(lx, m));
+    if (two) lp = P::combine(lp, P::shfl_xor(lp, m));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = lx;
+    red[1][w] = lp;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int r = 0; r < NR; r++) {
-      S tx = red[0][r][0], tp = red[1][r][0];
-      for (int k = 1; k < kWarps; k++) {
-        tx = P::combine(tx, red[0][r][k]);
-        if (!QX) tp = P::combine(tp, red[1][r][k]);
-      }
-      sx[r] = tx;
-      sp[r] = (QX || same[r]) ? tx : tp;
-    }
+  S tx = red[0][0], tp = red[1][0];
+  for (int k = 1; k < kWarps; k++) {
+    tx = P::combine(tx, red[0][k]);
+    if (two) tp = P::combine(tp, red[1][k]);
   }
+  sx = tx;
+  sp = two ? tp : tx;
   __syncthreads();
 }
 
@@ -515,63 +520,72 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
   return s;
 }
 
-// One sweep over the CTA's tiles: the fused SpMV at y, x update and reduction
-// terms.  `compute_x` is false on a residual-only sweep (no x^s is formed).
-// Reduction slots: 0 d, 2 rr, 3 <x, Qx> and 4 <b, x> (objective stop only);
-// slot 1 is unused.
+// Per right-hand side r < nr, the CTA's sum of v over the lanes that own r:
+// a xor tree over the lanes of equal r within each warp, then the warps in
+// order.  Result valid in thread r.  `sm` holds kWarps * kMaxRhs doubles.
+// With one lane per row (lg = 0) this is block_sum.
+__device__ __forceinline__ double block_sum_rhs(double v, double* sm, int lg, int nr) {
+  for (int m = 16; m >= (1 << lg); m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane < (1 << lg)) sm[w * kMaxRhs + lane] = v;
+  __syncthreads();
+  double s = 0.0;
+  if ((int)threadIdx.x < nr)
+    for (int i = 0; i < kWarps; i++) s += sm[i * kMaxRhs + threadIdx.x];
+  __syncthreads();
+  return s;
+}
+
 // Entries per unrolled chunk of a short row: as many gathers in flight as the
-// register budget allows for NR right-hand sides and the sweep form.
+// register budget allows for the sweep form.
 #ifndef AJ_ROW_UNROLL
 #define AJ_ROW_UNROLL 8
 #endif
-__host__ __device__ constexpr int row_unroll(int nr, bool qx) {
-  return nr * (qx ? 1 : 2) * 8 / AJ_ROW_UNROLL >= 8   ? 1
-         : nr * (qx ? 1 : 2) * 8 / AJ_ROW_UNROLL >= 4 ? 2
-         : nr * (qx ? 1 : 2) * 8 / AJ_ROW_UNROLL >= 2 ? 4
-                                                       : 8;
+__host__ __device__ constexpr int row_unroll(bool qx) {
+  return (qx ? 1 : 2) * 8 / AJ_ROW_UNROLL >= 2 ? 4 : 8;
 }
 
+// One sweep over the CTA's tiles: the fused SpMV at y, x update and reduction
+// terms.  `compute_x` is false on a residual-only sweep (no x^s is formed).
+// Reduction slots (per lane, for the lane's right-hand side): 0 d, 2 rr,
+// 3 <x, Qx> and 4 <b, x> (objective stop only); slot 1 is unused.
 // ANY: the kernel handles both formats (runtime a.fmt); otherwise CSR only,
-// which keeps the SELL code and its registers out of the CSR kernel.
-template <class P, int NR, bool QX, bool ANY>
+// which keeps the SELL code and its registers out of the CSR kernel.  MULTI:
+// nrhs and the lanes per row come from the arguments; otherwise one.
+template <class P, bool QX, bool ANY, bool MULTI>
 __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, bool compute_x,
-                                      bool want_obj, typename P::A (&acc)[NR][kNRed], int cta,
+                                      bool want_obj, typename P::A (&acc)[kNRed], int cta,
                                       int ncta) {
   using S = typename P::S;
   using V = typename P::V;
   using X = typename P::X;
-  const X* xc[NR];
-  const X* xp[NR];
-  X* xn[NR];
-  const X* up[NR];
-  X* uc[NR];
-  bool same[NR], active[NR];
-  S beta[NR];
-#pragma unroll
-  for (int r = 0; r < NR; r++) {
-    xc[r] = a.x[st[r].cur];
-    xp[r] = a.x[st[r].prev];
-    xn[r] = a.x[st[r].nxt];
-    if (QX) {
-      uc[r] = a.u[st[r].uw];
-      up[r] = a.u[1 - st[r].uw];
-    }
-    same[r] = st[r].cur == st[r].prev;
-    active[r] = st[r].done == 0;
-    beta[r] = P::coef(st[r].beta);
-  }
+  const int nr = MULTI ? a.nrhs : 1;
+  const int lg = MULTI ? a.lgr : 0;
+  const int r = threadIdx.x & ((1 << lg) - 1);   // this lane's right-hand side
+  const int slot = threadIdx.x >> lg;            // this lane group's row slot in a tile
+  const int rpt = kThreads >> lg;                // rows per tile
+  const bool lane_on = r < nr;
+  const RhsState& me = st[lane_on ? r : 0];
+  const X* xc = xbuf(a, me.cur);
+  const X* xp = xbuf(a, me.prev);
+  X* xn = xbuf(a, me.nxt);
+  X* uc = QX ? ubuf(a, me.uw) : nullptr;
+  const X* up = QX ? ubuf(a, 1 - me.uw) : nullptr;
+  const bool same = me.cur == me.prev;
+  const bool active = lane_on && me.done == 0;
+  const S beta = P::coef(me.beta);
   const int lane = threadIdx.x & 31;
   const bool sell = ANY && a.fmt != 0;
-  const int ntiles = sell ? a.ntiles_sell + a.nltiles + a.nhuge : (a.n + kThreads - 1) / kThreads;
+  const int ntiles = sell ? a.ntiles_sell + a.nltiles + a.nhuge : (a.n + rpt - 1) / rpt;
   for (int tile = cta; tile < ntiles; tile += ncta) {
-    // this thread's row i, its entries colp[k * stride], valp[k * stride]
+    // this lane group's row i, its entries colp[k * stride], valp[k * stride]
     // (k < cnt) and, for long rows, its CSR range rs .. re
     int i, rs = 0, re = 0, cnt = 0, stride = 1;
     bool valid, is_long, huge = false;
     const int* colp = a.col;
     const V* valp = a.val;
     if (!sell) {
-      i = tile * kThreads + threadIdx.x;
+      i = tile * rpt + slot;
       valid = i < a.n;
       if (valid) {
         rs = ld_ro(a.row_ptr + i);
@@ -582,7 +596,7 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       colp += rs;
       valp += rs;
     } else if (tile < a.ntiles_sell) {
-      const int pos = tile * kThreads + threadIdx.x;
+      const int pos = tile * rpt + slot;
       valid = pos < a.nsell;
       i = valid ? ld_ro(a.perm + pos) : 0;
       if (valid) {
@@ -595,9 +609,9 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       is_long = false;
     } else if (tile < a.ntiles_sell + a.nltiles) {
       // long rows dealt round-robin over the warps: row j of the tile goes to
-      // warp j % 8, lane j / 8
+      // warp j % 8, row slot j / 8 of that warp
       const int lt = tile - a.ntiles_sell;
-      const int pos = ld_ro(a.ltp + lt) + (threadIdx.x & 31) * kWarps + (threadIdx.x >> 5);
+      const int pos = ld_ro(a.ltp + lt) + (lane >> lg) * kWarps + (threadIdx.x >> 5);
       valid = pos < ld_ro(a.ltp + lt + 1);
       i = valid ? ld_ro(a.long_rows + pos) : 0;
       if (valid) {
@@ -611,17 +625,20 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       re = ld_ro(a.row_ptr + i + 1);
       huge = true;
       is_long = false;
-      valid = threadIdx.x == 0;  // thread 0 owns the row's update
+      valid = slot == 0;  // the first lane group owns the row's update
     }
-    S sx[NR], sp[NR];
-#pragma unroll
-    for (int r = 0; r < NR; r++) { sx[r] = P::zero(); sp[r] = P::zero(); }
+    S sx = P::zero(), sp = P::zero();
     if (ANY && huge) {
-      cta_row_sums<P, NR, QX>(a, rs, re, xc, xp, same, active, sx, sp);
-    } else if (valid && !is_long) {
+      for (int k = 0; k < nr; k++) {
+        S hx, hp;
+        cta_row_sums<P, QX>(a, st[k], nr, k, rs, re, hx, hp);
+        if (k == r) { sx = hx; sp = hp; }
+      }
+    } else if (valid && !is_long && active) {
       // chunks of U entries: every load of a chunk is issued before its
       // multiply-adds, which then run in ascending entry order
-      constexpr int U = row_unroll(NR, QX);
+      constexpr int U = row_unroll(QX);
+      const bool two = !QX && !same;
       for (int q0 = 0; q0 < cnt; q0 += U) {
         int cc[U];
         V vv[U];
@@ -631,95 +648,79 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
           cc[k] = in ? ld_ro(colp + (q0 + k) * stride) : 0;
           vv[k] = in ? P::ldv(valp + (q0 + k) * stride) : P::vzero();
         }
-        S xv[U][NR], pv[U][NR];
+        S xv[U], pv[U];
 #pragma unroll
-        for (int k = 0; k < U; k++)
-#pragma unroll
-          for (int r = 0; r < NR; r++) {
-            xv[k][r] = P::zero();
-            pv[k][r] = P::zero();
-            if (q0 + k < cnt && active[r]) {
-              xv[k][r] = P::ldx(xc[r] + (size_t)cc[k] * NR + r);
-              if (!QX && !same[r]) pv[k][r] = P::ldx(xp[r] + (size_t)cc[k] * NR + r);
-            }
+        for (int k = 0; k < U; k++) {
+          xv[k] = P::zero();
+          pv[k] = P::zero();
+          if (q0 + k < cnt) {
+            xv[k] = P::ldx(xc + (size_t)cc[k] * nr + r);
+            if (two) pv[k] = P::ldx(xp + (size_t)cc[k] * nr + r);
           }
+        }
 #pragma unroll
         for (int k = 0; k < U; k++) {
           if (q0 + k >= cnt) break;
-#pragma unroll
-          for (int r = 0; r < NR; r++) {
-            if (!active[r]) continue;
-            P::macv(sx[r], vv[k], xv[k][r]);
-            if (!QX && !same[r]) P::macv(sp[r], vv[k], pv[k][r]);
-          }
+          P::macv(sx, vv[k], xv[k]);
+          if (two) P::macv(sp, vv[k], pv[k]);
         }
       }
-#pragma unroll
-      for (int r = 0; r < NR; r++) {
-        sx[r] = P::finish(sx[r]);
-        if (!QX) sp[r] = same[r] ? sx[r] : P::finish(sp[r]);
-      }
+      sx = P::finish(sx);
+      if (!QX) sp = same ? sx : P::finish(sp);
     }
-    unsigned lm = __ballot_sync(0xffffffffu, is_long);
+    // long rows: the whole warp sums each one for every right-hand side; the
+    // lane of right-hand side k of the row's group takes sum k
+    unsigned lm = __ballot_sync(0xffffffffu, is_long && r == 0);
     while (lm) {
       const int src = __ffs(lm) - 1;
       lm &= lm - 1;
       const int lrs = __shfl_sync(0xffffffffu, rs, src);
       const int lre = __shfl_sync(0xffffffffu, re, src);
-      S tx[NR], tp[NR];
-      long_row_sums<P, NR, QX>(a, lrs, lre, xc, xp, same, active, tx, tp);
-      if (lane == src) {
-#pragma unroll
-        for (int r = 0; r < NR; r++) {
-          sx[r] = tx[r];
-          if (!QX) sp[r] = tp[r];
-        }
+      for (int k = 0; k < nr; k++) {
+        S tx, tp;
+        long_row_sums<P, QX>(a, st[k], nr, k, lrs, lre, tx, tp);
+        if (lane == src + k) { sx = tx; sp = tp; }
       }
     }
-    if (!valid) continue;
+    if (!valid || !active) continue;
     const S ji = P::ldr(a.jinv + i);
-#pragma unroll
-    for (int r = 0; r < NR; r++) {
-      if (!active[r]) continue;
-      const size_t e = (size_t)i * NR + r;
-      const S xi = P::ldx(xc[r] + e);
-      const S bi = P::ldr(a.b + e);
-      // g0 = Q x^{s-1} - b: minus the exact residual of x^{s-1}
-      const S g0 = P::sub(sx[r], bi);
-      P::acc_prod(acc[r][2], g0, g0);
-      if (want_obj) {
-        P::acc_prod(acc[r][3], xi, sx[r]);
-        P::acc_prod(acc[r][4], bi, xi);
-      }
-      if (QX) P::stx(uc[r] + e, sx[r]);
-      if (!compute_x) continue;
-      S g, yi;
-      if (same[r]) {
-        g = g0;
-        yi = xi;
-      } else {
-        const S xpi = P::ldx(xp[r] + e);
-        const S spi = QX ? P::ldx(up[r] + e) : sp[r];
-        g = P::fma_(beta[r], P::sub(sx[r], spi), g0);
-        yi = P::fma_(beta[r], P::sub(xi, xpi), xi);
-      }
-      const S xnew = P::fnma(ji, g, yi);
-      P::stx(xn[r] + e, xnew);
-      P::acc_prod(acc[r][0], g, P::sub(xnew, xi));
+    const size_t e = (size_t)i * nr + r;
+    const S xi = P::ldx(xc + e);
+    const S bi = P::ldr(a.b + e);
+    // g0 = Q x^{s-1} - b: minus the exact residual of x^{s-1}
+    const S g0 = P::sub(sx, bi);
+    P::acc_prod(acc[2], g0, g0);
+    if (want_obj) {
+      P::acc_prod(acc[3], xi, sx);
+      P::acc_prod(acc[4], bi, xi);
     }
+    if (QX) P::stx(uc + e, sx);
+    if (!compute_x) continue;
+    S g, yi;
+    if (same) {
+      g = g0;
+      yi = xi;
+    } else {
+      const S xpi = P::ldx(xp + e);
+      const S spi = QX ? P::ldx(up + e) : sp;
+      g = P::fma_(beta, P::sub(sx, spi), g0);
+      yi = P::fma_(beta, P::sub(xi, xpi), xi);
+    }
+    const S xnew = P::fnma(ji, g, yi);
+    P::stx(xn + e, xnew);
+    P::acc_prod(acc[0], g, P::sub(xnew, xi));
   }
 }
 
 // Scalar step after the grid barrier, run by one thread per CTA with the
 // grid totals tot[r][k].  Identical inputs give identical decisions in every
 // CTA.  Returns true when every right-hand side is done.
-template <int NR>
-__device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kNRed], long long s,
+__device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kNRed], int nr, long long s,
                                             long long maxit, int stop, int restart, int momentum,
                                             double tol, double fstar, double fscale, long long* rlog,
                                             int rlog_cap, bool log_it) {
   bool all_done = true;
-  for (int r = 0; r < NR; r++) {
+  for (int r = 0; r < nr; r++) {
     RhsState& q = st[r];
     if (q.done) continue;
     const double d = tot[r][0];
@@ -785,16 +786,15 @@ __device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kN
 // Co-resident CTAs per SM the register allocation must allow.  The sweep is
 // latency bound (gathers from L2, the matrix stream from DRAM), so warps in
 // flight matter more than registers: measured on the 256^3 Poisson system,
-// 4 CTAs/SM beat the compiler's own choice of 2-3 by 1.3-1.7x for one
-// right-hand side.  More right-hand sides need more registers per thread.
-__host__ __device__ constexpr int min_blocks(int nr) { return nr == 1 ? 4 : nr == 2 ? 2 : 1; }
+// 4 CTAs/SM beat the compiler's own choice of 2-3 by 1.3-1.7x.  A lane holds
+// one right-hand side whatever nrhs is, so every instantiation aims at 4.
+constexpr int kMinBlocks = 4;
 
 // Shared memory of one solve: per-RHS state, grid totals, reduction scratch.
-template <int NR>
 struct SolveSmem {
-  RhsState st[NR];
-  double tot[NR][kNRed];
-  double red[kWarps];
+  RhsState st[kMaxRhs];
+  double tot[kMaxRhs][kNRed];
+  double red[kWarps * kMaxRhs];
   int done;
 };
 
@@ -804,43 +804,39 @@ struct SolveSmem {
 // arrival count so far and `sw` the sweep counter that parity-buffers the
 // partials; both carry over between systems that reuse the same barrier.
 // Returns false when a barrier gave up (error already recorded in *a.err).
-template <class P, int NR, bool QX, bool ANY>
-__device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem<NR>& sm, int cta,
-                                          int ncta, unsigned long long& target, long long& sw) {
+template <class P, bool QX, bool ANY, bool MULTI>
+__device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, int cta, int ncta,
+                                          unsigned long long& target, long long& sw) {
   using A = typename P::A;
   const bool want_obj = a.stop == kStopObjgap;
+  const int nr = MULTI ? a.nrhs : 1;
+  const int lg = MULTI ? a.lgr : 0;
   for (long long s0 = 0; s0 < a.max_sweeps; s0++, sw++) {
     // sweep number in the run's own numbering: x^{s-1} is checked, x^s formed
     long long s_run = 0;
     bool compute_x = false;
-#pragma unroll
-    for (int r = 0; r < NR; r++) {
+    for (int r = 0; r < nr; r++) {
       if (!sm.st[r].done) {
         s_run = sm.st[r].t + 1;
         compute_x = compute_x || (sm.st[r].t < a.maxit);
       }
     }
-    A acc[NR][kNRed];
+    A acc[kNRed];
 #pragma unroll
-    for (int r = 0; r < NR; r++)
-#pragma unroll
-      for (int k = 0; k < kNRed; k++) acc_zero(acc[r][k]);
-    sweep<P, NR, QX, ANY>(a, sm.st, compute_x, want_obj, acc, cta, ncta);
+    for (int k = 0; k < kNRed; k++) acc_zero(acc[k]);
+    sweep<P, QX, ANY, MULTI>(a, sm.st, compute_x, want_obj, acc, cta, ncta);
     // CTA partials -> global (parity-buffered by sweep)
-    double* part = a.partials + (size_t)(sw & 1) * ncta * NR * kNRed;
+    double* part = a.partials + (size_t)(sw & 1) * ncta * nr * kNRed;
 #pragma unroll
-    for (int r = 0; r < NR; r++)
-#pragma unroll
-      for (int k = 0; k < kNRed; k++) {
-        if (!slot_used(k, want_obj)) continue;
-        const double v = block_sum(acc_value(acc[r][k]), sm.red);
-        if (threadIdx.x == 0) __stcg(part + ((size_t)cta * NR + r) * kNRed + k, v);
-      }
+    for (int k = 0; k < kNRed; k++) {
+      if (!slot_used(k, want_obj)) continue;
+      const double v = block_sum_rhs(acc_value(acc[k]), sm.red, lg, nr);
+      if ((int)threadIdx.x < nr) __stcg(part + ((size_t)cta * nr + threadIdx.x) * kNRed + k, v);
+    }
     target += (unsigned long long)ncta;
     if (!grid_sync(a.bar, target, a.err, (unsigned)ncta)) return false;
     // every CTA sums the partials in the same fixed order
-#pragma unroll
-    for (int r = 0; r < NR; r++)
+    for (int r = 0; r < nr; r++)
 #pragma unroll
       for (int k = 0; k < kNRed; k++) {
         if (!slot_used(k, want_obj)) {
@@ -849,22 +845,22 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem<NR>& s
         }
         double v = 0.0;
         for (int c = threadIdx.x; c < ncta; c += kThreads)
-          v += __ldcg(part + ((size_t)c * NR + r) * kNRed + k);
+          v += __ldcg(part + ((size_t)c * nr + r) * kNRed + k);
         v = block_sum(v, sm.red);
         if (threadIdx.x == 0) sm.tot[r][k] = v;
       }
     if (threadIdx.x == 0) {
       if (a.trace && cta == 0 && s_run >= 1 && s_run <= a.trace_cap) {
-        for (int r = 0; r < NR; r++) {
-          double* tr = a.trace + ((size_t)(s_run - 1) * NR + r) * 4;
+        for (int r = 0; r < nr; r++) {
+          double* tr = a.trace + ((size_t)(s_run - 1) * nr + r) * 4;
           tr[0] = sm.tot[r][0];
           tr[1] = sm.tot[r][1];
           tr[2] = sm.tot[r][2];
           tr[3] = sm.st[r].beta;
         }
       }
-      sm.done = scalar_step<NR>(sm.st, sm.tot, s_run, a.maxit, a.stop, a.restart, a.momentum,
-                                a.tol, a.fstar, a.fscale, a.rlog, a.rlog_cap, cta == 0)
+      sm.done = scalar_step(sm.st, sm.tot, nr, s_run, a.maxit, a.stop, a.restart, a.momentum, a.tol,
+                            a.fstar, a.fscale, a.rlog, a.rlog_cap, cta == 0)
                     ? 1
                     : 0;
     }
@@ -879,16 +875,18 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem<NR>& s
 
 // The persistent fused AJ kernel for one system.  Launch cooperatively with
 // kThreads threads per CTA; every CTA of the grid works on the system.  ANY
-// selects the instantiation that also reads the SELL-C-sigma format.
-template <class P, int NR, bool QX, bool ANY>
-__global__ void __launch_bounds__(kThreads, min_blocks(NR)) aj_persistent_kernel(IterArgs<P> a) {
-  __shared__ SolveSmem<NR> sm;
-  if (threadIdx.x < NR) sm.st[threadIdx.x] = a.state[threadIdx.x];
+// selects the instantiation that also reads the SELL-C-sigma format, MULTI
+// the one for several right-hand sides.
+template <class P, bool QX, bool ANY, bool MULTI>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) aj_persistent_kernel(IterArgs<P> a) {
+  __shared__ SolveSmem sm;
+  const int nr = MULTI ? a.nrhs : 1;
+  if ((int)threadIdx.x < nr) sm.st[threadIdx.x] = a.state[threadIdx.x];
   __syncthreads();
   unsigned long long target = 0;
   long long sw = 0;
-  if (!run_solve<P, NR, QX, ANY>(a, sm, blockIdx.x, gridDim.x, target, sw)) return;
-  if (blockIdx.x == 0 && threadIdx.x < NR) a.state[threadIdx.x] = sm.st[threadIdx.x];
+  if (!run_solve<P, QX, ANY, MULTI>(a, sm, blockIdx.x, gridDim.x, target, sw)) return;
+  if (blockIdx.x == 0 && (int)threadIdx.x < nr) a.state[threadIdx.x] = sm.st[threadIdx.x];
 }
 
 // ----------------------------------------------------------------------------
@@ -898,7 +896,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(NR)) aj_persistent_kernel
 // .. cls_begin[k+1]) (largest first) through an atomic head, solves each one
 // with its own gang barrier and then takes the next.  Each system keeps its
 // own state, restart log and stop test; its arithmetic depends only on the
-// system and the gang size, not on the other systems in the batch.
+// system and the gang size, not on the other systems in the batch.  Systems
+// of any right-hand-side count share the launch.
 template <class P>
 struct BatchArgs {
   const IterArgs<P>* sys;       // per system (partials, bar and err are ignored)
@@ -908,13 +907,13 @@ struct BatchArgs {
   const int4* cta_gang;         // [grid]
   unsigned long long* gang_bar; // [ngangs] barrier counters, zero at launch
   int* gang_slot;               // [ngangs] system handed to the gang
-  double* gang_part;            // [grid][2][NR][kNRed] partials (indexed from the gang's first CTA)
+  double* gang_part;            // [grid][2][kMaxRhs][kNRed] partials (indexed from the gang's first CTA)
   int* err;                     // device error word, zero at launch
 };
 
-template <class P, int NR, bool QX>
-__global__ void __launch_bounds__(kThreads, min_blocks(NR)) aj_batched_kernel(BatchArgs<P> b) {
-  __shared__ SolveSmem<NR> sm;
+template <class P, bool QX>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) aj_batched_kernel(BatchArgs<P> b) {
+  __shared__ SolveSmem sm;
   const int4 g = b.cta_gang[blockIdx.x];
   const int base = g.x, size = g.y, cls = g.z, gid = g.w;
   const int rank = (int)blockIdx.x - base;
@@ -928,13 +927,13 @@ __global__ void __launch_bounds__(kThreads, min_blocks(NR)) aj_batched_kernel(Ba
     const int k = __ldcg(b.gang_slot + gid);
     if (k >= qlen) break;
     IterArgs<P> a = b.sys[b.order[qbeg + k]];
-    a.partials = b.gang_part + (size_t)base * 2 * NR * kNRed;
+    a.partials = b.gang_part + (size_t)base * 2 * kMaxRhs * kNRed;
     a.bar = b.gang_bar + gid;
     a.err = b.err;
-    if (threadIdx.x < NR) sm.st[threadIdx.x] = a.state[threadIdx.x];
+    if ((int)threadIdx.x < a.nrhs) sm.st[threadIdx.x] = a.state[threadIdx.x];
     __syncthreads();
-    if (!run_solve<P, NR, QX, true>(a, sm, rank, size, target, sw)) return;
-    if (rank == 0 && threadIdx.x < NR) a.state[threadIdx.x] = sm.st[threadIdx.x];
+    if (!run_solve<P, QX, true, true>(a, sm, rank, size, target, sw)) return;
+    if (rank == 0 && (int)threadIdx.x < a.nrhs) a.state[threadIdx.x] = sm.st[threadIdx.x];
     __syncthreads();
   }
 }

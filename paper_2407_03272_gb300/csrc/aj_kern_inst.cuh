@@ -1,5 +1,5 @@
-// aj_kern_inst.cuh -- instantiates the persistent kernel of one precision
-// policy for 1..4 right-hand sides.  Included once per translation unit with
+// aj_kern_inst.cuh -- instantiates the persistent and batched kernels of one
+// precision policy (one right-hand side, and 2..4 with lanes per row).  Included once per translation unit with
 // AJ_POL (policy type) and AJ_SUFFIX (name suffix) defined.
 #include <string.h>
 
@@ -17,6 +17,8 @@ template <class P>
 static IterArgs<P> typed_args(const IterLaunch& L) {
   IterArgs<P> a;
   a.n = L.n;
+  a.nrhs = L.nrhs;
+  a.lgr = lanes_log2(L.nrhs);
   a.row_ptr = L.row_ptr;
   a.col = L.col;
   a.val = static_cast<const typename P::V*>(L.val);
@@ -56,8 +58,8 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
   return a;
 }
 
-template <class P, int NR>
-static cudaError_t launch_batched_nr(int qx, const BatchLaunch& B, int grid, cudaStream_t s) {
+template <class P>
+static cudaError_t launch_batched_p(int qx, const BatchLaunch& B, int grid, cudaStream_t s) {
   BatchArgs<P> b;
   b.sys = static_cast<const IterArgs<P>*>(B.sys);
   b.order = B.order;
@@ -69,29 +71,7 @@ static cudaError_t launch_batched_nr(int qx, const BatchLaunch& B, int grid, cud
   b.gang_part = B.gang_part;
   b.err = B.err;
   void* args[] = {&b};
-  const void* k = qx ? (const void*)aj_batched_kernel<P, NR, true>
-                     : (const void*)aj_batched_kernel<P, NR, false>;
-  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
-}
-
-template <class P, int NR>
-static int occ_batched_nr(int qx) {
-  int nb = 0;
-  cudaError_t e = qx ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                           &nb, aj_batched_kernel<P, NR, true>, kThreads, 0)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                           &nb, aj_batched_kernel<P, NR, false>, kThreads, 0);
-  return e == cudaSuccess ? nb : 0;
-}
-
-template <class P, int NR>
-static cudaError_t launch_nr(const IterLaunch& L, int grid, cudaStream_t s) {
-  IterArgs<P> a = typed_args<P>(L);
-  void* args[] = {&a};
-  const void* k = L.fmt ? (L.qx ? (const void*)aj_persistent_kernel<P, NR, true, true>
-                                : (const void*)aj_persistent_kernel<P, NR, false, true>)
-                       : (L.qx ? (const void*)aj_persistent_kernel<P, NR, true, false>
-                               : (const void*)aj_persistent_kernel<P, NR, false, false>);
+  const void* k = qx ? (const void*)aj_batched_kernel<P, true> : (const void*)aj_batched_kernel<P, false>;
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
 }
 
@@ -101,35 +81,36 @@ static int occ_of(K k) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, 0) == cudaSuccess ? nb : 0;
 }
 
+template <class P, bool MULTI>
+static cudaError_t launch_m(const IterLaunch& L, int grid, cudaStream_t s) {
+  IterArgs<P> a = typed_args<P>(L);
+  void* args[] = {&a};
+  const void* k = L.fmt ? (L.qx ? (const void*)aj_persistent_kernel<P, true, true, MULTI>
+                                : (const void*)aj_persistent_kernel<P, false, true, MULTI>)
+                       : (L.qx ? (const void*)aj_persistent_kernel<P, true, false, MULTI>
+                               : (const void*)aj_persistent_kernel<P, false, false, MULTI>);
+  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
+}
+
 // Co-resident CTAs of the persistent kernel: the smaller of its CSR-only and
 // any-format instantiations, so that a grid sized by it fits either.
-template <class P, int NR>
-static int occ_nr(int qx) {
-  return qx ? std::min(occ_of(aj_persistent_kernel<P, NR, true, false>),
-                       occ_of(aj_persistent_kernel<P, NR, true, true>))
-            : std::min(occ_of(aj_persistent_kernel<P, NR, false, false>),
-                       occ_of(aj_persistent_kernel<P, NR, false, true>));
+template <class P, bool MULTI>
+static int occ_m(int qx) {
+  return qx ? std::min(occ_of(aj_persistent_kernel<P, true, false, MULTI>),
+                       occ_of(aj_persistent_kernel<P, true, true, MULTI>))
+            : std::min(occ_of(aj_persistent_kernel<P, false, false, MULTI>),
+                       occ_of(aj_persistent_kernel<P, false, true, MULTI>));
 }
 
 cudaError_t AJ_CAT(launch_persistent_, AJ_SUFFIX)(int nrhs, const IterLaunch& L, int grid,
                                                   cudaStream_t s) {
-  switch (nrhs) {
-    case 1: return launch_nr<AJ_POL, 1>(L, grid, s);
-    case 2: return launch_nr<AJ_POL, 2>(L, grid, s);
-    case 3: return launch_nr<AJ_POL, 3>(L, grid, s);
-    case 4: return launch_nr<AJ_POL, 4>(L, grid, s);
-  }
-  return cudaErrorInvalidValue;
+  if (nrhs < 1 || nrhs > kMaxRhs || L.nrhs != nrhs) return cudaErrorInvalidValue;
+  return nrhs == 1 ? launch_m<AJ_POL, false>(L, grid, s) : launch_m<AJ_POL, true>(L, grid, s);
 }
 
 int AJ_CAT(blocks_per_sm_, AJ_SUFFIX)(int nrhs, int qx) {
-  switch (nrhs) {
-    case 1: return occ_nr<AJ_POL, 1>(qx);
-    case 2: return occ_nr<AJ_POL, 2>(qx);
-    case 3: return occ_nr<AJ_POL, 3>(qx);
-    case 4: return occ_nr<AJ_POL, 4>(qx);
-  }
-  return 0;
+  if (nrhs < 1 || nrhs > kMaxRhs) return 0;
+  return nrhs == 1 ? occ_m<AJ_POL, false>(qx) : occ_m<AJ_POL, true>(qx);
 }
 
 void AJ_CAT(pack_iter_args_, AJ_SUFFIX)(const IterLaunch& L, void* dst) {
@@ -138,25 +119,12 @@ void AJ_CAT(pack_iter_args_, AJ_SUFFIX)(const IterLaunch& L, void* dst) {
   memcpy(dst, &a, sizeof(a));
 }
 
-cudaError_t AJ_CAT(launch_batched_, AJ_SUFFIX)(int nrhs, int qx, const BatchLaunch& B, int grid,
-                                                cudaStream_t s) {
-  switch (nrhs) {
-    case 1: return launch_batched_nr<AJ_POL, 1>(qx, B, grid, s);
-    case 2: return launch_batched_nr<AJ_POL, 2>(qx, B, grid, s);
-    case 3: return launch_batched_nr<AJ_POL, 3>(qx, B, grid, s);
-    case 4: return launch_batched_nr<AJ_POL, 4>(qx, B, grid, s);
-  }
-  return cudaErrorInvalidValue;
+cudaError_t AJ_CAT(launch_batched_, AJ_SUFFIX)(int qx, const BatchLaunch& B, int grid, cudaStream_t s) {
+  return launch_batched_p<AJ_POL>(qx, B, grid, s);
 }
 
-int AJ_CAT(batched_blocks_per_sm_, AJ_SUFFIX)(int nrhs, int qx) {
-  switch (nrhs) {
-    case 1: return occ_batched_nr<AJ_POL, 1>(qx);
-    case 2: return occ_batched_nr<AJ_POL, 2>(qx);
-    case 3: return occ_batched_nr<AJ_POL, 3>(qx);
-    case 4: return occ_batched_nr<AJ_POL, 4>(qx);
-  }
-  return 0;
+int AJ_CAT(batched_blocks_per_sm_, AJ_SUFFIX)(int qx) {
+  return qx ? occ_of(aj_batched_kernel<AJ_POL, true>) : occ_of(aj_batched_kernel<AJ_POL, false>);
 }
 
 }  // namespace aj

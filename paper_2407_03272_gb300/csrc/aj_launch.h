@@ -11,6 +11,7 @@ struct RhsState;
 // Untyped mirror of IterArgs<P>; the pointer types follow the precision.
 struct IterLaunch {
   int n;
+  int nrhs;  // right-hand sides, 1..4
   const int* row_ptr;
   const int* col;
   const void* val;
@@ -68,9 +69,10 @@ struct BatchLaunch {
 // Size in bytes of one packed per-system argument block, and the packing.
 size_t iter_args_bytes();
 void pack_iter_args(int pol, const IterLaunch& L, void* dst);
-// Cooperative launch of the batched kernel and its co-resident CTAs per SM.
-cudaError_t launch_batched(int pol, int nrhs, int qx, const BatchLaunch& B, int grid, cudaStream_t s);
-int batched_blocks_per_sm(int pol, int nrhs, int qx);
+// Cooperative launch of the batched kernel (systems of any right-hand-side
+// count) and its co-resident CTAs per SM.
+cudaError_t launch_batched(int pol, int qx, const BatchLaunch& B, int grid, cudaStream_t s);
+int batched_blocks_per_sm(int pol, int qx);
 
 // Cooperative launch of the persistent kernel for precision `pol`
 // (0 F64, 1 DF64, 2 F32, 3 BF16), nrhs in [1, 4] and the sweep form L.qx.
@@ -89,9 +91,8 @@ int blocks_per_sm_b16(int nrhs, int qx);
 
 #define AJ_DECLARE_BATCHED(suf)                                                              \
   void pack_iter_args_##suf(const IterLaunch& L, void* dst);                                 \
-  cudaError_t launch_batched_##suf(int nrhs, int qx, const BatchLaunch& B, int grid,         \
-                                   cudaStream_t s);                                          \
-  int batched_blocks_per_sm_##suf(int nrhs, int qx);
+  cudaError_t launch_batched_##suf(int qx, const BatchLaunch& B, int grid, cudaStream_t s);  \
+  int batched_blocks_per_sm_##suf(int qx);
 AJ_DECLARE_BATCHED(f64)
 AJ_DECLARE_BATCHED(df64)
 AJ_DECLARE_BATCHED(f32)

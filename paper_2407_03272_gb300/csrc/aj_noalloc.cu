@@ -264,6 +264,7 @@ extern "C" aj_status aj_solve_noalloc(const aj_csr* Q, const double* b, const aj
   IterLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.n = n;
+  L.nrhs = 1;
   L.row_ptr = Q->row_ptr;
   L.col = Q->col;
   L.val = Q->val;

@@ -92,23 +92,28 @@ def from_edges(n, u, v, w):
     u = np.asarray(u, np.int64)
     v = np.asarray(v, np.int64)
     w = np.asarray(w, np.float64)
-    deg = np.zeros(n)
-    np.add.at(deg, u, w)
-    np.add.at(deg, v, w)
-    has = deg != 0
-    dr = np.nonzero(has)[0]
+    # weighted degrees, summed in edge order (all u-ends, then all v-ends)
+    deg = np.bincount(np.concatenate([u, v]), weights=np.concatenate([w, w]), minlength=n)
+    dr = np.nonzero(deg != 0)[0]
     rows = np.concatenate([u, v, dr])
     cols = np.concatenate([v, u, dr])
     vals = np.concatenate([-w, -w, deg[dr]])
-    order = np.lexsort((cols, rows))
-    rows, cols, vals = rows[order], cols[order], vals[order]
-    counts = np.bincount(rows, minlength=n)
-    row_ptr = np.zeros(n + 1, dtype=np.int64)
-    np.cumsum(counts, out=row_ptr[1:])
-    if row_ptr[-1] >= 2 ** 31:
+    if rows.size >= 2 ** 31:
         raise ValueError("nnz exceeds int32 indices")
-    return {"n": n, "row_ptr": row_ptr.astype(np.int32), "col": cols.astype(np.int32),
-            "val": vals}
+    # COO -> CSR with ascending columns (no duplicate pairs, so nothing is summed)
+    A = _sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    A.sort_indices()
+    return {"n": n, "row_ptr": A.indptr.astype(np.int32), "col": A.indices.astype(np.int32),
+            "val": np.asarray(A.data, np.float64)}
+
+
+def _inverse_cdf(cdf, u):
+    """searchsorted(cdf, u, side="right"), with the queries sorted first so
+    that the binary searches walk the table in order (same result)."""
+    order = np.argsort(u)
+    out = np.empty(u.size, dtype=np.int64)
+    out[order] = np.searchsorted(cdf, u[order], side="right")
+    return out
 
 
 def chung_lu_laplacian(n, mean_degree=16.0, exponent=2.5, seed=3, wlo=0.5, whi=1.5):
@@ -143,8 +148,8 @@ def chung_lu_laplacian(n, mean_degree=16.0, exponent=2.5, seed=3, wlo=0.5, whi=1
     target = mean_degree * n / 2.0
     m = int(round(target))
     for _ in range(6):
-        a = np.searchsorted(cdf, rng.random(m), side="right")
-        b = np.searchsorted(cdf, rng.random(m), side="right")
+        a = _inverse_cdf(cdf, rng.random(m))
+        b = _inverse_cdf(cdf, rng.random(m))
         np.minimum(a, n - 1, out=a)
         np.minimum(b, n - 1, out=b)
         wt = rng.uniform(wlo, whi, m)
@@ -226,3 +231,56 @@ def workload(name, seed=None):
     else:
         raise KeyError(name)
     return Q, rhs(Q, xs), xs
+
+
+def _log_uniform_int(rng, lo, hi, size):
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), size)).astype(np.int64)
+
+
+def batch_mix(count, seed=4, pool=48, side=(32, 1024), rgg_n=(1000, 500000), max_rhs=4):
+    """Independent systems shaped like the batched workload: half 2-D Poisson
+    grids with side log-uniform in ``side``, half k-NN random-geometric-graph
+    Laplacians with n log-uniform in ``rgg_n``, each with 1..max_rhs
+    right-hand sides b = Q x*, x* ~ U(-1, 1).
+
+    To bound the generation time, the matrices come from a pool of ``pool``
+    distinct ones (half of each kind, sizes drawn as above); every system picks
+    one of its kind at random and draws its own x*.  Returns a list of
+    ``(pool_index, nrhs, seeds)`` and the pool (a list of CSR dicts), so that
+    callers can share device copies of pooled matrices.
+    """
+    rng = _rng(seed)
+    half = max(1, pool // 2)
+    sides = _log_uniform_int(rng, side[0], side[1] + 1, half)
+    ns = _log_uniform_int(rng, rgg_n[0], rgg_n[1] + 1, half)
+    mats = [poisson2d(int(s)) for s in sides]
+    mats += [rgg_knn_laplacian(int(n), seed=seed * 100003 + k) for k, n in enumerate(ns)]
+    systems = []
+    for k in range(count):
+        kind = k % 2
+        j = int(rng.integers(0, half)) + kind * half
+        nrhs = int(rng.integers(1, max_rhs + 1))
+        systems.append((j, nrhs, [int(seed * 1000003 + 10 * k + r) for r in range(nrhs)]))
+    return systems, mats
+
+
+def served_mix(count, seed=5, pool=48, side3=(64, 192), frac3=0.2, **kw):
+    """Requests shaped like the served workload: a fraction ``frac3`` are 3-D
+    Poisson grids with side uniform in ``side3``; the rest follow
+    ``batch_mix``.  Same pooled return form as ``batch_mix``."""
+    systems, mats = batch_mix(count, seed=seed, pool=pool, **kw)
+    rng = _rng(seed + 7)
+    n3 = max(1, pool // 6)
+    base = len(mats)
+    mats += [poisson3d(int(s)) for s in rng.integers(side3[0], side3[1] + 1, n3)]
+    out = []
+    for j, nrhs, seeds in systems:
+        if rng.random() < frac3:
+            j = base + int(rng.integers(0, n3))
+        out.append((j, nrhs, seeds))
+    return out, mats
+
+
+def mix_rhs(Q, seeds):
+    """b (n x nrhs, column-major, flattened) for the x* seeds of one system."""
+    return np.concatenate([rhs(Q, uniform(Q["n"], s)) for s in seeds])

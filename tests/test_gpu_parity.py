@@ -210,6 +210,40 @@ def test_multi_rhs_equals_single(nrhs, precision):
         assert _relres(Q, B[:, r], X[r]) <= 1e-9
 
 
+@pytest.mark.parametrize("nrhs", [2, 3, 4])
+@pytest.mark.parametrize("case", ["poisson_lazy", "poisson_stored", "long_rows", "sell_powerlaw"])
+def test_multi_rhs_200_iterations_match_oracle(nrhs, case):
+    """Several right-hand sides share a row's lanes (lane r gathers column r
+    of the interleaved vectors); every column must follow the FP64 oracle."""
+    if case.startswith("poisson"):
+        Q = synth.poisson2d(41)  # n = 1681: a ragged last tile for every lane count
+        kw = dict(sweep_form=FORMS[case.split("_")[1]])
+    elif case == "long_rows":
+        # power-law rows: the hubs exceed the warp-cooperative threshold of 32 entries
+        Q = synth.chung_lu_laplacian(3000, seed=19, mean_degree=12.0)
+        kw = dict(format=aj.AJ_FMT_CSR)
+    else:
+        Q = synth.chung_lu_laplacian(20000, seed=29)
+        kw = dict(format=aj.AJ_FMT_SELL, sell_sigma=256, sell_lmax=16)
+    n = Q["n"]
+    B = np.stack([synth.rhs(Q, synth.uniform(n, 40 + r)) for r in range(nrhs)], axis=1)
+    ctx = aj.from_csr(Q, np.ascontiguousarray(B.T).reshape(-1), nrhs=nrhs)
+    T = 200
+    ctx.set(stop=aj.AJ_STOP_NONE, maxit=T, **kw)
+    X, infos = ctx.solve(per_rhs=True)
+    X = X.reshape(nrhs, n)
+    J = oracle.j_absrowsum(Q)
+    for r in range(nrhs):
+        assert infos[r]["iters"] == T
+        ref = oracle.solve(Q, B[:, r], J, maxit=T, stop=oracle.STOP_NONE)
+        if np.linalg.norm(X[r] - ref["x"]) > REL * np.linalg.norm(ref["x"]):
+            ref = oracle.solve(Q, B[:, r], J, maxit=T, stop=oracle.STOP_NONE, forced=ctx.restart_log(r))
+        err = np.linalg.norm(X[r] - ref["x"]) / np.linalg.norm(ref["x"])
+        assert err <= REL, (r, err)
+    if case == "long_rows":
+        assert np.diff(Q["row_ptr"]).max() > 32
+
+
 # ---------------------------------------------------------------- checkpoint / resume
 @pytest.mark.parametrize("form", ["lazy", "stored"])
 def test_resume_is_bit_identical(form):
