@@ -110,21 +110,21 @@ void pack_iter_args(int pol, const IterLaunch& L, void* dst) {
     case 3: pack_iter_args_b16(L, dst); break;
   }
 }
-cudaError_t launch_batched(int pol, int qx, const BatchLaunch& B, int grid, cudaStream_t s) {
+cudaError_t launch_lockstep(int pol, int qx, const LockLaunch& B, int grid, cudaStream_t s) {
   switch (pol) {
-    case 0: return launch_batched_f64(qx, B, grid, s);
-    case 1: return launch_batched_df64(qx, B, grid, s);
-    case 2: return launch_batched_f32(qx, B, grid, s);
-    case 3: return launch_batched_b16(qx, B, grid, s);
+    case 0: return launch_lockstep_f64(qx, B, grid, s);
+    case 1: return launch_lockstep_df64(qx, B, grid, s);
+    case 2: return launch_lockstep_f32(qx, B, grid, s);
+    case 3: return launch_lockstep_b16(qx, B, grid, s);
   }
   return cudaErrorInvalidValue;
 }
-int batched_blocks_per_sm(int pol, int qx) {
+int lockstep_blocks_per_sm(int pol, int qx) {
   switch (pol) {
-    case 0: return batched_blocks_per_sm_f64(qx);
-    case 1: return batched_blocks_per_sm_df64(qx);
-    case 2: return batched_blocks_per_sm_f32(qx);
-    case 3: return batched_blocks_per_sm_b16(qx);
+    case 0: return lockstep_blocks_per_sm_f64(qx);
+    case 1: return lockstep_blocks_per_sm_df64(qx);
+    case 2: return lockstep_blocks_per_sm_f32(qx);
+    case 3: return lockstep_blocks_per_sm_b16(qx);
   }
   return 0;
 }
@@ -175,6 +175,7 @@ struct aj_ctx {
   double sb[kMaxRhs] = {1, 1, 1, 1};
   double L_used = 0.0;
   int grid = 1;
+  int part_cap = 0;  // CTAs the partial-sum buffer holds
   double* partials = nullptr;
   unsigned long long* bar = nullptr;
   int* err = nullptr;
@@ -503,6 +504,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
                               persistent_blocks_per_sm(kp, nrhs, 1)});
     const int maxg = bps * c->sm_count;
     c->partials = (double*)c->pws.alloc((size_t)2 * maxg * nrhs * kNRed * 8);
+    c->part_cap = maxg;
     c->bar = (unsigned long long*)c->pws.alloc(64);
     c->state = (RhsState*)c->pws.alloc(sizeof(RhsState) * kMaxRhs);
     c->rlog = (long long*)c->pws.alloc((size_t)kMaxRhs * c->rlog_cap * 8);
@@ -948,168 +950,203 @@ struct BatchItem {
   long long max_sweeps;  // sweeps this launch may run (maxit + 2: to the end)
 };
 
-static int pow2_ceil(long long v) {
-  int p = 1;
-  while (p < v && p < (1 << 30)) p <<= 1;
-  return p;
-}
-
-// CTAs (the gang size) a system gets in a batched launch: one per 8 tiles of
-// 256 rows rounded up to a power of two and at most 64, so that many systems
-// run side by side; a context's own grid_ctas overrides it.  A system's
-// arithmetic depends only on this count, so a batch member with grid_ctas set
-// computes exactly what aj_solve computes with the same grid_ctas.
-static int batch_gang(const aj_ctx* c, int gmax) {
-  if (c->prm.grid_ctas > 0) return std::max(1, std::min(c->prm.grid_ctas, gmax));
+// Tiles of a context's sweep (rows per tile 256 >> lgr).
+static long long ctx_tiles(const aj_ctx* c) {
   const long long rpt = kThreads >> lanes_log2(c->nrhs);
-  const long long ntiles = std::max<long long>(1, (c->n + rpt - 1) / rpt);
-  return std::max(1, std::min({pow2_ceil((ntiles + 7) / 8), 64, gmax}));
+  return std::max<long long>(1, (c->n + rpt - 1) / rpt);
 }
 
-// Solves every item (all of one precision and sweep form, any right-hand-side
-// counts) with one batched persistent launch.  Gangs of equal size form a
-// class; a class gets CTAs in proportion to its estimated work (stored
-// entries x sqrt(n), the AJ iteration count of 2-D Laplacians growing like
-// the grid side), at least one gang, and at most one gang per system.
-static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, double* kernel_ms) {
+// Units a system gets in a lockstep launch (V_s).  A context's own grid_ctas
+// fixes it; a system's arithmetic depends only on this count, so such a
+// batch member computes exactly what aj_solve computes with the same
+// grid_ctas.  Otherwise it follows the launch's load: about 16 units per CTA
+// over all active systems (active_tiles in total), a system's share in
+// proportion to its tiles -- coarse units while many systems run, fine ones
+// when a few large systems remain -- at most one per tile and at most the
+// CTA count its partial-sum buffer holds.  The reduction grouping then
+// changes between launches, which moves the FP64 sums by rounding only.
+static int batch_units(const aj_ctx* c, long long active_tiles, int grid) {
+  const int cap = std::max(1, c->part_cap);
+  if (c->prm.grid_ctas > 0) return std::max(1, std::min(c->prm.grid_ctas, cap));
+  const long long nt = ctx_tiles(c);
+  const double want = (double)nt * 16.0 * grid / (double)std::max<long long>(active_tiles, 1);
+  const long long v = (long long)std::ceil(want);
+  return (int)std::max<long long>(1, std::min<long long>({v, nt, (long long)cap}));
+}
+
+// Device buffers of lockstep launches, kept between launches and grown on
+// demand (a server keeps one for its lifetime).
+struct LockWs {
+  Workspace mem;
+  size_t cap_m = 0, cap_nu = 0;
+  void* d_sys = nullptr;
+  int *d_unit = nullptr, *d_u0 = nullptr, *d_nu = nullptr, *d_cta = nullptr, *d_err = nullptr;
+  RhsState *d_st2 = nullptr, *d_out = nullptr;
+  unsigned long long* d_bar = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LockWs() = default;
+  LockWs(const LockWs&) = delete;
+  LockWs& operator=(const LockWs&) = delete;
+  ~LockWs() {
+    mem.release();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+  size_t cap_g = 0;
+  bool reserve(size_t m, size_t nu, size_t g, size_t abytes) {
+    if (d_sys && m <= cap_m && nu <= cap_nu && g <= cap_g) return true;
+    mem.release();
+    cap_m = std::max(m, 2 * cap_m);
+    cap_nu = std::max(nu, 2 * cap_nu);
+    cap_g = std::max(g, cap_g);
+    d_sys = mem.alloc(cap_m * abytes);
+    d_cta = (int*)mem.alloc((cap_g + 1) * 4);
+    d_u0 = (int*)mem.alloc(cap_m * 4);
+    d_nu = (int*)mem.alloc(cap_m * 4);
+    d_unit = (int*)mem.alloc(cap_nu * 4);
+    d_st2 = (RhsState*)mem.alloc(cap_m * 2 * kMaxRhs * sizeof(RhsState));
+    d_out = (RhsState*)mem.alloc(cap_m * kMaxRhs * sizeof(RhsState));
+    d_bar = (unsigned long long*)mem.alloc(64);
+    d_err = (int*)mem.alloc(64);
+    if (!e0 && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) return false;
+    return d_sys && d_u0 && d_nu && d_cta && d_unit && d_st2 && d_out && d_bar && d_err;
+  }
+};
+
+// Solves every item (one precision and sweep form, any right-hand-side
+// counts) with lockstep launches.  Each launch runs a chunk of sweeps over
+// the systems still running (at most what each item has left of its
+// max_sweeps) and drops those that stopped; the chunk starts at chunk0 and
+// doubles while a launch takes under 5 ms of device time, so small systems
+// retire early and the large ones run long launches.  Each item's state
+// (host copy, in/out) is carried from launch to launch.
+static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, double* kernel_ms,
+                             LockWs* wsp = nullptr, long long chunk0 = 16) {
   if (items.empty()) return AJ_OK;
   aj_ctx* c0 = items[0].c;
   cudaStream_t s = c0->stream;
   const int pol = c0->pol, qx = c0->qx;
-  for (auto& it : items) {
-    aj_status e = stage_state(it.c, *it.st, log_restarts);
-    if (e != AJ_OK) return e;
-  }
-  Workspace ws;
-  struct Release {
-    Workspace& w;
-    ~Release() { w.release(); }
-  } release{ws};
+  LockWs local;
+  LockWs& ws = wsp ? *wsp : local;
   const size_t abytes = iter_args_bytes();
-  {
-    std::vector<int> idx;
-    for (int i = 0; i < (int)items.size(); i++) idx.push_back(i);
-    const int bps = batched_blocks_per_sm(pol, qx);
-    if (bps < 1) return AJ_ECUDA;
-    const int gmax = bps * c0->sm_count;
-    const int m = (int)idx.size();
-    std::vector<int> gsz(m);
-    std::vector<double> cost(m);
-    std::vector<int> sizes;
+  const int bps = lockstep_blocks_per_sm(pol, qx);
+  if (bps < 1) return AJ_ECUDA;
+  const int gmax = bps * c0->sm_count;
+  const int m_all = (int)items.size();
+  std::vector<int> V(m_all, 1);
+  std::vector<long long> left(m_all);
+  std::vector<unsigned char> args_all((size_t)m_all * abytes);
+  for (int i = 0; i < m_all; i++) {
+    const BatchItem& it = items[i];
+    left[i] = it.max_sweeps;
+    IterLaunch L = make_launch(it.c, it.bvec, it.maxit, it.stop, it.tol, it.fstar, it.fscale);
+    pack_iter_args(pol, L, args_all.data() + (size_t)i * abytes);
+    if (log_restarts) CK(cudaMemsetAsync(it.c->rlog, 0xff, (size_t)kMaxRhs * it.c->rlog_cap * 8, s));
+  }
+  auto running = [&](int i) {
+    if (left[i] <= 0) return false;
+    for (int r = 0; r < items[i].c->nrhs; r++)
+      if (!(*items[i].st)[r].done) return true;
+    return false;
+  };
+  long long chunk = std::max<long long>(1, chunk0);
+  std::vector<int> act, u0, nu, unit, cta;
+  std::vector<double> ucost;
+  std::vector<unsigned char> sysh;
+  std::vector<RhsState> st2, out;
+  for (;;) {
+    act.clear();
+    for (int i = 0; i < m_all; i++)
+      if (running(i)) act.push_back(i);
+    if (act.empty()) break;
+    long long sweeps = chunk;
+    for (int i : act) sweeps = std::min(sweeps, left[i]);
+    const int m = (int)act.size();
+    long long active_tiles = 0;
+    for (int i : act) active_tiles += ctx_tiles(items[i].c);
+    for (int i : act) V[i] = batch_units(items[i].c, active_tiles, gmax);
+    u0.assign(m, 0);
+    nu.assign(m, 0);
+    unit.clear();
+    ucost.clear();
+    sysh.resize((size_t)m * abytes);
+    st2.assign((size_t)m * 2 * kMaxRhs, RhsState());
     for (int j = 0; j < m; j++) {
-      const aj_ctx* c = items[idx[j]].c;
-      gsz[j] = batch_gang(c, gmax);
-      cost[j] = (double)(c->nnz + c->n) * (1.0 + 0.5 * (c->nrhs - 1)) * std::sqrt((double)std::max<int64_t>(c->n, 1));
-      sizes.push_back(gsz[j]);
-    }
-    std::sort(sizes.begin(), sizes.end());
-    sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
-    const int ncls = (int)sizes.size();
-    std::vector<std::vector<int>> mem(ncls);
-    std::vector<double> work(ncls, 0.0);
-    double W = 0.0;
-    for (int j = 0; j < m; j++) {
-      const int k = (int)(std::lower_bound(sizes.begin(), sizes.end(), gsz[j]) - sizes.begin());
-      mem[k].push_back(j);
-      work[k] += cost[j];
-      W += cost[j];
-    }
-    for (auto& v : mem)
-      std::stable_sort(v.begin(), v.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-    std::vector<int> kg(ncls);
-    for (int k = 0; k < ncls; k++) {
-      const double share = W > 0 ? work[k] / W : 1.0 / ncls;
-      kg[k] = std::max(1, std::min((int)mem[k].size(), (int)std::floor(share * gmax / sizes[k])));
-    }
-    auto used = [&]() {
-      long long u = 0;
-      for (int k = 0; k < ncls; k++) u += (long long)kg[k] * sizes[k];
-      return u;
-    };
-    while (used() > gmax) {
-      int best = -1;
-      for (int k = 0; k < ncls; k++)
-        if (kg[k] > 1 && (best < 0 || (long long)kg[k] * sizes[k] > (long long)kg[best] * sizes[best])) best = k;
-      if (best < 0) break;
-      kg[best]--;
-    }
-    if (used() > gmax) return AJ_EINVAL;  // more distinct gang sizes than the GPU holds
-    for (;;) {  // hand out what is left to the class with the most work per CTA
-      int best = -1;
-      double bw = 0.0;
-      for (int k = 0; k < ncls; k++) {
-        if (kg[k] >= (int)mem[k].size() || used() + sizes[k] > gmax) continue;
-        const double wpc = work[k] / ((double)kg[k] * sizes[k]);
-        if (best < 0 || wpc > bw) { best = k; bw = wpc; }
+      const int i = act[j];
+      u0[j] = (int)unit.size();
+      nu[j] = V[i];
+      // estimated work of unit v: its tiles x row-RHS pairs per tile x
+      // (stored entries per row + the per-row update)
+      // (stored entries per row + the per-row update), plus a fixed cost of
+      // about one tile for the unit's own reductions
+      const aj_ctx* c = items[i].c;
+      const long long rpt = kThreads >> lanes_log2(c->nrhs);
+      const long long ntiles = ctx_tiles(c);
+      const double per_tile = (double)rpt * c->nrhs * ((double)c->nnz / std::max<int64_t>(c->n, 1) + 9.0);
+      for (int v = 0; v < V[i]; v++) {
+        unit.push_back(j);
+        const long long tv = v < ntiles ? (ntiles - 1 - v) / V[i] + 1 : 0;
+        ucost.push_back(per_tile * (double)(tv + 1));
       }
-      if (best < 0) break;
-      kg[best]++;
+      std::memcpy(sysh.data() + (size_t)j * abytes, args_all.data() + (size_t)i * abytes, abytes);
+      for (int r = 0; r < items[i].c->nrhs; r++) st2[(size_t)j * 2 * kMaxRhs + r] = (*items[i].st)[r];
     }
-    const int grid = (int)used();
-    std::vector<int> order, cls_begin(ncls + 1, 0);
-    std::vector<int4> cta_gang;
-    int ngang = 0;
-    for (int k = 0; k < ncls; k++) {
-      cls_begin[k] = (int)order.size();
-      for (int j : mem[k]) order.push_back(j);
-      for (int q = 0; q < kg[k]; q++) {
-        const int base = (int)cta_gang.size();
-        for (int r = 0; r < sizes[k]; r++) cta_gang.push_back(make_int4(base, sizes[k], k, ngang));
-        ngang++;
+    // contiguous unit ranges of about equal estimated work, one per CTA
+    const int grid = std::max(1, std::min(gmax, (int)unit.size()));
+    double total = 0.0;
+    for (double w : ucost) total += w;
+    cta.assign((size_t)grid + 1, (int)unit.size());
+    cta[0] = 0;
+    {
+      double acc = 0.0;
+      int c = 1;
+      for (size_t u = 0; u < unit.size() && c < grid; u++) {
+        // unit u starts at acc; it opens CTA c's range once acc reaches c/grid of the total
+        while (c < grid && acc >= total * c / grid) cta[c++] = (int)u;
+        acc += ucost[u];
       }
     }
-    cls_begin[ncls] = (int)order.size();
-    std::vector<unsigned char> sysh((size_t)m * abytes);
-    for (int j = 0; j < m; j++) {
-      const BatchItem& it = items[idx[j]];
-      IterLaunch L = make_launch(it.c, it.bvec, it.maxit, it.stop, it.tol, it.fstar, it.fscale);
-      L.max_sweeps = it.max_sweeps;
-      pack_iter_args(pol, L, sysh.data() + (size_t)j * abytes);
-    }
-    void* d_sys = ws.alloc(sysh.size());
-    int* d_order = (int*)ws.alloc(order.size() * 4);
-    int* d_cb = (int*)ws.alloc(cls_begin.size() * 4);
-    int* d_head = (int*)ws.alloc((size_t)ncls * 4);
-    int4* d_cg = (int4*)ws.alloc(cta_gang.size() * sizeof(int4));
-    unsigned long long* d_bar = (unsigned long long*)ws.alloc((size_t)ngang * 8);
-    int* d_slot = (int*)ws.alloc((size_t)ngang * 4);
-    double* d_part = (double*)ws.alloc((size_t)grid * 2 * kMaxRhs * kNRed * 8);
-    int* d_err = (int*)ws.alloc(64);
-    if (!d_sys || !d_order || !d_cb || !d_head || !d_cg || !d_bar || !d_slot || !d_part || !d_err)
-      return AJ_ENOMEM;
-    CK(cudaMemcpyAsync(d_sys, sysh.data(), sysh.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d_cb, cls_begin.data(), cls_begin.size() * 4, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d_cg, cta_gang.data(), cta_gang.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(d_head, 0, (size_t)ncls * 4, s));
-    CK(cudaMemsetAsync(d_bar, 0, (size_t)ngang * 8, s));
-    CK(cudaMemsetAsync(d_err, 0, 64, s));
-    BatchLaunch B;
-    B.sys = d_sys;
-    B.order = d_order;
-    B.cls_begin = d_cb;
-    B.cls_head = d_head;
-    B.cta_gang = d_cg;
-    B.gang_bar = d_bar;
-    B.gang_slot = d_slot;
-    B.gang_part = d_part;
-    B.err = d_err;
-    CK(cudaEventRecord(c0->kev0, s));
-    CK(launch_batched(pol, qx, B, grid, s));
+    if (!ws.reserve(m, unit.size(), grid, abytes)) return AJ_ENOMEM;
+    CK(cudaMemcpyAsync(ws.d_cta, cta.data(), cta.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ws.d_sys, sysh.data(), sysh.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ws.d_unit, unit.data(), unit.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ws.d_u0, u0.data(), (size_t)m * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ws.d_nu, nu.data(), (size_t)m * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ws.d_st2, st2.data(), st2.size() * sizeof(RhsState), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ws.d_bar, 0, 64, s));
+    CK(cudaMemsetAsync(ws.d_err, 0, 64, s));
+    LockLaunch B;
+    B.sys = ws.d_sys;
+    B.unit_sys = ws.d_unit;
+    B.sys_u0 = ws.d_u0;
+    B.sys_nu = ws.d_nu;
+    B.cta_u0 = ws.d_cta;
+    B.st2 = ws.d_st2;
+    B.st_out = ws.d_out;
+    B.nu = (int)unit.size();
+    B.sweeps = sweeps;
+    B.bar = ws.d_bar;
+    B.err = ws.d_err;
+    CK(cudaEventRecord(ws.e0, s));
+    CK(launch_lockstep(pol, qx, B, grid, s));
     counted();
-    CK(cudaEventRecord(c0->kev1, s));
+    CK(cudaEventRecord(ws.e1, s));
+    out.resize((size_t)m * kMaxRhs);
     int err = 0;
-    CK(cudaMemcpyAsync(&err, d_err, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(out.data(), ws.d_out, out.size() * sizeof(RhsState), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&err, ws.d_err, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     float kms = 0.f;
-    cudaEventElapsedTime(&kms, c0->kev0, c0->kev1);
+    cudaEventElapsedTime(&kms, ws.e0, ws.e1);
     if (kernel_ms) *kernel_ms += kms;
     if (err != 0) return err == kETimeout ? AJ_ETIMEOUT : AJ_ECUDA;
+    for (int j = 0; j < m; j++) {
+      const int i = act[j];
+      for (int r = 0; r < items[i].c->nrhs; r++) (*items[i].st)[r] = out[(size_t)j * kMaxRhs + r];
+      left[i] -= sweeps;
+    }
+    if (kms < 5.0f && chunk < 4096) chunk *= 2;
   }
-  for (auto& it : items)
-    CK(cudaMemcpyAsync(it.st->data(), it.c->state, sizeof(RhsState) * it.c->nrhs,
-                       cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
   return AJ_OK;
 }
 
@@ -1736,6 +1773,7 @@ struct aj_server {
   int dev = 0;
   cudaStream_t stream = nullptr;
   long long round_sweeps = 32;
+  LockWs lws;  // lockstep launch buffers, kept for the server's lifetime
   std::mutex mu;
   std::condition_variable cv;
   std::deque<ServerReq*> queue;
@@ -1911,7 +1949,7 @@ static void server_main(aj_server* s) {
     double kms = 0.0;
     aj_status e = AJ_OK;
     for (auto& g : groups) {
-      e = run_batched(g.second, false, &kms);
+      e = run_batched(g.second, false, &kms, &s->lws, s->round_sweeps);
       if (e != AJ_OK) break;
     }
     {

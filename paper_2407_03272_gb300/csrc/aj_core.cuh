@@ -794,9 +794,49 @@ constexpr int kMinBlocks = 4;
 struct SolveSmem {
   RhsState st[kMaxRhs];
   double tot[kMaxRhs][kNRed];
-  double red[kWarps * kMaxRhs];
+  double red[kWarps * kMaxRhs * kNRed];
   int done;
 };
+
+// Grid totals tot[r][k] of the per-CTA partials part[c][r][k] (c < ncta) for
+// every right-hand side r < nr and used slot k, in one pass.  Each total is
+// summed in a fixed order that does not depend on nr or on which CTA runs
+// this: thread t adds the partials of CTAs t, t + 256, ... in ascending
+// order, then a xor tree over the lanes and the warps in order.  Every
+// thread must call it; the totals are valid in sm.tot after it returns.
+__device__ __forceinline__ void grid_totals(const double* part, int ncta, int nr, bool want_obj,
+                                            SolveSmem& sm) {
+  constexpr int NV = kMaxRhs * kNRed;
+  double v[NV];
+#pragma unroll
+  for (int q = 0; q < NV; q++) v[q] = 0.0;
+  const int nslot = want_obj ? kNRed : 3;
+  for (int c = threadIdx.x; c < ncta; c += kThreads) {
+    const double* pc = part + (size_t)c * nr * kNRed;
+#pragma unroll
+    for (int r = 0; r < kMaxRhs; r++)
+#pragma unroll
+      for (int k = 0; k < kNRed; k++)
+        if (r < nr && k < nslot && slot_used(k, want_obj)) v[r * kNRed + k] += __ldcg(pc + r * kNRed + k);
+  }
+  const int w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; q++) {
+    if (q / kNRed >= nr || !slot_used(q % kNRed, want_obj)) continue;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], m);
+    if ((threadIdx.x & 31) == 0) sm.red[w * NV + q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    const int q = threadIdx.x;
+    double t = 0.0;
+    if (q / kNRed < nr && slot_used(q % kNRed, want_obj))
+      for (int i = 0; i < kWarps; i++) t += sm.red[i * NV + q];
+    sm.tot[q / kNRed][q % kNRed] = t;
+  }
+  __syncthreads();
+}
 
 // Runs sweeps of one system on `ncta` co-resident CTAs (this one is `cta`)
 // until every right-hand side is done or a.max_sweeps sweeps have run.  The
@@ -836,19 +876,7 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, i
     target += (unsigned long long)ncta;
     if (!grid_sync(a.bar, target, a.err, (unsigned)ncta)) return false;
     // every CTA sums the partials in the same fixed order
-    for (int r = 0; r < nr; r++)
-#pragma unroll
-      for (int k = 0; k < kNRed; k++) {
-        if (!slot_used(k, want_obj)) {
-          if (threadIdx.x == 0) sm.tot[r][k] = 0.0;
-          continue;
-        }
-        double v = 0.0;
-        for (int c = threadIdx.x; c < ncta; c += kThreads)
-          v += __ldcg(part + ((size_t)c * nr + r) * kNRed + k);
-        v = block_sum(v, sm.red);
-        if (threadIdx.x == 0) sm.tot[r][k] = v;
-      }
+    grid_totals(part, ncta, nr, want_obj, sm);
     if (threadIdx.x == 0) {
       if (a.trace && cta == 0 && s_run >= 1 && s_run <= a.trace_cap) {
         for (int r = 0; r < nr; r++) {
@@ -890,51 +918,145 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) aj_persistent_kernel(Ite
 }
 
 // ----------------------------------------------------------------------------
-// Many independent systems in one persistent launch.  The grid is cut into
-// gangs of co-resident CTAs (cta_gang[c] = {first CTA, size, class, gang id});
-// every gang of class k takes systems from the class's queue order[cls_begin[k]
-// .. cls_begin[k+1]) (largest first) through an atomic head, solves each one
-// with its own gang barrier and then takes the next.  Each system keeps its
-// own state, restart log and stop test; its arithmetic depends only on the
-// system and the gang size, not on the other systems in the batch.  Systems
-// of any right-hand-side count share the launch.
+// Many independent systems in lockstep.  System s is cut into V_s units: unit
+// v holds its tiles v, v + V_s, ... -- exactly the tiles CTA v of a solo run
+// with V_s CTAs sweeps, in the same order, with the same per-unit reduction,
+// so a system computes bit for bit what aj_solve computes with grid_ctas =
+// V_s.  Every sweep each CTA takes a contiguous range of the unit list, the
+// ranges cut so that each holds about the same estimated work (the units of
+// a system are consecutive, so a CTA meets few systems), then all CTAs meet
+// at one grid barrier: a sweep costs the combined work of the active systems
+// spread over the whole GPU.
+//
+// State.  The state a system uses in sweep k of this launch is kept in
+// st2[s][k & 1] (st2[s][0] staged by the host).  A CTA that meets system s in
+// sweep k >= 1 first turns state k-1 and the partial sums of sweep k-1 into
+// state k (identical bits in every CTA); the CTA that holds unit 0 stores it.
+// A system whose right-hand sides are all done stops sweeping.  After the
+// last sweep the CTA holding unit 0 applies the last transition and writes
+// the state to st_out[s], so that a launch takes a state and returns one,
+// exactly as a solo run of `sweeps` sweeps would.
 template <class P>
-struct BatchArgs {
-  const IterArgs<P>* sys;       // per system (partials, bar and err are ignored)
-  const int* order;             // system indices grouped by class
-  const int* cls_begin;         // [ncls + 1] offsets into order
-  int* cls_head;                // [ncls] queue heads, zero at launch
-  const int4* cta_gang;         // [grid]
-  unsigned long long* gang_bar; // [ngangs] barrier counters, zero at launch
-  int* gang_slot;               // [ngangs] system handed to the gang
-  double* gang_part;            // [grid][2][kMaxRhs][kNRed] partials (indexed from the gang's first CTA)
-  int* err;                     // device error word, zero at launch
+struct LockArgs {
+  const IterArgs<P>* sys;     // [m] per system; partials [2][V_s][nrhs][kNRed] are its own
+  const int* unit_sys;        // [nu] system of each unit (the units of a system are consecutive)
+  const int* sys_u0;          // [m] first unit of each system
+  const int* sys_nu;          // [m] V_s
+  const int* cta_u0;          // [gridDim + 1] CTA c sweeps units cta_u0[c] .. cta_u0[c+1]-1
+  RhsState* st2;              // [m][2][kMaxRhs]
+  RhsState* st_out;           // [m][kMaxRhs]
+  int nu;
+  long long sweeps;           // sweeps of this launch, >= 1
+  unsigned long long* bar;    // grid barrier counter, zero at launch
+  int* err;                   // device error word, zero at launch
 };
 
+// RhsState moved word by word through L2 (other CTAs write it between sweeps).
+static_assert(sizeof(RhsState) % 8 == 0, "state of whole 64-bit words");
+__device__ __forceinline__ RhsState ld_state_l2(const RhsState* p) {
+  RhsState v;
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&v);
+#pragma unroll
+  for (int k = 0; k < (int)(sizeof(RhsState) / 8); k++) dst[k] = __ldcg(src + k);
+  return v;
+}
+__device__ __forceinline__ void st_state_l2(RhsState* p, const RhsState& v) {
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&v);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(p);
+#pragma unroll
+  for (int k = 0; k < (int)(sizeof(RhsState) / 8); k++) __stcg(dst + k, src[k]);
+}
+
+// Loads system s's arguments into shared memory and brings its state to
+// sweep k (applying the transition of sweep k-1 when k >= 1).  Returns, in
+// every thread, whether the system is done.  `store` makes this CTA the one
+// that keeps the new state in st2; `log_it` the one that records restarts.
+template <class P>
+__device__ __forceinline__ bool lock_enter(const LockArgs<P>& b, IterArgs<P>& a, SolveSmem& sm, int s,
+                                           long long k, bool store, bool log_it) {
+  constexpr int kWords = (int)(sizeof(IterArgs<P>) / 4);
+  static_assert(sizeof(IterArgs<P>) % 4 == 0, "argument block of whole words");
+  __syncthreads();
+  const unsigned* src = reinterpret_cast<const unsigned*>(b.sys + s);
+  unsigned* dst = reinterpret_cast<unsigned*>(&a);
+  for (int w = threadIdx.x; w < kWords; w += kThreads) dst[w] = __ldg(src + w);
+  __syncthreads();
+  const int nr = a.nrhs;
+  const bool want_obj = a.stop == kStopObjgap;
+  const int V = __ldg(b.sys_nu + s);
+  RhsState* stc = b.st2 + ((size_t)s * 2 + (k & 1)) * kMaxRhs;
+  const RhsState* stp = b.st2 + ((size_t)s * 2 + ((k - 1) & 1)) * kMaxRhs;
+  if ((int)threadIdx.x < nr) sm.st[threadIdx.x] = ld_state_l2(k == 0 ? stc + threadIdx.x : stp + threadIdx.x);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int d = 1;
+    for (int r = 0; r < nr; r++) d = d && sm.st[r].done;
+    sm.done = d;
+  }
+  __syncthreads();
+  if (k > 0 && !sm.done) {
+    long long s_run = 0;
+    for (int r = 0; r < nr; r++)
+      if (!sm.st[r].done) s_run = sm.st[r].t + 1;
+    grid_totals(a.partials + (size_t)((k - 1) & 1) * V * nr * kNRed, V, nr, want_obj, sm);
+    if (threadIdx.x == 0)
+      sm.done = scalar_step(sm.st, sm.tot, nr, s_run, a.maxit, a.stop, a.restart, a.momentum, a.tol,
+                            a.fstar, a.fscale, a.rlog, a.rlog_cap, log_it)
+                    ? 1
+                    : 0;
+    __syncthreads();
+  }
+  if (store && k > 0 && (int)threadIdx.x < nr) st_state_l2(stc + threadIdx.x, sm.st[threadIdx.x]);
+  return sm.done != 0;
+}
+
 template <class P, bool QX>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) aj_batched_kernel(BatchArgs<P> b) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) aj_lockstep_kernel(LockArgs<P> b) {
   __shared__ SolveSmem sm;
-  const int4 g = b.cta_gang[blockIdx.x];
-  const int base = g.x, size = g.y, cls = g.z, gid = g.w;
-  const int rank = (int)blockIdx.x - base;
-  const int qbeg = b.cls_begin[cls], qlen = b.cls_begin[cls + 1] - qbeg;
+  __shared__ IterArgs<P> a;
+  using A = typename P::A;
+  const int u_lo = __ldg(b.cta_u0 + blockIdx.x);
+  const int u_hi = __ldg(b.cta_u0 + blockIdx.x + 1);
   unsigned long long target = 0;
-  long long sw = 0;
-  for (;;) {
-    if (rank == 0 && threadIdx.x == 0) __stcg(b.gang_slot + gid, atomicAdd(b.cls_head + cls, 1));
-    target += (unsigned long long)size;
-    if (!grid_sync(b.gang_bar + gid, target, b.err, (unsigned)size)) return;
-    const int k = __ldcg(b.gang_slot + gid);
-    if (k >= qlen) break;
-    IterArgs<P> a = b.sys[b.order[qbeg + k]];
-    a.partials = b.gang_part + (size_t)base * 2 * kMaxRhs * kNRed;
-    a.bar = b.gang_bar + gid;
-    a.err = b.err;
-    if ((int)threadIdx.x < a.nrhs) sm.st[threadIdx.x] = a.state[threadIdx.x];
-    __syncthreads();
-    if (!run_solve<P, QX, true, true>(a, sm, rank, size, target, sw)) return;
-    if (rank == 0 && (int)threadIdx.x < a.nrhs) a.state[threadIdx.x] = sm.st[threadIdx.x];
-    __syncthreads();
+  for (long long k = 0; k < b.sweeps; k++) {
+    int cur = -1;
+    bool done = false;
+    for (int u = u_lo; u < u_hi; u++) {
+      const int s = __ldg(b.unit_sys + u);
+      const int v = u - __ldg(b.sys_u0 + s);
+      if (s != cur) {
+        done = lock_enter(b, a, sm, s, k, v == 0, v == 0);
+        cur = s;
+      }
+      if (done) continue;
+      const int nr = a.nrhs;
+      const bool want_obj = a.stop == kStopObjgap;
+      const int V = __ldg(b.sys_nu + s);
+      bool compute_x = false;
+      for (int r = 0; r < nr; r++)
+        if (!sm.st[r].done) compute_x = compute_x || (sm.st[r].t < a.maxit);
+      A acc[kNRed];
+#pragma unroll
+      for (int q = 0; q < kNRed; q++) acc_zero(acc[q]);
+      sweep<P, QX, true, true>(a, sm.st, compute_x, want_obj, acc, v, V);
+      double* part = a.partials + (size_t)(k & 1) * V * nr * kNRed;
+#pragma unroll
+      for (int q = 0; q < kNRed; q++) {
+        if (!slot_used(q, want_obj)) continue;
+        const double t = block_sum_rhs(acc_value(acc[q]), sm.red, a.lgr, nr);
+        if ((int)threadIdx.x < nr) __stcg(part + ((size_t)v * nr + threadIdx.x) * kNRed + q, t);
+      }
+    }
+    target += (unsigned long long)gridDim.x;
+    if (!grid_sync(b.bar, target, b.err, gridDim.x)) return;
+  }
+  // the last transition, by the CTA that holds each system's unit 0
+  for (int u = u_lo; u < u_hi; u++) {
+    const int s = __ldg(b.unit_sys + u);
+    if (u != __ldg(b.sys_u0 + s)) continue;
+    lock_enter(b, a, sm, s, b.sweeps, false, true);
+    if ((int)threadIdx.x < a.nrhs) b.st_out[(size_t)s * kMaxRhs + threadIdx.x] = sm.st[threadIdx.x];
   }
 }
 

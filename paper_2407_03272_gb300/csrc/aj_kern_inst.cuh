@@ -59,19 +59,21 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
 }
 
 template <class P>
-static cudaError_t launch_batched_p(int qx, const BatchLaunch& B, int grid, cudaStream_t s) {
-  BatchArgs<P> b;
+static cudaError_t launch_lockstep_p(int qx, const LockLaunch& B, int grid, cudaStream_t s) {
+  LockArgs<P> b;
   b.sys = static_cast<const IterArgs<P>*>(B.sys);
-  b.order = B.order;
-  b.cls_begin = B.cls_begin;
-  b.cls_head = B.cls_head;
-  b.cta_gang = B.cta_gang;
-  b.gang_bar = B.gang_bar;
-  b.gang_slot = B.gang_slot;
-  b.gang_part = B.gang_part;
+  b.unit_sys = B.unit_sys;
+  b.sys_u0 = B.sys_u0;
+  b.sys_nu = B.sys_nu;
+  b.cta_u0 = B.cta_u0;
+  b.st2 = B.st2;
+  b.st_out = B.st_out;
+  b.nu = B.nu;
+  b.sweeps = B.sweeps;
+  b.bar = B.bar;
   b.err = B.err;
   void* args[] = {&b};
-  const void* k = qx ? (const void*)aj_batched_kernel<P, true> : (const void*)aj_batched_kernel<P, false>;
+  const void* k = qx ? (const void*)aj_lockstep_kernel<P, true> : (const void*)aj_lockstep_kernel<P, false>;
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
 }
 
@@ -119,12 +121,12 @@ void AJ_CAT(pack_iter_args_, AJ_SUFFIX)(const IterLaunch& L, void* dst) {
   memcpy(dst, &a, sizeof(a));
 }
 
-cudaError_t AJ_CAT(launch_batched_, AJ_SUFFIX)(int qx, const BatchLaunch& B, int grid, cudaStream_t s) {
-  return launch_batched_p<AJ_POL>(qx, B, grid, s);
+cudaError_t AJ_CAT(launch_lockstep_, AJ_SUFFIX)(int qx, const LockLaunch& B, int grid, cudaStream_t s) {
+  return launch_lockstep_p<AJ_POL>(qx, B, grid, s);
 }
 
-int AJ_CAT(batched_blocks_per_sm_, AJ_SUFFIX)(int qx) {
-  return qx ? occ_of(aj_batched_kernel<AJ_POL, true>) : occ_of(aj_batched_kernel<AJ_POL, false>);
+int AJ_CAT(lockstep_blocks_per_sm_, AJ_SUFFIX)(int qx) {
+  return qx ? occ_of(aj_lockstep_kernel<AJ_POL, true>) : occ_of(aj_lockstep_kernel<AJ_POL, false>);
 }
 
 }  // namespace aj

@@ -51,28 +51,30 @@ struct IterLaunch {
   int qx;  // 1: stored sweep form (u = Q x kept), 0: lazy form (two row sums)
 };
 
-// Untyped mirror of BatchArgs<P>: many systems in one persistent launch.
+// Untyped mirror of LockArgs<P>: many systems in lockstep in one launch.
 // `sys` is a device array of per-system kernel arguments packed with
 // pack_iter_args (the layout is the same for every precision policy).
-struct BatchLaunch {
+struct LockLaunch {
   const void* sys;
-  const int* order;
-  const int* cls_begin;
-  int* cls_head;
-  const int4* cta_gang;
-  unsigned long long* gang_bar;
-  int* gang_slot;
-  double* gang_part;
+  const int* unit_sys;
+  const int* sys_u0;
+  const int* sys_nu;
+  const int* cta_u0;
+  RhsState* st2;
+  RhsState* st_out;
+  int nu;
+  long long sweeps;
+  unsigned long long* bar;
   int* err;
 };
 
 // Size in bytes of one packed per-system argument block, and the packing.
 size_t iter_args_bytes();
 void pack_iter_args(int pol, const IterLaunch& L, void* dst);
-// Cooperative launch of the batched kernel (systems of any right-hand-side
+// Cooperative launch of the lockstep kernel (systems of any right-hand-side
 // count) and its co-resident CTAs per SM.
-cudaError_t launch_batched(int pol, int qx, const BatchLaunch& B, int grid, cudaStream_t s);
-int batched_blocks_per_sm(int pol, int qx);
+cudaError_t launch_lockstep(int pol, int qx, const LockLaunch& B, int grid, cudaStream_t s);
+int lockstep_blocks_per_sm(int pol, int qx);
 
 // Cooperative launch of the persistent kernel for precision `pol`
 // (0 F64, 1 DF64, 2 F32, 3 BF16), nrhs in [1, 4] and the sweep form L.qx.
@@ -91,8 +93,8 @@ int blocks_per_sm_b16(int nrhs, int qx);
 
 #define AJ_DECLARE_BATCHED(suf)                                                              \
   void pack_iter_args_##suf(const IterLaunch& L, void* dst);                                 \
-  cudaError_t launch_batched_##suf(int qx, const BatchLaunch& B, int grid, cudaStream_t s);  \
-  int batched_blocks_per_sm_##suf(int qx);
+  cudaError_t launch_lockstep_##suf(int qx, const LockLaunch& B, int grid, cudaStream_t s);  \
+  int lockstep_blocks_per_sm_##suf(int qx);
 AJ_DECLARE_BATCHED(f64)
 AJ_DECLARE_BATCHED(df64)
 AJ_DECLARE_BATCHED(f32)
