@@ -15,6 +15,7 @@
 #include <condition_variable>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <tuple>
@@ -42,22 +43,67 @@ inline void counted() {
   t_launches++;
 }
 
+// Device memory of the library comes from one memory pool per device, in
+// stream order: cudaMallocFromPoolAsync and cudaFreeAsync neither
+// synchronise the device nor hand memory back to the driver (the pool's
+// release threshold is "never"), so contexts and server requests that come
+// and go reuse blocks for the price of a pool lookup instead of paying
+// cudaMalloc / cudaFree every time.  If the pool cannot be created, plain
+// cudaMalloc / cudaFree are used.
+cudaMemPool_t device_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    pool = nullptr;
+  } else {
+    uint64_t never = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &never);
+  }
+  pools[dev] = pool;
+  return pool;
+}
+
+// Allocations of one owner, made and freed in the order of the owner's stream
+// (*stream; the legacy default stream when null).  Work that uses them on
+// another stream must be ordered after that stream first.
 struct Workspace {
-  std::vector<void*> ptrs;
+  std::vector<std::pair<void*, bool>> ptrs;  // (pointer, from the pool)
   size_t bytes = 0;
+  const cudaStream_t* stream = nullptr;
+  cudaStream_t st() const { return stream ? *stream : nullptr; }
   void* alloc(size_t b) {
     void* p = nullptr;
     if (b == 0) b = 16;
-    if (cudaMalloc(&p, b) != cudaSuccess) {
+    cudaMemPool_t pool = device_pool();
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, b, pool, st()) : cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
-    ptrs.push_back(p);
+    ptrs.push_back({p, pool != nullptr});
     bytes += b;
     return p;
   }
   void release() {
-    for (void* p : ptrs) cudaFree(p);
+    for (auto& q : ptrs) {
+      if (q.second) cudaFreeAsync(q.first, st());
+      else cudaFree(q.first);
+    }
     ptrs.clear();
     bytes = 0;
   }
@@ -284,6 +330,7 @@ extern "C" aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ct
   if (Q->nnz > 0 && (!Q->col || !Q->val)) return AJ_EINVAL;
   aj_ctx* c = new aj_ctx();
   aj_params_default(&c->prm);
+  c->base.stream = c->pws.stream = c->sws.stream = &c->stream;
   cudaGetDevice(&c->dev);
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
   c->n = Q->n;
@@ -372,6 +419,9 @@ extern "C" aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ct
 
 extern "C" aj_status aj_set_stream(aj_ctx* c, void* stream) {
   if (!c) return AJ_EINVAL;
+  // the context's memory was allocated in the order of its old stream
+  if (c->stream != (cudaStream_t)stream && cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
   c->stream = (cudaStream_t)stream;
   return AJ_OK;
 }
@@ -978,13 +1028,14 @@ static int batch_units(const aj_ctx* c, long long active_tiles, int grid) {
 // demand (a server keeps one for its lifetime).
 struct LockWs {
   Workspace mem;
+  cudaStream_t stream = nullptr;  // stream of the launches (allocations follow it)
   size_t cap_m = 0, cap_nu = 0;
   void* d_sys = nullptr;
   int *d_unit = nullptr, *d_u0 = nullptr, *d_nu = nullptr, *d_cta = nullptr, *d_err = nullptr;
   RhsState *d_st2 = nullptr, *d_out = nullptr;
   unsigned long long* d_bar = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  LockWs() = default;
+  LockWs() { mem.stream = &stream; }
   LockWs(const LockWs&) = delete;
   LockWs& operator=(const LockWs&) = delete;
   ~LockWs() {
@@ -1027,6 +1078,7 @@ static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, d
   cudaStream_t s = c0->stream;
   const int pol = c0->pol, qx = c0->qx;
   LockWs local;
+  local.stream = s;
   LockWs& ws = wsp ? *wsp : local;
   const size_t abytes = iter_args_bytes();
   const int bps = lockstep_blocks_per_sm(pol, qx);
@@ -1761,10 +1813,13 @@ struct ServerReq {
   BatchItem item;
 };
 
+// A finished request's result: x is allocated when the request finishes,
+// uninitialised (the device copy fills it), and handed over by aj_poll.
 struct ServerDone {
   aj_status st = AJ_OK;
   aj_info info;
-  std::vector<double> x;
+  std::unique_ptr<double[]> x;
+  size_t m = 0;
 };
 
 struct aj_server {
@@ -1802,7 +1857,7 @@ static size_t estimate_bytes(int64_t n, int64_t nnz, int nrhs, int precision) {
 }
 
 static void server_complete(aj_server* s, ServerReq* r, aj_status st, const aj_info* per,
-                            std::vector<double>&& x) {
+                            std::unique_ptr<double[]>&& x, size_t m) {
   ServerDone dn;
   dn.st = st;
   std::memset(&dn.info, 0, sizeof(dn.info));
@@ -1811,6 +1866,7 @@ static void server_complete(aj_server* s, ServerReq* r, aj_status st, const aj_i
   dn.info.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
                                                          r->t_submit).count();
   dn.x = std::move(x);
+  dn.m = dn.x ? m : 0;
   if (r->c) {
     if (r->owned) aj_destroy(r->c);
     else r->c->stream = r->user_stream;
@@ -1883,12 +1939,13 @@ static bool server_advance(aj_server* s, ServerReq* r) {
   aj_info per[kMaxRhs];
   std::memset(per, 0, sizeof(per));
   const size_t m = (size_t)c->n * c->nrhs;
-  std::vector<double> x(m);
+  std::unique_ptr<double[]> x;
   aj_status e = AJ_OK;
   if (!r->ir) {
     for (int k = 0; k < c->nrhs; k++)
       if (!r->d.st[k].done) return false;
-    e = direct_finish(c, r->d, x.data(), 0, per);
+    x.reset(new double[std::max<size_t>(m, 1)]);
+    e = direct_finish(c, r->d, x.get(), 0, per);
   } else {
     if (!r->q.finished) {
       for (int k = 0; k < c->nrhs; k++)
@@ -1901,13 +1958,17 @@ static bool server_advance(aj_server* s, ServerReq* r) {
         return false;
       }
     }
-    if (e == AJ_OK) e = ir_end(c, r->q, x.data(), 0, per);
+    if (e == AJ_OK) {
+      x.reset(new double[std::max<size_t>(m, 1)]);
+      e = ir_end(c, r->q, x.get(), 0, per);
+    }
   }
   aj_status st = e;
   if (st == AJ_OK)
     for (int k = 0; k < c->nrhs; k++)
       if (per[k].status != AJ_OK && st == AJ_OK) st = per[k].status;
-  server_complete(s, r, st, e == AJ_OK ? per : nullptr, std::move(x));
+  if (e != AJ_OK) x.reset();
+  server_complete(s, r, st, e == AJ_OK ? per : nullptr, std::move(x), m);
   return true;
 }
 
@@ -1935,7 +1996,7 @@ static void server_main(aj_server* s) {
     }
     for (ServerReq* r : admit) {
       aj_status e = server_start(s, r);
-      if (e != AJ_OK) server_complete(s, r, e, nullptr, {});
+      if (e != AJ_OK) server_complete(s, r, e, nullptr, nullptr, 0);
       else if (r->ir && r->q.finished) server_advance(s, r);
       else s->active.push_back(r);
     }
@@ -1963,12 +2024,12 @@ static void server_main(aj_server* s) {
     else if (kms > 4.0 && s->round_sweeps > 4) s->round_sweeps /= 2;
     std::vector<ServerReq*> still;
     for (ServerReq* r : s->active) {
-      if (e != AJ_OK) server_complete(s, r, e, nullptr, {});
+      if (e != AJ_OK) server_complete(s, r, e, nullptr, nullptr, 0);
       else if (!server_advance(s, r)) still.push_back(r);
     }
     s->active.swap(still);
   }
-  for (ServerReq* r : s->active) server_complete(s, r, AJ_ECUDA, nullptr, {});
+  for (ServerReq* r : s->active) server_complete(s, r, AJ_ECUDA, nullptr, nullptr, 0);
   s->active.clear();
 }
 
@@ -1982,9 +2043,11 @@ extern "C" aj_status aj_server_create(size_t hbm_budget_bytes, int max_slots, aj
   cudaGetDevice(&s->dev);
   if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
+    s->stream = nullptr;
     delete s;
     return AJ_ECUDA;
   }
+  s->lws.stream = s->stream;
   s->th = std::thread(server_main, s);
   *out = s;
   return AJ_OK;
@@ -2061,7 +2124,7 @@ extern "C" aj_status aj_poll(aj_server* s, uint64_t ticket, double* x_out, aj_in
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->done.find(ticket);
   if (it == s->done.end()) return s->pending.count(ticket) ? AJ_PENDING : AJ_EINVAL;
-  if (x_out && !it->second.x.empty()) std::memcpy(x_out, it->second.x.data(), it->second.x.size() * 8);
+  if (x_out && it->second.x) std::memcpy(x_out, it->second.x.get(), it->second.m * 8);
   if (info) *info = it->second.info;
   const aj_status st = it->second.st;
   s->done.erase(it);
@@ -2098,6 +2161,7 @@ extern "C" void aj_server_destroy(aj_server* s) {
   for (ServerReq* r : s->queue) delete r;
   s->queue.clear();
   if (s->stream) {
+    s->lws.mem.release();
     cudaStreamSynchronize(s->stream);
     cudaStreamDestroy(s->stream);
   }
