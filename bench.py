@@ -126,6 +126,21 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def job_throughput(local_ms, local_bytes, dist=None, device=None):
+    """Whole-job figures over replicas: every rank solves its own copy of the
+    workload (no collective on the data path), so the job takes as long as
+    the slowest rank (max over ranks) and moves the bytes of all ranks (sum).
+    Returns (max_ms, total_bytes, GB/s)."""
+    import torch
+    mx = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(local_bytes)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    ms, byt = float(mx.item()), float(sm.item())
+    return ms, byt, byt / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -428,13 +443,9 @@ def main():
     ctx = make(args.precision, form)
     with Clocks(dev.index) as clk:
         ms, infos, launches = time_solves(ctx, args.steps, args.warmup)
-    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
     B = algorithmic_bytes(n, nnz, args.precision, form)
     iters = sum(i["iters"] for i in infos)
-    value = B * iters * ws / (ms * 1e-3) / 1e9
+    ms, _, value = job_throughput(ms, B * iters, dist, dev)
     kernel_ms = sum(i["kernel_ms"] for i in infos)
     sweeps = sum(i["sweeps"] for i in infos)
     hbm_peak, peak_kind = load_peaks()
