@@ -114,6 +114,21 @@ typedef struct {
 #define AJ_FMT_CSR 1
 #define AJ_FMT_SELL 2
 
+/* Row order of Q for the fused sweep (a format choice; the paper has no
+ * counterpart).  RCM renumbers rows and columns by reverse Cuthill-McKee
+ * (George and Liu, "Computer Solution of Large Sparse Positive Definite
+ * Systems", 1981), so that the x entries a tile gathers lie close together
+ * and stay in cache.  Each row keeps its entries in the caller's order, so
+ * every row sum is bit for bit the one of the caller's order; only the
+ * grouping of the FP64 reductions changes.  b, x0 and the returned x stay in
+ * the caller's order.  AUTO applies RCM to large matrices without heavy rows
+ * (n >= 16384, no row above 16x the mean length plus 16) whose current order
+ * gathers from far away, and keeps it only when it shrinks the summed row
+ * spans (max minus min column) at least fourfold. */
+#define AJ_REORDER_AUTO 0
+#define AJ_REORDER_NONE 1
+#define AJ_REORDER_RCM 2
+
 typedef struct {
   int j_policy;          /* AJ_J_ABSROWSUM (default) | AJ_J_SCALED_DIAG */
   double L;              /* AJ_J_SCALED_DIAG step constant; 0 = estimate by power iteration */
@@ -135,6 +150,7 @@ typedef struct {
   int sweep_form;        /* AJ_SWEEP_AUTO (default) | AJ_SWEEP_LAZY | AJ_SWEEP_STORED */
   int sell_sigma;        /* AJ_FMT_SELL: sorting window sigma in rows (0 = 256) */
   int sell_lmax;         /* AJ_FMT_SELL: rows longer than this go to the warp-per-row bucket (0 = 64) */
+  int reorder;           /* AJ_REORDER_AUTO (default) | AJ_REORDER_NONE | AJ_REORDER_RCM */
 } aj_params;
 
 /* Per-solve report. */
@@ -171,6 +187,11 @@ aj_status aj_set(aj_ctx* ctx, const aj_params* p);
  * threshold (0 for CSR), and the stored SELL entries per stored entry of Q
  * (padding overhead, 1.0 for CSR). */
 aj_status aj_get_format(aj_ctx* ctx, int* format, int* sigma, int* lmax, double* fill_ratio);
+
+/* Whether aj_set renumbered the rows (1: reverse Cuthill-McKee order in use,
+ * 0: the caller's order), and the summed row spans before and after (equal
+ * when no reordering was tried). */
+aj_status aj_get_order(aj_ctx* ctx, int* reordered, double* span_before, double* span_after);
 
 /* Run all GPU work of ctx on this cudaStream_t (NULL = legacy default stream). */
 aj_status aj_set_stream(aj_ctx* ctx, void* cuda_stream);

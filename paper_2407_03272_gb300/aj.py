@@ -21,6 +21,7 @@ AJ_STOP_RELRES, AJ_STOP_OBJGAP, AJ_STOP_NONE = 0, 1, 2
 AJ_FP64, AJ_DF64, AJ_FP32_IR, AJ_BF16_IR = 0, 1, 2, 3
 AJ_FMT_AUTO, AJ_FMT_CSR, AJ_FMT_SELL = 0, 1, 2
 AJ_SWEEP_AUTO, AJ_SWEEP_LAZY, AJ_SWEEP_STORED = 0, 1, 2
+AJ_REORDER_AUTO, AJ_REORDER_NONE, AJ_REORDER_RCM = 0, 1, 2
 AJ_NOALLOC_MAX_N = 131072
 
 PRECISIONS = {"fp64": AJ_FP64, "df64": AJ_DF64, "fp32_ir": AJ_FP32_IR, "bf16_ir": AJ_BF16_IR}
@@ -39,7 +40,7 @@ class aj_params(ctypes.Structure):
                 ("x0", ctypes.c_void_p), ("x0_on_device", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int64),
                 ("grid_ctas", ctypes.c_int), ("sweep_form", ctypes.c_int),
-                ("sell_sigma", ctypes.c_int), ("sell_lmax", ctypes.c_int)]
+                ("sell_sigma", ctypes.c_int), ("sell_lmax", ctypes.c_int), ("reorder", ctypes.c_int)]
 
 
 class aj_info(ctypes.Structure):
@@ -78,6 +79,8 @@ SIGNATURES = [
                                  ctypes.POINTER(ctypes.c_void_p)]),
     ("aj_set", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(aj_params)]),
     ("aj_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("aj_get_order", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)]),
     ("aj_get_format", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     ("aj_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(aj_info)]),
@@ -195,6 +198,12 @@ class Context:
         _check(lib().aj_get_format(self._h, ctypes.byref(f), ctypes.byref(sg), ctypes.byref(lm),
                                    ctypes.byref(fr)), "aj_get_format")
         return f.value, sg.value, lm.value, fr.value
+
+    def order(self):
+        """(reordered, span_before, span_after) decided by aj_set."""
+        o, a, b = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().aj_get_order(self._h, ctypes.byref(o), ctypes.byref(a), ctypes.byref(b)), "aj_get_order")
+        return o.value, a.value, b.value
 
     def set_stream(self, stream):
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream

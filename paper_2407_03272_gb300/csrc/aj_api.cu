@@ -12,6 +12,7 @@
 #include <array>
 #include <atomic>
 #include <chrono>
+#include <climits>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -238,6 +239,20 @@ struct aj_ctx {
   bool resume = false;
   std::vector<RhsState> st_h;
   std::vector<std::vector<long long>> rlog_h;
+  // locality ordering (aj_set, AJ_REORDER_*): while `ordered`, rp, ci, val64,
+  // diag and b64 point at renumbered copies in ows; the caller's order stays
+  // in rp0 .. b0
+  Workspace ows;
+  int ordered = 0;
+  bool order_tried = false;  // AUTO already evaluated for this matrix
+  double span0 = 0.0, span1 = 0.0;
+  int* rp0 = nullptr;
+  int* ci0 = nullptr;
+  double* val0 = nullptr;
+  double* diag0 = nullptr;
+  double* b0 = nullptr;
+  int* perm = nullptr;      // device [n]: new row -> caller's row
+  std::vector<int> perm_h;  // host copy
 };
 
 static aj_status cuda_fail(cudaError_t e) {
@@ -301,6 +316,7 @@ extern "C" void aj_destroy(aj_ctx* c) {
   else cudaDeviceSynchronize();
   c->sws.release();
   c->pws.release();
+  c->ows.release();
   c->base.release();
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -330,7 +346,7 @@ extern "C" aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ct
   if (Q->nnz > 0 && (!Q->col || !Q->val)) return AJ_EINVAL;
   aj_ctx* c = new aj_ctx();
   aj_params_default(&c->prm);
-  c->base.stream = c->pws.stream = c->sws.stream = &c->stream;
+  c->base.stream = c->pws.stream = c->sws.stream = c->ows.stream = &c->stream;
   cudaGetDevice(&c->dev);
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
   c->n = Q->n;
@@ -413,6 +429,11 @@ extern "C" aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ct
     aj_destroy(c);
     return st;
   }
+  c->rp0 = c->rp;
+  c->ci0 = c->ci;
+  c->val0 = c->val64;
+  c->diag0 = c->diag;
+  c->b0 = c->b64;
   *out = c;
   return AJ_OK;
 }
@@ -476,6 +497,249 @@ static aj_status estimate_L(aj_ctx* c, double* L_out) {
   return AJ_OK;
 }
 
+// ---------------------------------------------------------------- locality ordering
+// Reverse Cuthill-McKee order of the graph of Q (rows as vertices, stored
+// entries as edges; George and Liu 1981): in each connected component a
+// breadth-first search starts from a pseudo-peripheral vertex (repeat the
+// search from a least-degree vertex of the last level while the depth
+// grows), visits the neighbours of each vertex by increasing degree, and the
+// whole order is reversed.  perm[new] = old.
+static void rcm_order(int n, const std::vector<int>& rp, const std::vector<int>& ci, std::vector<int>& perm) {
+  std::vector<int> deg(n), mark(n, -1), queue;
+  for (int i = 0; i < n; i++) deg[i] = rp[i + 1] - rp[i];
+  queue.reserve(n);
+  int stamp = 0;
+  // levels of a BFS from r (marks vertices with this stamp); returns depth and last level
+  auto bfs_levels = [&](int r, std::vector<int>& last) {
+    const int st = stamp++;
+    std::vector<int> cur(1, r), nxt;
+    mark[r] = st;
+    int depth = 0;
+    for (;;) {
+      nxt.clear();
+      for (int v : cur)
+        for (int q = rp[v]; q < rp[v + 1]; q++) {
+          const int u = ci[q];
+          if (mark[u] != st) { mark[u] = st; nxt.push_back(u); }
+        }
+      if (nxt.empty()) break;
+      cur.swap(nxt);
+      depth++;
+    }
+    last = cur;
+    return depth;
+  };
+  std::vector<char> done(n, 0);
+  std::vector<int> order, last, nb;
+  order.reserve(n);
+  for (int s0 = 0; s0 < n; s0++) {
+    if (done[s0]) continue;
+    int root = s0, ecc = -1;
+    for (int it = 0; it < 6; it++) {
+      const int d = bfs_levels(root, last);
+      if (d <= ecc) break;
+      ecc = d;
+      int best = last[0];
+      for (int v : last) if (deg[v] < deg[best] || (deg[v] == deg[best] && v < best)) best = v;
+      root = best;
+    }
+    // Cuthill-McKee from root
+    size_t head = order.size();
+    order.push_back(root);
+    done[root] = 1;
+    while (head < order.size()) {
+      const int v = order[head++];
+      nb.clear();
+      for (int q = rp[v]; q < rp[v + 1]; q++) {
+        const int u = ci[q];
+        if (!done[u]) { done[u] = 1; nb.push_back(u); }
+      }
+      std::sort(nb.begin(), nb.end(), [&](int x, int y) { return deg[x] < deg[y] || (deg[x] == deg[y] && x < y); });
+      order.insert(order.end(), nb.begin(), nb.end());
+    }
+  }
+  perm.assign(order.rbegin(), order.rend());
+}
+
+// Summed row spans (largest minus smallest column) with columns renamed by
+// iperm (identity when empty).
+static double row_spans(int n, const std::vector<int>& rp, const std::vector<int>& ci, const std::vector<int>& iperm) {
+  double tot = 0.0;
+  for (int i = 0; i < n; i++) {
+    int lo = INT_MAX, hi = -1;
+    for (int q = rp[i]; q < rp[i + 1]; q++) {
+      const int c = iperm.empty() ? ci[q] : iperm[ci[q]];
+      lo = std::min(lo, c);
+      hi = std::max(hi, c);
+    }
+    if (hi >= lo) tot += (double)(hi - lo);
+  }
+  return tot;
+}
+
+// Orderings already computed, keyed by the matrix's pattern (n, nnz and a
+// 64-bit hash of row_ptr and col), so that a server that sees the same
+// operator again, or a caller that builds several contexts of one matrix,
+// skips the host-side search.  Any permutation of the rows is a valid
+// ordering, so a hash collision could cost locality but never accuracy.
+struct OrderEntry {
+  bool use = false;  // AUTO's decision
+  double span0 = 0.0, span1 = 0.0;
+  std::vector<int> perm;
+};
+static std::map<std::tuple<int64_t, int64_t, uint64_t>, OrderEntry> g_order;
+static std::deque<std::tuple<int64_t, int64_t, uint64_t>> g_order_fifo;
+static std::mutex g_order_mu;
+static const size_t kOrderCacheEntries = 64;
+
+static uint64_t pattern_hash(const std::vector<int>& rp, const std::vector<int>& ci) {
+  uint64_t h = 0x9e3779b97f4a7c15ull;
+  auto mix = [&](uint64_t v) {
+    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    h *= 0xbf58476d1ce4e5b9ull;
+    h ^= h >> 31;
+  };
+  for (int v : rp) mix((uint32_t)v);
+  for (int v : ci) mix((uint32_t)v);
+  return h;
+}
+
+// Back to the caller's row order.
+static void order_drop(aj_ctx* c) {
+  c->rp = c->rp0;
+  c->ci = c->ci0;
+  c->val64 = c->val0;
+  c->diag = c->diag0;
+  c->b64 = c->b0;
+  c->ows.release();
+  c->perm = nullptr;
+  c->perm_h.clear();
+  c->ordered = 0;
+}
+
+// Renumbered copies of the matrix, its diagonal and b for perm (host, new ->
+// old); the context then runs in that order.
+static aj_status order_apply(aj_ctx* c, const std::vector<int>& perm, const std::vector<int>& rp) {
+  const int n = (int)c->n;
+  const long long nnz = c->nnz;
+  const int nrhs = c->nrhs;
+  cudaStream_t s = c->stream;
+  order_drop(c);
+  std::vector<int> iperm(n), rp1((size_t)n + 1);
+  rp1[0] = 0;
+  for (int i = 0; i < n; i++) {
+    iperm[perm[i]] = i;
+    rp1[i + 1] = rp1[i] + (rp[perm[i] + 1] - rp[perm[i]]);
+  }
+  int* d_perm = (int*)c->ows.alloc((size_t)(n + 1) * 4);
+  int* d_iperm = (int*)c->ows.alloc((size_t)(n + 1) * 4);
+  int* rp_o = (int*)c->ows.alloc((size_t)(n + 1 + 16) * 4);
+  int* ci_o = (int*)c->ows.alloc((size_t)(nnz + 16) * 4);
+  double* val_o = (double*)c->ows.alloc((size_t)(nnz + 16) * 8);
+  double* diag_o = (double*)c->ows.alloc((size_t)(n + 1) * 8);
+  double* b_o = (double*)c->ows.alloc((size_t)((long long)n * nrhs + 1) * 8);
+  if (!d_perm || !d_iperm || !rp_o || !ci_o || !val_o || !diag_o || !b_o) {
+    c->ows.release();
+    return AJ_ENOMEM;
+  }
+  CK(cudaMemcpyAsync(d_perm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_iperm, iperm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(rp_o, rp1.data(), (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ci_o + nnz, 0, 16 * 4, s));
+  CK(cudaMemsetAsync(val_o + nnz, 0, 16 * 8, s));
+  if (n > 0) {
+    k_permute_csr<<<(unsigned)(((long long)n * 32 + kSetupThreads - 1) / kSetupThreads), kSetupThreads, 0, s>>>(
+        n, d_perm, d_iperm, c->rp0, c->ci0, c->val0, rp_o, ci_o, val_o);
+    counted();
+    k_gather_rows<<<grid1d(n), kSetupThreads, 0, s>>>(n, 1, d_perm, c->diag0, diag_o);
+    counted();
+    k_gather_rows<<<grid1d((long long)n * nrhs), kSetupThreads, 0, s>>>(n, nrhs, d_perm, c->b0, b_o);
+    counted();
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  c->rp = rp_o;
+  c->ci = ci_o;
+  c->val64 = val_o;
+  c->diag = diag_o;
+  c->b64 = b_o;
+  c->perm = d_perm;
+  c->perm_h = perm;
+  c->ordered = 1;
+  return AJ_OK;
+}
+
+// The row order aj_set asks for (see AJ_REORDER_* in aj.h).
+static aj_status choose_order(aj_ctx* c, int mode) {
+  if (mode == AJ_REORDER_NONE) {
+    if (c->ordered) order_drop(c);
+    return AJ_OK;
+  }
+  if (c->ordered) return AJ_OK;                          // already renumbered
+  if (mode == AJ_REORDER_AUTO && c->order_tried) return AJ_OK;  // evaluated before: keep the caller's order
+  const int n = (int)c->n;
+  if (n < 2 || c->nnz == 0) return AJ_OK;
+  cudaStream_t s = c->stream;
+  std::vector<int> rp((size_t)n + 1);
+  CK(cudaMemcpyAsync(rp.data(), c->rp0, rp.size() * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (mode == AJ_REORDER_AUTO) {
+    c->order_tried = true;
+    int maxlen = 0;
+    for (int i = 0; i < n; i++) maxlen = std::max(maxlen, rp[i + 1] - rp[i]);
+    const double mean = (double)c->nnz / n;
+    if (n < 16384 || maxlen > 16.0 * mean + 16.0) return AJ_OK;
+  }
+  std::vector<int> ci((size_t)c->nnz);
+  CK(cudaMemcpyAsync(ci.data(), c->ci0, ci.size() * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const auto key = std::make_tuple(c->n, c->nnz, pattern_hash(rp, ci));
+  OrderEntry ent;
+  bool hit = false;
+  {
+    std::lock_guard<std::mutex> lk(g_order_mu);
+    auto it = g_order.find(key);
+    if (it != g_order.end() && (it->second.use || mode == AJ_REORDER_AUTO)) {
+      ent = it->second;
+      hit = true;
+    }
+  }
+  if (!hit) {
+    const std::vector<int> none;
+    ent.span0 = ent.span1 = row_spans(n, rp, ci, none);
+    // rows that already gather from a small part of x on average (a natural
+    // stencil order spans 2 N^(d-1) of n = N^d) keep the caller's order
+    if (mode == AJ_REORDER_RCM || ent.span0 > (double)n * (n / 8.0)) {
+      rcm_order(n, rp, ci, ent.perm);
+      std::vector<int> iperm(n);
+      for (int i = 0; i < n; i++) iperm[ent.perm[i]] = i;
+      ent.span1 = row_spans(n, rp, ci, iperm);
+      ent.use = ent.span1 * 4.0 <= ent.span0;
+    }
+    std::lock_guard<std::mutex> lk(g_order_mu);
+    if (!g_order.count(key)) {
+      if (g_order_fifo.size() >= kOrderCacheEntries) {
+        g_order.erase(g_order_fifo.front());
+        g_order_fifo.pop_front();
+      }
+      g_order_fifo.push_back(key);
+    }
+    g_order[key] = ent;
+  }
+  c->span0 = ent.span0;
+  c->span1 = ent.span1;
+  if (mode == AJ_REORDER_AUTO && !ent.use) return AJ_OK;
+  return order_apply(c, ent.perm, rp);
+}
+
+extern "C" aj_status aj_get_order(aj_ctx* c, int* reordered, double* span_before, double* span_after) {
+  if (!c) return AJ_EINVAL;
+  if (reordered) *reordered = c->ordered;
+  if (span_before) *span_before = c->span0;
+  if (span_after) *span_after = c->span1;
+  return AJ_OK;
+}
+
 static aj_status choose_format(aj_ctx* c, const aj_params* p);
 
 // (Re)build everything that depends on the parameters.
@@ -491,6 +755,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   if (p->grid_ctas < 0) return AJ_EINVAL;
   if (p->sweep_form < AJ_SWEEP_AUTO || p->sweep_form > AJ_SWEEP_STORED) return AJ_EINVAL;
   if (p->sell_sigma < 0 || p->sell_lmax < 0) return AJ_EINVAL;
+  if (p->reorder < AJ_REORDER_AUTO || p->reorder > AJ_REORDER_RCM) return AJ_EINVAL;
   if ((p->precision == AJ_FP32_IR || p->precision == AJ_BF16_IR) &&
       (!(p->inner_tol > 0.0) || p->max_outer < 1))
     return AJ_EINVAL;
@@ -503,6 +768,13 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   const int nrhs = c->nrhs;
   const long long m = (long long)n * nrhs;
   cudaStream_t s = c->stream;
+  // --- row order (before anything is derived from the matrix)
+  {
+    const int was = c->ordered;
+    aj_status st = choose_order(c, p->reorder);
+    if (st != AJ_OK) return st;
+    if (was != c->ordered) c->sws.release(), c->fmt = 0;
+  }
   // --- J^{-1} in FP64
   double L = 0.0;
   if (p->j_policy == AJ_J_SCALED_DIAG) {
@@ -915,10 +1187,10 @@ static aj_status time_sweeps(aj_ctx* c, double* ms_per_sweep) {
 
 struct TuneKey {
   int64_t n, nnz, sumsq, maxlen;
-  int pol, nrhs, qx;
+  int pol, nrhs, qx, ordered;
   bool operator<(const TuneKey& o) const {
-    return std::tie(n, nnz, sumsq, maxlen, pol, nrhs, qx) <
-           std::tie(o.n, o.nnz, o.sumsq, o.maxlen, o.pol, o.nrhs, o.qx);
+    return std::tie(n, nnz, sumsq, maxlen, pol, nrhs, qx, ordered) <
+           std::tie(o.n, o.nnz, o.sumsq, o.maxlen, o.pol, o.nrhs, o.qx, o.ordered);
   }
 };
 static std::map<TuneKey, std::array<int, 3>> g_tune;  // -> {fmt, sigma, lmax}
@@ -946,7 +1218,7 @@ static aj_status choose_format(aj_ctx* c, const aj_params* p) {
   }
   const double mean = (double)c->nnz / n;
   if (maxlen <= 2.0 * mean + 8.0) return AJ_OK;
-  const TuneKey key{c->n, c->nnz, sumsq, maxlen, c->pol, c->nrhs, c->qx};
+  const TuneKey key{c->n, c->nnz, sumsq, maxlen, c->pol, c->nrhs, c->qx, c->ordered};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
@@ -1269,8 +1541,10 @@ static aj_status load_x0(aj_ctx* c) {
   CK(cudaMemcpyAsync(h.data(), c->prm.x0, (size_t)m * 8,
                      c->prm.x0_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
   CK(cudaStreamSynchronize(s));
+  // (row i of the run's order is the caller's row perm[i] when renumbered)
   for (int r = 0; r < c->nrhs; r++)
-    for (int i = 0; i < n; i++) il[(size_t)i * c->nrhs + r] = h[(size_t)r * n + i];
+    for (int i = 0; i < n; i++)
+      il[(size_t)i * c->nrhs + r] = h[(size_t)r * n + (c->ordered ? c->perm_h[i] : i)];
   CK(cudaMemcpyAsync(c->tmp64, il.data(), (size_t)m * 8, cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
   return AJ_OK;
@@ -1281,6 +1555,17 @@ static aj_status write_output(aj_ctx* c, const double* x_il, double* x_out, int 
   const long long m = (long long)n * c->nrhs;
   cudaStream_t s = c->stream;
   if (m == 0) return AJ_OK;
+  if (c->ordered) {
+    // back to the caller's rows and column-major layout in one gather
+    double* cm = x_il == c->tmp64 ? c->r64 : c->tmp64;
+    if (!cm || cm == x_il) return AJ_EINVAL;
+    k_unpermute_deinterleave<<<grid1d(m), kSetupThreads, 0, s>>>(n, c->nrhs, c->perm, x_il, cm);
+    counted();
+    CK(cudaMemcpyAsync(x_out, cm, (size_t)m * 8,
+                       x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return AJ_OK;
+  }
   if (c->nrhs == 1) {
     CK(cudaMemcpyAsync(x_out, x_il, (size_t)m * 8,
                        x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
@@ -1646,7 +1931,7 @@ struct StateHeader {
   uint64_t magic;
   int64_t n;
   int32_t nrhs, pol;
-  int32_t state_bytes, pad;  // pad: sweep form of the saved run
+  int32_t state_bytes, pad;  // pad: sweep form of the saved run | row order (bit 8)
   double sb[kMaxRhs];
 };
 static const uint64_t kStateMagic = 0x414a535441544531ull;  // "AJSTATE1"
@@ -1667,7 +1952,7 @@ extern "C" aj_status aj_get_state(aj_ctx* c, void* buf, size_t* size) {
   h.nrhs = c->nrhs;
   h.pol = c->pol;
   h.state_bytes = (int)sizeof(RhsState);
-  h.pad = c->qx;
+  h.pad = c->qx | (c->ordered << 8);
   for (int r = 0; r < kMaxRhs; r++) h.sb[r] = c->sb[r];
   std::memcpy(p, &h, sizeof(h));
   p += sizeof(h);
@@ -1692,7 +1977,7 @@ extern "C" aj_status aj_set_state(aj_ctx* c, const void* buf, size_t size) {
   const size_t vb = (size_t)c->n * c->nrhs * xelem_bytes(c->pol);
   const size_t need = sizeof(StateHeader) + sizeof(RhsState) * c->nrhs + 5 * vb;
   if (h.magic != kStateMagic || h.n != c->n || h.nrhs != c->nrhs || h.pol != c->pol ||
-      h.state_bytes != (int)sizeof(RhsState) || h.pad != c->qx || size < need)
+      h.state_bytes != (int)sizeof(RhsState) || h.pad != (c->qx | (c->ordered << 8)) || size < need)
     return AJ_EINVAL;
   const char* p = (const char*)buf + sizeof(h);
   c->st_h.resize(c->nrhs);
@@ -1842,7 +2127,7 @@ struct aj_server {
   aj_server_stats stats;
 };
 
-static size_t ctx_bytes(const aj_ctx* c) { return c->base.bytes + c->pws.bytes; }
+static size_t ctx_bytes(const aj_ctx* c) { return c->base.bytes + c->pws.bytes + c->sws.bytes + c->ows.bytes; }
 
 // Device bytes a context of this shape allocates (aj_create + aj_set).
 static size_t estimate_bytes(int64_t n, int64_t nnz, int nrhs, int precision) {

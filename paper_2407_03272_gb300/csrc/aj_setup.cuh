@@ -267,4 +267,38 @@ __global__ void k_axpy_masked(long long m, int nrhs, unsigned mask, const double
   if (e < m && ((mask >> (e % nrhs)) & 1u)) x[e] += c * d[e];
 }
 
+// Locality ordering.  New row i is old row perm[i]: its entries keep their
+// original order (so every row sums exactly as before) and their columns are
+// renamed through iperm (old -> new).  One warp per row.
+__global__ void k_permute_csr(int n, const int* perm, const int* iperm, const int* rp0, const int* ci0,
+                              const double* val0, const int* rp1, int* ci1, double* val1) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const int i = (int)w, o = perm[i];
+  const int s0 = rp0[o], len = rp0[o + 1] - s0, s1 = rp1[i];
+  for (int k = lane; k < len; k += 32) {
+    ci1[s1 + k] = iperm[ci0[s0 + k]];
+    val1[s1 + k] = val0[s0 + k];
+  }
+}
+// dst[i * nrhs + r] = src[perm[i] * nrhs + r]: an interleaved vector (or, with
+// nrhs = 1, a per-row array) into the new order.
+__global__ void k_gather_rows(int n, int nrhs, const int* perm, const double* src, double* dst) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * nrhs) return;
+  const int r = (int)(e % nrhs);
+  const long long i = e / nrhs;
+  dst[e] = src[(long long)perm[i] * nrhs + r];
+}
+// cm[r * n + perm[i]] = il[i * nrhs + r]: an interleaved vector in the new
+// order back to the caller's column-major layout and row order.
+__global__ void k_unpermute_deinterleave(int n, int nrhs, const int* perm, const double* il, double* cm) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * nrhs) return;
+  const int r = (int)(e % nrhs);
+  const long long i = e / nrhs;
+  cm[(long long)r * n + perm[i]] = il[e];
+}
+
 }  // namespace aj

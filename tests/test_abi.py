@@ -63,4 +63,4 @@ def test_struct_layouts_match_header():
     # sizes a C compiler gives the three public structs on LP64
     assert ctypes.sizeof(aj.aj_csr) == 48
     assert ctypes.sizeof(aj.aj_info) == 88
-    assert ctypes.sizeof(aj.aj_params) == 128
+    assert ctypes.sizeof(aj.aj_params) == 136
