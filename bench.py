@@ -51,6 +51,17 @@ def algorithmic_bytes(n, nnz, precision, form="stored"):
     return nnz * (vb + 4) + 4 * (n + 1) + n * kvec * sb
 
 
+# DRAM bytes (read + written) per fused sweep over the algorithmic bytes of the
+# same sweep, from the ncu capture of this kernel on the 128^3 Poisson system
+# (50 iterations, 51 sweeps per launch): FP64 15.968 GB / 51 / 300.8 MB, FP32
+# values 9.382 GB / 51 / 183.8 MB.  The bench scales it to a full launch by the
+# sweeps it runs; traffic grows in proportion to the rows swept.
+TRAFFIC_PER_ALGORITHMIC = {"fp64": 15.967641e9 / 51 / 300810244.0,
+                           "fp32_ir": 9.382468e9 / 51 / 183762948.0}
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 128^3 capture, "
+                  "scaled by rows and sweeps to one launch of this workload")
+
+
 def fp64_ops(n, nnz, form="stored"):
     """FP64 instructions of one FP64 fused iteration (an FMA counts once):
     stored form, one FMA per stored entry and 9 per row (g0, rr, two
@@ -462,6 +473,13 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": kern_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": kern_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind + " (burst copy)"}
+    ratio = TRAFFIC_PER_ALGORITHMIC.get(args.precision) if form == "stored" else None
+    if ratio is not None:
+        # per launch of the fused kernel: one per solve in FP64, one per inner solve otherwise
+        per_launch_sweeps = sweeps / max(1, len(infos) * max(1, infos[-1]["outer"]))
+        roof["traffic"] = ratio * B * per_launch_sweeps
+        roof["traffic_per_algorithmic"] = ratio
+        roof["traffic_source"] = TRAFFIC_SOURCE
     roof["kernel"] = "aj_persistent_kernel<%s, 1, %s>" % (
         {"fp64": "PolF64", "df64": "PolDF64", "fp32_ir": "PolF32", "bf16_ir": "PolB16"}[args.precision],
         "true" if form == "stored" else "false")
