@@ -367,7 +367,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32_ir", "bf16_ir"])
     ap.add_argument("--form", default="auto", choices=["auto", "lazy", "stored"],
-                    help="sweep form; auto = stored")
+                    help="sweep form; auto = stored for fp64, lazy otherwise (the library's AUTO)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -409,8 +409,9 @@ def main():
     stream = torch.cuda.current_stream()
 
     def form_of(precision, form):
+        # the library's AUTO choice on this (CSR) workload: stored for FP64, lazy otherwise
         if form == "auto":
-            return "stored"
+            return "stored" if precision == "fp64" else "lazy"
         return form
 
     SWEEP = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED}

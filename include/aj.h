@@ -95,10 +95,12 @@ typedef struct {
  * Both give the same iterates up to rounding.  LAZY sums both products over
  * the gathered x^{t-1} and x^{t-2} (two multiply-adds per stored entry, fewer
  * bytes); STORED keeps u = Q x per row and re-reads u^{t-2} (one multiply-add
- * per stored entry, two more n-vectors of traffic).  AUTO picks STORED: it
- * halves the FP64 issue (the binding resource of AJ_FP64 on GB300) and the
- * random gathers of graph matrices, and measured faster in every precision
- * on the 3-D Poisson and Chung-Lu systems. */
+ * per stored entry, two more n-vectors of traffic).  AUTO picks STORED for
+ * AJ_FP64, whose FP64 issue rate binds on GB300, and for matrices stored as
+ * SELL (irregular rows, whose gathers are random: one per entry instead of
+ * two); LAZY for the other precisions on CSR, where the second row sum
+ * gathers from the same cached lines (measured faster on the 3-D Poisson
+ * system and on 2-D grids with 4 RHS). */
 #define AJ_SWEEP_AUTO 0
 #define AJ_SWEEP_LAZY 1
 #define AJ_SWEEP_STORED 2

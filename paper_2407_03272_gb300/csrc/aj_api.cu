@@ -253,7 +253,17 @@ struct aj_ctx {
   double* b0 = nullptr;
   int* perm = nullptr;      // device [n]: new row -> caller's row
   std::vector<int> perm_h;  // host copy
+  // rows longer than kResidLong entries, in the run's order, for the FP64
+  // residual's warp-per-row pass (rebuilt when the order changes)
+  int maxlen = 0;
+  Workspace rws;
+  int* d_resid_long = nullptr;
+  int n_resid_long = 0;
+  double* part_long = nullptr;
+  int resid_long_order = -1;  // `ordered` the list was built for
 };
+
+static const int kResidLong = 32;
 
 static aj_status cuda_fail(cudaError_t e) {
   (void)e;
@@ -317,6 +327,7 @@ extern "C" void aj_destroy(aj_ctx* c) {
   c->sws.release();
   c->pws.release();
   c->ows.release();
+  c->rws.release();
   c->base.release();
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -346,7 +357,7 @@ extern "C" aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ct
   if (Q->nnz > 0 && (!Q->col || !Q->val)) return AJ_EINVAL;
   aj_ctx* c = new aj_ctx();
   aj_params_default(&c->prm);
-  c->base.stream = c->pws.stream = c->sws.stream = c->ows.stream = &c->stream;
+  c->base.stream = c->pws.stream = c->sws.stream = c->ows.stream = c->rws.stream = &c->stream;
   cudaGetDevice(&c->dev);
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
   c->n = Q->n;
@@ -413,6 +424,16 @@ extern "C" aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ct
       break;
     }
     if (flags) { st = AJ_EINVAL; break; }
+    // longest row (c->err is zero again: flags was 0)
+    if (n > 0) {
+      k_max_row_len<<<std::min<unsigned>(grid1d(n), 4096), kSetupThreads, 0, s>>>(n, c->rp, c->err);
+      counted();
+      if (cudaMemcpyAsync(&c->maxlen, c->err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaMemsetAsync(c->err, 0, 4, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        st = cuda_fail(cudaGetLastError());
+        break;
+      }
+    }
     // ||b_r||^2 in FP64 and b finite
     std::vector<double> hb((size_t)m);
     if (m > 0 && (cudaMemcpyAsync(hb.data(), c->b64, (size_t)m * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -834,6 +855,8 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     c->pol = pol;
   }
   // --- sweep form and grid: a multiple of the SM count when the problem is large enough
+  // AUTO: the stored form while the format is chosen; after it, the lazy form
+  // for the other precisions on CSR (see the end of aj_set)
   c->qx = p->sweep_form == AJ_SWEEP_LAZY ? 0 : 1;
   {
     const int kp = kernel_pol(pol);
@@ -892,7 +915,22 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     c->sQ = 1.0;
   }
   CK(cudaStreamSynchronize(s));
-  return choose_format(c, p);
+  aj_status fe = choose_format(c, p);
+  if (fe != AJ_OK) return fe;
+  // AUTO sweep form: stored for FP64 (one FMA per entry; FP64 issue binds)
+  // and for SELL (irregular rows: one random gather per entry instead of
+  // two); lazy for the other precisions on CSR, where the second row sum
+  // gathers from the same cached lines and saves two n-vectors of traffic
+  if (p->sweep_form == AJ_SWEEP_AUTO && p->precision != AJ_FP64 && c->fmt == 0) {
+    c->qx = 0;
+    const int bps = std::max(1, persistent_blocks_per_sm(kernel_pol(pol), nrhs, c->qx));
+    const int rpt = kThreads >> lanes_log2(nrhs);
+    const int ntiles = std::max(1, (int)((n + rpt - 1) / rpt));
+    int g = std::min(bps * c->sm_count, ntiles);
+    if (p->grid_ctas > 0) g = std::min(p->grid_ctas, bps * c->sm_count);
+    c->grid = std::max(1, g);
+  }
+  return AJ_OK;
 }
 
 // Load interleaved FP64 data, scaled per right-hand side, into an
@@ -1490,21 +1528,62 @@ static aj_status fetch_rlog(aj_ctx* c, const std::vector<RhsState>& st, bool app
 }
 
 // FP64 residual of an interleaved FP64 iterate: relres and objgap per RHS.
+// The rows longer than kResidLong in the run's order, for the residual's
+// warp-per-row pass: built on first use and again after a change of order.
+static aj_status resid_long_rows(aj_ctx* c) {
+  if (c->maxlen <= kResidLong) {
+    c->n_resid_long = 0;
+    return AJ_OK;
+  }
+  if (c->resid_long_order == c->ordered) return AJ_OK;
+  const int n = (int)c->n;
+  std::vector<int> rp((size_t)n + 1), rows;
+  CK(cudaMemcpyAsync(rp.data(), c->rp, rp.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < n; i++)
+    if (rp[i + 1] - rp[i] > kResidLong) rows.push_back(i);
+  c->rws.release();
+  c->n_resid_long = (int)rows.size();
+  const int nb = (c->n_resid_long + kSetupThreads / 32 - 1) / (kSetupThreads / 32);
+  c->d_resid_long = (int*)c->rws.alloc((rows.size() + 1) * 4);
+  c->part_long = (double*)c->rws.alloc((size_t)std::max(nb, 1) * kMaxRhs * 3 * 8);
+  if (!c->d_resid_long || !c->part_long) return AJ_ENOMEM;
+  if (!rows.empty())
+    CK(cudaMemcpyAsync(c->d_resid_long, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  c->resid_long_order = c->ordered;
+  return AJ_OK;
+}
+
 static aj_status fp64_report(aj_ctx* c, const double* x_il, double* relres, double* objgap,
                              double* r_out) {
   const int n = (int)c->n;
   const int nrhs = c->nrhs;
   const int blocks = std::max(1, (int)grid1d(n));
+  aj_status st = resid_long_rows(c);
+  if (st != AJ_OK) return st;
+  const int nl = c->n_resid_long;
+  const int lblocks = (nl + kSetupThreads / 32 - 1) / (kSetupThreads / 32);
   if (n > 0) {
     k_residual<<<blocks, kSetupThreads, 0, c->stream>>>(n, nrhs, c->rp, c->ci, c->val64, c->b64,
-                                                        x_il, r_out, c->part_small);
+                                                        x_il, r_out, c->part_small, nl > 0 ? kResidLong : -1);
     counted();
+    if (nl > 0) {
+      k_residual_long<<<lblocks, kSetupThreads, 0, c->stream>>>(nl, c->d_resid_long, nrhs, c->rp, c->ci,
+                                                                c->val64, c->b64, x_il, r_out, c->part_long);
+      counted();
+    }
   } else
     CK(cudaMemsetAsync(c->part_small, 0, (size_t)nrhs * 3 * 8, c->stream));
   CK(cudaGetLastError());
   double sums[kMaxRhs * 3];
-  aj_status st = host_sum_parts(c, c->part_small, n > 0 ? blocks : 1, nrhs * 3, sums);
+  st = host_sum_parts(c, c->part_small, n > 0 ? blocks : 1, nrhs * 3, sums);
   if (st != AJ_OK) return st;
+  if (n > 0 && nl > 0) {
+    double more[kMaxRhs * 3];
+    st = host_sum_parts(c, c->part_long, lblocks, nrhs * 3, more);
+    if (st != AJ_OK) return st;
+    for (int k = 0; k < nrhs * 3; k++) sums[k] += more[k];
+  }
   for (int r = 0; r < nrhs; r++) {
     const double rn = std::sqrt(sums[r * 3 + 0]);
     const double bn = std::sqrt(c->bnorm2[r]);
@@ -1710,7 +1789,18 @@ static aj_status ir_begin(aj_ctx* c, IrRun& q) {
 
 // FP64 residual of x64 and the outer stop test; sets q.finished.
 static aj_status ir_check(aj_ctx* c, IrRun& q) {
-  aj_status e = fp64_report(c, c->x64, q.rel, q.og, c->r64);
+  aj_status e = AJ_OK;
+  if (q.outer == 0 && !c->prm.x0) {
+    // x^0 = 0: the residual is b itself (relative residual 1, f = 0)
+    const long long m = (long long)c->n * c->nrhs;
+    if (m > 0) CK(cudaMemcpyAsync(c->r64, c->b64, (size_t)m * 8, cudaMemcpyDeviceToDevice, c->stream));
+    for (int r = 0; r < c->nrhs; r++) {
+      q.rel[r] = c->bnorm2[r] > 0.0 ? 1.0 : 0.0;
+      q.og[r] = std::fabs(c->prm.fstar) / (1.0 + std::fabs(c->prm.fstar));
+    }
+  } else {
+    e = fp64_report(c, c->x64, q.rel, q.og, c->r64);
+  }
   if (e != AJ_OK) return e;
   bool all = true;
   for (int r = 0; r < c->nrhs; r++) {

@@ -201,13 +201,38 @@ __device__ __forceinline__ void acc_zero(double& a) { a = 0.0; }
 __device__ __forceinline__ double acc_value(double a) { return a; }
 
 // ----------------------------------------------------------------------------
-// Precision policies.
+// Precision policies.  kMinBlocks / kMinBlocksMulti: co-resident CTAs per SM
+// the register allocation must allow for one right-hand side and for the
+// lanes-per-row form of several (measured on GB300, fixed-iteration sweeps of
+// the 256^3 Poisson system and of a 1024^2 grid with 4 RHS):
+//   FP64   4 / 4  (FP64-issue bound; 3 CTAs/SM is 18 % slower)
+//   DF64   4 / 4  (5 CTAs/SM is 7 % slower)
+//   FP32   6 / 4  (one RHS: 6 CTAs/SM 23 % faster than 4 in the lazy form;
+//                  4 RHS: 4 CTAs/SM 20 % faster than 6)
+//   BF16   8 / 4  (one RHS: 8 CTAs/SM 30 % faster than 4 in the lazy form)
+#ifndef AJ_MINB_F64
+#define AJ_MINB_F64 4
+#endif
+#ifndef AJ_MINB_DF64
+#define AJ_MINB_DF64 4
+#endif
+#ifndef AJ_MINB_F32
+#define AJ_MINB_F32 6
+#endif
+#ifndef AJ_MINB_B16
+#define AJ_MINB_B16 8
+#endif
+#ifndef AJ_MINB_MULTI
+#define AJ_MINB_MULTI 4
+#endif
 struct PolF64 {
   using V = double;  // stored matrix value
   using X = double;  // stored vector element
   using S = double;  // row arithmetic
   using A = double;  // per-thread reduction accumulator
   static constexpr int kId = 0;
+  static constexpr int kMinBlocks = AJ_MINB_F64;
+  static constexpr int kMinBlocksMulti = AJ_MINB_MULTI;
   __device__ static S zero() { return 0.0; }
   __device__ static S ldx(const X* p) { return ld_l2(p); }
   __device__ static S ldr(const X* p) { return ld_ro(p); }
@@ -236,6 +261,8 @@ struct PolDF64 {
   using S = dw;
   using A = acc_dw;
   static constexpr int kId = 1;
+  static constexpr int kMinBlocks = AJ_MINB_DF64;
+  static constexpr int kMinBlocksMulti = AJ_MINB_MULTI;
   __device__ static S zero() { return {0.f, 0.f}; }
   __device__ static S ldx(const X* p) { float2 v = ld_l2(p); return {v.x, v.y}; }
   __device__ static S ldr(const X* p) { float2 v = ld_ro(p); return {v.x, v.y}; }
@@ -283,6 +310,8 @@ struct PolF32 {
   using S = float;
   using A = acc_dw;
   static constexpr int kId = 2;
+  static constexpr int kMinBlocks = AJ_MINB_F32;
+  static constexpr int kMinBlocksMulti = AJ_MINB_MULTI;
   __device__ static S zero() { return 0.f; }
   __device__ static S ldx(const X* p) { return ld_l2(p); }
   __device__ static S ldr(const X* p) { return ld_ro(p); }
@@ -311,6 +340,7 @@ struct PolF32 {
 struct PolB16 : PolF32 {
   using V = __nv_bfloat16;
   static constexpr int kId = 3;
+  static constexpr int kMinBlocks = AJ_MINB_B16;
   __device__ static V ldv(const V* p) { return ld_ro(p); }
   __device__ static V vzero() { return __float2bfloat16_rn(0.f); }
   __device__ static void macv(S& acc, V v, S x) { acc = __fmaf_rn(__bfloat162float(v), x, acc); }
@@ -783,12 +813,11 @@ __device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kN
   return all_done;
 }
 
-// Co-resident CTAs per SM the register allocation must allow.  The sweep is
-// latency bound (gathers from L2, the matrix stream from DRAM), so warps in
-// flight matter more than registers: measured on the 256^3 Poisson system,
-// 4 CTAs/SM beat the compiler's own choice of 2-3 by 1.3-1.7x.  A lane holds
-// one right-hand side whatever nrhs is, so every instantiation aims at 4.
-constexpr int kMinBlocks = 4;
+// Co-resident CTAs per SM (P::kMinBlocks, P::kMinBlocksMulti) the register
+// allocation must allow.  The sweep is latency bound (gathers from L2, the
+// matrix stream from DRAM), so warps in flight matter more than registers:
+// on the 256^3 Poisson system 4 CTAs/SM beat the compiler's own choice of
+// 2-3 by 1.3-1.7x in FP64, and the FP32/BF16 policies gain again from 6-8.
 
 // Shared memory of one solve: per-RHS state, grid totals, reduction scratch.
 struct SolveSmem {
@@ -906,7 +935,7 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, i
 // selects the instantiation that also reads the SELL-C-sigma format, MULTI
 // the one for several right-hand sides.
 template <class P, bool QX, bool ANY, bool MULTI>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) aj_persistent_kernel(IterArgs<P> a) {
+__global__ void __launch_bounds__(kThreads, MULTI ? P::kMinBlocksMulti : P::kMinBlocks) aj_persistent_kernel(IterArgs<P> a) {
   __shared__ SolveSmem sm;
   const int nr = MULTI ? a.nrhs : 1;
   if ((int)threadIdx.x < nr) sm.st[threadIdx.x] = a.state[threadIdx.x];
@@ -1012,7 +1041,7 @@ __device__ __forceinline__ bool lock_enter(const LockArgs<P>& b, IterArgs<P>& a,
 }
 
 template <class P, bool QX>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) aj_lockstep_kernel(LockArgs<P> b) {
+__global__ void __launch_bounds__(kThreads, P::kMinBlocksMulti) aj_lockstep_kernel(LockArgs<P> b) {
   __shared__ SolveSmem sm;
   __shared__ IterArgs<P> a;
   using A = typename P::A;

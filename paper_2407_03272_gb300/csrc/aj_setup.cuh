@@ -142,13 +142,16 @@ __global__ void k_deinterleave(int n, int nrhs, const double* il, double* cm) {
 
 // FP64 residual r = b - Q x for interleaved multi-RHS vectors; per-block
 // partial sums of r_r^2 and (optionally) <x, Qx>, <b, x> go to part[block][nrhs][3].
+// Rows longer than long_len are left to k_residual_long (a warp per row) and
+// contribute nothing here; long_len < 0 keeps every row.
 __global__ void k_residual(int n, int nrhs, const int* rp, const int* ci, const double* val,
-                           const double* b, const double* x, double* r_out, double* part) {
+                           const double* b, const double* x, double* r_out, double* part,
+                           int long_len) {
   __shared__ double sm[kMaxRhs * 3][kSetupThreads / 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[kMaxRhs * 3];
   for (int k = 0; k < kMaxRhs * 3; k++) acc[k] = 0.0;
-  if (i < n) {
+  if (i < n && (long_len < 0 || rp[i + 1] - rp[i] <= long_len)) {
     double s[kMaxRhs] = {0.0, 0.0, 0.0, 0.0};
     for (int q = rp[i]; q < rp[i + 1]; q++) {
       const double v = val[q];
@@ -265,6 +268,56 @@ __global__ void k_axpy_masked(long long m, int nrhs, unsigned mask, const double
                               double* x) {
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < m && ((mask >> (e % nrhs)) & 1u)) x[e] += c * d[e];
+}
+
+// Longest row of the matrix (atomicMax into *out, which starts at 0).
+__global__ void k_max_row_len(int n, const int* rp, int* out) {
+  int m = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = max(m, rp[i + 1] - rp[i]);
+  for (int k = 16; k >= 1; k >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, k));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
+}
+
+// The long rows of the FP64 residual: one warp per row (lanes stride over the
+// entries, a fixed xor tree), eight rows per block, block partials of the same
+// three sums as k_residual in part[block][nrhs][3].
+__global__ void k_residual_long(int nlong, const int* rows, int nrhs, const int* rp, const int* ci,
+                                const double* val, const double* b, const double* x, double* r_out,
+                                double* part) {
+  __shared__ double sm[kMaxRhs * 3][kSetupThreads / 32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (kSetupThreads / 32) + w;
+  double acc[kMaxRhs * 3];
+  for (int k = 0; k < kMaxRhs * 3; k++) acc[k] = 0.0;
+  if (j < nlong) {
+    const int i = rows[j];
+    double s[kMaxRhs] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+      const double v = val[q];
+      const long long c = ci[q];
+      for (int r = 0; r < nrhs; r++) s[r] = fma(v, x[c * nrhs + r], s[r]);
+    }
+    for (int r = 0; r < nrhs; r++)
+      for (int m = 16; m >= 1; m >>= 1) s[r] += __shfl_xor_sync(0xffffffffu, s[r], m);
+    if (lane == 0)
+      for (int r = 0; r < nrhs; r++) {
+        const long long e = (long long)i * nrhs + r;
+        const double res = b[e] - s[r];
+        if (r_out) r_out[e] = res;
+        acc[r * 3 + 0] = res * res;
+        acc[r * 3 + 1] = x[e] * s[r];
+        acc[r * 3 + 2] = b[e] * x[e];
+      }
+  }
+  if (lane == 0)
+    for (int k = 0; k < nrhs * 3; k++) sm[k][w] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < nrhs * 3) {
+    double v = 0.0;
+    for (int k = 0; k < kSetupThreads / 32; k++) v += sm[threadIdx.x][k];
+    part[(size_t)blockIdx.x * nrhs * 3 + threadIdx.x] = v;
+  }
 }
 
 // Locality ordering.  New row i is old row perm[i]: its entries keep their
