@@ -39,23 +39,25 @@ FALLBACK_HBM_GBS = 6800.0
 FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
 
 
-def algorithmic_bytes(n, nnz, precision, form="stored"):
-    """Bytes one fused iteration must move: the matrix once (values + int32
-    column indices), row pointers, and the n-vectors of the sweep form.
-    lazy: read x^t, x^{t-1} (both gathered, each counted once), b, J^{-1};
-    write x^{t+1} (5 vectors).  stored: the same plus read u^{t-1} = Q x^{t-1}
-    and write u^t = Q x^t (7 vectors)."""
+def algorithmic_bytes(n, nnz, precision, form="min"):
+    """Bytes one fused iteration must move, per right-hand side: the matrix once
+    (values + int32 column indices), the row pointers, and 5 n-vectors -- read
+    x^t and x^{t-1} (gathered, each counted once), b and J^{-1}, write x^{t+1}.
+    That is the method's minimum (the lazy form moves exactly this); form =
+    "stored" adds the two n-vectors that form also moves (read Q x^{t-1},
+    write Q x^t), form = "delta" one more (write x^t - x^{t-1}; it reads that
+    difference in place of x^{t-1}), for the traffic comparison only."""
     vb = {"fp64": 8, "df64": 8, "fp32_ir": 4, "bf16_ir": 2}[precision]
     sb = {"fp64": 8, "df64": 8, "fp32_ir": 4, "bf16_ir": 4}[precision]
-    kvec = 7 if form == "stored" else 5
+    kvec = {"stored": 7, "delta": 8}.get(form, 5)
     return nnz * (vb + 4) + 4 * (n + 1) + n * kvec * sb
 
 
-# DRAM bytes (read + written) per fused sweep over the algorithmic bytes of the
-# same sweep, from the ncu capture of this kernel on the 128^3 Poisson system
-# (50 iterations, 51 sweeps per launch): FP64 15.968 GB / 51 / 300.8 MB, FP32
-# values 9.382 GB / 51 / 183.8 MB.  The bench scales it to a full launch by the
-# sweeps it runs; traffic grows in proportion to the rows swept.
+# DRAM bytes (read + written) per fused sweep over the bytes the stored sweep
+# form moves in that sweep, from the ncu capture of this kernel on the 128^3
+# Poisson system (50 iterations, 51 sweeps per launch): FP64 15.968 GB / 51 /
+# 300.8 MB, FP32 values 9.382 GB / 51 / 183.8 MB.  The bench scales it to a
+# full launch by the sweeps it runs; traffic grows in proportion to the rows.
 TRAFFIC_PER_ALGORITHMIC = {"fp64": 15.967641e9 / 51 / 300810244.0,
                            "fp32_ir": 9.382468e9 / 51 / 183762948.0}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 128^3 capture, "
@@ -65,9 +67,12 @@ TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 128^3
 def fp64_ops(n, nnz, form="stored"):
     """FP64 instructions of one FP64 fused iteration (an FMA counts once):
     stored form, one FMA per stored entry and 9 per row (g0, rr, two
-    differences, g, y, x update, x difference, d); lazy form, two FMA per
-    stored entry and 11 per row (qy, y, g, x update, differences, d, rr,
-    ||g||^2)."""
+    differences, g, y, x update, x difference, d); difference form, the same
+    less the x difference that y no longer needs (8 per row); lazy form, two
+    FMA per stored entry and 11 per row (qy, y, g, x update, differences, d,
+    rr, ||g||^2)."""
+    if form == "delta":
+        return nnz + 8 * n
     return (nnz + 9 * n) if form == "stored" else (2 * nnz + 11 * n)
 
 
@@ -366,7 +371,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32_ir", "bf16_ir"])
-    ap.add_argument("--form", default="auto", choices=["auto", "lazy", "stored"],
+    ap.add_argument("--form", default="auto", choices=["auto", "lazy", "stored", "delta"],
                     help="sweep form; auto = stored for fp64, lazy otherwise (the library's AUTO)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -409,12 +414,13 @@ def main():
     stream = torch.cuda.current_stream()
 
     def form_of(precision, form):
-        # the library's AUTO choice on this (CSR) workload: stored for FP64, lazy otherwise
+        # the library's AUTO choice on this (CSR) workload: the difference form
+        # for FP64, lazy otherwise
         if form == "auto":
-            return "stored" if precision == "fp64" else "lazy"
+            return "delta" if precision == "fp64" else "lazy"
         return form
 
-    SWEEP = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED}
+    SWEEP = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED, "delta": aj.AJ_SWEEP_DELTA}
 
     def make(precision, form):
         ctx = aj.Context(*tensors, n=n)
@@ -455,7 +461,7 @@ def main():
     ctx = make(args.precision, form)
     with Clocks(dev.index) as clk:
         ms, infos, launches = time_solves(ctx, args.steps, args.warmup)
-    B = algorithmic_bytes(n, nnz, args.precision, form)
+    B = algorithmic_bytes(n, nnz, args.precision)
     iters = sum(i["iters"] for i in infos)
     ms, _, value = job_throughput(ms, B * iters, dist, dev)
     kernel_ms = sum(i["kernel_ms"] for i in infos)
@@ -475,16 +481,17 @@ def main():
         roof = {"bound": "hbm", "achieved": kern_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": kern_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind + " (burst copy)"}
     ratio = TRAFFIC_PER_ALGORITHMIC.get(args.precision) if form == "stored" else None
+    B_form = algorithmic_bytes(n, nnz, args.precision, form)
     if ratio is not None:
         # per launch of the fused kernel: one per solve in FP64, one per inner solve otherwise
         per_launch_sweeps = sweeps / max(1, len(infos) * max(1, infos[-1]["outer"]))
-        roof["traffic"] = ratio * B * per_launch_sweeps
-        roof["traffic_per_algorithmic"] = ratio
+        roof["traffic"] = ratio * B_form * per_launch_sweeps
+        roof["traffic_per_form_bytes"] = ratio
         roof["traffic_source"] = TRAFFIC_SOURCE
-    roof["kernel"] = "aj_persistent_kernel<%s, 1, %s>" % (
-        {"fp64": "PolF64", "df64": "PolDF64", "fp32_ir": "PolF32", "bf16_ir": "PolB16"}[args.precision],
-        "true" if form == "stored" else "false")
+    roof["kernel"] = "aj_persistent_kernel<%s, sweep form %s, CSR, 1 RHS>" % (
+        {"fp64": "PolF64", "df64": "PolDF64", "fp32_ir": "PolF32", "bf16_ir": "PolB16"}[args.precision], form)
     roof["bytes_per_iteration"] = B
+    roof["form_bytes_per_iteration"] = B_form
     roof["kernel_ms_per_iteration"] = kernel_ms / max(iters, 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -514,10 +521,10 @@ def main():
     if not args.no_variants:
         var = {}
         for p in ("fp64", "df64", "fp32_ir", "bf16_ir"):
-            for fm in ("stored", "lazy"):
+            for fm in (("delta", "stored", "lazy") if p == "fp64" else ("stored", "lazy")):
                 c = make(p, fm)
                 vms, vinf, _ = time_solves(c, 2, 1)
-                vb = algorithmic_bytes(n, nnz, p, fm)
+                vb = algorithmic_bytes(n, nnz, p)
                 it = sum(i["iters"] for i in vinf)
                 kms = sum(i["kernel_ms"] for i in vinf)
                 var[p + "/" + fm] = {

@@ -92,18 +92,25 @@ typedef struct {
 #define AJ_BF16_IR 3 /* BF16 values x FP32 arithmetic inside, FP64 refinement outside */
 
 /* How one fused sweep obtains Q y^t = Q x^{t-1} + beta (Q x^{t-1} - Q x^{t-2}).
- * Both give the same iterates up to rounding.  LAZY sums both products over
- * the gathered x^{t-1} and x^{t-2} (two multiply-adds per stored entry, fewer
- * bytes); STORED keeps u = Q x per row and re-reads u^{t-2} (one multiply-add
- * per stored entry, two more n-vectors of traffic).  AUTO picks STORED for
- * AJ_FP64, whose FP64 issue rate binds on GB300, and for matrices stored as
- * SELL (irregular rows, whose gathers are random: one per entry instead of
- * two); LAZY for the other precisions on CSR, where the second row sum
- * gathers from the same cached lines (measured faster on the 3-D Poisson
- * system and on 2-D grids with 4 RHS). */
+ * All give the same iterates up to rounding (STORED and DELTA bit for bit).
+ *   LAZY    sums both products over the gathered x^{t-1} and x^{t-2} (two
+ *           multiply-adds per stored entry, fewest bytes);
+ *   STORED  keeps u = Q x per row and re-reads u^{t-2} (one multiply-add per
+ *           stored entry, two more n-vectors of traffic);
+ *   DELTA   STORED that also keeps x^{t-1} - x^{t-2} per row in place of
+ *           re-reading x^{t-2}, so y = x + beta (x - x_prev) costs one
+ *           instruction instead of two (the kept difference is the one the
+ *           update computes anyway for the restart test); AJ_FP64 only, one
+ *           more n-vector written per sweep.
+ * AUTO picks DELTA for AJ_FP64, whose FP64 issue rate binds on GB300; STORED
+ * for matrices stored as SELL (irregular rows, whose gathers are random: one
+ * per entry instead of two); LAZY for the other precisions on CSR, where the
+ * second row sum gathers from the same cached lines (measured faster on the
+ * 3-D Poisson system and on 2-D grids with 4 RHS). */
 #define AJ_SWEEP_AUTO 0
 #define AJ_SWEEP_LAZY 1
 #define AJ_SWEEP_STORED 2
+#define AJ_SWEEP_DELTA 3
 
 /* Storage of Q for the fused sweep.  CSR: one row per thread.  SELL: the
  * SELL-C-sigma layout (C = 32, rows sorted by length within windows of sigma
@@ -149,7 +156,7 @@ typedef struct {
   double inner_tol;      /* IR modes: relative tolerance of each inner solve (default 1e-4) */
   int64_t max_outer;     /* IR modes: outer refinement steps (default 30) */
   int grid_ctas;         /* 0 = automatic; otherwise the number of persistent CTAs */
-  int sweep_form;        /* AJ_SWEEP_AUTO (default) | AJ_SWEEP_LAZY | AJ_SWEEP_STORED */
+  int sweep_form;        /* AJ_SWEEP_AUTO (default) | AJ_SWEEP_LAZY | AJ_SWEEP_STORED | AJ_SWEEP_DELTA */
   int sell_sigma;        /* AJ_FMT_SELL: sorting window sigma in rows (0 = 256) */
   int sell_lmax;         /* AJ_FMT_SELL: rows longer than this go to the warp-per-row bucket (0 = 64) */
   int reorder;           /* AJ_REORDER_AUTO (default) | AJ_REORDER_NONE | AJ_REORDER_RCM */
@@ -301,7 +308,9 @@ const char* aj_strerror(aj_status s);
  *   Q       CSR on the current device (Q->on_device must be 1); read only.
  *   b       n device doubles; read only.
  *   p       parameters as for aj_set; precision must be AJ_FP64 (the sweep
- *           form is always AJ_SWEEP_STORED, what AUTO picks for FP64), and
+ *           form is always AJ_SWEEP_STORED, which computes the same iterates
+ *           bit for bit as the AJ_SWEEP_DELTA form AUTO picks for FP64;
+ *           p->reorder is ignored: rows keep the caller's order), and
  *           AJ_J_SCALED_DIAG needs p->L > 0 (no power-iteration estimate);
  *           p->x0, if given, must be a device pointer (x0_on_device = 1).
  *   x_out   n device doubles; receives the returned iterate x^t.

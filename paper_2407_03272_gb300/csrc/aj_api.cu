@@ -208,7 +208,8 @@ struct aj_ctx {
   void* bp = nullptr;
   void* jinvp = nullptr;
   void* x[3] = {nullptr, nullptr, nullptr};
-  void* u[2] = {nullptr, nullptr};  // Q x^t, Q x^{t-1} (stored sweep form)
+  void* u[2] = {nullptr, nullptr};  // Q x^t, Q x^{t-1} (stored sweep forms)
+  void* dl = nullptr;               // x^t - x^{t-1} (difference sweep form)
   // SELL-C-sigma copy of Q (fmt = 1), rebuilt by aj_set
   Workspace sws;
   int fmt = 0, sell_sigma = 0, sell_lmax = 0;
@@ -774,7 +775,8 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   if (p->precision < AJ_FP64 || p->precision > AJ_BF16_IR) return AJ_EINVAL;
   if (p->format < AJ_FMT_AUTO || p->format > AJ_FMT_SELL) return AJ_EINVAL;
   if (p->grid_ctas < 0) return AJ_EINVAL;
-  if (p->sweep_form < AJ_SWEEP_AUTO || p->sweep_form > AJ_SWEEP_STORED) return AJ_EINVAL;
+  if (p->sweep_form < AJ_SWEEP_AUTO || p->sweep_form > AJ_SWEEP_DELTA) return AJ_EINVAL;
+  if (p->sweep_form == AJ_SWEEP_DELTA && p->precision != AJ_FP64) return AJ_EINVAL;
   if (p->sell_sigma < 0 || p->sell_lmax < 0) return AJ_EINVAL;
   if (p->reorder < AJ_REORDER_AUTO || p->reorder > AJ_REORDER_RCM) return AJ_EINVAL;
   if ((p->precision == AJ_FP32_IR || p->precision == AJ_BF16_IR) &&
@@ -819,6 +821,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     c->valp = c->bp = c->jinvp = nullptr;
     c->x[0] = c->x[1] = c->x[2] = nullptr;
     c->u[0] = c->u[1] = nullptr;
+    c->dl = nullptr;
     c->partials = nullptr;
     c->bar = nullptr;
     c->state = nullptr;
@@ -839,12 +842,15 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
       c->u[k] = c->pws.alloc((size_t)(m + 1) * xe);
       if (!c->u[k]) return AJ_ENOMEM;
     }
+    c->dl = c->pws.alloc((size_t)(m + 1) * xe);
+    if (!c->dl) return AJ_ENOMEM;
     c->x64 = (double*)c->pws.alloc((size_t)(m + 1) * 8);
     c->r64 = (double*)c->pws.alloc((size_t)(m + 1) * 8);
     if (!c->x64 || !c->r64) return AJ_ENOMEM;
     const int kp = kernel_pol(pol);
     const int bps = std::max({1, persistent_blocks_per_sm(kp, nrhs, 0),
-                              persistent_blocks_per_sm(kp, nrhs, 1)});
+                              persistent_blocks_per_sm(kp, nrhs, 1),
+                              persistent_blocks_per_sm(kp, nrhs, 2)});
     const int maxg = bps * c->sm_count;
     c->partials = (double*)c->pws.alloc((size_t)2 * maxg * nrhs * kNRed * 8);
     c->part_cap = maxg;
@@ -855,9 +861,13 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     c->pol = pol;
   }
   // --- sweep form and grid: a multiple of the SM count when the problem is large enough
-  // AUTO: the stored form while the format is chosen; after it, the lazy form
-  // for the other precisions on CSR (see the end of aj_set)
-  c->qx = p->sweep_form == AJ_SWEEP_LAZY ? 0 : 1;
+  // AUTO: the difference form for FP64; for the other precisions the stored
+  // form while the format is chosen, then the lazy form on CSR (see the end
+  // of aj_set)
+  c->qx = p->sweep_form == AJ_SWEEP_LAZY     ? 0
+          : p->sweep_form == AJ_SWEEP_STORED ? 1
+          : p->sweep_form == AJ_SWEEP_DELTA  ? 2
+          : (p->precision == AJ_FP64 ? 2 : 1);
   {
     const int kp = kernel_pol(pol);
     const int bps = std::max(1, persistent_blocks_per_sm(kp, nrhs, c->qx));
@@ -917,10 +927,11 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   CK(cudaStreamSynchronize(s));
   aj_status fe = choose_format(c, p);
   if (fe != AJ_OK) return fe;
-  // AUTO sweep form: stored for FP64 (one FMA per entry; FP64 issue binds)
-  // and for SELL (irregular rows: one random gather per entry instead of
-  // two); lazy for the other precisions on CSR, where the second row sum
-  // gathers from the same cached lines and saves two n-vectors of traffic
+  // AUTO sweep form: the difference form for FP64 (one FMA per entry and one
+  // FP64 instruction less per row: FP64 issue binds), stored for SELL
+  // (irregular rows: one random gather per entry instead of two), lazy for
+  // the other precisions on CSR, where the second row sum gathers from the
+  // same cached lines and saves two n-vectors of traffic
   if (p->sweep_form == AJ_SWEEP_AUTO && p->precision != AJ_FP64 && c->fmt == 0) {
     c->qx = 0;
     const int bps = std::max(1, persistent_blocks_per_sm(kernel_pol(pol), nrhs, c->qx));
@@ -1032,6 +1043,7 @@ static IterLaunch make_launch(aj_ctx* c, const void* bvec, long long maxit, int 
   L.jinv = c->pol == AJ_FP64 ? (const void*)c->jinv64 : c->jinvp;
   for (int k = 0; k < 3; k++) L.x[k] = c->x[k];
   for (int k = 0; k < 2; k++) L.u[k] = c->u[k];
+  L.dl = c->dl;
   L.qx = c->qx;
   L.partials = c->partials;
   L.bar = c->bar;
@@ -2031,7 +2043,7 @@ extern "C" aj_status aj_get_state(aj_ctx* c, void* buf, size_t* size) {
   if (c->pol != AJ_FP64 && c->pol != AJ_DF64) return AJ_EINVAL;
   if ((int)c->st_h.size() != c->nrhs) return AJ_EINVAL;  // no finished solve yet
   const size_t vb = (size_t)c->n * c->nrhs * xelem_bytes(c->pol);
-  const size_t need = sizeof(StateHeader) + sizeof(RhsState) * c->nrhs + 5 * vb;
+  const size_t need = sizeof(StateHeader) + sizeof(RhsState) * c->nrhs + 6 * vb;
   if (!buf) { *size = need; return AJ_OK; }
   if (*size < need) { *size = need; return AJ_EINVAL; }
   char* p = (char*)buf;
@@ -2048,8 +2060,8 @@ extern "C" aj_status aj_get_state(aj_ctx* c, void* buf, size_t* size) {
   p += sizeof(h);
   std::memcpy(p, c->st_h.data(), sizeof(RhsState) * c->nrhs);
   p += sizeof(RhsState) * c->nrhs;
-  for (int k = 0; k < 5; k++) {
-    void* src = k < 3 ? c->x[k] : c->u[k - 3];
+  for (int k = 0; k < 6; k++) {
+    void* src = k < 3 ? c->x[k] : k < 5 ? c->u[k - 3] : c->dl;
     if (vb) CK(cudaMemcpyAsync(p, src, vb, cudaMemcpyDeviceToHost, c->stream));
     p += vb;
   }
@@ -2065,7 +2077,7 @@ extern "C" aj_status aj_set_state(aj_ctx* c, const void* buf, size_t size) {
   StateHeader h;
   std::memcpy(&h, buf, sizeof(h));
   const size_t vb = (size_t)c->n * c->nrhs * xelem_bytes(c->pol);
-  const size_t need = sizeof(StateHeader) + sizeof(RhsState) * c->nrhs + 5 * vb;
+  const size_t need = sizeof(StateHeader) + sizeof(RhsState) * c->nrhs + 6 * vb;
   if (h.magic != kStateMagic || h.n != c->n || h.nrhs != c->nrhs || h.pol != c->pol ||
       h.state_bytes != (int)sizeof(RhsState) || h.pad != (c->qx | (c->ordered << 8)) || size < need)
     return AJ_EINVAL;
@@ -2073,8 +2085,8 @@ extern "C" aj_status aj_set_state(aj_ctx* c, const void* buf, size_t size) {
   c->st_h.resize(c->nrhs);
   std::memcpy(c->st_h.data(), p, sizeof(RhsState) * c->nrhs);
   p += sizeof(RhsState) * c->nrhs;
-  for (int k = 0; k < 5; k++) {
-    void* dst = k < 3 ? c->x[k] : c->u[k - 3];
+  for (int k = 0; k < 6; k++) {
+    void* dst = k < 3 ? c->x[k] : k < 5 ? c->u[k - 3] : c->dl;
     if (vb) CK(cudaMemcpyAsync(dst, p, vb, cudaMemcpyHostToDevice, c->stream));
     p += vb;
   }

@@ -395,6 +395,7 @@ struct IterArgs {
   const typename P::X* jinv;  // [n]
   typename P::X* x[3];        // three iterate buffers, [n * nrhs] each
   typename P::X* u[2];        // stored form: Q x^t and Q x^{t-1}, [n * nrhs] each
+  typename P::X* dl;          // difference form: x^t - x^{t-1}, [n * nrhs], own rows only
   double* partials;           // [2][gridDim][nrhs][kNRed]
   unsigned long long* bar;    // barrier arrival counter, zero at launch
   int* err;                   // device error word, zero at launch
@@ -582,13 +583,19 @@ __host__ __device__ constexpr int row_unroll(bool qx) {
 // ANY: the kernel handles both formats (runtime a.fmt); otherwise CSR only,
 // which keeps the SELL code and its registers out of the CSR kernel.  MULTI:
 // nrhs and the lanes per row come from the arguments; otherwise one.
-template <class P, bool QX, bool ANY, bool MULTI>
+// SF: sweep form -- 0 lazy, 1 stored, 2 stored with the difference
+// delta = x^{s-1} - x^{s-2} kept in a.dl (y = x + beta delta costs one
+// instruction instead of two; delta is the same rounded difference the
+// update computes anyway for the restart test).
+template <class P, int SF, bool ANY, bool MULTI>
 __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, bool compute_x,
                                       bool want_obj, typename P::A (&acc)[kNRed], int cta,
                                       int ncta) {
   using S = typename P::S;
   using V = typename P::V;
   using X = typename P::X;
+  constexpr bool QX = SF != 0;
+  constexpr bool DL = SF == 2;
   const int nr = MULTI ? a.nrhs : 1;
   const int lg = MULTI ? a.lgr : 0;
   const int r = threadIdx.x & ((1 << lg) - 1);   // this lane's right-hand side
@@ -731,14 +738,20 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       g = g0;
       yi = xi;
     } else {
-      const S xpi = P::ldx(xp + e);
       const S spi = QX ? P::ldx(up + e) : sp;
       g = P::fma_(beta, P::sub(sx, spi), g0);
-      yi = P::fma_(beta, P::sub(xi, xpi), xi);
+      if (DL) {
+        yi = P::fma_(beta, P::ldx(a.dl + e), xi);
+      } else {
+        const S xpi = P::ldx(xp + e);
+        yi = P::fma_(beta, P::sub(xi, xpi), xi);
+      }
     }
     const S xnew = P::fnma(ji, g, yi);
+    const S dx = P::sub(xnew, xi);
     P::stx(xn + e, xnew);
-    P::acc_prod(acc[0], g, P::sub(xnew, xi));
+    if (DL) P::stx(a.dl + e, dx);
+    P::acc_prod(acc[0], g, dx);
   }
 }
 
@@ -873,7 +886,7 @@ __device__ __forceinline__ void grid_totals(const double* part, int ncta, int nr
 // arrival count so far and `sw` the sweep counter that parity-buffers the
 // partials; both carry over between systems that reuse the same barrier.
 // Returns false when a barrier gave up (error already recorded in *a.err).
-template <class P, bool QX, bool ANY, bool MULTI>
+template <class P, int SF, bool ANY, bool MULTI>
 __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, int cta, int ncta,
                                           unsigned long long& target, long long& sw) {
   using A = typename P::A;
@@ -893,7 +906,7 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, i
     A acc[kNRed];
 #pragma unroll
     for (int k = 0; k < kNRed; k++) acc_zero(acc[k]);
-    sweep<P, QX, ANY, MULTI>(a, sm.st, compute_x, want_obj, acc, cta, ncta);
+    sweep<P, SF, ANY, MULTI>(a, sm.st, compute_x, want_obj, acc, cta, ncta);
     // CTA partials -> global (parity-buffered by sweep)
     double* part = a.partials + (size_t)(sw & 1) * ncta * nr * kNRed;
 #pragma unroll
@@ -934,7 +947,7 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, i
 // kThreads threads per CTA; every CTA of the grid works on the system.  ANY
 // selects the instantiation that also reads the SELL-C-sigma format, MULTI
 // the one for several right-hand sides.
-template <class P, bool QX, bool ANY, bool MULTI>
+template <class P, int SF, bool ANY, bool MULTI>
 __global__ void __launch_bounds__(kThreads, MULTI ? P::kMinBlocksMulti : P::kMinBlocks) aj_persistent_kernel(IterArgs<P> a) {
   __shared__ SolveSmem sm;
   const int nr = MULTI ? a.nrhs : 1;
@@ -942,7 +955,7 @@ __global__ void __launch_bounds__(kThreads, MULTI ? P::kMinBlocksMulti : P::kMin
   __syncthreads();
   unsigned long long target = 0;
   long long sw = 0;
-  if (!run_solve<P, QX, ANY, MULTI>(a, sm, blockIdx.x, gridDim.x, target, sw)) return;
+  if (!run_solve<P, SF, ANY, MULTI>(a, sm, blockIdx.x, gridDim.x, target, sw)) return;
   if (blockIdx.x == 0 && (int)threadIdx.x < nr) a.state[threadIdx.x] = sm.st[threadIdx.x];
 }
 
@@ -1040,7 +1053,7 @@ __device__ __forceinline__ bool lock_enter(const LockArgs<P>& b, IterArgs<P>& a,
   return sm.done != 0;
 }
 
-template <class P, bool QX>
+template <class P, int SF>
 __global__ void __launch_bounds__(kThreads, P::kMinBlocksMulti) aj_lockstep_kernel(LockArgs<P> b) {
   __shared__ SolveSmem sm;
   __shared__ IterArgs<P> a;
@@ -1068,7 +1081,7 @@ __global__ void __launch_bounds__(kThreads, P::kMinBlocksMulti) aj_lockstep_kern
       A acc[kNRed];
 #pragma unroll
       for (int q = 0; q < kNRed; q++) acc_zero(acc[q]);
-      sweep<P, QX, true, true>(a, sm.st, compute_x, want_obj, acc, v, V);
+      sweep<P, SF, true, true>(a, sm.st, compute_x, want_obj, acc, v, V);
       double* part = a.partials + (size_t)(k & 1) * V * nr * kNRed;
 #pragma unroll
       for (int q = 0; q < kNRed; q++) {

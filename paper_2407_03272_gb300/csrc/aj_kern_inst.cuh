@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "aj_core.cuh"
 #include "aj_launch.h"
@@ -39,6 +40,7 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
   a.jinv = static_cast<const typename P::X*>(L.jinv);
   for (int k = 0; k < 3; k++) a.x[k] = static_cast<typename P::X*>(L.x[k]);
   for (int k = 0; k < 2; k++) a.u[k] = static_cast<typename P::X*>(L.u[k]);
+  a.dl = static_cast<typename P::X*>(L.dl);
   a.partials = L.partials;
   a.bar = L.bar;
   a.err = L.err;
@@ -58,6 +60,11 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
   return a;
 }
 
+// The difference sweep form (SF = 2) is built for FP64 only, the policy whose
+// FP64 issue rate it relieves.
+template <class P>
+constexpr bool kHasDelta = std::is_same<P, PolF64>::value;
+
 template <class P>
 static cudaError_t launch_lockstep_p(int qx, const LockLaunch& B, int grid, cudaStream_t s) {
   LockArgs<P> b;
@@ -73,24 +80,38 @@ static cudaError_t launch_lockstep_p(int qx, const LockLaunch& B, int grid, cuda
   b.bar = B.bar;
   b.err = B.err;
   void* args[] = {&b};
-  const void* k = qx ? (const void*)aj_lockstep_kernel<P, true> : (const void*)aj_lockstep_kernel<P, false>;
+  const void* k = nullptr;
+  if (qx == 0) k = (const void*)aj_lockstep_kernel<P, 0>;
+  else if (qx == 1) k = (const void*)aj_lockstep_kernel<P, 1>;
+  else if constexpr (kHasDelta<P>) k = (const void*)aj_lockstep_kernel<P, 2>;
+  if (!k) return cudaErrorInvalidValue;
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
 }
 
-template <class K>
-static int occ_of(K k) {
+static int occ_of(const void* k) {
   int nb = 0;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, 0) == cudaSuccess ? nb : 0;
+}
+
+// The persistent kernel for sweep form sf and format (CSR only or any).
+template <class P, bool MULTI>
+static const void* persistent_fn(int sf, bool any) {
+  if (sf == 0) return any ? (const void*)aj_persistent_kernel<P, 0, true, MULTI>
+                          : (const void*)aj_persistent_kernel<P, 0, false, MULTI>;
+  if (sf == 1) return any ? (const void*)aj_persistent_kernel<P, 1, true, MULTI>
+                          : (const void*)aj_persistent_kernel<P, 1, false, MULTI>;
+  if constexpr (kHasDelta<P>)
+    if (sf == 2) return any ? (const void*)aj_persistent_kernel<P, 2, true, MULTI>
+                            : (const void*)aj_persistent_kernel<P, 2, false, MULTI>;
+  return nullptr;
 }
 
 template <class P, bool MULTI>
 static cudaError_t launch_m(const IterLaunch& L, int grid, cudaStream_t s) {
   IterArgs<P> a = typed_args<P>(L);
   void* args[] = {&a};
-  const void* k = L.fmt ? (L.qx ? (const void*)aj_persistent_kernel<P, true, true, MULTI>
-                                : (const void*)aj_persistent_kernel<P, false, true, MULTI>)
-                       : (L.qx ? (const void*)aj_persistent_kernel<P, true, false, MULTI>
-                               : (const void*)aj_persistent_kernel<P, false, false, MULTI>);
+  const void* k = persistent_fn<P, MULTI>(L.qx, L.fmt != 0);
+  if (!k) return cudaErrorInvalidValue;
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
 }
 
@@ -98,10 +119,10 @@ static cudaError_t launch_m(const IterLaunch& L, int grid, cudaStream_t s) {
 // any-format instantiations, so that a grid sized by it fits either.
 template <class P, bool MULTI>
 static int occ_m(int qx) {
-  return qx ? std::min(occ_of(aj_persistent_kernel<P, true, false, MULTI>),
-                       occ_of(aj_persistent_kernel<P, true, true, MULTI>))
-            : std::min(occ_of(aj_persistent_kernel<P, false, false, MULTI>),
-                       occ_of(aj_persistent_kernel<P, false, true, MULTI>));
+  const void* k0 = persistent_fn<P, MULTI>(qx, false);
+  const void* k1 = persistent_fn<P, MULTI>(qx, true);
+  if (!k0 || !k1) return 0;
+  return std::min(occ_of(k0), occ_of(k1));
 }
 
 cudaError_t AJ_CAT(launch_persistent_, AJ_SUFFIX)(int nrhs, const IterLaunch& L, int grid,
@@ -126,7 +147,11 @@ cudaError_t AJ_CAT(launch_lockstep_, AJ_SUFFIX)(int qx, const LockLaunch& B, int
 }
 
 int AJ_CAT(lockstep_blocks_per_sm_, AJ_SUFFIX)(int qx) {
-  return qx ? occ_of(aj_lockstep_kernel<AJ_POL, true>) : occ_of(aj_lockstep_kernel<AJ_POL, false>);
+  if (qx == 0) return occ_of((const void*)aj_lockstep_kernel<AJ_POL, 0>);
+  if (qx == 1) return occ_of((const void*)aj_lockstep_kernel<AJ_POL, 1>);
+  if constexpr (kHasDelta<AJ_POL>)
+    if (qx == 2) return occ_of((const void*)aj_lockstep_kernel<AJ_POL, 2>);
+  return 0;
 }
 
 }  // namespace aj

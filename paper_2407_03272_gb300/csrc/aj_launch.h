@@ -31,7 +31,8 @@ struct IterLaunch {
   const void* b;
   const void* jinv;
   void* x[3];
-  void* u[2];  // stored sweep form only
+  void* u[2];  // stored sweep forms only
+  void* dl;    // difference sweep form only: x^t - x^{t-1}
   double* partials;
   unsigned long long* bar;
   int* err;
@@ -48,7 +49,7 @@ struct IterLaunch {
   double fstar;
   double fscale;
   long long max_sweeps;
-  int qx;  // 1: stored sweep form (u = Q x kept), 0: lazy form (two row sums)
+  int qx;  // sweep form: 0 lazy (two row sums), 1 stored (u = Q x kept), 2 stored + difference
 };
 
 // Untyped mirror of LockArgs<P>: many systems in lockstep in one launch.

@@ -43,7 +43,7 @@ def _oracle_J(Q, j_policy, L=None):
     return oracle.j_scaled_diag(Q, L)
 
 
-FORMS = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED}
+FORMS = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED, "delta": aj.AJ_SWEEP_DELTA}
 
 
 def _compare_fixed(Q, b, T, precision="fp64", restart=True, momentum=True, j_policy=0, L=0.0,
@@ -66,11 +66,37 @@ def _compare_fixed(Q, b, T, precision="fp64", restart=True, momentum=True, j_pol
 
 
 # ---------------------------------------------------------------- fixed-iteration parity
-@pytest.mark.parametrize("form", ["lazy", "stored"])
+@pytest.mark.parametrize("form", ["lazy", "stored", "delta"])
 @pytest.mark.parametrize("precision", ["fp64", "df64"])
 def test_poisson64_200_iterations_match_oracle(precision, form):
+    if form == "delta" and precision != "fp64":
+        pytest.skip("the difference form is built for FP64 only")
     Q, b, xs = synth.workload("poisson2d_64")
     _compare_fixed(Q, b, 200, precision=precision, form=form)
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_difference_form_equals_stored_form_bitwise(nrhs):
+    """x + beta*delta with delta kept from the previous sweep is the same
+    rounded operation as x + beta*(x - x_prev): identical iterates."""
+    Q = synth.chung_lu_laplacian(5000, seed=81, mean_degree=10.0)  # long rows too
+    B = np.stack([synth.rhs(Q, synth.uniform(Q["n"], 60 + r)) for r in range(nrhs)], axis=1)
+    bc = np.ascontiguousarray(B.T).reshape(-1)
+    out = {}
+    for form in ("stored", "delta"):
+        ctx = aj.from_csr(Q, bc, nrhs=nrhs)
+        ctx.set(tol=1e-10, maxit=20000, sweep_form=FORMS[form], grid_ctas=16)
+        x, info = ctx.solve(per_rhs=True)
+        out[form] = (x, [i["iters"] for i in info])
+    np.testing.assert_array_equal(out["stored"][0], out["delta"][0])
+    assert out["stored"][1] == out["delta"][1]
+
+
+def test_difference_form_is_fp64_only():
+    Q, b, xs = synth.workload("poisson2d_64")
+    ctx = aj.from_csr(Q, b)
+    with pytest.raises(aj.AJError):
+        ctx.set(precision="fp32_ir", sweep_form=aj.AJ_SWEEP_DELTA)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "df64", "fp32_ir", "bf16_ir"])
@@ -80,12 +106,16 @@ def test_lazy_and_stored_forms_agree(precision):
     T = 150
     xs_ = {}
     for form in FORMS:
+        if form == "delta" and precision != "fp64":
+            continue  # built for FP64 only
         ctx, x, info = _gpu(Q, b, precision=precision, stop=aj.AJ_STOP_NONE, maxit=T,
                             sweep_form=FORMS[form], restart=0)
         assert info["iters"] == T
         xs_[form] = x
     tol = 1e-12 if precision in ("fp64", "df64") else 1e-4
     assert np.linalg.norm(xs_["lazy"] - xs_["stored"]) <= tol * np.linalg.norm(xs_["lazy"])
+    if "delta" in xs_:
+        np.testing.assert_array_equal(xs_["delta"], xs_["stored"])
 
 
 @pytest.mark.parametrize("precision", ["fp64", "df64"])
@@ -245,7 +275,7 @@ def test_multi_rhs_200_iterations_match_oracle(nrhs, case):
 
 
 # ---------------------------------------------------------------- checkpoint / resume
-@pytest.mark.parametrize("form", ["lazy", "stored"])
+@pytest.mark.parametrize("form", ["lazy", "stored", "delta"])
 def test_resume_is_bit_identical(form):
     Q, b, xs = synth.workload("poisson2d_48")
     full = aj.from_csr(Q, b)
