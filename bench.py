@@ -53,13 +53,15 @@ def algorithmic_bytes(n, nnz, precision, form="min"):
     return nnz * (vb + 4) + 4 * (n + 1) + n * kvec * sb
 
 
-# DRAM bytes (read + written) per fused sweep over the bytes the stored sweep
-# form moves in that sweep, from the ncu capture of this kernel on the 128^3
-# Poisson system (50 iterations, 51 sweeps per launch): FP64 15.968 GB / 51 /
-# 300.8 MB, FP32 values 9.382 GB / 51 / 183.8 MB.  The bench scales it to a
-# full launch by the sweeps it runs; traffic grows in proportion to the rows.
-TRAFFIC_PER_ALGORITHMIC = {"fp64": 15.967641e9 / 51 / 300810244.0,
-                           "fp32_ir": 9.382468e9 / 51 / 183762948.0}
+# DRAM bytes (read + written) per fused sweep over the bytes the sweep form
+# moves in that sweep, from the ncu captures of the kernel on the 128^3
+# Poisson system (50 iterations, 51 sweeps per launch): FP64 difference form
+# 16.706 GB / 51 / 317.6 MB, FP64 stored 15.968 GB / 51 / 300.8 MB, FP32
+# values stored 9.382 GB / 51 / 183.8 MB.  The bench scales it to a full
+# launch by the sweeps it runs; traffic grows in proportion to the rows.
+TRAFFIC_PER_FORM_BYTES = {("fp64", "delta"): 16.706409e9 / 51 / 317587460.0,
+                          ("fp64", "stored"): 15.967641e9 / 51 / 300810244.0,
+                          ("fp32_ir", "stored"): 9.382468e9 / 51 / 183762948.0}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 128^3 capture, "
                   "scaled by rows and sweeps to one launch of this workload")
 
@@ -480,7 +482,7 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": kern_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": kern_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind + " (burst copy)"}
-    ratio = TRAFFIC_PER_ALGORITHMIC.get(args.precision) if form == "stored" else None
+    ratio = TRAFFIC_PER_FORM_BYTES.get((args.precision, form))
     B_form = algorithmic_bytes(n, nnz, args.precision, form)
     if ratio is not None:
         # per launch of the fused kernel: one per solve in FP64, one per inner solve otherwise
