@@ -2213,7 +2213,11 @@ struct aj_server {
   size_t budget = 0;
   int max_slots = 1;
   int dev = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;      // rounds
+  cudaStream_t adm_stream = nullptr;  // admission: context creation and set-up
+  std::thread adm_th;
+  std::deque<ServerReq*> ready;       // started by the admission thread, waiting for a round
+  int preparing = 0;                  // being started by the admission thread
   long long round_sweeps = 32;
   LockWs lws;  // lockstep launch buffers, kept for the server's lifetime
   std::mutex mu;
@@ -2256,7 +2260,7 @@ static void server_complete(aj_server* s, ServerReq* r, aj_status st, const aj_i
   dn.m = dn.x ? m : 0;
   if (r->c) {
     if (r->owned) aj_destroy(r->c);
-    else r->c->stream = r->user_stream;
+    else aj_set_stream(r->c, r->user_stream);
   }
   std::lock_guard<std::mutex> lk(s->mu);
   s->in_use -= std::min(s->in_use, r->bytes);
@@ -2267,8 +2271,9 @@ static void server_complete(aj_server* s, ServerReq* r, aj_status st, const aj_i
   s->cv.notify_all();
 }
 
-// Admission: create the context if the server owns it and start its run.
-static aj_status server_start(aj_server* s, ServerReq* r) {
+// Admission, on the admission thread: create the context if the server owns
+// it and start its run, all on stream st; the round thread takes it over.
+static aj_status server_start(aj_server* s, ServerReq* r, cudaStream_t st) {
   if (r->owned) {
     aj_csr Q;
     Q.n = r->n;
@@ -2279,7 +2284,8 @@ static aj_status server_start(aj_server* s, ServerReq* r) {
     Q.on_device = 0;
     aj_status e = aj_create(&Q, r->b.data(), r->nrhs, &r->c);
     if (e != AJ_OK) return e;
-    aj_set_stream(r->c, s->stream);
+    e = aj_set_stream(r->c, st);
+    if (e != AJ_OK) return e;
     aj_params p = r->prm;
     p.x0 = r->x0.empty() ? nullptr : r->x0.data();
     p.x0_on_device = 0;
@@ -2291,7 +2297,8 @@ static aj_status server_start(aj_server* s, ServerReq* r) {
     r->bytes = actual;
   } else {
     r->user_stream = r->c->stream;
-    r->c->stream = s->stream;
+    aj_status e = aj_set_stream(r->c, st);
+    if (e != AJ_OK) return e;
     if (!r->c->have_prm) {
       aj_params p;
       aj_params_default(&p);
@@ -2302,7 +2309,7 @@ static aj_status server_start(aj_server* s, ServerReq* r) {
   aj_ctx* c = r->c;
   c->resume = false;
   c->kernel_ms = 0.0;
-  CK(cudaMemsetAsync(c->rlog, 0xff, (size_t)kMaxRhs * c->rlog_cap * 8, s->stream));
+  CK(cudaMemsetAsync(c->rlog, 0xff, (size_t)kMaxRhs * c->rlog_cap * 8, st));
   r->ir = !(c->pol == AJ_FP64 || c->pol == AJ_DF64);
   if (!r->ir) {
     aj_status e = direct_prepare(c, r->d);
@@ -2316,7 +2323,8 @@ static aj_status server_start(aj_server* s, ServerReq* r) {
     if (!r->q.finished) r->item = ir_inner_setup(c, r->q);
   }
   CK(cudaGetLastError());
-  return AJ_OK;
+  // hand the context to the round stream (waits for the set-up above)
+  return aj_set_stream(c, s->stream);
 }
 
 // After a round: retire what finished, start the next inner solve of the
@@ -2359,6 +2367,51 @@ static bool server_advance(aj_server* s, ServerReq* r) {
   return true;
 }
 
+// The admission thread: takes queued requests first fit, in submission
+// order, while the device memory of admitted requests stays within the
+// budget and the slots allow, creates and starts them on its own stream
+// (host-to-device copies, set-up kernels, format and order choice), and
+// hands them to the round thread.  That work overlaps the rounds.
+static void server_admit_main(aj_server* s) {
+  cudaSetDevice(s->dev);
+  for (;;) {
+    ServerReq* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      auto pick = [&]() -> std::deque<ServerReq*>::iterator {
+        const int used = (int)(s->active.size() + s->ready.size()) + s->preparing;
+        if (used >= s->max_slots) return s->queue.end();
+        for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+          if (s->in_use + (*it)->bytes <= s->budget) return it;
+        return s->queue.end();
+      };
+      s->cv.wait(lk, [&] { return s->stop || pick() != s->queue.end(); });
+      if (s->stop) break;
+      auto it = pick();
+      r = *it;
+      s->queue.erase(it);
+      s->in_use += r->bytes;
+      s->stats.admitted++;
+      s->stats.peak_bytes = std::max<uint64_t>(s->stats.peak_bytes, s->in_use);
+      s->preparing++;
+    }
+    const aj_status e = server_start(s, r, s->adm_stream);
+    if (e != AJ_OK) {
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->preparing--;
+      }
+      server_complete(s, r, e, nullptr, nullptr, 0);
+      continue;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->preparing--;
+    s->ready.push_back(r);
+    s->cv.notify_all();
+  }
+}
+
+// The round thread: takes the started requests and runs rounds over them.
 static void server_main(aj_server* s) {
   cudaSetDevice(s->dev);
   for (;;) {
@@ -2366,25 +2419,13 @@ static void server_main(aj_server* s) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       if (s->active.empty())
-        s->cv.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+        s->cv.wait(lk, [&] { return s->stop || !s->ready.empty(); });
       if (s->stop) break;
-      for (auto it = s->queue.begin(); it != s->queue.end();) {
-        if ((int)(s->active.size() + admit.size()) >= s->max_slots) break;
-        if (s->in_use + (*it)->bytes <= s->budget) {
-          s->in_use += (*it)->bytes;
-          s->stats.admitted++;
-          s->stats.peak_bytes = std::max<uint64_t>(s->stats.peak_bytes, s->in_use);
-          admit.push_back(*it);
-          it = s->queue.erase(it);
-        } else {
-          ++it;
-        }
-      }
+      admit.assign(s->ready.begin(), s->ready.end());
+      s->ready.clear();
     }
     for (ServerReq* r : admit) {
-      aj_status e = server_start(s, r);
-      if (e != AJ_OK) server_complete(s, r, e, nullptr, nullptr, 0);
-      else if (r->ir && r->q.finished) server_advance(s, r);
+      if (r->ir && r->q.finished) server_advance(s, r);
       else s->active.push_back(r);
     }
     if (s->active.empty()) continue;
@@ -2434,8 +2475,17 @@ extern "C" aj_status aj_server_create(size_t hbm_budget_bytes, int max_slots, aj
     delete s;
     return AJ_ECUDA;
   }
+  if (cudaStreamCreateWithFlags(&s->adm_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    s->adm_stream = nullptr;
+    cudaStreamDestroy(s->stream);
+    s->stream = nullptr;
+    delete s;
+    return AJ_ECUDA;
+  }
   s->lws.stream = s->stream;
   s->th = std::thread(server_main, s);
+  s->adm_th = std::thread(server_admit_main, s);
   *out = s;
   return AJ_OK;
 }
@@ -2545,12 +2595,21 @@ extern "C" void aj_server_destroy(aj_server* s) {
     s->cv.notify_all();
   }
   if (s->th.joinable()) s->th.join();
+  if (s->adm_th.joinable()) s->adm_th.join();
+  // started but never run: drop them (owned contexts destroyed, others get their stream back)
+  std::vector<ServerReq*> left(s->ready.begin(), s->ready.end());
+  s->ready.clear();
+  for (ServerReq* r : left) server_complete(s, r, AJ_ECUDA, nullptr, nullptr, 0);
   for (ServerReq* r : s->queue) delete r;
   s->queue.clear();
   if (s->stream) {
     s->lws.mem.release();
     cudaStreamSynchronize(s->stream);
     cudaStreamDestroy(s->stream);
+  }
+  if (s->adm_stream) {
+    cudaStreamSynchronize(s->adm_stream);
+    cudaStreamDestroy(s->adm_stream);
   }
   delete s;
 }
