@@ -1409,12 +1409,11 @@ static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, d
   const int m_all = (int)items.size();
   std::vector<int> V(m_all, 1);
   std::vector<long long> left(m_all);
-  std::vector<unsigned char> args_all((size_t)m_all * abytes);
+  std::vector<IterLaunch> Ls(m_all);
   for (int i = 0; i < m_all; i++) {
     const BatchItem& it = items[i];
     left[i] = it.max_sweeps;
-    IterLaunch L = make_launch(it.c, it.bvec, it.maxit, it.stop, it.tol, it.fstar, it.fscale);
-    pack_iter_args(pol, L, args_all.data() + (size_t)i * abytes);
+    Ls[i] = make_launch(it.c, it.bvec, it.maxit, it.stop, it.tol, it.fstar, it.fscale);
     if (log_restarts) CK(cudaMemsetAsync(it.c->rlog, 0xff, (size_t)kMaxRhs * it.c->rlog_cap * 8, s));
   }
   auto running = [&](int i) {
@@ -1433,8 +1432,11 @@ static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, d
     for (int i = 0; i < m_all; i++)
       if (running(i)) act.push_back(i);
     if (act.empty()) break;
-    long long sweeps = chunk;
-    for (int i : act) sweeps = std::min(sweeps, left[i]);
+    // the launch runs as many sweeps as the item with the most left may use
+    // (at most the chunk); each item runs at most what it has left
+    long long most = 0;
+    for (int i : act) most = std::max(most, left[i]);
+    const long long sweeps = std::min(chunk, most);
     const int m = (int)act.size();
     long long active_tiles = 0;
     for (int i : act) active_tiles += ctx_tiles(items[i].c);
@@ -1457,12 +1459,14 @@ static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, d
       const long long rpt = kThreads >> lanes_log2(c->nrhs);
       const long long ntiles = ctx_tiles(c);
       const double per_tile = (double)rpt * c->nrhs * ((double)c->nnz / std::max<int64_t>(c->n, 1) + 9.0);
+      const long long mine = std::min(left[i], sweeps);  // sweeps this item runs in the launch
       for (int v = 0; v < V[i]; v++) {
         unit.push_back(j);
         const long long tv = v < ntiles ? (ntiles - 1 - v) / V[i] + 1 : 0;
-        ucost.push_back(per_tile * (double)(tv + 1));
+        ucost.push_back(per_tile * (double)(tv + 1) * (double)mine / (double)sweeps);
       }
-      std::memcpy(sysh.data() + (size_t)j * abytes, args_all.data() + (size_t)i * abytes, abytes);
+      Ls[i].max_sweeps = mine;
+      pack_iter_args(pol, Ls[i], sysh.data() + (size_t)j * abytes);
       for (int r = 0; r < items[i].c->nrhs; r++) st2[(size_t)j * 2 * kMaxRhs + r] = (*items[i].st)[r];
     }
     // contiguous unit ranges of about equal estimated work, one per CTA
@@ -1517,7 +1521,7 @@ static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, d
     for (int j = 0; j < m; j++) {
       const int i = act[j];
       for (int r = 0; r < items[i].c->nrhs; r++) (*items[i].st)[r] = out[(size_t)j * kMaxRhs + r];
-      left[i] -= sweeps;
+      left[i] -= std::min(left[i], sweeps);
     }
     if (kms < 5.0f && chunk < 4096) chunk *= 2;
   }

@@ -1033,9 +1033,12 @@ __device__ __forceinline__ void st_state_l2(RhsState* p, const RhsState& v) {
 }
 
 // Loads system s's arguments into shared memory and brings its state to
-// sweep k (applying the transition of sweep k-1 when k >= 1).  Returns, in
-// every thread, whether the system is done.  `store` makes this CTA the one
-// that keeps the new state in st2; `log_it` the one that records restarts.
+// sweep k (applying the transition of sweep k-1 when k >= 1).  A system runs
+// kmax = min(launch sweeps, a.max_sweeps) sweeps in this launch: at k = kmax
+// its last transition is applied and kept, and from then on it pauses (its
+// state stays in st2[kmax & 1]).  Returns, in every thread, whether the
+// system skips sweep k (done or paused).  `store` makes this CTA the one that
+// keeps the new state in st2; `log_it` the one that records restarts.
 template <class P>
 __device__ __forceinline__ bool lock_enter(const LockArgs<P>& b, IterArgs<P>& a, SolveSmem& sm, int s,
                                            long long k, bool store, bool log_it) {
@@ -1049,9 +1052,13 @@ __device__ __forceinline__ bool lock_enter(const LockArgs<P>& b, IterArgs<P>& a,
   const int nr = a.nrhs;
   const bool want_obj = a.stop == kStopObjgap;
   const int V = __ldg(b.sys_nu + s);
-  RhsState* stc = b.st2 + ((size_t)s * 2 + (k & 1)) * kMaxRhs;
-  const RhsState* stp = b.st2 + ((size_t)s * 2 + ((k - 1) & 1)) * kMaxRhs;
-  if ((int)threadIdx.x < nr) sm.st[threadIdx.x] = ld_state_l2(k == 0 ? stc + threadIdx.x : stp + threadIdx.x);
+  const long long kmax = a.max_sweeps < b.sweeps ? a.max_sweeps : b.sweeps;
+  const bool paused = k > kmax;
+  const long long kk = paused ? kmax : k;
+  RhsState* stc = b.st2 + ((size_t)s * 2 + (kk & 1)) * kMaxRhs;
+  const RhsState* stp = b.st2 + ((size_t)s * 2 + ((kk - 1) & 1)) * kMaxRhs;
+  if ((int)threadIdx.x < nr)
+    sm.st[threadIdx.x] = ld_state_l2((paused || k == 0) ? stc + threadIdx.x : stp + threadIdx.x);
   __syncthreads();
   if (threadIdx.x == 0) {
     int d = 1;
@@ -1059,7 +1066,7 @@ __device__ __forceinline__ bool lock_enter(const LockArgs<P>& b, IterArgs<P>& a,
     sm.done = d;
   }
   __syncthreads();
-  if (k > 0 && !sm.done) {
+  if (!paused && k > 0 && !sm.done) {
     long long s_run = 0;
     for (int r = 0; r < nr; r++)
       if (!sm.st[r].done) s_run = sm.st[r].t + 1;
@@ -1071,8 +1078,8 @@ __device__ __forceinline__ bool lock_enter(const LockArgs<P>& b, IterArgs<P>& a,
                     : 0;
     __syncthreads();
   }
-  if (store && k > 0 && (int)threadIdx.x < nr) st_state_l2(stc + threadIdx.x, sm.st[threadIdx.x]);
-  return sm.done != 0;
+  if (!paused && store && k > 0 && (int)threadIdx.x < nr) st_state_l2(stc + threadIdx.x, sm.st[threadIdx.x]);
+  return sm.done != 0 || k >= kmax;
 }
 
 template <class P, int SF>
