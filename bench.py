@@ -545,21 +545,29 @@ def main():
         h2d = sum(t.numel() * t.element_size() for t in host)
         d2h = xh.numel() * xh.element_size()
         walls, its = [], 0
+        phases = {"create": 0.0, "set": 0.0, "solve": 0.0, "close": 0.0}
         for k in range(1 + 2):
             barrier()
             t0 = time.perf_counter()
             c = aj.Context(*host, n=n)
             c.set_stream(stream)
+            t1 = time.perf_counter()
             c.set(precision=args.precision, tol=1e-8, maxit=200000, sweep_form=SWEEP[form])
+            t2 = time.perf_counter()
             _, inf = c.solve(out=xh)
+            t3 = time.perf_counter()
             c.close()
             barrier()
+            t4 = time.perf_counter()
             if k > 0:
-                walls.append(time.perf_counter() - t0)
+                walls.append(t4 - t0)
                 its += inf["iters"]
+                for key, dt in (("create", t1 - t0), ("set", t2 - t1), ("solve", t3 - t2), ("close", t4 - t3)):
+                    phases[key] += dt
         e2e_v = B * its / sum(walls) / 1e9
         line["e2e"] = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * sum(walls) / len(walls)}
+                       "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * sum(walls) / len(walls),
+                       "ms_per_phase": {k: 1e3 * v / len(walls) for k, v in phases.items()}}
     # ---- the graph, batched and served workloads (untimed by the headline)
     if rank == 0 and not args.fixed_iters:
         if not args.no_graph:

@@ -702,16 +702,30 @@ static aj_status choose_order(aj_ctx* c, int mode) {
   const int n = (int)c->n;
   if (n < 2 || c->nnz == 0) return AJ_OK;
   cudaStream_t s = c->stream;
+  if (mode == AJ_REORDER_AUTO) {
+    c->order_tried = true;
+    const double mean = (double)c->nnz / n;
+    if (n < 16384 || c->maxlen > 16.0 * mean + 16.0) return AJ_OK;
+    // rows that already gather from a small part of x on average (a natural
+    // stencil order spans 2 N^(d-1) of n = N^d) keep the caller's order; the
+    // summed spans come from a device pass, so such matrices cost no copy
+    const int blocks = (int)grid1d(n);
+    Workspace tmp;
+    tmp.stream = &c->stream;
+    double* part = (double*)tmp.alloc((size_t)blocks * 8);
+    if (!part) return AJ_ENOMEM;
+    k_row_spans<<<blocks, kSetupThreads, 0, s>>>(n, c->rp0, c->ci0, part);
+    counted();
+    double span = 0.0;
+    aj_status e = host_sum_parts(c, part, blocks, 1, &span);
+    tmp.release();
+    if (e != AJ_OK) return e;
+    c->span0 = c->span1 = span;
+    if (span <= (double)n * (n / 8.0)) return AJ_OK;
+  }
   std::vector<int> rp((size_t)n + 1);
   CK(cudaMemcpyAsync(rp.data(), c->rp0, rp.size() * 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (mode == AJ_REORDER_AUTO) {
-    c->order_tried = true;
-    int maxlen = 0;
-    for (int i = 0; i < n; i++) maxlen = std::max(maxlen, rp[i + 1] - rp[i]);
-    const double mean = (double)c->nnz / n;
-    if (n < 16384 || maxlen > 16.0 * mean + 16.0) return AJ_OK;
-  }
   std::vector<int> ci((size_t)c->nnz);
   CK(cudaMemcpyAsync(ci.data(), c->ci0, ci.size() * 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -729,8 +743,6 @@ static aj_status choose_order(aj_ctx* c, int mode) {
   if (!hit) {
     const std::vector<int> none;
     ent.span0 = ent.span1 = row_spans(n, rp, ci, none);
-    // rows that already gather from a small part of x on average (a natural
-    // stencil order spans 2 N^(d-1) of n = N^d) keep the caller's order
     if (mode == AJ_REORDER_RCM || ent.span0 > (double)n * (n / 8.0)) {
       rcm_order(n, rp, ci, ent.perm);
       std::vector<int> iperm(n);
@@ -1257,6 +1269,7 @@ static aj_status choose_format(aj_ctx* c, const aj_params* p) {
   // AUTO: CSR unless the rows are long-tailed and the system is large
   const int n = (int)c->n;
   if (n < 65536) return AJ_OK;
+  if (c->maxlen <= 2.0 * ((double)c->nnz / n) + 8.0) return AJ_OK;  // near-uniform rows
   std::vector<int> rp((size_t)n + 1);
   CK(cudaMemcpyAsync(rp.data(), c->rp, rp.size() * 4, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));

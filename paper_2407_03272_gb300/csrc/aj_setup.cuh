@@ -279,6 +279,30 @@ __global__ void k_max_row_len(int n, const int* rp, int* out) {
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
 }
 
+// Summed row spans (largest minus smallest column of each row): per-block
+// partial sums in part[block] (FP64, exact for spans below 2^53).
+__global__ void k_row_spans(int n, const int* rp, const int* ci, double* part) {
+  __shared__ double sm[kSetupThreads / 32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (i < n) {
+    int lo = 0x7fffffff, hi = -1;
+    for (int q = rp[i]; q < rp[i + 1]; q++) {
+      lo = min(lo, ci[q]);
+      hi = max(hi, ci[q]);
+    }
+    if (hi >= lo) v = (double)(hi - lo);
+  }
+  for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kSetupThreads / 32; k++) t += sm[k];
+    part[blockIdx.x] = t;
+  }
+}
+
 // The long rows of the FP64 residual: one warp per row (lanes stride over the
 // entries, a fixed xor tree), eight rows per block, block partials of the same
 // three sums as k_residual in part[block][nrhs][3].
