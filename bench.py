@@ -424,14 +424,15 @@ def main():
 
     SWEEP = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED, "delta": aj.AJ_SWEEP_DELTA}
 
-    def make(precision, form):
+    def make(precision, form, auto=False):
+        # auto: leave the sweep form and format to the library (what a caller gets)
         ctx = aj.Context(*tensors, n=n)
         ctx.set_stream(stream)
+        sf = aj.AJ_SWEEP_AUTO if auto else SWEEP[form]
         if args.fixed_iters:
-            ctx.set(precision=precision, stop=aj.AJ_STOP_NONE, maxit=args.fixed_iters,
-                    sweep_form=SWEEP[form])
+            ctx.set(precision=precision, stop=aj.AJ_STOP_NONE, maxit=args.fixed_iters, sweep_form=sf)
         else:
-            ctx.set(precision=precision, tol=1e-8, maxit=200000, sweep_form=SWEEP[form])
+            ctx.set(precision=precision, tol=1e-8, maxit=200000, sweep_form=sf)
         return ctx
 
     def barrier():
@@ -460,7 +461,9 @@ def main():
 
     # ---- headline: the chosen precision, K timed solves
     form = form_of(args.precision, args.form)
-    ctx = make(args.precision, form)
+    ctx = make(args.precision, form, auto=args.form == "auto")
+    if args.form == "auto" and args.precision != "fp64" and ctx.format()[0] == aj.AJ_FMT_SELL:
+        form = "stored"  # the library's AUTO choice for SELL
     with Clocks(dev.index) as clk:
         ms, infos, launches = time_solves(ctx, args.steps, args.warmup)
     B = algorithmic_bytes(n, nnz, args.precision)
