@@ -39,18 +39,21 @@ FALLBACK_HBM_GBS = 6800.0
 FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
 
 
-def algorithmic_bytes(n, nnz, precision, form="min"):
+def algorithmic_bytes(n, nnz, precision, form="min", stencil=False, nrhs=1):
     """Bytes one fused iteration must move, per right-hand side: the matrix once
     (values + int32 column indices), the row pointers, and 5 n-vectors -- read
     x^t and x^{t-1} (gathered, each counted once), b and J^{-1}, write x^{t+1}.
     That is the method's minimum (the lazy form moves exactly this); form =
     "stored" adds the two n-vectors that form also moves (read Q x^{t-1},
     write Q x^t), form = "delta" one more (write x^t - x^{t-1}; it reads that
-    difference in place of x^{t-1}), for the traffic comparison only."""
+    difference in place of x^{t-1}), for the traffic comparison only.  In the
+    stencil format the sweep loads no matrix: the n-vectors alone.  nrhs
+    right-hand sides share one pass over the matrix."""
     vb = {"fp64": 8, "df64": 8, "fp32_ir": 4, "bf16_ir": 2}[precision]
     sb = {"fp64": 8, "df64": 8, "fp32_ir": 4, "bf16_ir": 4}[precision]
     kvec = {"stored": 7, "delta": 8}.get(form, 5)
-    return nnz * (vb + 4) + 4 * (n + 1) + n * kvec * sb
+    matrix = 0 if stencil else nnz * (vb + 4) + 4 * (n + 1)
+    return matrix + nrhs * n * kvec * sb
 
 
 # DRAM bytes (read + written) per fused sweep over the bytes the sweep form
@@ -61,7 +64,8 @@ def algorithmic_bytes(n, nnz, precision, form="min"):
 # launch by the sweeps it runs; traffic grows in proportion to the rows.
 TRAFFIC_PER_FORM_BYTES = {("fp64", "delta"): 16.706409e9 / 51 / 317587460.0,
                           ("fp64", "stored"): 15.967641e9 / 51 / 300810244.0,
-                          ("fp32_ir", "stored"): 9.382468e9 / 51 / 183762948.0}
+                          ("fp32_ir", "stored"): 9.382468e9 / 51 / 183762948.0,
+                          ("fp32_ir", "lazy"): 9.156e9 / 51 / 166985732.0}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 128^3 capture, "
                   "scaled by rows and sweeps to one launch of this workload")
 
@@ -295,10 +299,12 @@ def bench_batched(aj, torch, dev, stream, count, pool):
         aj.solve_batch(cs[:4], outs[:4], on_device=True)  # warm-up
         ms, wall, infos = timed(lambda: aj.solve_batch(cs, outs, on_device=True))
         ok = sum(1 for i in infos if i["status"] == aj.AJ_OK)
-        byt = sum(algorithmic_bytes(mats[j]["n"], int(mats[j]["row_ptr"][-1]), prec) * i["iters"]
-                  for (j, _, _), i in zip(systems, infos))
+        stn = [c.format()[0] == aj.AJ_FMT_STENCIL for c in cs]
+        byt = sum(algorithmic_bytes(mats[j]["n"], int(mats[j]["row_ptr"][-1]), prec, stencil=st, nrhs=nr)
+                  * i["iters"] for (j, nr, _), i, st in zip(systems, infos, stn))
         res["batched_" + prec] = {"makespan_ms": ms, "wall_ms": wall, "systems_per_s": count / (ms * 1e-3),
                                   "ok": ok, "max_relres": max(i["relres"] for i in infos),
+                                  "stencil_systems": int(sum(stn)),
                                   "approx_GBps": byt / (ms * 1e-3) / 1e9,
                                   "iterations_total": int(sum(i["iters"] for i in infos))}
         if prec == "fp64":
@@ -424,15 +430,18 @@ def main():
 
     SWEEP = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED, "delta": aj.AJ_SWEEP_DELTA}
 
-    def make(precision, form, auto=False):
-        # auto: leave the sweep form and format to the library (what a caller gets)
+    def make(precision, form, auto=False, fmt=None):
+        # auto: leave the sweep form to the library (what a caller gets); the
+        # format is CSR, as the workload states, unless fmt names another
         ctx = aj.Context(*tensors, n=n)
         ctx.set_stream(stream)
         sf = aj.AJ_SWEEP_AUTO if auto else SWEEP[form]
+        fm = aj.AJ_FMT_CSR if fmt is None else fmt
         if args.fixed_iters:
-            ctx.set(precision=precision, stop=aj.AJ_STOP_NONE, maxit=args.fixed_iters, sweep_form=sf)
+            ctx.set(precision=precision, stop=aj.AJ_STOP_NONE, maxit=args.fixed_iters, sweep_form=sf,
+                    format=fm)
         else:
-            ctx.set(precision=precision, tol=1e-8, maxit=200000, sweep_form=sf)
+            ctx.set(precision=precision, tol=1e-8, maxit=200000, sweep_form=sf, format=fm)
         return ctx
 
     def barrier():
@@ -539,6 +548,24 @@ def main():
                     "fused_hbm_frac": vb * it / (kms * 1e-3) / 1e9 / hbm_peak,
                     "kernel_ms_per_iteration": kms / max(it, 1)}
                 del c
+        # the stencil format on the same system (where Q is a grid stencil):
+        # the sweep computes Q's entries, so it moves the n-vectors alone
+        for p, fm in (("fp64", "delta"), ("fp32_ir", "lazy")):
+            try:
+                c = make(p, fm, fmt=aj.AJ_FMT_STENCIL)
+            except RuntimeError:
+                break
+            vms, vinf, _ = time_solves(c, 2, 1)
+            vb = algorithmic_bytes(n, nnz, p, stencil=True)
+            it = sum(i["iters"] for i in vinf)
+            kms = sum(i["kernel_ms"] for i in vinf)
+            var[p + "/stencil-" + fm] = {
+                "time_to_tol_ms": vms / 2, "iterations": vinf[-1]["iters"],
+                "outer": vinf[-1]["outer"], "relres": vinf[-1]["relres"],
+                "fused_GBps": vb * it / (kms * 1e-3) / 1e9,
+                "fused_hbm_frac": vb * it / (kms * 1e-3) / 1e9 / hbm_peak,
+                "kernel_ms_per_iteration": kms / max(it, 1)}
+            del c
         line["variants"] = var
     # ---- end to end through the C ABI with pinned host buffers
     if not args.no_e2e:
@@ -555,7 +582,8 @@ def main():
             c = aj.Context(*host, n=n)
             c.set_stream(stream)
             t1 = time.perf_counter()
-            c.set(precision=args.precision, tol=1e-8, maxit=200000, sweep_form=SWEEP[form])
+            c.set(precision=args.precision, tol=1e-8, maxit=200000, sweep_form=SWEEP[form],
+                  format=aj.AJ_FMT_CSR)
             t2 = time.perf_counter()
             _, inf = c.solve(out=xh)
             t3 = time.perf_counter()

@@ -116,12 +116,24 @@ typedef struct {
  * SELL-C-sigma layout (C = 32, rows sorted by length within windows of sigma
  * rows, each 32-row slice stored column-major so that a warp's loads are
  * coalesced), with rows longer than sell_lmax summed warp-cooperatively and
- * rows longer than 4096 entries CTA-cooperatively from CSR.  AUTO keeps CSR for rows of near-uniform length and otherwise times
- * CSR and SELL candidates for a few sweeps and keeps the fastest (the choice
- * is cached per matrix shape and precision for the process). */
+ * rows longer than 4096 entries CTA-cooperatively from CSR.  STENCIL: Q is
+ * a constant-coefficient 5-point (n = N^2) or 7-point (n = N^3) stencil with
+ * Dirichlet boundary in natural row order (i = x + N y + N^2 z), every row's
+ * columns ascending, one diagonal and one off-diagonal value bitwise (the
+ * grid Laplacians of Sec. 4); the sweep computes each row's columns and
+ * values instead of loading them, in the CSR order and with the CSR values,
+ * so its iterates equal those of CSR bit for bit.  aj_set checks every row on
+ * the device and returns AJ_EINVAL for an explicit STENCIL on any other Q.
+ * AUTO takes STENCIL where Q is one (rows not renumbered; not for AJ_FP64
+ * with several right-hand sides or in the lazy form, where it measured
+ * slower than CSR), keeps CSR for rows
+ * of near-uniform length and otherwise times CSR and SELL candidates for a
+ * few sweeps and keeps the fastest (the choice is cached per matrix shape
+ * and precision for the process). */
 #define AJ_FMT_AUTO 0
 #define AJ_FMT_CSR 1
 #define AJ_FMT_SELL 2
+#define AJ_FMT_STENCIL 3
 
 /* Row order of Q for the fused sweep (a format choice; the paper has no
  * counterpart).  RCM renumbers rows and columns by reverse Cuthill-McKee
@@ -150,7 +162,7 @@ typedef struct {
   double fstar;          /* f* for AJ_STOP_OBJGAP */
   int64_t maxit;         /* iteration limit (inner iterations in total for the IR modes) */
   int precision;         /* AJ_FP64 (default) | AJ_DF64 | AJ_FP32_IR | AJ_BF16_IR */
-  int format;            /* AJ_FMT_AUTO (default) | AJ_FMT_CSR | AJ_FMT_SELL */
+  int format;            /* AJ_FMT_AUTO (default) | AJ_FMT_CSR | AJ_FMT_SELL | AJ_FMT_STENCIL */
   const double* x0;      /* initial point x^0 = y^1, n x nrhs column-major; NULL = 0 */
   int x0_on_device;
   double inner_tol;      /* IR modes: relative tolerance of each inner solve (default 1e-4) */
@@ -192,9 +204,10 @@ aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ctx** out);
  * D^-1/2 Q D^-1/2 in FP64.  AJ_EINVAL on a bad parameter. */
 aj_status aj_set(aj_ctx* ctx, const aj_params* p);
 
-/* The format aj_set chose (AJ_FMT_CSR or AJ_FMT_SELL), its sigma and long-row
- * threshold (0 for CSR), and the stored SELL entries per stored entry of Q
- * (padding overhead, 1.0 for CSR). */
+/* The format aj_set chose (AJ_FMT_CSR, AJ_FMT_SELL or AJ_FMT_STENCIL), its
+ * sigma and long-row threshold (0 unless SELL), and the entries the sweep
+ * loads per stored entry of Q (SELL padding overhead; 1.0 for CSR, 0.0 for
+ * STENCIL). */
 aj_status aj_get_format(aj_ctx* ctx, int* format, int* sigma, int* lmax, double* fill_ratio);
 
 /* Whether aj_set renumbered the rows (1: reverse Cuthill-McKee order in use,

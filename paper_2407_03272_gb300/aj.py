@@ -19,7 +19,7 @@ AJ_J_ABSROWSUM, AJ_J_SCALED_DIAG = 0, 1
 AJ_RESTART_NONE, AJ_RESTART_ADAPTIVE = 0, 1
 AJ_STOP_RELRES, AJ_STOP_OBJGAP, AJ_STOP_NONE = 0, 1, 2
 AJ_FP64, AJ_DF64, AJ_FP32_IR, AJ_BF16_IR = 0, 1, 2, 3
-AJ_FMT_AUTO, AJ_FMT_CSR, AJ_FMT_SELL = 0, 1, 2
+AJ_FMT_AUTO, AJ_FMT_CSR, AJ_FMT_SELL, AJ_FMT_STENCIL = 0, 1, 2, 3
 AJ_SWEEP_AUTO, AJ_SWEEP_LAZY, AJ_SWEEP_STORED, AJ_SWEEP_DELTA = 0, 1, 2, 3
 AJ_REORDER_AUTO, AJ_REORDER_NONE, AJ_REORDER_RCM = 0, 1, 2
 AJ_NOALLOC_MAX_N = 131072

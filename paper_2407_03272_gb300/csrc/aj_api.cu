@@ -213,6 +213,7 @@ struct aj_ctx {
   // SELL-C-sigma copy of Q (fmt = 1), rebuilt by aj_set
   Workspace sws;
   int fmt = 0, sell_sigma = 0, sell_lmax = 0;
+  int sdim = 0, sN = 0;  // stencil format (fmt = 2): dimensions and grid side
   double fill = 1.0;
   int nsell = 0, ntiles_sell = 0, nltiles = 0, nhuge = 0;
   int *d_perm = nullptr, *d_rlen = nullptr, *d_sptr = nullptr, *d_scol = nullptr;
@@ -785,7 +786,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     return AJ_EINVAL;
   if (p->stop < AJ_STOP_RELRES || p->stop > AJ_STOP_NONE) return AJ_EINVAL;
   if (p->precision < AJ_FP64 || p->precision > AJ_BF16_IR) return AJ_EINVAL;
-  if (p->format < AJ_FMT_AUTO || p->format > AJ_FMT_SELL) return AJ_EINVAL;
+  if (p->format < AJ_FMT_AUTO || p->format > AJ_FMT_STENCIL) return AJ_EINVAL;
   if (p->grid_ctas < 0) return AJ_EINVAL;
   if (p->sweep_form < AJ_SWEEP_AUTO || p->sweep_form > AJ_SWEEP_DELTA) return AJ_EINVAL;
   if (p->sweep_form == AJ_SWEEP_DELTA && p->precision != AJ_FP64) return AJ_EINVAL;
@@ -944,7 +945,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   // (irregular rows: one random gather per entry instead of two), lazy for
   // the other precisions on CSR, where the second row sum gathers from the
   // same cached lines and saves two n-vectors of traffic
-  if (p->sweep_form == AJ_SWEEP_AUTO && p->precision != AJ_FP64 && c->fmt == 0) {
+  if (p->sweep_form == AJ_SWEEP_AUTO && p->precision != AJ_FP64 && c->fmt != 1) {
     c->qx = 0;
     const int bps = std::max(1, persistent_blocks_per_sm(kernel_pol(pol), nrhs, c->qx));
     const int rpt = kThreads >> lanes_log2(nrhs);
@@ -1037,6 +1038,19 @@ static IterLaunch make_launch(aj_ctx* c, const void* bvec, long long maxit, int 
   L.col = c->ci;
   L.val = c->pol == AJ_FP64 ? (const void*)c->val64 : c->valp;
   L.fmt = c->fmt;
+  if (c->fmt == 2) {
+    L.sdim = c->sdim;
+    L.sN = c->sN;
+    L.sdiag_at = 0;
+    L.soff_at = 1;
+    // division by N as a multiply and shift (Granlund and Montgomery, PLDI
+    // 1994, Thm. 4.2 with 31-bit numerators): l = ceil(log2 N),
+    // m = floor(2^(31+l) / N) + 1, then q / N = (q m) >> (31 + l)
+    int l = 0;
+    while ((1ll << l) < c->sN) l++;
+    L.smag = (unsigned long long)((1ull << (31 + l)) / (unsigned long long)c->sN) + 1ull;
+    L.sshift = 31 + l;
+  }
   if (c->fmt == 1) {
     L.nsell = c->nsell;
     L.ntiles_sell = c->ntiles_sell;
@@ -1258,6 +1272,49 @@ struct TuneKey {
 static std::map<TuneKey, std::array<int, 3>> g_tune;  // -> {fmt, sigma, lmax}
 static std::mutex g_tune_mu;
 
+// The constant-coefficient stencil format: Q in natural row order is the
+// 5-point (N x N) or 7-point (N^3) stencil with one diagonal and one
+// off-diagonal value (a Dirichlet Laplacian, Sec. 4's grid problems).  The
+// sweep then computes each row's columns and values instead of loading them,
+// in the same ascending order and with the same values as the CSR rows, so
+// its iterates are the CSR iterates bit for bit.  *is says whether Q is one.
+static aj_status detect_stencil(aj_ctx* c, bool* is) {
+  *is = false;
+  const long long n = c->n, nnz = c->nnz;
+  if (c->ordered || n < 4 || c->maxlen > 7) return AJ_OK;
+  int dim = 0, N = 0;
+  for (int d = 2; d <= 3 && !dim; d++) {
+    const long long r = (long long)std::llround(std::pow((double)n, 1.0 / d));
+    for (long long g = std::max(2ll, r - 1); g <= r + 1; g++) {
+      const long long gd = d == 2 ? g * g : g * g * g;
+      const long long want = d == 2 ? 5 * n - 4 * g : 7 * n - 6 * g * g;
+      if (gd == n && nnz == want) { dim = d; N = (int)g; break; }
+    }
+  }
+  if (!dim) return AJ_OK;
+  cudaStream_t s = c->stream;
+  // row 0 (a corner): the diagonal first, then the off-diagonal of column 1
+  int c01[2];
+  double v01[2];
+  CK(cudaMemcpyAsync(c01, c->ci, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(v01, c->val64, 16, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (c01[0] != 0 || c01[1] != 1) return AJ_OK;
+  CK(cudaMemsetAsync(c->err, 0, 4, s));
+  k_check_stencil<<<std::min<unsigned>(grid1d(n), 4096), kSetupThreads, 0, s>>>(
+      (int)n, N, dim, c->rp, c->ci, c->val64, v01[0], v01[1], c->err);
+  counted();
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, c->err, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemsetAsync(c->err, 0, 4, s));
+  CK(cudaStreamSynchronize(s));
+  if (bad) return AJ_OK;
+  c->sdim = dim;
+  c->sN = N;
+  *is = true;
+  return AJ_OK;
+}
+
 static aj_status choose_format(aj_ctx* c, const aj_params* p) {
   const int sig = p->sell_sigma > 0 ? p->sell_sigma : 256;
   const int lmx = p->sell_lmax > 0 ? p->sell_lmax : 64;
@@ -1266,6 +1323,22 @@ static aj_status choose_format(aj_ctx* c, const aj_params* p) {
   c->fmt = 0;
   c->fill = 1.0;
   if (p->format == AJ_FMT_CSR) return AJ_OK;
+  // AUTO leaves FP64 with several right-hand sides, or in the lazy form, on
+  // CSR: measured slower there in the stencil format (a 1024^2 grid, 4 RHS:
+  // 0.91x in the difference form, 0.80x lazy); every other precision and form
+  // gains (FP32 values on 256^3: 1.43x per sweep)
+  const bool stencil_pays = !(c->pol == AJ_FP64 && (c->nrhs > 1 || c->qx == 0));
+  if (p->format == AJ_FMT_STENCIL || (p->format == AJ_FMT_AUTO && stencil_pays)) {
+    bool is = false;
+    aj_status e = detect_stencil(c, &is);
+    if (e != AJ_OK) return e;
+    if (is) {
+      c->fmt = 2;
+      c->fill = 0.0;
+      return AJ_OK;
+    }
+    if (p->format == AJ_FMT_STENCIL) return AJ_EINVAL;
+  }
   // AUTO: CSR unless the rows are long-tailed and the system is large
   const int n = (int)c->n;
   if (n < 65536) return AJ_OK;
@@ -1315,9 +1388,9 @@ static aj_status choose_format(aj_ctx* c, const aj_params* p) {
 
 extern "C" aj_status aj_get_format(aj_ctx* c, int* format, int* sigma, int* lmax, double* fill_ratio) {
   if (!c) return AJ_EINVAL;
-  if (format) *format = c->fmt ? AJ_FMT_SELL : AJ_FMT_CSR;
-  if (sigma) *sigma = c->fmt ? c->sell_sigma : 0;
-  if (lmax) *lmax = c->fmt ? c->sell_lmax : 0;
+  if (format) *format = c->fmt == 1 ? AJ_FMT_SELL : c->fmt == 2 ? AJ_FMT_STENCIL : AJ_FMT_CSR;
+  if (sigma) *sigma = c->fmt == 1 ? c->sell_sigma : 0;
+  if (lmax) *lmax = c->fmt == 1 ? c->sell_lmax : 0;
   if (fill_ratio) *fill_ratio = c->fill;
   return AJ_OK;
 }
@@ -1465,13 +1538,14 @@ static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, d
       u0[j] = (int)unit.size();
       nu[j] = V[i];
       // estimated work of unit v: its tiles x row-RHS pairs per tile x
-      // (stored entries per row + the per-row update)
-      // (stored entries per row + the per-row update), plus a fixed cost of
-      // about one tile for the unit's own reductions
+      // (entries per row + the per-row update), plus a fixed cost of about
+      // one tile for the unit's own reductions; a stencil row loads no
+      // column or value, only its x gathers, about 0.4 of a CSR entry's cost
       const aj_ctx* c = items[i].c;
       const long long rpt = kThreads >> lanes_log2(c->nrhs);
       const long long ntiles = ctx_tiles(c);
-      const double per_tile = (double)rpt * c->nrhs * ((double)c->nnz / std::max<int64_t>(c->n, 1) + 9.0);
+      const double epr = (double)c->nnz / std::max<int64_t>(c->n, 1) * (c->fmt == 2 ? 0.4 : 1.0);
+      const double per_tile = (double)rpt * c->nrhs * (epr + 9.0);
       const long long mine = std::min(left[i], sweeps);  // sweeps this item runs in the launch
       for (int v = 0; v < V[i]; v++) {
         unit.push_back(j);

@@ -400,7 +400,12 @@ struct IterArgs {
   const int* row_ptr;
   const int* col;
   const typename P::V* val;
-  int fmt;                    // 0 CSR, 1 SELL
+  int fmt;                    // 0 CSR, 1 SELL, 2 constant-coefficient stencil
+  int sdim;                   // stencil: 2 (5-point, N x N) or 3 (7-point, N^3), natural row order
+  int sN;                     // stencil: grid side N
+  int sdiag_at, soff_at;      // stencil: entries of val holding the diagonal and the off-diagonal value
+  unsigned long long smag;    // stencil: q / N = (q * smag) >> sshift for 0 <= q < 2^31
+  int sshift;
   int nsell;                  // SELL: rows in the sliced part
   int ntiles_sell;            // SELL: tiles of the sliced part
   int nltiles;                // SELL: tiles of long rows
@@ -634,7 +639,16 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
   const bool active = lane_on && me.done == 0;
   const S beta = P::coef(me.beta);
   const int lane = threadIdx.x & 31;
-  const bool sell = ANY && a.fmt != 0;
+  const bool sell = ANY && a.fmt == 1;
+  // stencil: the rows of a constant-coefficient Dirichlet Laplacian in natural
+  // order, their entries known without loading them (same values, same
+  // ascending column order as in CSR, so the sums are the CSR sums bit for bit)
+  const bool stn = ANY && a.fmt == 2;
+  V s_diag = P::vzero(), s_off = P::vzero();
+  if (stn) {
+    s_diag = P::ldv(a.val + a.sdiag_at);
+    s_off = P::ldv(a.val + a.soff_at);
+  }
   const int ntiles = sell ? a.ntiles_sell + a.nltiles + a.nhuge : (a.n + rpt - 1) / rpt;
   for (int tile = cta; tile < ntiles; tile += ncta) {
     // this lane group's row i, its entries colp[k * stride], valp[k * stride]
@@ -646,7 +660,7 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
     if (!sell) {
       i = tile * rpt + slot;
       valid = i < a.n;
-      if (valid) {
+      if (valid && !stn) {
         rs = ld_ro(a.row_ptr + i);
         re = ld_ro(a.row_ptr + i + 1);
       }
@@ -693,6 +707,47 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
         cta_row_sums<P, QX>(a, st[k], nr, k, rs, re, hx, hp);
         if (k == r) { sx = hx; sp = hp; }
       }
+    } else if (ANY && stn && valid && active) {
+      // the up to 7 neighbours in ascending column order: -N^2, -N, -1, 0, +1, +N, +N^2
+      // (bit k of inm: neighbour k lies in the grid); grid coordinates by
+      // multiply-shift division (Granlund and Montgomery, PLDI 1994)
+      const int N = a.sN, NN = a.sdim == 3 ? N * N : 0;
+      const int q = (int)(((unsigned long long)i * a.smag) >> a.sshift);  // i / N
+      const int ix = i - q * N;
+      const int iy = a.sdim == 3 ? q - (int)(((unsigned long long)q * a.smag) >> a.sshift) * N : q;
+      const unsigned inm = (ix > 0 ? 4u : 0u) | 8u | (ix < N - 1 ? 16u : 0u) | (iy > 0 ? 2u : 0u) |
+                           (iy < N - 1 ? 32u : 0u) | (i >= NN && NN ? 1u : 0u) |
+                           (NN && i < a.n - NN ? 64u : 0u);
+      const bool two = !QX && !same;
+      // chunks of U neighbours, as for CSR rows: loads first, then the
+      // multiply-adds in ascending order
+      constexpr int U = row_unroll(QX);
+#pragma unroll
+      for (int k0 = 0; k0 < 7; k0 += U) {
+        S xv[U], pv[U];
+#pragma unroll
+        for (int j = 0; j < U; j++) {
+          const int k = k0 + j;
+          const int off = k == 0 ? -NN : k == 1 ? -N : k == 2 ? -1 : k == 3 ? 0 : k == 4 ? 1 : k == 5 ? N : NN;
+          xv[j] = P::zero();
+          pv[j] = P::zero();
+          if (k < 7 && (inm >> k & 1u)) {
+            const size_t e = (size_t)(i + off) * nr + r;
+            xv[j] = P::ldg(xc + e);
+            if (two) pv[j] = P::ldg(xp + e);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < U; j++) {
+          const int k = k0 + j;
+          if (k >= 7 || !(inm >> k & 1u)) continue;
+          const V v = k == 3 ? s_diag : s_off;
+          P::macv(sx, v, xv[j]);
+          if (two) P::macv(sp, v, pv[j]);
+        }
+      }
+      sx = P::finish(sx);
+      if (!QX) sp = same ? sx : P::finish(sp);
     } else if (valid && !is_long && active) {
       // chunks of U entries: every load of a chunk is issued before its
       // multiply-adds, which then run in ascending entry order

@@ -24,6 +24,12 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
   a.col = L.col;
   a.val = static_cast<const typename P::V*>(L.val);
   a.fmt = L.fmt;
+  a.sdim = L.sdim;
+  a.sN = L.sN;
+  a.sdiag_at = L.sdiag_at;
+  a.soff_at = L.soff_at;
+  a.smag = L.smag;
+  a.sshift = L.sshift;
   a.nsell = L.nsell;
   a.ntiles_sell = L.ntiles_sell;
   a.nltiles = L.nltiles;

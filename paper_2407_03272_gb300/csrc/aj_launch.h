@@ -15,7 +15,10 @@ struct IterLaunch {
   const int* row_ptr;
   const int* col;
   const void* val;
-  int fmt;  // 0 CSR, 1 SELL-C-sigma (fields below)
+  int fmt;  // 0 CSR, 1 SELL-C-sigma (fields below), 2 constant-coefficient stencil
+  int sdim, sN, sdiag_at, soff_at;  // stencil: 2 or 3 dimensions, grid side, entries of val
+  unsigned long long smag;          // stencil: q / N = (q * smag) >> sshift for 0 <= q < 2^31
+  int sshift;
   int nsell;
   int ntiles_sell;
   int nltiles;

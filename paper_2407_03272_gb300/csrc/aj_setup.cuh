@@ -279,6 +279,32 @@ __global__ void k_max_row_len(int n, const int* rp, int* out) {
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
 }
 
+// Whether Q is a constant-coefficient (2*dim+1)-point stencil on an N^dim grid
+// with Dirichlet boundary, rows in natural order (i = x + N*y + N^2*z): every
+// row holds exactly its in-grid neighbours, columns ascending, the diagonal
+// entry bitwise equal to d and every other entry bitwise equal to o.  Sets
+// *bad on any row that differs.
+__global__ void k_check_stencil(int n, int N, int dim, const int* rp, const int* ci, const double* val,
+                                double d, double o, int* bad) {
+  const long long d_bits = __double_as_longlong(d), o_bits = __double_as_longlong(o);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)t;
+    const int NN = dim == 3 ? N * N : 0;
+    const int ix = i % N, iy = (i / N) % N, iz = dim == 3 ? i / NN : 0;
+    const bool in[7] = {dim == 3 && iz > 0, iy > 0, ix > 0, true, ix < N - 1, iy < N - 1, dim == 3 && iz < N - 1};
+    const int cc[7] = {i - NN, i - N, i - 1, i, i + 1, i + N, i + NN};
+    int q = rp[i];
+    const int qe = rp[i + 1];
+    bool ok = true;
+    for (int k = 0; k < 7 && ok; k++) {
+      if (!in[k]) continue;
+      ok = q < qe && ci[q] == cc[k] && __double_as_longlong(val[q]) == (k == 3 ? d_bits : o_bits);
+      q++;
+    }
+    if (!ok || q != qe) *bad = 1;
+  }
+}
+
 // Summed row spans (largest minus smallest column of each row): per-block
 // partial sums in part[block] (FP64, exact for spans below 2^53).
 __global__ void k_row_spans(int n, const int* rp, const int* ci, double* part) {

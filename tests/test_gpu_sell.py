@@ -98,8 +98,14 @@ def test_autotuner_picks_a_format_and_solves():
     ctx2 = aj.from_csr(Q, b, device="cuda")
     ctx2.set(tol=1e-8, maxit=40000, precision="fp32_ir")
     assert ctx2.format()[:3] == fmt[:3]
-    # stencils keep CSR
+    # grid stencils get the stencil format, never SELL; their rows are uniform,
+    # so with the stencil format off they keep CSR without timing
     Qp, bp, _ = synth.workload("poisson3d_64")
     c3 = aj.from_csr(Qp, bp, device="cuda")
     c3.set(tol=1e-8)
-    assert c3.format()[0] == aj.AJ_FMT_CSR
+    assert c3.format()[0] == aj.AJ_FMT_STENCIL
+    Qp["val"] = Qp["val"] * 1.0
+    Qp["val"][0] = 6.5  # row 0's diagonal: no longer one diagonal value
+    c4 = aj.from_csr(Qp, bp, device="cuda")
+    c4.set(tol=1e-8)
+    assert c4.format()[0] == aj.AJ_FMT_CSR
