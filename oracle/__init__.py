@@ -6,7 +6,9 @@ shares no code with the CUDA library (``paper_2407_03272_gb300``) and neither
 imports the other.
 
 ``solve`` runs Algorithm alg-jacobi (Section 3) with the adaptive restart of
-Algorithm alg-apg-re (Section 2.2) in plain C, FP64, one thread.  Dense helpers
+Algorithm alg-apg-re (Section 2.2) in plain C, FP64, one thread, with a
+diagonal J (eq. J-diag and its variants) or a block-diagonal J
+(eq. J-blkdiag, built by ``j_blkdiag``).  Dense helpers
 for tiny inputs (the step constant L = lambda_max(D^-1/2 Q D^-1/2), direct
 solves) live in ``oracle.dense``.
 """
@@ -25,7 +27,8 @@ class _Params(ctypes.Structure):
                 ("val", ctypes.c_void_p), ("b", ctypes.c_void_p), ("J", ctypes.c_void_p),
                 ("x0", ctypes.c_void_p), ("is_restart", ctypes.c_int), ("momentum", ctypes.c_int),
                 ("K0", ctypes.c_int64), ("maxit", ctypes.c_int64), ("stop", ctypes.c_int),
-                ("tol", ctypes.c_double), ("fstar", ctypes.c_double), ("forced", ctypes.c_void_p)]
+                ("tol", ctypes.c_double), ("fstar", ctypes.c_double), ("forced", ctypes.c_void_p),
+                ("bs", ctypes.c_int64), ("Jblk", ctypes.c_void_p)]
 
 
 class _Info(ctypes.Structure):
@@ -90,12 +93,61 @@ def j_scaled_diag(Q, c):
     return J
 
 
-def solve(Q, b, J, *, restart=True, momentum=True, K0=2, maxit=1000, stop=STOP_RELRES,
+def j_blkdiag(Q, bs):
+    """eq. J-blkdiag with s = ceil(n / bs) blocks of bs consecutive rows:
+    J^{ii} = Q^{ii} + (sum_{j != i} ||Q^{ij}||_2) I, the spectral norm of each
+    off-diagonal block by a dense SVD (numpy.linalg.norm(., 2)).
+
+    Reading where the paper is silent: a block whose J^{ii} is singular (a
+    part of Q wholly inside the block that is itself singular, e.g. a
+    component of a graph Laplacian, or a zero row) gets eq. J-diag's diagonal
+    instead; singular means lambda_min(J^{ii}) <= 1e-12 * max_k J^{ii}_kk.
+
+    Returns an (s, bs, bs) array; the last block's rows and columns beyond n
+    hold the identity."""
+    n, rp, ci, v = _csr(Q)
+    bs = int(bs)
+    s = (n + bs - 1) // bs
+    out = np.zeros((s, bs, bs))
+    jd = j_absrowsum(Q)
+    for ib in range(s):
+        r0 = ib * bs
+        nb = min(bs, n - r0)
+        D = np.zeros((bs, bs))
+        off = {}
+        for k in range(nb):
+            i = r0 + k
+            for p in range(rp[i], rp[i + 1]):
+                c = int(ci[p])
+                jb = c // bs
+                if jb == ib:
+                    D[k, c - r0] += v[p]
+                else:
+                    A = off.setdefault(jb, np.zeros((bs, bs)))
+                    A[k, c - jb * bs] += v[p]
+        c_i = sum(np.linalg.norm(off[jb], 2) for jb in sorted(off))
+        Jb = D[:nb, :nb] + c_i * np.eye(nb)
+        if nb > 0 and np.linalg.eigvalsh(Jb)[0] <= 1e-12 * max(np.max(np.diag(Jb)), 0.0):
+            Jb = np.diag(jd[r0:r0 + nb])
+        out[ib, :nb, :nb] = Jb
+        for k in range(nb, bs):
+            out[ib, k, k] = 1.0
+    return out
+
+
+def solve(Q, b, J=None, *, Jblk=None, restart=True, momentum=True, K0=2, maxit=1000, stop=STOP_RELRES,
           tol=1e-8, fstar=0.0, x0=None, forced=None, trace=False, trace_iterates=False):
-    """Run Algorithm alg-jacobi; returns a dict with x, iters, restarts, relres,
-    f, converged and (trace=True) per-iteration arrays indexed by t."""
+    """Run Algorithm alg-jacobi with the diagonal J or, if given, the block
+    diagonal Jblk (from ``j_blkdiag``); returns a dict with x, iters,
+    restarts, relres, f, converged and (trace=True) per-iteration arrays
+    indexed by t."""
     n, rp, ci, v = _csr(Q)
     b = np.ascontiguousarray(b, dtype=np.float64)
+    bs = 0
+    if Jblk is not None:
+        Jblk = np.ascontiguousarray(Jblk, dtype=np.float64)
+        bs = int(Jblk.shape[1])
+        J = np.ones(max(n, 1))
     J = np.ascontiguousarray(J, dtype=np.float64)
     x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
     fa = None
@@ -105,7 +157,8 @@ def solve(Q, b, J, *, restart=True, momentum=True, K0=2, maxit=1000, stop=STOP_R
             if 1 <= t <= maxit:
                 fa[t] = 1
     P = _Params(n, _p(rp), _p(ci), _p(v), _p(b), _p(J), _p(x0a), int(bool(restart)),
-                int(bool(momentum)), int(K0), int(maxit), int(stop), float(tol), float(fstar), _p(fa))
+                int(bool(momentum)), int(K0), int(maxit), int(stop), float(tol), float(fstar), _p(fa),
+                bs, _p(Jblk))
     info = _Info()
     x = np.empty(n, dtype=np.float64)
     tr = {}

@@ -19,6 +19,9 @@
  *                                                          c = 1/omega gives weighted Jacobi, eq. weighted-jacobi)
  *   orc_aj_solve      Algorithm alg-jacobi with the restart rule of Algorithm alg-apg-re
  *                     (Section 2.2) and, when is_restart = 0, plain Algorithm alg-apg.
+ *                     J is diagonal (eq. J-diag and variants) or block diagonal
+ *                     (eq. J-blkdiag, blocks given by the caller); a block update
+ *                     x^i = y^i - (J^{ii})^{-1} g^i solves with the block's Cholesky factor.
  *                     momentum = 0 replaces the alpha/beta extrapolation by beta = 0, which with
  *                     J = D / omega is the (weighted) Jacobi method of eqs. jacobi / weighted-jacobi.
  */
@@ -92,6 +95,10 @@ typedef struct {
   double tol;
   double fstar;
   const uint8_t* forced; /* optional, length maxit + 1: restart at t iff forced[t] (replay) */
+  int64_t bs;           /* block size of Jblk */
+  const double* Jblk;   /* optional block-diagonal J (replaces J): s = ceil(n / bs) blocks
+                           J^{ii}, each bs x bs row-major; the last block's rows and
+                           columns beyond n are ignored */
 } orc_params;
 
 typedef struct {
@@ -144,6 +151,41 @@ static int stop_met(const orc_params* P, double relres, double f) {
   return 0;
 }
 
+/* Cholesky factor (lower triangular, row-major, m x m with leading
+ * dimension ld) of the symmetric m x m matrix A, in place of L:
+ *   L_jj = sqrt(A_jj - sum_{k<j} L_jk^2),  L_ij = (A_ij - sum_{k<j} L_ik L_jk) / L_jj.
+ * Returns -1 if a pivot is not positive. */
+static int cholesky(int64_t m, int64_t ld, const double* A, double* L) {
+  for (int64_t i = 0; i < m; i++)
+    for (int64_t j = 0; j < m; j++) L[i * ld + j] = 0.0;
+  for (int64_t j = 0; j < m; j++) {
+    double d = A[j * ld + j];
+    for (int64_t k = 0; k < j; k++) d -= L[j * ld + k] * L[j * ld + k];
+    if (!(d > 0.0)) return -1;
+    L[j * ld + j] = sqrt(d);
+    for (int64_t i = j + 1; i < m; i++) {
+      double v = A[i * ld + j];
+      for (int64_t k = 0; k < j; k++) v -= L[i * ld + k] * L[j * ld + k];
+      L[i * ld + j] = v / L[j * ld + j];
+    }
+  }
+  return 0;
+}
+
+/* z = (L L^T)^{-1} r: forward substitution L w = r, then back substitution L^T z = w. */
+static void chol_solve(int64_t m, int64_t ld, const double* L, const double* r, double* z) {
+  for (int64_t i = 0; i < m; i++) {
+    double v = r[i];
+    for (int64_t k = 0; k < i; k++) v -= L[i * ld + k] * z[k];
+    z[i] = v / L[i * ld + i];
+  }
+  for (int64_t i = m - 1; i >= 0; i--) {
+    double v = z[i];
+    for (int64_t k = i + 1; k < m; k++) v -= L[k * ld + i] * z[k];
+    z[i] = v / L[i * ld + i];
+  }
+}
+
 /* Algorithm alg-jacobi (Section 3) with diagonal J:
  *   x^t = y^t + J^{-1}(b - Q y^t)
  *   restart if IsRestart and t > K_re + K_ell and <Q y^t - b, x^t - x^{t-1}> >= 0:
@@ -163,6 +205,24 @@ int orc_aj_solve(const orc_params* P, double* x_out, orc_info* info, const orc_t
   if (!xprev || !x || !y || !g || !qx) {
     free(xprev); free(x); free(y); free(g); free(qx);
     return -1;
+  }
+  /* block-diagonal J: the Cholesky factor of every block, once */
+  double* Lf = NULL;
+  double* zb = NULL;
+  const int64_t bs = P->bs;
+  if (P->Jblk) {
+    const int64_t s = bs > 0 ? (n + bs - 1) / bs : 0;
+    Lf = (double*)calloc((size_t)(s > 0 ? s : 1) * (size_t)(bs > 0 ? bs * bs : 1), sizeof(double));
+    zb = (double*)calloc((size_t)(bs > 0 ? bs : 1), sizeof(double));
+    int bad = bs < 1 || !Lf || !zb;
+    for (int64_t ib = 0; ib < s && !bad; ib++) {
+      const int64_t nb = (n - ib * bs < bs) ? n - ib * bs : bs;
+      bad = cholesky(nb, bs, P->Jblk + ib * bs * bs, Lf + ib * bs * bs) != 0;
+    }
+    if (bad) {
+      free(xprev); free(x); free(y); free(g); free(qx); free(Lf); free(zb);
+      return -1;
+    }
   }
   if (P->x0)
     for (int64_t i = 0; i < n; i++) xprev[i] = P->x0[i];
@@ -184,8 +244,16 @@ int orc_aj_solve(const orc_params* P, double* x_out, orc_info* info, const orc_t
     /* g = Q y^t - b */
     orc_spmv(n, P->row_ptr, P->col, P->val, y, g);
     for (int64_t i = 0; i < n; i++) g[i] -= P->b[i];
-    /* x^t = y^t + J^{-1}(b - Q y^t) = y^t - g / J */
-    for (int64_t i = 0; i < n; i++) x[i] = y[i] - g[i] / P->J[i];
+    /* x^t = y^t + J^{-1}(b - Q y^t) = y^t - J^{-1} g */
+    if (P->Jblk) {
+      for (int64_t r0 = 0; r0 < n; r0 += bs) {
+        const int64_t nb = (n - r0 < bs) ? n - r0 : bs;
+        chol_solve(nb, bs, Lf + (r0 / bs) * bs * bs, g + r0, zb);
+        for (int64_t k = 0; k < nb; k++) x[r0 + k] = y[r0 + k] - zb[k];
+      }
+    } else {
+      for (int64_t i = 0; i < n; i++) x[i] = y[i] - g[i] / P->J[i];
+    }
     /* restart test quantity <Q y^t - b, x^t - x^{t-1}> */
     double d = 0.0, gg = 0.0;
     for (int64_t i = 0; i < n; i++) { d += g[i] * (x[i] - xprev[i]); gg += g[i] * g[i]; }
@@ -233,6 +301,6 @@ int orc_aj_solve(const orc_params* P, double* x_out, orc_info* info, const orc_t
     info->f = f;
     info->converged = conv;
   }
-  free(xprev); free(x); free(y); free(g); free(qx);
+  free(xprev); free(x); free(y); free(g); free(qx); free(Lf); free(zb);
   return 0;
 }

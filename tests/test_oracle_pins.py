@@ -420,3 +420,92 @@ def test_restart_is_a_fresh_start_from_previous_iterate():
     for s in range(0, T - tr + 1):
         np.testing.assert_array_equal(X[tr + s], fresh["trace"]["x"][s])
     np.testing.assert_array_equal(forced["x"], fresh["x"])
+
+
+# --------------------------------------------------------------------------- block-diagonal J (eq. J-blkdiag)
+def _block_dense(Jb, n):
+    s, bs, _ = Jb.shape
+    J = np.zeros((s * bs, s * bs))
+    for i in range(s):
+        J[i * bs:(i + 1) * bs, i * bs:(i + 1) * bs] = Jb[i]
+    return J[:n, :n]
+
+
+def test_j_blkdiag_hand_values_use_the_spectral_norm():
+    # Laplacian of the unit-weight graph 0-2, 0-3, 1-2, 2-3; blocks {0, 1}, {2, 3}.
+    # Q^{12} = [[-1, -1], [-1, 0]]: (Q^{12})^T Q^{12} = [[2, 1], [1, 1]] has eigenvalues
+    # (3 +- sqrt 5) / 2, so ||Q^{12}||_2 = sqrt((3 + sqrt 5) / 2) = phi, the golden ratio
+    # (the Frobenius norm sqrt 3, the largest entry 1 and the row-sum norm 2 all differ).
+    Q = synth.from_edges(4, [0, 0, 1, 2], [2, 3, 2, 3], [1.0, 1.0, 1.0, 1.0])
+    phi = (1 + math.sqrt(5)) / 2
+    Jb = oracle.j_blkdiag(Q, 2)
+    np.testing.assert_allclose(Jb[0], [[2 + phi, 0], [0, 1 + phi]], rtol=1e-15)
+    np.testing.assert_allclose(Jb[1], [[3 + phi, -1], [-1, 2 + phi]], rtol=1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_j_blkdiag_of_size_one_is_j_diag(seed):
+    # 1 x 1 blocks: ||Q_ij||_2 = |Q_ij|, so eq. J-blkdiag reduces to eq. J-diag
+    Q, _ = _random_csr(30, 0.3, 40 + seed, symmetric=True, spd_shift=0.1)
+    for M in (Q, synth.chung_lu_laplacian(300, seed=seed + 2, mean_degree=5.0)):
+        np.testing.assert_allclose(oracle.j_blkdiag(M, 1)[:, 0, 0], oracle.j_absrowsum(M), rtol=1e-15)
+
+
+@pytest.mark.parametrize("bs", [2, 3, 5, 8])
+@pytest.mark.parametrize("case", [_tiny_spd, _tiny_laplacian])
+def test_j_blkdiag_gives_psd_S_and_pd_J(case, bs):
+    # Section 3: S = J - Q is positive semidefinite and J positive definite
+    Q, A, _, _ = case()
+    J = _block_dense(oracle.j_blkdiag(Q, bs), Q["n"])
+    np.testing.assert_array_equal(J, J.T)
+    scale = np.abs(A).max()
+    assert np.linalg.eigvalsh(J - A)[0] >= -1e-12 * scale
+    assert np.linalg.eigvalsh(J)[0] > 1e-9 * scale
+
+
+def test_one_block_is_q_and_solves_in_one_step():
+    # s = 1: J = Q, so x^1 = y^1 - Q^{-1}(Q y^1 - b) = Q^{-1} b
+    Q, A, xs, b = _tiny_spd()
+    Jb = oracle.j_blkdiag(Q, 32)
+    np.testing.assert_allclose(_block_dense(Jb, Q["n"]), A, rtol=0, atol=0)
+    r = oracle.solve(Q, b, Jblk=Jb, maxit=1, stop=oracle.STOP_NONE)
+    np.testing.assert_allclose(r["x"], xs, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("bs", [3, 4])
+@pytest.mark.parametrize("case", [_tiny_spd, _tiny_laplacian])
+def test_block_update_prox_optimality_every_iterate(case, bs):
+    # Lemma lemma-diff-f proof with the block J: Q x^t - b + S (x^t - y^t) = 0, S = J - Q
+    Q, A, xs, b = case()
+    Jb = oracle.j_blkdiag(Q, bs)
+    J = _block_dense(Jb, Q["n"])
+    T = 60
+    r = oracle.solve(Q, b, Jblk=Jb, restart=False, maxit=T, stop=oracle.STOP_NONE, trace_iterates=True)
+    X, Y = r["trace"]["x"], r["trace"]["y"]
+    for t in range(1, T + 1):
+        res = A @ X[t] - b + (J - A) @ (X[t] - Y[t])
+        assert np.abs(res).max() <= 1e-12 * (1 + np.abs(b).max())
+
+
+def test_block_j_solves_and_singular_blocks_take_j_diag():
+    # a component {0, 1} wholly inside block 0 makes Q^{00} singular with no coupling:
+    # that block takes eq. J-diag's diagonal (here diag(2, 2))
+    u = [0, 2, 3, 4, 5, 2]
+    v = [1, 3, 4, 5, 6, 6]
+    Q = synth.from_edges(7, u, v, [1.0] * 6)
+    Jb = oracle.j_blkdiag(Q, 2)
+    np.testing.assert_array_equal(Jb[0], np.diag(oracle.j_absrowsum(Q)[:2]))
+    assert np.linalg.eigvalsh(_block_dense(Jb, 7) - dense.to_dense(Q))[0] >= -1e-12
+    b = synth.rhs(Q, synth.uniform(7, 3))
+    r = oracle.solve(Q, b, Jblk=Jb, maxit=5000, tol=1e-10)
+    assert r["converged"] and r["relres"] <= 1e-10
+
+
+def test_block_j_converges_on_poisson_like_diagonal_j():
+    # Section 4 notes that eq. J-blkdiag performs about as well as eq. J-diag
+    Q = synth.poisson2d(16)
+    b = synth.rhs(Q, synth.uniform(Q["n"], 5))
+    it_d = oracle.solve(Q, b, oracle.j_absrowsum(Q), maxit=5000, tol=1e-10)["iters"]
+    for bs in (2, 4, 16):
+        r = oracle.solve(Q, b, Jblk=oracle.j_blkdiag(Q, bs), maxit=5000, tol=1e-10)
+        assert r["converged"] and 0.5 * it_d <= r["iters"] <= 1.5 * it_d
