@@ -381,6 +381,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32_ir", "bf16_ir"])
     ap.add_argument("--form", default="auto", choices=["auto", "lazy", "stored", "delta"],
                     help="sweep form; auto = stored for fp64, lazy otherwise (the library's AUTO)")
+    ap.add_argument("--format", default="csr", choices=["csr", "stencil"],
+                    help="format of the timed context (the headline workload is CSR)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -430,7 +432,7 @@ def main():
 
     SWEEP = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED, "delta": aj.AJ_SWEEP_DELTA}
 
-    def make(precision, form, auto=False, fmt=None):
+    def make(precision, form, auto=False, fmt=None, **extra):
         # auto: leave the sweep form to the library (what a caller gets); the
         # format is CSR, as the workload states, unless fmt names another
         ctx = aj.Context(*tensors, n=n)
@@ -439,9 +441,9 @@ def main():
         fm = aj.AJ_FMT_CSR if fmt is None else fmt
         if args.fixed_iters:
             ctx.set(precision=precision, stop=aj.AJ_STOP_NONE, maxit=args.fixed_iters, sweep_form=sf,
-                    format=fm)
+                    format=fm, **extra)
         else:
-            ctx.set(precision=precision, tol=1e-8, maxit=200000, sweep_form=sf, format=fm)
+            ctx.set(precision=precision, tol=1e-8, maxit=200000, sweep_form=sf, format=fm, **extra)
         return ctx
 
     def barrier():
@@ -470,12 +472,14 @@ def main():
 
     # ---- headline: the chosen precision, K timed solves
     form = form_of(args.precision, args.form)
-    ctx = make(args.precision, form, auto=args.form == "auto")
+    FMT = {"csr": aj.AJ_FMT_CSR, "stencil": aj.AJ_FMT_STENCIL}
+    stn = args.format == "stencil"
+    ctx = make(args.precision, form, auto=args.form == "auto", fmt=FMT[args.format])
     if args.form == "auto" and args.precision != "fp64" and ctx.format()[0] == aj.AJ_FMT_SELL:
         form = "stored"  # the library's AUTO choice for SELL
     with Clocks(dev.index) as clk:
         ms, infos, launches = time_solves(ctx, args.steps, args.warmup)
-    B = algorithmic_bytes(n, nnz, args.precision)
+    B = algorithmic_bytes(n, nnz, args.precision, stencil=stn)
     iters = sum(i["iters"] for i in infos)
     ms, _, value = job_throughput(ms, B * iters, dist, dev)
     kernel_ms = sum(i["kernel_ms"] for i in infos)
@@ -494,16 +498,17 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": kern_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": kern_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind + " (burst copy)"}
-    ratio = TRAFFIC_PER_FORM_BYTES.get((args.precision, form))
-    B_form = algorithmic_bytes(n, nnz, args.precision, form)
+    ratio = None if stn else TRAFFIC_PER_FORM_BYTES.get((args.precision, form))
+    B_form = algorithmic_bytes(n, nnz, args.precision, form, stencil=stn)
     if ratio is not None:
         # per launch of the fused kernel: one per solve in FP64, one per inner solve otherwise
         per_launch_sweeps = sweeps / max(1, len(infos) * max(1, infos[-1]["outer"]))
         roof["traffic"] = ratio * B_form * per_launch_sweeps
         roof["traffic_per_form_bytes"] = ratio
         roof["traffic_source"] = TRAFFIC_SOURCE
-    roof["kernel"] = "aj_persistent_kernel<%s, sweep form %s, CSR, 1 RHS>" % (
-        {"fp64": "PolF64", "df64": "PolDF64", "fp32_ir": "PolF32", "bf16_ir": "PolB16"}[args.precision], form)
+    roof["kernel"] = "aj_persistent_kernel<%s, sweep form %s, %s, 1 RHS>" % (
+        {"fp64": "PolF64", "df64": "PolDF64", "fp32_ir": "PolF32", "bf16_ir": "PolB16"}[args.precision], form,
+        "stencil" if stn else "CSR")
     roof["bytes_per_iteration"] = B
     roof["form_bytes_per_iteration"] = B_form
     roof["kernel_ms_per_iteration"] = kernel_ms / max(iters, 1)
@@ -516,13 +521,14 @@ def main():
         "data": "synthetic",
         "config": {"workload": ("3-D 7-point Dirichlet Poisson 256^3 (n=16777216, nnz=117047296), "
                                 "FP64 CSR int32, x*~N(0,1) seed 2, b=Qx*; solve to rel. residual 1e-8")
-                   if args.workload == WORKLOAD and not args.fixed_iters else
+                   if args.workload == WORKLOAD and not args.fixed_iters and not stn else
                    "%s (n=%d, nnz=%d), %s" % (args.workload, n, nnz,
                                               "%d fixed iterations" % args.fixed_iters
                                               if args.fixed_iters else "solve to 1e-8"),
-                   "precision": args.precision, "sweep_form": form,
+                   "precision": args.precision, "sweep_form": form, "format": args.format,
                    "parallelism": "replicas x%d" % ws,
-                   "l2": "inputs larger than L2 (%.2f GB per sweep)" % (B / 1e9)},
+                   "l2": ("inputs larger than L2 (%.2f GB per sweep)" if B > 129e6 else
+                          "%.3f GB per sweep, within L2 (no flush between solves)") % (B / 1e9)},
         "time_to_tol_ms": ms / args.steps,
         "iterations": infos[-1]["iters"], "restarts": infos[-1]["restarts"],
         "relres": infos[-1]["relres"], "sweeps_per_solve": sweeps / len(infos),
@@ -566,6 +572,19 @@ def main():
                 "fused_hbm_frac": vb * it / (kms * 1e-3) / 1e9 / hbm_peak,
                 "kernel_ms_per_iteration": kms / max(it, 1)}
             del c
+        # the block-diagonal J (eq. J-blkdiag, blocks of 4 rows) on the same system, CSR
+        for p, fm in (("fp64", "delta"), ("fp32_ir", "lazy")):
+            c = make(p, fm, j_policy=aj.AJ_J_BLKDIAG, j_block=4)
+            vms, vinf, _ = time_solves(c, 2, 1)
+            vb = algorithmic_bytes(n, nnz, p) + 3 * n * (8 if p == "fp64" else 4)
+            it = sum(i["iters"] for i in vinf)
+            kms = sum(i["kernel_ms"] for i in vinf)
+            var[p + "/blkdiag4-" + fm] = {
+                "time_to_tol_ms": vms / 2, "iterations": vinf[-1]["iters"],
+                "outer": vinf[-1]["outer"], "relres": vinf[-1]["relres"],
+                "fused_GBps": vb * it / (kms * 1e-3) / 1e9,
+                "kernel_ms_per_iteration": kms / max(it, 1)}
+            del c
         line["variants"] = var
     # ---- end to end through the C ABI with pinned host buffers
     if not args.no_e2e:
@@ -583,7 +602,7 @@ def main():
             c.set_stream(stream)
             t1 = time.perf_counter()
             c.set(precision=args.precision, tol=1e-8, maxit=200000, sweep_form=SWEEP[form],
-                  format=aj.AJ_FMT_CSR)
+                  format=FMT[args.format])
             t2 = time.perf_counter()
             _, inf = c.solve(out=xh)
             t3 = time.perf_counter()

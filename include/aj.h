@@ -73,9 +73,20 @@ typedef struct {
   int on_device; /* 1: the three arrays (and b in aj_create) are device pointers */
 } aj_csr;
 
-/* Choice of the diagonal proximal matrix J (S = J - Q must be PSD). */
+/* Choice of the proximal matrix J (S = J - Q must be PSD). */
 #define AJ_J_ABSROWSUM 0   /* eq. J-diag: J_kk = Q_kk + sum_{j != k} |Q_kj| (the paper's default) */
 #define AJ_J_SCALED_DIAG 1 /* J = L D with L >= lambda_max(D^-1/2 Q D^-1/2) (Remark remark-preconditioner) */
+/* eq. J-blkdiag (Sec. 3): J = diag(J^{1,1}, ..., J^{s,s}) over blocks of
+ * j_block consecutive rows (2, 4 or 8; 1 is eq. J-diag), J^{ii} = Q^{ii} +
+ * (sum_{j != i} ||Q^{ij}||_2) I with each spectral norm computed exactly (up
+ * to rounding) at aj_set.  A block whose J^{ii} is singular (a singular part
+ * of Q wholly inside the block with no coupling, such as a small component
+ * of a graph Laplacian) takes eq. J-diag's diagonal, which keeps J
+ * invertible and S PSD.  The sweep applies each block's inverse: j_block
+ * n-vectors of J^{-1} per sweep instead of one.  Needs CSR or STENCIL
+ * storage in the caller's row order (AJ_EINVAL with AJ_FMT_SELL or
+ * AJ_REORDER_RCM; AUTO choices avoid both) and rows of at most 1024 entries. */
+#define AJ_J_BLKDIAG 2
 
 #define AJ_RESTART_NONE 0     /* Algorithm alg-apg: no restart (IsRestart = False) */
 #define AJ_RESTART_ADAPTIVE 1 /* Algorithm alg-apg-re restart rule (IsRestart = True) */
@@ -151,7 +162,7 @@ typedef struct {
 #define AJ_REORDER_RCM 2
 
 typedef struct {
-  int j_policy;          /* AJ_J_ABSROWSUM (default) | AJ_J_SCALED_DIAG */
+  int j_policy;          /* AJ_J_ABSROWSUM (default) | AJ_J_SCALED_DIAG | AJ_J_BLKDIAG */
   double L;              /* AJ_J_SCALED_DIAG step constant; 0 = estimate by power iteration */
   double L_margin;       /* estimate used is (1 + L_margin) * lambda_hat (default 0.02) */
   int restart;           /* AJ_RESTART_ADAPTIVE (default) | AJ_RESTART_NONE */
@@ -172,6 +183,7 @@ typedef struct {
   int sell_sigma;        /* AJ_FMT_SELL: sorting window sigma in rows (0 = 256) */
   int sell_lmax;         /* AJ_FMT_SELL: rows longer than this go to the warp-per-row bucket (0 = 64) */
   int reorder;           /* AJ_REORDER_AUTO (default) | AJ_REORDER_NONE | AJ_REORDER_RCM */
+  int j_block;           /* AJ_J_BLKDIAG: rows per block, 1, 2, 4 or 8 (0 = 4) */
 } aj_params;
 
 /* Per-solve report. */

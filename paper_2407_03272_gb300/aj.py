@@ -15,7 +15,7 @@ from . import build as _build
 AJ_OK, AJ_EINVAL, AJ_ENOMEM, AJ_ECUDA = 0, -1, -2, -3
 AJ_EMAXIT, AJ_EDIVERGED, AJ_ENONFINITE, AJ_ETIMEOUT, AJ_EBUSY = -4, -5, -6, -7, -8
 AJ_PENDING = 1
-AJ_J_ABSROWSUM, AJ_J_SCALED_DIAG = 0, 1
+AJ_J_ABSROWSUM, AJ_J_SCALED_DIAG, AJ_J_BLKDIAG = 0, 1, 2
 AJ_RESTART_NONE, AJ_RESTART_ADAPTIVE = 0, 1
 AJ_STOP_RELRES, AJ_STOP_OBJGAP, AJ_STOP_NONE = 0, 1, 2
 AJ_FP64, AJ_DF64, AJ_FP32_IR, AJ_BF16_IR = 0, 1, 2, 3
@@ -40,7 +40,8 @@ class aj_params(ctypes.Structure):
                 ("x0", ctypes.c_void_p), ("x0_on_device", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int64),
                 ("grid_ctas", ctypes.c_int), ("sweep_form", ctypes.c_int),
-                ("sell_sigma", ctypes.c_int), ("sell_lmax", ctypes.c_int), ("reorder", ctypes.c_int)]
+                ("sell_sigma", ctypes.c_int), ("sell_lmax", ctypes.c_int), ("reorder", ctypes.c_int),
+                ("j_block", ctypes.c_int)]
 
 
 class aj_info(ctypes.Structure):

@@ -214,6 +214,12 @@ struct aj_ctx {
   Workspace sws;
   int fmt = 0, sell_sigma = 0, sell_lmax = 0;
   int sdim = 0, sN = 0;  // stencil format (fmt = 2): dimensions and grid side
+  // block-diagonal J (eq. J-blkdiag, jblk > 1 rows per block): row k of each
+  // block's inverse in FP64 and in the iteration precision, rebuilt by aj_set
+  Workspace bws;
+  int jblk = 1;
+  double* jb64 = nullptr;
+  void* jbp = nullptr;
   double fill = 1.0;
   int nsell = 0, ntiles_sell = 0, nltiles = 0, nhuge = 0;
   int *d_perm = nullptr, *d_rlen = nullptr, *d_sptr = nullptr, *d_scol = nullptr;
@@ -266,6 +272,9 @@ struct aj_ctx {
 };
 
 static const int kResidLong = 32;
+// eq. J-blkdiag: longest row accepted (the setup thread of a block scans its
+// entries once per neighbouring block)
+static const int kBlkMaxRow = 1024;
 
 static aj_status cuda_fail(cudaError_t e) {
   (void)e;
@@ -327,6 +336,7 @@ extern "C" void aj_destroy(aj_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   c->sws.release();
+  c->bws.release();
   c->pws.release();
   c->ows.release();
   c->rws.release();
@@ -359,7 +369,7 @@ extern "C" aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ct
   if (Q->nnz > 0 && (!Q->col || !Q->val)) return AJ_EINVAL;
   aj_ctx* c = new aj_ctx();
   aj_params_default(&c->prm);
-  c->base.stream = c->pws.stream = c->sws.stream = c->ows.stream = c->rws.stream = &c->stream;
+  c->base.stream = c->pws.stream = c->sws.stream = c->ows.stream = c->rws.stream = c->bws.stream = &c->stream;
   cudaGetDevice(&c->dev);
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev);
   c->n = Q->n;
@@ -780,7 +790,11 @@ static aj_status choose_format(aj_ctx* c, const aj_params* p);
 // (Re)build everything that depends on the parameters.
 extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   if (!c || !p) return AJ_EINVAL;
-  if (p->j_policy != AJ_J_ABSROWSUM && p->j_policy != AJ_J_SCALED_DIAG) return AJ_EINVAL;
+  if (p->j_policy != AJ_J_ABSROWSUM && p->j_policy != AJ_J_SCALED_DIAG && p->j_policy != AJ_J_BLKDIAG)
+    return AJ_EINVAL;
+  const int jblk = p->j_policy != AJ_J_BLKDIAG ? 1 : p->j_block == 0 ? 4 : p->j_block;
+  if (p->j_policy == AJ_J_BLKDIAG && jblk != 1 && jblk != 2 && jblk != 4 && jblk != 8) return AJ_EINVAL;
+  if (jblk > 1 && (p->format == AJ_FMT_SELL || p->reorder == AJ_REORDER_RCM)) return AJ_EINVAL;
   if (p->restart != AJ_RESTART_NONE && p->restart != AJ_RESTART_ADAPTIVE) return AJ_EINVAL;
   if (p->K0 < 2 || p->maxit < 0 || !(p->tol >= 0.0) || p->L < 0.0 || !(p->L_margin >= 0.0))
     return AJ_EINVAL;
@@ -807,7 +821,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   // --- row order (before anything is derived from the matrix)
   {
     const int was = c->ordered;
-    aj_status st = choose_order(c, p->reorder);
+    aj_status st = choose_order(c, jblk > 1 ? AJ_REORDER_NONE : p->reorder);
     if (st != AJ_OK) return st;
     if (was != c->ordered) c->sws.release(), c->fmt = 0;
   }
@@ -823,10 +837,33 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   c->L_used = L;
   if (n > 0) {
     k_jinv<<<grid1d(n), kSetupThreads, 0, s>>>(n, c->rp, c->ci, c->val64, c->diag,
-                                               p->j_policy == AJ_J_ABSROWSUM ? 0 : 1, L, c->jinv64);
+                                               p->j_policy == AJ_J_SCALED_DIAG ? 1 : 0, L, c->jinv64);
     counted();
   }
   CK(cudaGetLastError());
+  // --- eq. J-blkdiag: the inverse of every block (eq. J-diag's inverse in
+  // jinv64 stands in for blocks whose J^{ii} is singular)
+  c->bws.release();
+  c->jb64 = nullptr;
+  c->jbp = nullptr;
+  c->jblk = 1;
+  if (jblk > 1 && n > 0) {
+    if (c->maxlen > kBlkMaxRow) return AJ_EINVAL;
+    const long long nblk = ((long long)n + jblk - 1) / jblk;
+    c->jb64 = (double*)c->bws.alloc((size_t)(nblk * jblk * jblk + 16) * 8);
+    if (!c->jb64) return AJ_ENOMEM;
+    CK(cudaMemsetAsync(c->err, 0, 4, s));
+    k_jblk<<<(unsigned)std::min<long long>((nblk + 127) / 128, 65535), 128, 0, s>>>(
+        n, jblk, c->rp, c->ci, c->val64, c->jinv64, c->jb64, c->err);
+    counted();
+    int bad = 0;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&bad, c->err, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemsetAsync(c->err, 0, 4, s));
+    CK(cudaStreamSynchronize(s));
+    if (bad) return AJ_EINVAL;
+    c->jblk = jblk;
+  }
   // --- precision-specific arrays
   const int pol = p->precision;
   if (pol != old_pol) {
@@ -914,6 +951,13 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
         k_to_dw<<<grid1d(n), kSetupThreads, 0, s>>>(n, c->jinv64, 1.0 / c->sQ, (float2*)c->jinvp);
         counted();
       }
+      if (c->jblk > 1) {
+        const long long nb = ((long long)n + c->jblk - 1) / c->jblk * c->jblk * c->jblk;
+        c->jbp = c->bws.alloc((size_t)(nb + 16) * sizeof(float2));
+        if (!c->jbp) return AJ_ENOMEM;
+        k_to_dw<<<grid1d(nb), kSetupThreads, 0, s>>>(nb, c->jb64, 1.0 / c->sQ, (float2*)c->jbp);
+        counted();
+      }
     } else if (pol == AJ_FP32_IR) {
       if (nnz > 0) {
         k_to_f32<<<grid1d(nnz), kSetupThreads, 0, s>>>(nnz, c->val64, c->sQ, (float*)c->valp);
@@ -936,6 +980,15 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     CK(cudaGetLastError());
   } else {
     c->sQ = 1.0;
+  }
+  if (pol != AJ_FP64 && pol != AJ_DF64 && c->jblk > 1) {
+    // FP32 and BF16 values: J^{-1} in FP32
+    const long long nb = ((long long)n + c->jblk - 1) / c->jblk * c->jblk * c->jblk;
+    c->jbp = c->bws.alloc((size_t)(nb + 16) * sizeof(float));
+    if (!c->jbp) return AJ_ENOMEM;
+    k_to_f32<<<grid1d(nb), kSetupThreads, 0, s>>>(nb, c->jb64, 1.0 / c->sQ, (float*)c->jbp);
+    counted();
+    CK(cudaGetLastError());
   }
   CK(cudaStreamSynchronize(s));
   aj_status fe = choose_format(c, p);
@@ -1067,6 +1120,8 @@ static IterLaunch make_launch(aj_ctx* c, const void* bvec, long long maxit, int 
   }
   L.b = bvec;
   L.jinv = c->pol == AJ_FP64 ? (const void*)c->jinv64 : c->jinvp;
+  if (c->jblk > 1) L.jinv = c->pol == AJ_FP64 ? (const void*)c->jb64 : c->jbp;
+  L.jblk = c->jblk;
   for (int k = 0; k < 3; k++) L.x[k] = c->x[k];
   for (int k = 0; k < 2; k++) L.u[k] = c->u[k];
   L.dl = c->dl;
@@ -1339,6 +1394,8 @@ static aj_status choose_format(aj_ctx* c, const aj_params* p) {
     }
     if (p->format == AJ_FMT_STENCIL) return AJ_EINVAL;
   }
+  // a block-diagonal J needs each block's rows in adjacent lanes: CSR order
+  if (c->jblk > 1) return AJ_OK;
   // AUTO: CSR unless the rows are long-tailed and the system is large
   const int n = (int)c->n;
   if (n < 65536) return AJ_OK;

@@ -406,6 +406,8 @@ struct IterArgs {
   int sdiag_at, soff_at;      // stencil: entries of val holding the diagonal and the off-diagonal value
   unsigned long long smag;    // stencil: q / N = (q * smag) >> sshift for 0 <= q < 2^31
   int sshift;
+  int jblk;                   // rows per block of J (1: diagonal J; 2, 4, 8: eq. J-blkdiag,
+                              // jinv then holds row k of each block's inverse at jinv[k * jblk])
   int nsell;                  // SELL: rows in the sliced part
   int ntiles_sell;            // SELL: tiles of the sliced part
   int nltiles;                // SELL: tiles of long rows
@@ -795,6 +797,52 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
         long_row_sums<P, QX>(a, st[k], nr, k, lrs, lre, tx, tp);
         if (lane == src + k) { sx = tx; sp = tp; }
       }
+    }
+    if (ANY && a.jblk > 1) {
+      // eq. J-blkdiag: x^t_i = y^t_i - sum_m (J^{bb})^{-1}_{im} g_m over the rows m
+      // of i's block, which sit in lanes of this warp (blocks align with tiles
+      // and jblk << lg <= 32); every lane takes part in the exchange
+      const int jb = a.jblk;
+      const bool upd = valid && active;
+      const size_t e = (size_t)i * nr + r;
+      S g = P::zero(), yi = P::zero(), xi = P::zero();
+      if (upd) {
+        xi = P::ldg(xc + e);
+        const S bi = P::ldr(a.b + e);
+        const S g0 = P::sub(sx, bi);
+        P::acc_prod(acc[2], g0, g0);
+        if (want_obj) {
+          P::acc_prod(acc[3], xi, sx);
+          P::acc_prod(acc[4], bi, xi);
+        }
+        if (QX) P::stx(uc + e, sx);
+        if (same) {
+          g = g0;
+          yi = xi;
+        } else {
+          const S spi = QX ? P::ldx(up + e) : sp;
+          g = P::fma_(beta, P::sub(sx, spi), g0);
+          yi = DL ? P::fma_(beta, P::ldx(a.dl + e), xi) : P::fma_(beta, P::sub(xi, P::ldx(xp + e)), xi);
+        }
+      }
+      if (!compute_x) continue;
+      const int src0 = ((((int)threadIdx.x >> lg) & ~(jb - 1)) << lg | r) & 31;
+      const X* jr = a.jinv + (size_t)i * jb;
+      S corr = P::zero();
+#pragma unroll
+      for (int m = 0; m < 8; m++) {
+        if (m >= jb) break;
+        const S gm = P::shfl(g, src0 + (m << lg));
+        if (upd) corr = P::fma_(P::ldr(jr + m), gm, corr);
+      }
+      if (upd) {
+        const S xnew = P::sub(yi, corr);
+        const S dx = P::sub(xnew, xi);
+        P::stx(xn + e, xnew);
+        if (DL) P::stx(a.dl + e, dx);
+        P::acc_prod(acc[0], g, dx);
+      }
+      continue;
     }
     if (!valid || !active) continue;
     const S ji = P::ldr(a.jinv + i);

@@ -30,6 +30,7 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
   a.soff_at = L.soff_at;
   a.smag = L.smag;
   a.sshift = L.sshift;
+  a.jblk = L.jblk < 1 ? 1 : L.jblk;
   a.nsell = L.nsell;
   a.ntiles_sell = L.ntiles_sell;
   a.nltiles = L.nltiles;
@@ -116,7 +117,7 @@ template <class P, bool MULTI>
 static cudaError_t launch_m(const IterLaunch& L, int grid, cudaStream_t s) {
   IterArgs<P> a = typed_args<P>(L);
   void* args[] = {&a};
-  const void* k = persistent_fn<P, MULTI>(L.qx, L.fmt != 0);
+  const void* k = persistent_fn<P, MULTI>(L.qx, L.fmt != 0 || L.jblk > 1);
   if (!k) return cudaErrorInvalidValue;
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
 }

@@ -19,6 +19,7 @@ struct IterLaunch {
   int sdim, sN, sdiag_at, soff_at;  // stencil: 2 or 3 dimensions, grid side, entries of val
   unsigned long long smag;          // stencil: q / N = (q * smag) >> sshift for 0 <= q < 2^31
   int sshift;
+  int jblk;                         // rows per block of J (1: diagonal)
   int nsell;
   int ntiles_sell;
   int nltiles;

@@ -5,6 +5,7 @@
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <stdint.h>
 
 #include "aj_core.cuh"
@@ -277,6 +278,147 @@ __global__ void k_max_row_len(int n, const int* rp, int* out) {
     m = max(m, rp[i + 1] - rp[i]);
   for (int k = 16; k >= 1; k >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, k));
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
+}
+
+// Eigenvalues of the symmetric m x m matrix B (m <= 8), left on its diagonal:
+// cyclic Jacobi rotations (Jacobi 1846; Golub and Van Loan, Matrix
+// Computations, Sec. 8.5), each zeroing B_pq by B <- R^T B R with
+// tau = (B_qq - B_pp) / (2 B_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
+// c = 1 / sqrt(1 + t^2), s = t c; until the off-diagonal mass is below 1e-32
+// of the total (at most 60 sweeps).
+__device__ void jb_jacobi_eig(double (&B)[8][8], int m) {
+  for (int sw = 0; sw < 60; sw++) {
+    double off = 0.0, tot = 0.0;
+    for (int p = 0; p < m; p++)
+      for (int q = 0; q < m; q++) {
+        const double v = B[p][q] * B[p][q];
+        tot += v;
+        if (p != q) off += v;
+      }
+    if (off <= 1e-32 * tot) return;
+    for (int p = 0; p < m; p++)
+      for (int q = p + 1; q < m; q++) {
+        const double bpq = B[p][q];
+        if (bpq == 0.0) continue;
+        const double tau = (B[q][q] - B[p][p]) / (2.0 * bpq);
+        const double t = fabs(tau) > 1e100 ? 0.5 / tau
+                                           : (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+        for (int k = 0; k < m; k++) {
+          const double bkp = B[k][p], bkq = B[k][q];
+          B[k][p] = c * bkp - sn * bkq;
+          B[k][q] = sn * bkp + c * bkq;
+        }
+        for (int k = 0; k < m; k++) {
+          const double bpk = B[p][k], bqk = B[q][k];
+          B[p][k] = c * bpk - sn * bqk;
+          B[q][k] = sn * bpk + c * bqk;
+        }
+      }
+  }
+}
+
+// eq. J-blkdiag for blocks of bs consecutive rows (bs <= 8), one thread per
+// block ib (rows r0 .. r0 + nb - 1):
+//   J = Q^{ib,ib} + (sum over column blocks jb != ib, ascending, ||Q^{ib,jb}||_2) I,
+// ||A||_2 = sqrt(lambda_max(A^T A)).  A block whose J has its smallest
+// eigenvalue at most 1e-12 of its largest diagonal entry (a singular part of
+// Q wholly inside the block, with no coupling) takes eq. J-diag's diagonal,
+// whose inverse jd holds.  Row k of J^{-1} (by the Cholesky factor J = L L^T:
+// column m of J^{-1} solves L y = e_m, L^T z = y) goes to out[(r0 + k) bs + m];
+// the last block's rows beyond n get identity rows.  *bad = 1 if J is not
+// positive definite.
+__global__ void k_jblk(int n, int bs, const int* rp, const int* ci, const double* val, const double* jd,
+                       double* out, int* bad) {
+  const long long nblk = ((long long)n + bs - 1) / bs;
+  for (long long ib = (long long)blockIdx.x * blockDim.x + threadIdx.x; ib < nblk;
+       ib += (long long)gridDim.x * blockDim.x) {
+    const int r0 = (int)(ib * bs);
+    const int nb = min(bs, n - r0);
+    double J[8][8], A[8][8];
+    for (int k = 0; k < 8; k++)
+      for (int m = 0; m < 8; m++) J[k][m] = 0.0;
+    for (int k = 0; k < nb; k++)
+      for (int q = rp[r0 + k]; q < rp[r0 + k + 1]; q++)
+        if (ci[q] / bs == ib) J[k][ci[q] - r0] += val[q];
+    double csum = 0.0;
+    long long prev = -1;
+    for (;;) {
+      long long nxt = LLONG_MAX;
+      for (int k = 0; k < nb; k++)
+        for (int q = rp[r0 + k]; q < rp[r0 + k + 1]; q++) {
+          const long long jb = ci[q] / bs;
+          if (jb != ib && jb > prev && jb < nxt) nxt = jb;
+        }
+      if (nxt == LLONG_MAX) break;
+      for (int k = 0; k < 8; k++)
+        for (int m = 0; m < 8; m++) A[k][m] = 0.0;
+      for (int k = 0; k < nb; k++)
+        for (int q = rp[r0 + k]; q < rp[r0 + k + 1]; q++)
+          if (ci[q] / bs == nxt) A[k][ci[q] - (int)(nxt * bs)] += val[q];
+      double B[8][8];
+      for (int p = 0; p < 8; p++)
+        for (int m = 0; m < 8; m++) {
+          double v = 0.0;
+          for (int k = 0; k < nb; k++) v += A[k][p] * A[k][m];
+          B[p][m] = v;
+        }
+      jb_jacobi_eig(B, bs);
+      double lmax = 0.0;
+      for (int p = 0; p < bs; p++) lmax = fmax(lmax, B[p][p]);
+      csum += sqrt(lmax);
+      prev = nxt;
+    }
+    for (int k = 0; k < nb; k++) J[k][k] += csum;
+    // singular J: eq. J-diag for this block
+    double E[8][8], dmax = 0.0;
+    for (int k = 0; k < 8; k++)
+      for (int m = 0; m < 8; m++) E[k][m] = J[k][m];
+    for (int k = 0; k < nb; k++) dmax = fmax(dmax, J[k][k]);
+    jb_jacobi_eig(E, nb);
+    double lmin = 1e300;
+    for (int k = 0; k < nb; k++) lmin = fmin(lmin, E[k][k]);
+    double* o = out + (size_t)r0 * bs;
+    if (!(lmin > 1e-12 * dmax)) {
+      for (int k = 0; k < bs; k++)
+        for (int m = 0; m < bs; m++) o[k * bs + m] = (k == m) ? (k < nb ? jd[r0 + k] : 1.0) : 0.0;
+      continue;
+    }
+    // Cholesky J = L L^T (rows k >= nb are left out), then the columns of J^{-1}
+    double L[8][8];
+    bool ok = true;
+    for (int j = 0; j < nb && ok; j++) {
+      double d = J[j][j];
+      for (int k = 0; k < j; k++) d -= L[j][k] * L[j][k];
+      ok = d > 0.0;
+      if (!ok) break;
+      L[j][j] = sqrt(d);
+      for (int i = j + 1; i < nb; i++) {
+        double v = J[i][j];
+        for (int k = 0; k < j; k++) v -= L[i][k] * L[j][k];
+        L[i][j] = v / L[j][j];
+      }
+    }
+    if (!ok) {
+      *bad = 1;
+      continue;
+    }
+    for (int mcol = 0; mcol < bs; mcol++) {
+      double z[8];
+      for (int i = 0; i < nb; i++) {
+        double v = (i == mcol) ? 1.0 : 0.0;
+        for (int k = 0; k < i; k++) v -= L[i][k] * z[k];
+        z[i] = v / L[i][i];
+      }
+      for (int i = nb - 1; i >= 0; i--) {
+        double v = z[i];
+        for (int k = i + 1; k < nb; k++) v -= L[k][i] * z[k];
+        z[i] = v / L[i][i];
+      }
+      for (int k = 0; k < bs; k++)
+        o[k * bs + mcol] = k < nb ? (mcol < nb ? z[k] : 0.0) : (k == mcol ? 1.0 : 0.0);
+    }
+  }
 }
 
 // Whether Q is a constant-coefficient (2*dim+1)-point stencil on an N^dim grid
