@@ -609,14 +609,16 @@ __host__ __device__ constexpr int row_unroll(bool qx) {
 // terms.  `compute_x` is false on a residual-only sweep (no x^s is formed).
 // Reduction slots (per lane, for the lane's right-hand side): 0 d, 2 rr,
 // 3 <x, Qx> and 4 <b, x> (objective stop only); slot 1 is unused.
-// ANY: the kernel handles both formats (runtime a.fmt); otherwise CSR only,
-// which keeps the SELL code and its registers out of the CSR kernel.  MULTI:
+// FM: the formats the instantiation reads -- 0 CSR only, which keeps the
+// other formats' code and registers out of the CSR kernel; 1 any (runtime
+// a.fmt: CSR, SELL or stencil; needed by the block-diagonal J on CSR and by
+// the batched kernel); 2 the stencil rows alone.  MULTI:
 // nrhs and the lanes per row come from the arguments; otherwise one.
 // SF: sweep form -- 0 lazy, 1 stored, 2 stored with the difference
 // delta = x^{s-1} - x^{s-2} kept in a.dl (y = x + beta delta costs one
 // instruction instead of two; delta is the same rounded difference the
 // update computes anyway for the restart test).
-template <class P, int SF, bool ANY, bool MULTI>
+template <class P, int SF, int FM, bool MULTI>
 __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, bool compute_x,
                                       bool want_obj, typename P::A (&acc)[kNRed], int cta,
                                       int ncta) {
@@ -641,11 +643,12 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
   const bool active = lane_on && me.done == 0;
   const S beta = P::coef(me.beta);
   const int lane = threadIdx.x & 31;
-  const bool sell = ANY && a.fmt == 1;
+  constexpr bool ANY = FM != 0;
+  const bool sell = FM == 1 && a.fmt == 1;
   // stencil: the rows of a constant-coefficient Dirichlet Laplacian in natural
   // order, their entries known without loading them (same values, same
   // ascending column order as in CSR, so the sums are the CSR sums bit for bit)
-  const bool stn = ANY && a.fmt == 2;
+  const bool stn = FM == 2 || (FM == 1 && a.fmt == 2);
   V s_diag = P::vzero(), s_off = P::vzero();
   if (stn) {
     s_diag = P::ldv(a.val + a.sdiag_at);
@@ -786,7 +789,7 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
     }
     // long rows: the whole warp sums each one for every right-hand side; the
     // lane of right-hand side k of the row's group takes sum k
-    unsigned lm = __ballot_sync(0xffffffffu, is_long && r == 0);
+    unsigned lm = FM == 2 ? 0u : __ballot_sync(0xffffffffu, is_long && r == 0);
     while (lm) {
       const int src = __ffs(lm) - 1;
       lm &= lm - 1;
@@ -1011,7 +1014,7 @@ __device__ __forceinline__ void grid_totals(const double* part, int ncta, int nr
 // arrival count so far and `sw` the sweep counter that parity-buffers the
 // partials; both carry over between systems that reuse the same barrier.
 // Returns false when a barrier gave up (error already recorded in *a.err).
-template <class P, int SF, bool ANY, bool MULTI>
+template <class P, int SF, int FM, bool MULTI>
 __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, int cta, int ncta,
                                           unsigned long long& target, long long& sw) {
   using A = typename P::A;
@@ -1031,7 +1034,7 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, i
     A acc[kNRed];
 #pragma unroll
     for (int k = 0; k < kNRed; k++) acc_zero(acc[k]);
-    sweep<P, SF, ANY, MULTI>(a, sm.st, compute_x, want_obj, acc, cta, ncta);
+    sweep<P, SF, FM, MULTI>(a, sm.st, compute_x, want_obj, acc, cta, ncta);
     // CTA partials -> global (parity-buffered by sweep)
     double* part = a.partials + (size_t)(sw & 1) * ncta * nr * kNRed;
 #pragma unroll
@@ -1069,10 +1072,10 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, i
 }
 
 // The persistent fused AJ kernel for one system.  Launch cooperatively with
-// kThreads threads per CTA; every CTA of the grid works on the system.  ANY
-// selects the instantiation that also reads the SELL-C-sigma format, MULTI
-// the one for several right-hand sides.
-template <class P, int SF, bool ANY, bool MULTI>
+// kThreads threads per CTA; every CTA of the grid works on the system.  FM
+// selects the formats the instantiation reads (see sweep), MULTI the one for
+// several right-hand sides.
+template <class P, int SF, int FM, bool MULTI>
 __global__ void __launch_bounds__(kThreads, MULTI ? P::kMinBlocksMulti : P::kMinBlocks) aj_persistent_kernel(IterArgs<P> a) {
   __shared__ SolveSmem sm;
   const int nr = MULTI ? a.nrhs : 1;
@@ -1080,7 +1083,7 @@ __global__ void __launch_bounds__(kThreads, MULTI ? P::kMinBlocksMulti : P::kMin
   __syncthreads();
   unsigned long long target = 0;
   long long sw = 0;
-  if (!run_solve<P, SF, ANY, MULTI>(a, sm, blockIdx.x, gridDim.x, target, sw)) return;
+  if (!run_solve<P, SF, FM, MULTI>(a, sm, blockIdx.x, gridDim.x, target, sw)) return;
   if (blockIdx.x == 0 && (int)threadIdx.x < nr) a.state[threadIdx.x] = sm.st[threadIdx.x];
 }
 
@@ -1213,7 +1216,7 @@ __global__ void __launch_bounds__(kThreads, P::kMinBlocksMulti) aj_lockstep_kern
       A acc[kNRed];
 #pragma unroll
       for (int q = 0; q < kNRed; q++) acc_zero(acc[q]);
-      sweep<P, SF, true, true>(a, sm.st, compute_x, want_obj, acc, v, V);
+      sweep<P, SF, 1, true>(a, sm.st, compute_x, want_obj, acc, v, V);
       double* part = a.partials + (size_t)(k & 1) * V * nr * kNRed;
 #pragma unroll
       for (int q = 0; q < kNRed; q++) {

@@ -100,36 +100,49 @@ static int occ_of(const void* k) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, 0) == cudaSuccess ? nb : 0;
 }
 
-// The persistent kernel for sweep form sf and format (CSR only or any).
+// The persistent kernel for sweep form sf and formats fm (0 CSR only, 1
+// any, 2 stencil only).
+template <class P, int SF, bool MULTI>
+static const void* persistent_fm(int fm) {
+  return fm == 0 ? (const void*)aj_persistent_kernel<P, SF, 0, MULTI>
+         : fm == 1 ? (const void*)aj_persistent_kernel<P, SF, 1, MULTI>
+                   : (const void*)aj_persistent_kernel<P, SF, 2, MULTI>;
+}
+
 template <class P, bool MULTI>
-static const void* persistent_fn(int sf, bool any) {
-  if (sf == 0) return any ? (const void*)aj_persistent_kernel<P, 0, true, MULTI>
-                          : (const void*)aj_persistent_kernel<P, 0, false, MULTI>;
-  if (sf == 1) return any ? (const void*)aj_persistent_kernel<P, 1, true, MULTI>
-                          : (const void*)aj_persistent_kernel<P, 1, false, MULTI>;
+static const void* persistent_fn(int sf, int fm) {
+  if (sf == 0) return persistent_fm<P, 0, MULTI>(fm);
+  if (sf == 1) return persistent_fm<P, 1, MULTI>(fm);
   if constexpr (kHasDelta<P>)
-    if (sf == 2) return any ? (const void*)aj_persistent_kernel<P, 2, true, MULTI>
-                            : (const void*)aj_persistent_kernel<P, 2, false, MULTI>;
+    if (sf == 2) return persistent_fm<P, 2, MULTI>(fm);
   return nullptr;
+}
+
+// The instantiation a launch needs: the stencil rows alone, CSR alone, or any.
+static int launch_fm(const IterLaunch& L) {
+  return L.fmt == 2 ? 2 : (L.fmt == 1 || L.jblk > 1) ? 1 : 0;
 }
 
 template <class P, bool MULTI>
 static cudaError_t launch_m(const IterLaunch& L, int grid, cudaStream_t s) {
   IterArgs<P> a = typed_args<P>(L);
   void* args[] = {&a};
-  const void* k = persistent_fn<P, MULTI>(L.qx, L.fmt != 0 || L.jblk > 1);
+  const void* k = persistent_fn<P, MULTI>(L.qx, launch_fm(L));
   if (!k) return cudaErrorInvalidValue;
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
 }
 
-// Co-resident CTAs of the persistent kernel: the smaller of its CSR-only and
-// any-format instantiations, so that a grid sized by it fits either.
+// Co-resident CTAs of the persistent kernel: the smallest over its format
+// instantiations, so that a grid sized by it fits any of them.
 template <class P, bool MULTI>
 static int occ_m(int qx) {
-  const void* k0 = persistent_fn<P, MULTI>(qx, false);
-  const void* k1 = persistent_fn<P, MULTI>(qx, true);
-  if (!k0 || !k1) return 0;
-  return std::min(occ_of(k0), occ_of(k1));
+  int occ = 1 << 30;
+  for (int fm = 0; fm < 3; fm++) {
+    const void* k = persistent_fn<P, MULTI>(qx, fm);
+    if (!k) return 0;
+    occ = std::min(occ, occ_of(k));
+  }
+  return occ;
 }
 
 cudaError_t AJ_CAT(launch_persistent_, AJ_SUFFIX)(int nrhs, const IterLaunch& L, int grid,
