@@ -321,6 +321,38 @@ def bench_batched(aj, torch, dev, stream, count, pool):
     return res
 
 
+def bench_sdd(aj, torch, dev, stream):
+    """Section 4.1's comparison on Q = (n + 1) I - 1 1^T, b = 1 (x* = 1, f* = -n/2),
+    n = 1000 .. 6000: classical Jacobi, weighted Jacobi with omega_opt = 2n / (n + 2),
+    Algorithm alg-apg and Algorithm alg-apg-re, each to a relative objective gap of
+    1e-10 within 5000 iterations, on the same fused kernel."""
+    import synth
+    out = {}
+    for n in (1000, 2000, 3000, 4000, 5000, 6000):
+        Q = synth.sdd(n)
+        t = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (Q["row_ptr"], Q["col"], Q["val"])]
+        b = torch.ones(n, dtype=torch.float64, device=dev)
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        om = 2.0 * n / (n + 2.0)
+        res = {}
+        for name, kw in (("jacobi", dict(j_policy=aj.AJ_J_SCALED_DIAG, L=1.0, momentum=0,
+                                         restart=aj.AJ_RESTART_NONE)),
+                         ("weighted_jacobi", dict(j_policy=aj.AJ_J_SCALED_DIAG, L=1.0 / om, momentum=0,
+                                                  restart=aj.AJ_RESTART_NONE)),
+                         ("alg_apg", dict(restart=aj.AJ_RESTART_NONE)),
+                         ("alg_apg_re", dict())):
+            c = aj.Context(*t, b, n=n)
+            c.set_stream(stream)
+            c.set(stop=aj.AJ_STOP_OBJGAP, tol=1e-10, fstar=-n / 2.0, maxit=5000, **kw)
+            _, info = c.solve(out=x)
+            res[name] = {"iterations": info["iters"], "converged": info["status"] == aj.AJ_OK,
+                         "objgap": info["objgap"], "ms": info["ms"]}
+            c.close()
+        out[str(n)] = res
+        del t
+    return out
+
+
 def bench_served(aj, torch, count, pool, rate, budget_gb):
     """Continuous-batching server under Poisson arrivals: the offered rate,
     then 0.8x the capacity measured there.  Latency = submission to result."""
@@ -392,6 +424,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-sdd", action="store_true")
     ap.add_argument("--graph-n", type=int, default=8388608)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--served-count", type=int, default=300)
@@ -626,6 +659,8 @@ def main():
             line["batched"] = bench_batched(aj, torch, dev, stream, args.batch_count, 48)
         if not args.no_served:
             line["served"] = bench_served(aj, torch, args.served_count, 48, args.served_rate, 120.0)
+        if not args.no_sdd:
+            line["sdd_comparison"] = bench_sdd(aj, torch, dev, stream)
     # ---- CPU oracle on a bounded sample (rank 0, N = 1)
     if not args.no_cpu and ws == 1 and rank == 0:
         T = args.cpu_iters

@@ -787,6 +787,19 @@ extern "C" aj_status aj_get_order(aj_ctx* c, int* reordered, double* span_before
 
 static aj_status choose_format(aj_ctx* c, const aj_params* p);
 
+// The persistent grid for the current format and sweep form: one CTA per
+// tile up to the co-resident limit (SELL counts its sliced, long-row and
+// huge-row tiles), or the caller's grid_ctas.
+static void size_grid(aj_ctx* c) {
+  const int bps = std::max(1, persistent_blocks_per_sm(kernel_pol(c->pol), c->nrhs, c->qx));
+  const long long rpt = kThreads >> lanes_log2(c->nrhs);
+  const long long ntiles = c->fmt == 1 ? (long long)c->ntiles_sell + c->nltiles + c->nhuge
+                                       : (c->n + rpt - 1) / rpt;
+  long long g = std::min<long long>((long long)bps * c->sm_count, std::max<long long>(1, ntiles));
+  if (c->prm.grid_ctas > 0) g = std::min<long long>(c->prm.grid_ctas, (long long)bps * c->sm_count);
+  c->grid = (int)std::max<long long>(1, g);
+}
+
 // (Re)build everything that depends on the parameters.
 extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   if (!c || !p) return AJ_EINVAL;
@@ -918,16 +931,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
           : p->sweep_form == AJ_SWEEP_STORED ? 1
           : p->sweep_form == AJ_SWEEP_DELTA  ? 2
           : (p->precision == AJ_FP64 ? 2 : 1);
-  {
-    const int kp = kernel_pol(pol);
-    const int bps = std::max(1, persistent_blocks_per_sm(kp, nrhs, c->qx));
-    const int maxg = bps * c->sm_count;
-    const int rpt = kThreads >> lanes_log2(nrhs);  // rows per tile
-    const int ntiles = std::max(1, (int)((n + rpt - 1) / rpt));
-    int g = std::min(maxg, ntiles);
-    if (p->grid_ctas > 0) g = std::min(p->grid_ctas, maxg);
-    c->grid = std::max(1, g);
-  }
+  size_grid(c);
   // --- scaled copies for the non-FP64 policies (powers of two: exact)
   if (pol != AJ_FP64) {
     double vmax = 0.0;
@@ -998,15 +1002,8 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   // (irregular rows: one random gather per entry instead of two), lazy for
   // the other precisions on CSR, where the second row sum gathers from the
   // same cached lines and saves two n-vectors of traffic
-  if (p->sweep_form == AJ_SWEEP_AUTO && p->precision != AJ_FP64 && c->fmt != 1) {
-    c->qx = 0;
-    const int bps = std::max(1, persistent_blocks_per_sm(kernel_pol(pol), nrhs, c->qx));
-    const int rpt = kThreads >> lanes_log2(nrhs);
-    const int ntiles = std::max(1, (int)((n + rpt - 1) / rpt));
-    int g = std::min(bps * c->sm_count, ntiles);
-    if (p->grid_ctas > 0) g = std::min(p->grid_ctas, bps * c->sm_count);
-    c->grid = std::max(1, g);
-  }
+  if (p->sweep_form == AJ_SWEEP_AUTO && p->precision != AJ_FP64 && c->fmt != 1) c->qx = 0;
+  size_grid(c);
   return AJ_OK;
 }
 
@@ -1232,11 +1229,19 @@ static aj_status build_sell(aj_ctx* c, int sigma, int lmax) {
   }
   sptr[nslices] = (int)tot;
   std::vector<int> ltp(1, 0);
+  // long-row tiles hold at most kLongTileEntries entries, fewer when that
+  // would leave fewer tiles than SMs (a few rows of many entries): then
+  // about eight tiles per SM, at least 4096 entries each
+  long long long_total = 0;
+  for (int r : lng) long_total += len(r);
+  long long tile_cap = kLongTileEntries;
+  if (long_total / kLongTileEntries < c->sm_count)
+    tile_cap = std::max<long long>(4096, long_total / (8ll * c->sm_count));
   long long acc = 0, long_entries = 0;
   int cnt = 0;
   for (int j = 0; j < (int)lng.size(); j++) {
     const int l = len(lng[j]);
-    if (cnt > 0 && (cnt == rpt || acc + l > kLongTileEntries)) {
+    if (cnt > 0 && (cnt == rpt || acc + l > tile_cap)) {
       ltp.push_back(j);
       acc = 0;
       cnt = 0;
@@ -1296,6 +1301,7 @@ static aj_status build_sell(aj_ctx* c, int sigma, int lmax) {
 // Device time per sweep of the current format: a few sweeps from x = 0 with
 // b = 0 (every load and multiply-add still runs).
 static aj_status time_sweeps(aj_ctx* c, double* ms_per_sweep) {
+  size_grid(c);
   const long long m = (long long)c->n * c->nrhs;
   cudaStream_t s = c->stream;
   const void* bvec = c->pol == AJ_FP64 ? (const void*)c->tmp64 : c->bp;
@@ -1396,8 +1402,17 @@ static aj_status choose_format(aj_ctx* c, const aj_params* p) {
   }
   // a block-diagonal J needs each block's rows in adjacent lanes: CSR order
   if (c->jblk > 1) return AJ_OK;
-  // AUTO: CSR unless the rows are long-tailed and the system is large
   const int n = (int)c->n;
+  // few rows of many entries (a dense or nearly dense Q): CSR runs one CTA per
+  // tile of rows, too few to fill the GPU; SELL's long-row bucket cuts such
+  // rows into tiles of at most kLongTileEntries entries
+  {
+    const long long rpt = kThreads >> lanes_log2(c->nrhs);
+    const long long ntiles = ((long long)n + rpt - 1) / rpt;
+    if (c->maxlen > kResidLong && ntiles < c->sm_count && c->nnz >= (long long)c->sm_count * kLongTileEntries / 8)
+      return build_sell(c, sig, lmx);
+  }
+  // AUTO: CSR unless the rows are long-tailed and the system is large
   if (n < 65536) return AJ_OK;
   if (c->maxlen <= 2.0 * ((double)c->nnz / n) + 8.0) return AJ_OK;  // near-uniform rows
   std::vector<int> rp((size_t)n + 1);
