@@ -52,6 +52,10 @@ def lib():
         L.orc_aj_solve.argtypes = [ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.POINTER(_Info),
                                    ctypes.POINTER(_Trace)]
         L.orc_aj_solve.restype = ctypes.c_int
+        L.orc_pcg_solve.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5 + [ctypes.c_int64, ctypes.c_double,
+                                                                              ctypes.c_void_p, ctypes.c_void_p,
+                                                                              ctypes.c_void_p]
+        L.orc_pcg_solve.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -133,6 +137,24 @@ def j_blkdiag(Q, bs):
         for k in range(nb, bs):
             out[ib, k, k] = 1.0
     return out
+
+
+def pcg(Q, b, *, maxit=1000, tol=1e-8, x0=None):
+    """The comparator of Section 4.2: conjugate gradients preconditioned by
+    M = diag(Q) (Saad's Alg. 9.1), stopping when the recursive residual
+    satisfies ||r^t|| <= tol ||b|| or after maxit iterations.  Returns a dict
+    with x, iters and rr (||r^t|| for t = 0 .. iters)."""
+    n, rp, ci, v = _csr(Q)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+    x = np.empty(n, dtype=np.float64)
+    rr = np.full(maxit + 1, np.nan)
+    it = ctypes.c_int64()
+    rc = lib().orc_pcg_solve(n, _p(rp), _p(ci), _p(v), _p(b), _p(x0a), int(maxit), float(tol), _p(x),
+                             ctypes.byref(it), _p(rr))
+    if rc != 0:
+        raise ValueError("oracle rejected the input")
+    return dict(x=x, iters=it.value, rr=rr[: it.value + 1])
 
 
 def solve(Q, b, J=None, *, Jblk=None, restart=True, momentum=True, K0=2, maxit=1000, stop=STOP_RELRES,

@@ -509,3 +509,45 @@ def test_block_j_converges_on_poisson_like_diagonal_j():
     for bs in (2, 4, 16):
         r = oracle.solve(Q, b, Jblk=oracle.j_blkdiag(Q, bs), maxit=5000, tol=1e-10)
         assert r["converged"] and 0.5 * it_d <= r["iters"] <= 1.5 * it_d
+
+
+# --------------------------------------------------------------------------- PCG comparator (Section 4.2)
+def test_pcg_matches_scipy_cg_with_jacobi_preconditioner():
+    # an independent implementation of the same recurrence: scipy's cg with M^{-1} = diag(Q)^{-1}
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    sp = pytest.importorskip("scipy.sparse")
+    Q, A = _random_csr(40, 0.2, 12, symmetric=True, spd_shift=0.3)
+    b = np.random.default_rng(1).standard_normal(40)
+    S = sp.csr_matrix((Q["val"], Q["col"], Q["row_ptr"]), shape=(40, 40))
+    Minv = sla.LinearOperator((40, 40), matvec=lambda v: v / np.diag(A))
+    xs = []
+    sla.cg(S, b, x0=np.zeros(40), rtol=1e-300, atol=0.0, maxiter=8, M=Minv, callback=lambda xk: xs.append(xk.copy()))
+    for t in range(1, 9):
+        r = oracle.pcg(Q, b, maxit=t, tol=0.0)
+        np.testing.assert_allclose(r["x"], xs[t - 1], rtol=1e-11, atol=1e-12)
+
+
+def test_pcg_finite_termination_with_two_preconditioned_eigenvalues():
+    # Q = D^1/2 B D^1/2 with B = (1 - c) I + c 1 1^T (unit diagonal): diag(Q) = D and
+    # M^{-1} Q is similar to B, which has two distinct eigenvalues, so PCG terminates
+    # after 2 iterations (a dropped beta, sign or preconditioner step would not)
+    n, c = 30, 0.3
+    d = np.random.default_rng(2).uniform(0.5, 4.0, n)
+    B = (1 - c) * np.eye(n) + c * np.ones((n, n))
+    A = np.sqrt(d)[:, None] * B * np.sqrt(d)[None, :]
+    Q = _dense_to_csr(A)
+    b = np.random.default_rng(3).standard_normal(n)
+    r = oracle.pcg(Q, b, maxit=50, tol=1e-12)
+    assert r["iters"] == 2
+    np.testing.assert_allclose(r["x"], np.linalg.solve(A, b), rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("case", [_tiny_spd, _tiny_laplacian])
+def test_pcg_recursive_residual_tracks_true_residual(case):
+    Q, A, xs, b = case()
+    for t in (5, 15, 25):
+        r = oracle.pcg(Q, b, maxit=t, tol=0.0)
+        true = np.linalg.norm(b - A @ r["x"])
+        assert abs(r["rr"][-1] - true) <= 1e-10 * np.linalg.norm(b)
+    r = oracle.pcg(Q, b, maxit=500, tol=1e-12)
+    assert np.linalg.norm(A @ r["x"] - b) <= 1e-11 * np.linalg.norm(b)
