@@ -22,6 +22,8 @@
  *                     J is diagonal (eq. J-diag and variants) or block diagonal
  *                     (eq. J-blkdiag, blocks given by the caller); a block update
  *                     x^i = y^i - (J^{ii})^{-1} g^i solves with the block's Cholesky factor.
+ *   orc_pcg_solve     the comparator: conjugate gradients with the diagonal preconditioner
+ *                     (Section 4.2), Saad's Alg. 9.1.
  *                     momentum = 0 replaces the alpha/beta extrapolation by beta = 0, which with
  *                     J = D / omega is the (weighted) Jacobi method of eqs. jacobi / weighted-jacobi.
  */
@@ -302,5 +304,71 @@ int orc_aj_solve(const orc_params* P, double* x_out, orc_info* info, const orc_t
     info->converged = conv;
   }
   free(xprev); free(x); free(y); free(g); free(qx); free(Lf); free(zb);
+  return 0;
+}
+
+/* Preconditioned conjugate gradients with the diagonal preconditioner
+ * M = diag(Q) (a zero diagonal entry -> 1), the paper's main comparator
+ * (Section 4.2, "PCG with a simple diagonal preconditioner"); the recurrence
+ * of Saad, Iterative Methods for Sparse Linear Systems, Alg. 9.1:
+ *   r^0 = b - Q x^0, z^0 = M^{-1} r^0, p^0 = z^0;
+ *   alpha_t = <r^t, z^t> / <Q p^t, p^t>;  x^{t+1} = x^t + alpha_t p^t;
+ *   r^{t+1} = r^t - alpha_t Q p^t;  z^{t+1} = M^{-1} r^{t+1};
+ *   beta_t = <r^{t+1}, z^{t+1}> / <r^t, z^t>;  p^{t+1} = z^{t+1} + beta_t p^t.
+ * Stops before iteration t when ||r^t||_2 <= tol ||b||_2 (the recursive
+ * residual) or t = maxit.  x0 may be NULL (x^0 = 0).  rr_trace (optional,
+ * length maxit + 1) receives ||r^t||_2.  Returns 0, or -1 on no memory. */
+int orc_pcg_solve(int64_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
+                  const double* b, const double* x0, int64_t maxit, double tol, double* x_out,
+                  int64_t* iters_out, double* rr_trace) {
+  size_t m = (size_t)(n > 0 ? n : 1);
+  double* x = (double*)calloc(m, sizeof(double));
+  double* r = (double*)calloc(m, sizeof(double));
+  double* z = (double*)calloc(m, sizeof(double));
+  double* p = (double*)calloc(m, sizeof(double));
+  double* q = (double*)calloc(m, sizeof(double));
+  double* dinv = (double*)calloc(m, sizeof(double));
+  if (!x || !r || !z || !p || !q || !dinv) {
+    free(x); free(r); free(z); free(p); free(q); free(dinv);
+    return -1;
+  }
+  for (int64_t k = 0; k < n; k++) {
+    double d = 0.0;
+    for (int32_t e = row_ptr[k]; e < row_ptr[k + 1]; e++)
+      if (col[e] == k) d += val[e];
+    dinv[k] = 1.0 / (d == 0.0 ? 1.0 : d);
+  }
+  if (x0)
+    for (int64_t i = 0; i < n; i++) x[i] = x0[i];
+  orc_spmv(n, row_ptr, col, val, x, q);
+  for (int64_t i = 0; i < n; i++) {
+    r[i] = b[i] - q[i];
+    z[i] = dinv[i] * r[i];
+    p[i] = z[i];
+  }
+  double rz = dot(n, r, z);
+  const double bnorm = sqrt(dot(n, b, b));
+  int64_t t = 0;
+  double rn = sqrt(dot(n, r, r));
+  if (rr_trace) rr_trace[0] = rn;
+  while (t < maxit && !(rn <= tol * bnorm)) {
+    orc_spmv(n, row_ptr, col, val, p, q);
+    const double alpha = rz / dot(n, p, q);
+    for (int64_t i = 0; i < n; i++) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * q[i];
+      z[i] = dinv[i] * r[i];
+    }
+    const double rz_new = dot(n, r, z);
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    for (int64_t i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
+    t++;
+    rn = sqrt(dot(n, r, r));
+    if (rr_trace) rr_trace[t] = rn;
+  }
+  memcpy(x_out, x, (size_t)n * sizeof(double));
+  if (iters_out) *iters_out = t;
+  free(x); free(r); free(z); free(p); free(q); free(dinv);
   return 0;
 }
