@@ -215,6 +215,23 @@ def _events(torch, stream):
     return e0, e1
 
 
+def time_pcg(aj, torch, stream, tens, n, out):
+    """Sec. 4.2's comparator on the same system: diagonally preconditioned CG
+    in FP64 to relative residual 1e-8 (one warm-up solve, one timed)."""
+    ctx = aj.Context(*tens, n=n)
+    ctx.set_stream(stream)
+    ctx.set(tol=1e-8, maxit=200000)
+    ctx.pcg_solve(out=out)
+    e0, e1 = _events(torch, stream)
+    e0.record(stream)
+    _, info = ctx.pcg_solve(out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.close()
+    return {"time_to_tol_ms": e0.elapsed_time(e1), "iterations": info["iters"], "relres": info["relres"],
+            "status": info["status"], "kernel_ms_per_iteration": info["kernel_ms"] / max(info["iters"], 1)}
+
+
 def bench_graph(aj, torch, dev, stream, hbm_peak, n):
     """Singular weighted Chung-Lu graph Laplacian (mean degree 16, exponent 2.5,
     weights U(0.5, 1.5)), b = Q x* in range(Q): FP32-value refinement and the
@@ -255,6 +272,7 @@ def bench_graph(aj, torch, dev, stream, hbm_peak, n):
                      "kernel_ms_per_iteration": info["kernel_ms"] / max(info["iters"], 1)}
         ctx.close()
     res["fp32_ir_speedup_vs_fp64"] = res["fp64"]["time_to_tol_ms"] / res["fp32_ir"]["time_to_tol_ms"]
+    res["pcg_fp64"] = time_pcg(aj, torch, stream, tens, n, out)
     return res
 
 
@@ -618,6 +636,7 @@ def main():
                 "fused_GBps": vb * it / (kms * 1e-3) / 1e9,
                 "kernel_ms_per_iteration": kms / max(it, 1)}
             del c
+        var["pcg_fp64"] = time_pcg(aj, torch, stream, tensors, n, out)
         line["variants"] = var
     # ---- end to end through the C ABI with pinned host buffers
     if not args.no_e2e:

@@ -238,6 +238,19 @@ aj_status aj_set_stream(aj_ctx* ctx, void* cuda_stream);
 aj_status aj_solve(aj_ctx* ctx, double* x_out, int x_on_device, aj_info* info);
 aj_status aj_solve_rhs(aj_ctx* ctx, double* x_out, int x_on_device, aj_info* info_per_rhs);
 
+/* The comparator of Sec. 4.2: conjugate gradients with the diagonal
+ * preconditioner M = diag(Q) (a zero diagonal entry counts as 1) on the same
+ * Q and b, in FP64 (Saad, Iterative Methods for Sparse Linear Systems,
+ * Alg. 9.1).  One persistent cooperative launch, two grid-synchronised passes
+ * per iteration.  It stops when the recursive residual satisfies
+ * ||r^t|| <= tol ||b|| or after maxit iterations.  tol, maxit, x0 and
+ * grid_ctas come from aj_set; the other parameters do not apply.  ctx must
+ * have one right-hand side (AJ_EINVAL otherwise).  x_out and info are as for
+ * aj_solve: info->iters counts CG iterations, info->sweeps the passes over Q,
+ * and relres is the FP64 residual of the returned x.  Returns AJ_OK,
+ * AJ_EMAXIT, AJ_ENONFINITE, AJ_ETIMEOUT (a grid barrier gave up) or AJ_ENOMEM. */
+aj_status aj_pcg_solve(aj_ctx* ctx, double* x_out, int x_on_device, aj_info* info);
+
 /* Solve count independent contexts in ONE persistent launch (their sizes
  * may differ; each keeps its own momentum and restart state).  x_out[i] is
  * the output of ctx[i] (n_i x nrhs_i), info[i] its report (info may be NULL).

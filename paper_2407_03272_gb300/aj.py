@@ -101,6 +101,7 @@ SIGNATURES = [
     ("aj_set_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     ("aj_restart_log", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                       ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    ("aj_pcg_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(aj_info)]),
     ("aj_destroy", None, [ctypes.c_void_p]),
     ("aj_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("aj_kernel_launches", ctypes.c_uint64, []),
@@ -227,6 +228,18 @@ class Context:
         if st not in (AJ_OK, AJ_EMAXIT, AJ_EDIVERGED, AJ_ENONFINITE) or (raise_on_error and st != AJ_OK):
             raise AJError(st, "aj_solve")
         return out, info
+
+    def pcg_solve(self, out=None):
+        """Sec. 4.2's comparator, diagonally preconditioned CG on the same
+        system (aj_pcg_solve); returns (x, info)."""
+        if out is None:
+            out = np.empty(self.n, dtype=np.float64)
+        xp, dev = _ptr(out)
+        inf = aj_info()
+        st = lib().aj_pcg_solve(self._h, xp, dev, ctypes.byref(inf))
+        if st not in (AJ_OK, AJ_EMAXIT, AJ_ENONFINITE):
+            raise AJError(st, "aj_pcg_solve")
+        return out, inf.as_dict()
 
     def restart_log(self, rhs=0):
         cnt = ctypes.c_int64()

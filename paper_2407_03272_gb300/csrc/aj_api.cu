@@ -29,6 +29,7 @@
 #include "aj.h"
 #include "aj_core.cuh"
 #include "aj_launch.h"
+#include "aj_pcg.cuh"
 #include "aj_setup.cuh"
 
 using namespace aj;
@@ -2177,6 +2178,113 @@ extern "C" aj_status aj_solve(aj_ctx* c, double* x_out, int x_on_device, aj_info
     summarize(per, c->nrhs, info);
   } else if (info) {
     std::memset(info, 0, sizeof(*info));
+    info->status = st;
+  }
+  return st;
+}
+
+// ---------------------------------------------------------------- PCG comparator
+// Conjugate gradients with M = diag(Q) (Sec. 4.2's comparator) on the
+// context's matrix and its one right-hand side, FP64, CSR rows in the
+// context's current order; tol, maxit and x0 from aj_set.
+extern "C" aj_status aj_pcg_solve(aj_ctx* c, double* x_out, int x_on_device, aj_info* info) {
+  if (!c || (!x_out && c->n > 0) || c->nrhs != 1) return AJ_EINVAL;
+  if (!c->have_prm) {
+    aj_params p;
+    aj_params_default(&p);
+    aj_status st = aj_set(c, &p);
+    if (st != AJ_OK) return st;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != c->dev) cudaSetDevice(c->dev);
+  struct Restore {
+    int dev, cur;
+    ~Restore() { if (cur != dev) cudaSetDevice(cur); }
+  } restore{c->dev, cur};
+  const int n = (int)c->n;
+  cudaStream_t s = c->stream;
+  t_launches = 0;
+  Workspace w;
+  w.stream = &c->stream;
+  struct Release {
+    Workspace& w;
+    ~Release() { w.release(); }
+  } release{w};
+  CK(cudaEventRecord(c->ev0, s));
+  const size_t vb = ((size_t)n + 1) * 8;
+  PcgArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.rp = c->rp;
+  a.ci = c->ci;
+  a.val = c->val64;
+  a.b = c->b64;
+  a.x = (double*)w.alloc(vb);
+  a.r = (double*)w.alloc(vb);
+  a.z = (double*)w.alloc(vb);
+  a.p[0] = (double*)w.alloc(vb);
+  a.p[1] = (double*)w.alloc(vb);
+  a.q = (double*)w.alloc(2 * vb);
+  int bps = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, aj_pcg_kernel, kThreads, 0));
+  const long long ntiles = std::max<long long>(1, ((long long)n + kThreads - 1) / kThreads);
+  long long g = std::min<long long>((long long)std::max(1, bps) * c->sm_count, ntiles);
+  if (c->prm.grid_ctas > 0) g = std::min<long long>(c->prm.grid_ctas, (long long)std::max(1, bps) * c->sm_count);
+  const int grid = (int)std::max<long long>(1, g);
+  a.part = (double*)w.alloc((size_t)2 * grid * 2 * 8);
+  a.bar = (unsigned long long*)w.alloc(64);
+  a.out_iters = (long long*)w.alloc(16);
+  a.out_rn = (double*)w.alloc(16);
+  if (!a.x || !a.r || !a.z || !a.p[0] || !a.p[1] || !a.q || !a.part || !a.bar || !a.out_iters || !a.out_rn)
+    return AJ_ENOMEM;
+  a.err = c->err;
+  a.maxit = c->prm.maxit;
+  a.tol = c->prm.tol;
+  a.bnorm = std::sqrt(c->bnorm2[0]);
+  aj_status e = load_x0(c);
+  if (e != AJ_OK) return e;
+  if (n > 0) CK(cudaMemcpyAsync(a.x, c->tmp64, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(a.bar, 0, 64, s));
+  CK(cudaMemsetAsync(c->err, 0, 4, s));
+  CK(cudaMemsetAsync(a.out_iters, 0, 16, s));
+  CK(cudaMemsetAsync(a.out_rn, 0, 16, s));
+  CK(cudaEventRecord(c->kev0, s));
+  if (n > 0) {
+    void* args[] = {&a};
+    CK(cudaLaunchCooperativeKernel((const void*)aj_pcg_kernel, dim3(grid), dim3(kThreads), args, 0, s));
+    counted();
+  }
+  CK(cudaEventRecord(c->kev1, s));
+  long long iters = 0;
+  double rn = 0.0;
+  int err = 0;
+  CK(cudaMemcpyAsync(&iters, a.out_iters, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&rn, a.out_rn, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&err, c->err, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (err != 0) return err == kETimeout ? AJ_ETIMEOUT : AJ_ECUDA;
+  double relres = 0.0, objgap = 0.0;
+  e = fp64_report(c, a.x, &relres, &objgap, nullptr);
+  if (e != AJ_OK) return e;
+  e = write_output(c, a.x, x_out, x_on_device);
+  if (e != AJ_OK) return e;
+  CK(cudaEventRecord(c->ev1, s));
+  CK(cudaEventSynchronize(c->ev1));
+  float ms = 0.f, kms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  cudaEventElapsedTime(&kms, c->kev0, c->kev1);
+  aj_status st = !std::isfinite(rn) ? AJ_ENONFINITE
+                 : (rn <= c->prm.tol * a.bnorm) ? AJ_OK : AJ_EMAXIT;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = iters;
+    info->sweeps = 2 * iters + 1;
+    info->relres = relres;
+    info->objgap = objgap;
+    info->ms = ms;
+    info->kernel_ms = kms;
+    info->launches = t_launches;
     info->status = st;
   }
   return st;
