@@ -59,13 +59,14 @@ def algorithmic_bytes(n, nnz, precision, form="min", stencil=False, nrhs=1):
 # DRAM bytes (read + written) per fused sweep over the bytes the sweep form
 # moves in that sweep, from the ncu captures of the kernel on the 128^3
 # Poisson system (50 iterations, 51 sweeps per launch): FP64 difference form
-# 16.706 GB / 51 / 317.6 MB, FP64 stored 15.968 GB / 51 / 300.8 MB, FP32
-# values stored 9.382 GB / 51 / 183.8 MB.  The bench scales it to a full
-# launch by the sweeps it runs; traffic grows in proportion to the rows.
-TRAFFIC_PER_FORM_BYTES = {("fp64", "delta"): 16.706409e9 / 51 / 317587460.0,
+# 16.687 GB / 51 / 317.6 MB, FP64 stored 15.968 GB / 51 / 300.8 MB, FP32
+# values stored 9.382 GB / 51 / 183.8 MB, FP32 values lazy 9.157 GB / 51 /
+# 167.0 MB.  The bench scales it to a full launch by the sweeps it runs;
+# traffic grows in proportion to the rows.
+TRAFFIC_PER_FORM_BYTES = {("fp64", "delta"): 16.687168e9 / 51 / 317587460.0,
                           ("fp64", "stored"): 15.967641e9 / 51 / 300810244.0,
                           ("fp32_ir", "stored"): 9.382468e9 / 51 / 183762948.0,
-                          ("fp32_ir", "lazy"): 9.156e9 / 51 / 166985732.0}
+                          ("fp32_ir", "lazy"): 9.157071e9 / 51 / 166985732.0}
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 128^3 capture, "
                   "scaled by rows and sweeps to one launch of this workload")
 
