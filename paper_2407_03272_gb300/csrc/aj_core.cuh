@@ -649,10 +649,14 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
   // order, their entries known without loading them (same values, same
   // ascending column order as in CSR, so the sums are the CSR sums bit for bit)
   const bool stn = FM == 2 || (FM == 1 && a.fmt == 2);
-  V s_diag = P::vzero(), s_off = P::vzero();
-  if (stn) {
-    s_diag = P::ldv(a.val + a.sdiag_at);
-    s_off = P::ldv(a.val + a.soff_at);
+  // (declared without an initial value: even an unused zero conversion of
+  // the BF16 policy changed register allocation in the CSR-only kernel)
+  V s_diag, s_off;
+  if constexpr (FM != 0) {
+    if (stn) {
+      s_diag = P::ldv(a.val + a.sdiag_at);
+      s_off = P::ldv(a.val + a.soff_at);
+    }
   }
   const int ntiles = sell ? a.ntiles_sell + a.nltiles + a.nhuge : (a.n + rpt - 1) / rpt;
   for (int tile = cta; tile < ntiles; tile += ncta) {
