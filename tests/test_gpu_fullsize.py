@@ -40,17 +40,21 @@ def _state_parts(blob, n):
     return t, beta, bufs[cur], bufs[prev]
 
 
-def test_fullsize_step_matches_oracle_step():
+@pytest.mark.parametrize("fmt", ["csr", "stencil"])
+def test_fullsize_step_matches_oracle_step(fmt):
+    # CSR is the benchmark's configuration; AUTO takes the stencil format here
     Q, b, xs = workload()
     n = Q["n"]
     T = 40
+    F = aj.AJ_FMT_CSR if fmt == "csr" else aj.AJ_FMT_STENCIL
     ctx = aj.from_csr(Q, b, device="cuda")
-    ctx.set(stop=aj.AJ_STOP_NONE, maxit=T)
+    ctx.set(stop=aj.AJ_STOP_NONE, maxit=T, format=F)
+    assert ctx.format()[0] == F
     ctx.solve(out=torch.empty(n, dtype=torch.float64, device="cuda"))
     t, beta, xT, xTm1 = _state_parts(ctx.get_state(), n)
     assert t == T
     ctx2 = aj.from_csr(Q, b, device="cuda")
-    ctx2.set(stop=aj.AJ_STOP_NONE, maxit=T + 1)
+    ctx2.set(stop=aj.AJ_STOP_NONE, maxit=T + 1, format=F)
     ctx2.set_state(ctx.get_state())
     x_next, info = ctx2.solve()
     assert info["iters"] == T + 1
@@ -64,14 +68,44 @@ def test_fullsize_step_matches_oracle_step():
     assert err <= 1e-12, err
 
 
-@pytest.mark.parametrize("precision", ["df64", "fp32_ir", "fp64"])
-def test_fullsize_solve_reaches_1e8(precision):
+@pytest.mark.parametrize("precision,kw", [
+    ("df64", {}), ("fp32_ir", {}), ("fp64", {}), ("bf16_ir", {}),
+    ("fp64", dict(format=aj.AJ_FMT_CSR)), ("fp32_ir", dict(format=aj.AJ_FMT_CSR)),
+    ("fp32_ir", dict(j_policy=aj.AJ_J_BLKDIAG, j_block=4)), ("fp64", dict(j_policy=aj.AJ_J_BLKDIAG, j_block=8))])
+def test_fullsize_solve_reaches_1e8(precision, kw):
     Q, b, xs = workload()
     ctx = aj.from_csr(Q, b, device="cuda")
-    ctx.set(precision=precision, tol=1e-8, maxit=30000)
+    ctx.set(precision=precision, tol=1e-8, maxit=30000, **kw)
     x, info = ctx.solve()
     assert info["status"] == aj.AJ_OK, info
     r = b - oracle.spmv(Q, x)
     rr = np.linalg.norm(r) / np.linalg.norm(b)
     assert rr <= 1e-8
     assert abs(rr - info["relres"]) <= 1e-3 * rr
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_ir", "bf16_ir"])
+def test_fullsize_stencil_equals_csr_bitwise(precision):
+    # the stencil rows are the CSR rows' sums bit for bit, at the full size too
+    Q, b, xs = workload()
+    n = Q["n"]
+    out = {}
+    for F in (aj.AJ_FMT_CSR, aj.AJ_FMT_STENCIL):
+        c = aj.from_csr(Q, b, device="cuda")
+        c.set(precision=precision, stop=aj.AJ_STOP_NONE, maxit=60, inner_tol=1e-30, format=F)
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        _, info = c.solve(out=x)
+        out[F] = (x.cpu().numpy(), info["iters"])
+        c.close()
+    np.testing.assert_array_equal(out[aj.AJ_FMT_CSR][0], out[aj.AJ_FMT_STENCIL][0])
+    assert out[aj.AJ_FMT_CSR][1] == out[aj.AJ_FMT_STENCIL][1]
+
+
+def test_fullsize_pcg_reaches_1e8():
+    Q, b, xs = workload()
+    c = aj.from_csr(Q, b, device="cuda")
+    c.set(tol=1e-8, maxit=5000)
+    x, info = c.pcg_solve()
+    assert info["status"] == aj.AJ_OK, info
+    rr = np.linalg.norm(b - oracle.spmv(Q, x)) / np.linalg.norm(b)
+    assert rr <= 1.01e-8 and abs(rr - info["relres"]) <= 1e-3 * rr
