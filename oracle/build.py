@@ -1,6 +1,6 @@
 """Compile the plain-C FP64 oracle into oracle/_build/liboracle.so.
 
-Test infrastructure: building the checker is not using it.  -ffp-contract=off
+Test infrastructure: building the oracle is not running it.  -ffp-contract=off
 keeps a*b+c as two roundings on every host (aarch64 gcc would otherwise fuse
 it), so the oracle gives the same bits on x86-64 and arm64.
 """
