@@ -447,16 +447,20 @@ extern "C" aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ct
         break;
       }
     }
-    // ||b_r||^2 in FP64 and b finite
-    std::vector<double> hb((size_t)m);
-    if (m > 0 && (cudaMemcpyAsync(hb.data(), c->b64, (size_t)m * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                  cudaStreamSynchronize(s) != cudaSuccess)) {
-      st = cuda_fail(cudaGetLastError());
-      break;
-    }
-    for (long long e = 0; e < m; e++) {
-      if (!std::isfinite(hb[e])) { st = AJ_EINVAL; break; }
-      c->bnorm2[e % nrhs] += hb[e] * hb[e];
+    // ||b_r||^2 in FP64 and b finite, on the device (c->err is zero here)
+    if (n > 0) {
+      const int blocks = (int)grid1d(n);
+      k_bnorm2<<<blocks, kSetupThreads, 0, s>>>(n, nrhs, c->b64, c->part_small, c->err);
+      counted();
+      int bad = 0;
+      double sums[kMaxRhs] = {0.0, 0.0, 0.0, 0.0};
+      if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(&bad, c->err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaMemsetAsync(c->err, 0, 4, s) != cudaSuccess || host_sum_parts(c, c->part_small, blocks, nrhs, sums) != AJ_OK) {
+        st = cuda_fail(cudaGetLastError());
+        break;
+      }
+      if (bad) { st = AJ_EINVAL; break; }
+      for (int r = 0; r < nrhs; r++) c->bnorm2[r] = sums[r];
     }
   } while (0);
   if (st != AJ_OK) {

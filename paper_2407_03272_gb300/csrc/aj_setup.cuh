@@ -182,6 +182,33 @@ __global__ void k_residual(int n, int nrhs, const int* rp, const int* ci, const 
   }
 }
 
+// ||b_r||^2 per right-hand side (b interleaved): per-block partials in
+// part[block][nrhs]; *bad = 1 if an entry is not finite.
+__global__ void k_bnorm2(int n, int nrhs, const double* b, double* part, int* bad) {
+  __shared__ double sm[kMaxRhs][kSetupThreads / 32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[kMaxRhs] = {0.0, 0.0, 0.0, 0.0};
+  if (i < n) {
+    for (int r = 0; r < nrhs; r++) {
+      const double v = b[(long long)i * nrhs + r];
+      if (!isfinite(v)) *bad = 1;
+      acc[r] = v * v;
+    }
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = 0; k < nrhs; k++) {
+    double v = acc[k];
+    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    if (lane == 0) sm[k][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nrhs) {
+    double v = 0.0;
+    for (int k = 0; k < kSetupThreads / 32; k++) v += sm[threadIdx.x][k];
+    part[(size_t)blockIdx.x * nrhs + threadIdx.x] = v;
+  }
+}
+
 // y = D^-1/2 Q D^-1/2 x (rows with zero diagonal give 0); per-block partials
 // of <x, y> and <y, y> go to part[block][2].
 __global__ void k_normalized_spmv(int n, const int* rp, const int* ci, const double* val,

@@ -309,6 +309,13 @@ def test_invalid_matrices_rejected():
     bad["val"][0] = -4.0
     with pytest.raises(aj.AJError):
         aj.from_csr(bad, np.ones(36))
+    # a non-finite right-hand side, in the first or a later column
+    for k, v in ((3, np.nan), (35, np.inf), (36 + 7, -np.inf)):
+        bb = np.ones(72)
+        bb[k] = v
+        with pytest.raises(aj.AJError) as e:
+            aj.from_csr(good, bb, nrhs=2)
+        assert e.value.status == aj.AJ_EINVAL
     ctx = aj.from_csr(good, np.ones(36))
     with pytest.raises(aj.AJError):
         ctx.set(K0=1)
