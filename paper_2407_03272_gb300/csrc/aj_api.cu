@@ -939,16 +939,19 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   size_grid(c);
   // --- scaled copies for the non-FP64 policies (powers of two: exact)
   if (pol != AJ_FP64) {
+    // max |Q_ij| via the diagonal bound: for SPSD Q, |Q_ij| <= sqrt(Q_ii Q_jj) <= max diag
+    // (the diagonal is non-negative: aj_create rejects a negative one)
     double vmax = 0.0;
-    {
-      std::vector<double> hv;
-      // max |Q_ij| via the diagonal bound: for SPSD Q, |Q_ij| <= sqrt(Q_ii Q_jj) <= max diag
-      std::vector<double> hd(n);
-      if (n > 0) {
-        CK(cudaMemcpyAsync(hd.data(), c->diag, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-      }
-      for (double d : hd) vmax = std::max(vmax, d);
+    if (n > 0) {
+      unsigned long long* dm = (unsigned long long*)c->part_small;
+      unsigned long long bits = 0ull;
+      CK(cudaMemsetAsync(dm, 0, 8, s));
+      k_max_nonneg<<<std::min<unsigned>(grid1d(n), 4096), kSetupThreads, 0, s>>>(n, c->diag, dm);
+      counted();
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(&bits, dm, 8, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      std::memcpy(&vmax, &bits, 8);
     }
     c->sQ = pow2_near(vmax);
     if (pol == AJ_DF64) {

@@ -182,6 +182,17 @@ __global__ void k_residual(int n, int nrhs, const int* rp, const int* ci, const 
   }
 }
 
+// The largest of n non-negative doubles, into *out (which starts at 0): for
+// non-negative IEEE-754 values the bit patterns, read as unsigned integers,
+// order as the values do, so an integer atomicMax gives the exact maximum.
+__global__ void k_max_nonneg(int n, const double* v, unsigned long long* out) {
+  unsigned long long m = 0ull;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = max(m, (unsigned long long)__double_as_longlong(v[i]));
+  for (int k = 16; k >= 1; k >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, k));
+  if ((threadIdx.x & 31) == 0 && m > 0ull) atomicMax(out, m);
+}
+
 // ||b_r||^2 per right-hand side (b interleaved): per-block partials in
 // part[block][nrhs]; *bad = 1 if an entry is not finite.
 __global__ void k_bnorm2(int n, int nrhs, const double* b, double* part, int* bad) {
