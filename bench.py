@@ -39,6 +39,10 @@ FALLBACK_HBM_GBS = 6800.0
 FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
 
 
+HEADLINE_WORKLOAD = ("3-D 7-point Dirichlet Poisson 256^3 (n=16777216, nnz=117047296), "
+                     "FP64 CSR int32, x*~N(0,1) seed 2, b=Qx*; solve to rel. residual 1e-8")
+
+
 def algorithmic_bytes(n, nnz, precision, form="min", stencil=False, nrhs=1):
     """Bytes one fused iteration must move, per right-hand side: the matrix once
     (values + int32 column indices), the row pointers, and 5 n-vectors -- read
@@ -199,8 +203,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "3-D 7-point Dirichlet Poisson 256^3 (n=16777216, nnz=117047296), "
-                               "FP64 CSR int32; each step %d oracle iterations" % per_step},
+        "config": {"workload": HEADLINE_WORKLOAD, "precision": "fp64", "format": "csr",
+                   "parallelism": "replicas x%d" % ws,
+                   "sample": "each step %d iterations of the oracle on this system" % per_step},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "%d steps x %d iterations of the FP64 C oracle, one thread"
                                    % (args.steps, per_step)},
@@ -571,8 +576,7 @@ def main():
         "dtype": {"fp64": "f64", "df64": "f32x2 (double-float)", "fp32_ir": "f32 inner / f64 outer",
                   "bf16_ir": "bf16 values, f32 inner / f64 outer"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": ("3-D 7-point Dirichlet Poisson 256^3 (n=16777216, nnz=117047296), "
-                                "FP64 CSR int32, x*~N(0,1) seed 2, b=Qx*; solve to rel. residual 1e-8")
+        "config": {"workload": HEADLINE_WORKLOAD
                    if args.workload == WORKLOAD and not args.fixed_iters and not stn else
                    "%s (n=%d, nnz=%d), %s" % (args.workload, n, nnz,
                                               "%d fixed iterations" % args.fixed_iters
