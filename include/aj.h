@@ -254,7 +254,11 @@ aj_status aj_pcg_solve(aj_ctx* ctx, double* x_out, int x_on_device, aj_info* inf
 /* Solve count independent contexts in ONE persistent launch (their sizes
  * may differ; each keeps its own momentum and restart state).  x_out[i] is
  * the output of ctx[i] (n_i x nrhs_i), info[i] its report (info may be NULL).
- * All contexts must share one precision and use the first context's stream. */
+ * All contexts must share one precision and device (AJ_EINVAL otherwise) and
+ * use the first context's stream.  Contexts whose sweep forms differ (AUTO
+ * gives SELL matrices the stored form, CSR and stencil ones the lazy form in
+ * the reduced precisions) run as one launch per sweep form, one after
+ * another. */
 aj_status aj_solve_batch(aj_ctx* const* ctx, int count, double* const* x_out, int x_on_device,
                          aj_info* info);
 

@@ -2392,8 +2392,35 @@ extern "C" aj_status aj_solve_batch(aj_ctx* const* ctx, int count, double* const
       if (st != AJ_OK) return st;
     }
   aj_ctx* c0 = ctx[0];
-  for (int i = 1; i < count; i++)
-    if (ctx[i]->dev != c0->dev || ctx[i]->pol != c0->pol || ctx[i]->qx != c0->qx) return AJ_EINVAL;
+  bool mixed = false;
+  for (int i = 1; i < count; i++) {
+    if (ctx[i]->dev != c0->dev || ctx[i]->pol != c0->pol) return AJ_EINVAL;
+    mixed = mixed || ctx[i]->qx != c0->qx;
+  }
+  if (mixed) {
+    // one lockstep batch per sweep form (AUTO gives SELL matrices the stored
+    // form and CSR ones the lazy form; the kernel runs one form), in turn
+    aj_status worst = AJ_OK;
+    for (int q = 0; q < 3; q++) {
+      std::vector<aj_ctx*> cs;
+      std::vector<double*> xs;
+      std::vector<int> idx;
+      for (int i = 0; i < count; i++)
+        if (ctx[i]->qx == q) {
+          cs.push_back(ctx[i]);
+          xs.push_back(x_out[i]);
+          idx.push_back(i);
+        }
+      if (cs.empty()) continue;
+      std::vector<aj_info> inf(cs.size());
+      const aj_status s = aj_solve_batch(cs.data(), (int)cs.size(), xs.data(), x_on_device, inf.data());
+      if (s != AJ_OK && s != AJ_EMAXIT && s != AJ_EDIVERGED && s != AJ_ENONFINITE) return s;
+      for (size_t k = 0; k < cs.size(); k++)
+        if (info) info[idx[k]] = inf[k];
+      if (s != AJ_OK && worst == AJ_OK) worst = s;
+    }
+    return worst;
+  }
   int dev_prev = 0;
   cudaGetDevice(&dev_prev);
   if (dev_prev != c0->dev) cudaSetDevice(c0->dev);

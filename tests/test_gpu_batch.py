@@ -134,3 +134,28 @@ def test_batch_rejects_mixed_precisions_and_duplicates():
         aj.solve_batch([c1, c2], [np.empty(64), np.empty(64)])
     with pytest.raises(aj.AJError):
         aj.solve_batch([c1, c1], [np.empty(64), np.empty(64)])
+
+
+@pytest.mark.parametrize("precision", ["fp32_ir", "fp64"])
+def test_batch_of_mixed_sweep_forms_equals_solo(precision):
+    # members of one precision whose sweep forms differ (SELL members take the
+    # stored form under AUTO in FP32; FP64 members here name their form) run as
+    # one lockstep batch per form, each member bit for bit its solo run
+    mix = _mix(9, seed=9)
+    kws = []
+    for k in range(len(mix)):
+        kw = dict(precision=precision, tol=1e-8, maxit=40000, grid_ctas=1 + k % 2)
+        if precision == "fp32_ir":
+            kw["format"] = aj.AJ_FMT_SELL if k % 3 == 0 else aj.AJ_FMT_CSR
+        else:
+            kw["sweep_form"] = (aj.AJ_SWEEP_DELTA, aj.AJ_SWEEP_STORED, aj.AJ_SWEEP_LAZY)[k % 3]
+        kws.append(kw)
+    ctxs = [_ctx(Q, B, **kw) for (Q, B), kw in zip(mix, kws)]
+    X, infos = _batch(ctxs, mix)
+    for (Q, B), kw, x, inf in zip(mix, kws, X, infos):
+        solo = _ctx(Q, B, **kw)
+        xs, sinf = solo.solve()
+        xs = xs.reshape(B.shape[1], Q["n"]).T
+        assert inf["status"] == sinf["status"] == aj.AJ_OK
+        assert inf["iters"] == sinf["iters"]
+        np.testing.assert_array_equal(x, xs)
