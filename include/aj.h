@@ -213,7 +213,10 @@ aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ctx** out);
 
 /* Set the solver parameters (copied).  Builds J^{-1} and, for
  * AJ_J_SCALED_DIAG with L = 0, estimates L by power iteration on
- * D^-1/2 Q D^-1/2 in FP64.  AJ_EINVAL on a bad parameter. */
+ * D^-1/2 Q D^-1/2 in FP64.  AJ_EINVAL on a bad parameter (the context keeps
+ * its previous parameters); AJ_ENOMEM or AJ_ECUDA if building the arrays
+ * fails, after which the context counts as never set: its next solve first
+ * applies the default parameters, as on a fresh context. */
 aj_status aj_set(aj_ctx* ctx, const aj_params* p);
 
 /* The format aj_set chose (AJ_FMT_CSR, AJ_FMT_SELL or AJ_FMT_STENCIL), its
@@ -377,6 +380,29 @@ aj_status aj_solve_noalloc(const aj_csr* Q, const double* b, const aj_params* p,
 
 /* Diagnostics: number of CUDA kernels libaj has launched in this process. */
 uint64_t aj_kernel_launches(void);
+
+/* ---- Failure-detection test hooks.  The paper has no counterpart: they let
+ * a test drive the library's error paths without faulting a GPU.
+ *
+ * aj_test_barrier_stall: the next persistent solve launched in this process
+ * (aj_solve, aj_solve_rhs) runs with every grid-barrier wait limited to
+ * timeout_ms (0 < timeout_ms <= 4000; the default limit is 4 s), and its CTA
+ * number `cta` withholds its arrival at the first barrier.  Every other wait
+ * then runs out, the kernel records the timeout and returns, and the solve
+ * returns AJ_ETIMEOUT; the context stays usable and its next solve runs
+ * normally.  A `cta` at or beyond the launch's grid withholds nothing;
+ * cta = -1 disarms the hook.  One shot: the hook is cleared by the launch
+ * that takes it.  AJ_EINVAL for a bad argument.
+ *
+ * aj_test_alloc_fail: the device allocation that comes after `after` more
+ * successful ones (0: the very next) fails as if the device were out of
+ * memory, once; the call that needed it returns AJ_ENOMEM having released
+ * what it had allocated.  after = -1 disarms the hook.  AJ_EINVAL if
+ * after < -1.
+ *
+ * Both hooks are process-wide and meant for single-threaded tests. */
+aj_status aj_test_barrier_stall(int cta, double timeout_ms);
+aj_status aj_test_alloc_fail(int64_t after);
 
 #ifdef __cplusplus
 }

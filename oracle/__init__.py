@@ -9,8 +9,9 @@ imports the other.
 Algorithm alg-apg-re (Section 2.2) in plain C, FP64, one thread, with a
 diagonal J (eq. J-diag and its variants) or a block-diagonal J
 (eq. J-blkdiag, built by ``j_blkdiag``).  Dense helpers
-for tiny inputs (the step constant L = lambda_max(D^-1/2 Q D^-1/2), direct
-solves) live in ``oracle.dense``.
+for tiny inputs (the step constant L = lambda_max(D^-1/2 Q D^-1/2), f(x))
+live in ``oracle.dense``; ``oracle.schedule`` checks a restart schedule
+against the rule of Algorithm alg-apg-re.
 """
 import ctypes
 import numpy as np
@@ -38,7 +39,7 @@ class _Info(ctypes.Structure):
 
 class _Trace(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in
-                ("alpha", "beta", "d", "restart", "f", "relres", "gnorm", "x", "y")]
+                ("alpha", "beta", "d", "restart", "f", "relres", "gnorm", "x", "y", "dxnorm")]
 
 
 def lib():
@@ -187,14 +188,14 @@ def solve(Q, b, J=None, *, Jblk=None, restart=True, momentum=True, K0=2, maxit=1
     T = None
     if trace or trace_iterates:
         m = maxit + 1
-        for k in ("alpha", "beta", "d", "f", "relres", "gnorm"):
+        for k in ("alpha", "beta", "d", "f", "relres", "gnorm", "dxnorm"):
             tr[k] = np.full(m, np.nan)
         tr["restart"] = np.zeros(m, dtype=np.uint8)
         if trace_iterates:
             tr["x"] = np.full((m, n), np.nan)
             tr["y"] = np.full((m, n), np.nan)
         T = _Trace(*[_p(tr.get(k)) for k in ("alpha", "beta", "d", "restart", "f", "relres",
-                                              "gnorm", "x", "y")])
+                                              "gnorm", "x", "y", "dxnorm")])
     rc = lib().orc_aj_solve(ctypes.byref(P), _p(x), ctypes.byref(info),
                             ctypes.byref(T) if T is not None else None)
     if rc != 0:

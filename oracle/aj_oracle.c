@@ -119,6 +119,8 @@ typedef struct {
  *   tr_f[t]       f(x^t) after the branch (t = 0: f(x^0))
  *   tr_relres[t]  relative residual of x^t after the branch
  *   tr_gnorm[t]   ||Q y^t - b||_2
+ *   tr_dxnorm[t]  ||x^t - x^{t-1}||_2 with x^t before the restart branch (the scale of the
+ *                 restart test: |d| <= ||Q y^t - b|| ||x^t - x^{t-1}|| by Cauchy-Schwarz)
  *   tr_x          (maxit + 1) x n: x^t after the branch, row t
  *   tr_y          (maxit + 1) x n: y^t, row t (row 0 unused)
  */
@@ -132,6 +134,7 @@ typedef struct {
   double* gnorm;
   double* x;
   double* y;
+  double* dxnorm;
 } orc_trace;
 
 static void eval_x(const orc_params* P, const double* x, double* qx, double bnorm,
@@ -257,8 +260,12 @@ int orc_aj_solve(const orc_params* P, double* x_out, orc_info* info, const orc_t
       for (int64_t i = 0; i < n; i++) x[i] = y[i] - g[i] / P->J[i];
     }
     /* restart test quantity <Q y^t - b, x^t - x^{t-1}> */
-    double d = 0.0, gg = 0.0;
-    for (int64_t i = 0; i < n; i++) { d += g[i] * (x[i] - xprev[i]); gg += g[i] * g[i]; }
+    double d = 0.0, gg = 0.0, dd = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+      d += g[i] * (x[i] - xprev[i]);
+      gg += g[i] * g[i];
+      dd += (x[i] - xprev[i]) * (x[i] - xprev[i]);
+    }
     int restart;
     if (P->forced) restart = P->forced[t] != 0;
     else restart = P->is_restart && (t > Kre + K) && (d >= 0.0);
@@ -288,6 +295,7 @@ int orc_aj_solve(const orc_params* P, double* x_out, orc_info* info, const orc_t
     if (T && T->d) T->d[t] = d;
     if (T && T->restart) T->restart[t] = (uint8_t)restart;
     if (T && T->gnorm) T->gnorm[t] = sqrt(gg);
+    if (T && T->dxnorm) T->dxnorm[t] = sqrt(dd);
     alpha = alpha_next;
     eval_x(P, x, qx, bnorm, &relres, &f);
     if (T && T->f) T->f[t] = f;

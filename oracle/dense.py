@@ -28,16 +28,6 @@ def step_constant_L(Q):
     return float(np.linalg.eigvalsh(M)[-1])
 
 
-def direct_solve(Q, b):
-    """Minimum-norm solution of Q x = b (Cholesky-free: eigendecomposition of
-    the symmetric matrix, eigenvalues below 1e-12 * lambda_max treated as 0)."""
-    A = to_dense(Q)
-    w, V = np.linalg.eigh(A)
-    cut = 1e-12 * max(abs(w).max(), 1e-300)
-    inv = np.where(np.abs(w) > cut, 1.0 / np.where(np.abs(w) > cut, w, 1.0), 0.0)
-    return V @ (inv * (V.T @ b))
-
-
 def f_value(A, b, x):
     """f(x) = 1/2 <x, Q x> - <b, x>  (eq. qp)."""
     return 0.5 * x @ (A @ x) - b @ x

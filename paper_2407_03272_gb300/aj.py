@@ -107,6 +107,8 @@ SIGNATURES = [
     ("aj_kernel_launches", ctypes.c_uint64, []),
     ("aj_solve_noalloc", ctypes.c_int, [ctypes.POINTER(aj_csr), ctypes.c_void_p, ctypes.POINTER(aj_params),
                                         ctypes.c_void_p, ctypes.POINTER(aj_info), ctypes.c_void_p]),
+    ("aj_test_barrier_stall", ctypes.c_int, [ctypes.c_int, ctypes.c_double]),
+    ("aj_test_alloc_fail", ctypes.c_int, [ctypes.c_int64]),
 ]
 
 
@@ -313,6 +315,19 @@ def solve_noalloc(row_ptr, col, val, b, x_out, stream=None, **kw):
     st = lib().aj_solve_noalloc(ctypes.byref(csr), ptrs[3][0], ctypes.byref(p), ptrs[4][0],
                                 ctypes.byref(inf), ctypes.c_void_p(s))
     return st, inf.as_dict()
+
+
+def inject_barrier_stall(cta, timeout_ms):
+    """Failure-detection hook (aj_test_barrier_stall): CTA `cta` of the next
+    persistent solve withholds its first barrier arrival, and that launch's
+    barrier waits give up after timeout_ms."""
+    _check(lib().aj_test_barrier_stall(int(cta), float(timeout_ms)), "aj_test_barrier_stall")
+
+
+def inject_alloc_failure(after):
+    """Failure-detection hook (aj_test_alloc_fail): the device allocation
+    after `after` more successful ones fails once (-1 disarms)."""
+    _check(lib().aj_test_alloc_fail(int(after)), "aj_test_alloc_fail")
 
 
 class Server:

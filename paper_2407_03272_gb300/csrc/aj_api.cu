@@ -45,6 +45,23 @@ inline void counted() {
   t_launches++;
 }
 
+// Failure-detection test hooks (aj_test_barrier_stall, aj_test_alloc_fail):
+// a CTA of the next persistent launch that withholds its first barrier
+// arrival, with the barrier's wait limit for that launch; and a device
+// allocation that fails after `g_alloc_fail_after` more successful ones.
+std::atomic<int> g_stall_cta{-1};
+std::atomic<long long> g_stall_timeout_ns{0};
+std::atomic<long long> g_alloc_fail_after{-1};
+
+bool alloc_hook_fails() {
+  long long v = g_alloc_fail_after.load();
+  while (v >= 0) {
+    const long long nv = v == 0 ? -1 : v - 1;
+    if (g_alloc_fail_after.compare_exchange_weak(v, nv)) return v == 0;
+  }
+  return false;
+}
+
 // Device memory of the library comes from one memory pool per device, in
 // stream order: cudaMallocFromPoolAsync and cudaFreeAsync neither
 // synchronise the device nor hand memory back to the driver (the pool's
@@ -91,6 +108,7 @@ struct Workspace {
   void* alloc(size_t b) {
     void* p = nullptr;
     if (b == 0) b = 16;
+    if (alloc_hook_fails()) return nullptr;
     cudaMemPool_t pool = device_pool();
     const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, b, pool, st()) : cudaMalloc(&p, b);
     if (e != cudaSuccess) {
@@ -829,7 +847,9 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     return AJ_EINVAL;
   const int old_pol = c->pol;
   c->prm = *p;
-  c->have_prm = true;
+  // until this call succeeds the context counts as never set: a solve then
+  // runs aj_set with the defaults first, as on a fresh context
+  c->have_prm = false;
   c->resume = false;
   const int n = (int)c->n;
   const long long nnz = c->nnz;
@@ -886,6 +906,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   const int pol = p->precision;
   if (pol != old_pol) {
     c->pws.release();
+    c->pol = -1;  // set again once every array of the new precision exists
     c->valp = c->bp = c->jinvp = nullptr;
     c->x[0] = c->x[1] = c->x[2] = nullptr;
     c->u[0] = c->u[1] = nullptr;
@@ -1012,6 +1033,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   // same cached lines and saves two n-vectors of traffic
   if (p->sweep_form == AJ_SWEEP_AUTO && p->precision != AJ_FP64 && c->fmt != 1) c->qx = 0;
   size_grid(c);
+  c->have_prm = true;
   return AJ_OK;
 }
 
@@ -1166,6 +1188,11 @@ static aj_status run_persistent(aj_ctx* c, std::vector<RhsState>& st, const void
                                 double fscale, bool log_restarts) {
   cudaStream_t s = c->stream;
   IterLaunch L = make_launch(c, bvec, maxit, stop, tol, fstar, fscale);
+  const int stall = g_stall_cta.exchange(-1);
+  if (stall >= 0) {
+    L.bar_withhold = stall + 1;
+    L.bar_timeout_ns = (unsigned long long)g_stall_timeout_ns.load();
+  }
   aj_status e = stage_state(c, st, log_restarts);
   if (e != AJ_OK) return e;
   CK(cudaEventRecord(c->kev0, s));
@@ -2920,3 +2947,16 @@ extern "C" void aj_server_destroy(aj_server* s) {
 }
 
 extern "C" uint64_t aj_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" aj_status aj_test_barrier_stall(int cta, double timeout_ms) {
+  if (cta < -1 || !(timeout_ms > 0.0) || timeout_ms > 4000.0) return AJ_EINVAL;
+  g_stall_timeout_ns.store((long long)(timeout_ms * 1e6));
+  g_stall_cta.store(cta);
+  return AJ_OK;
+}
+
+extern "C" aj_status aj_test_alloc_fail(int64_t after) {
+  if (after < -1) return AJ_EINVAL;
+  g_alloc_fail_after.store(after);
+  return AJ_OK;
+}

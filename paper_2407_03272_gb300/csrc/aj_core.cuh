@@ -122,24 +122,29 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Grid-wide barrier for a cooperative (co-resident) launch.  `target` is the
 // arrival count that completes this barrier (k * gridDim.x for the k-th).
-// Every wait is bounded: after kBarrierTimeoutNs the CTA records kETimeout in
-// *err and returns false; a CTA that sees *err != 0 also returns false.
+// Every wait is bounded: after timeout_ns (or kBarrierMaxSpins polls) the CTA
+// records kETimeout in *err and returns false; a CTA that sees *err != 0 also
+// returns false.  `withhold` keeps this CTA's arrival back (failure-detection
+// tests: the other CTAs' waits then run out and the launch ends with
+// kETimeout; the withholding CTA waits, bounded, like the others).
 __device__ __forceinline__ bool grid_sync(unsigned long long* bar, unsigned long long target,
-                                          int* err, unsigned int nctas) {
+                                          int* err, unsigned int nctas,
+                                          unsigned long long timeout_ns = kBarrierTimeoutNs,
+                                          bool withhold = false) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
     if (nctas > 1) {
       __threadfence();
-      red_release_add_u64(bar, 1ull);
+      if (!withhold) red_release_add_u64(bar, 1ull);
       unsigned long long t0 = global_ns();
       long long spins = 0;
       while (ld_acquire_u64(bar) < target) {
         ++spins;
         if ((spins & 63) == 0) {
           if (*(volatile int*)err != 0) { ok = 0; break; }
-          if (global_ns() - t0 > kBarrierTimeoutNs || spins > kBarrierMaxSpins) {
+          if (global_ns() - t0 > timeout_ns || spins > kBarrierMaxSpins) {
             atomicCAS(err, 0, kETimeout);
             ok = 0;
             break;
@@ -441,6 +446,9 @@ struct IterArgs {
   double fstar;
   double fscale;              // f(x) = fscale * (1/2 <x~, Q~ x~> - <b~, x~>) for scaled data
   long long max_sweeps;       // sweeps allowed in this launch (chunked runs), >= 1
+  unsigned long long bar_timeout_ns;  // limit of each grid-barrier wait
+  int bar_withhold_cta;       // failure-detection tests: this CTA withholds its first
+                              // barrier arrival (-1: none)
 };
 
 // log2 of the lanes per row for nrhs right-hand sides.
@@ -1048,7 +1056,9 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, i
       if ((int)threadIdx.x < nr) __stcg(part + ((size_t)cta * nr + threadIdx.x) * kNRed + k, v);
     }
     target += (unsigned long long)ncta;
-    if (!grid_sync(a.bar, target, a.err, (unsigned)ncta)) return false;
+    if (!grid_sync(a.bar, target, a.err, (unsigned)ncta, a.bar_timeout_ns,
+                   s0 == 0 && cta == a.bar_withhold_cta))
+      return false;
     // every CTA sums the partials in the same fixed order
     grid_totals(part, ncta, nr, want_obj, sm);
     if (threadIdx.x == 0) {

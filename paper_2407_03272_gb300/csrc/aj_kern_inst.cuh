@@ -64,6 +64,8 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
   a.fstar = L.fstar;
   a.fscale = L.fscale;
   a.max_sweeps = L.max_sweeps;
+  a.bar_timeout_ns = L.bar_timeout_ns ? L.bar_timeout_ns : kBarrierTimeoutNs;
+  a.bar_withhold_cta = L.bar_withhold - 1;
   return a;
 }
 

@@ -53,6 +53,9 @@ struct IterLaunch {
   double fstar;
   double fscale;
   long long max_sweeps;
+  unsigned long long bar_timeout_ns;  // limit of each grid-barrier wait (0: the default, 4 s)
+  int bar_withhold;                   // failure-detection tests: CTA index + 1 that withholds its
+                                      // first barrier arrival (0: none), see grid_sync
   int qx;  // sweep form: 0 lazy (two row sums), 1 stored (u = Q x kept), 2 stored + difference
 };
 

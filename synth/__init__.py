@@ -107,6 +107,37 @@ def from_edges(n, u, v, w):
             "val": np.asarray(A.data, np.float64)}
 
 
+def with_hubs(Q, hubs, degree, seed=7, wlo=0.5, whi=1.5):
+    """The Laplacian of Q's graph with each vertex in ``hubs`` joined to
+    ``degree`` more distinct vertices, drawn uniformly among those it is not yet
+    joined to, with U(wlo, whi) weights (a planted hub: rows of ``degree`` and
+    more entries).  Q must be a graph Laplacian (from ``from_edges``)."""
+    rng = _rng(seed)
+    n = int(Q["n"])
+    rp, ci, v = Q["row_ptr"], Q["col"], Q["val"]
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    keep = rows < ci  # each edge once, from its lower end
+    u, w_, wt = rows[keep], ci[keep].astype(np.int64), -v[keep]
+    have = set(zip(u.tolist(), w_.tolist()))
+    eu, ev, ew = [u], [w_], [wt]
+    for h in hubs:
+        h = int(h)
+        cand = rng.permutation(n)
+        picked = []
+        for c in cand.tolist():
+            if c == h or (min(c, h), max(c, h)) in have:
+                continue
+            picked.append(c)
+            have.add((min(c, h), max(c, h)))
+            if len(picked) == degree:
+                break
+        p = np.asarray(picked, np.int64)
+        eu.append(np.minimum(p, h))
+        ev.append(np.maximum(p, h))
+        ew.append(rng.uniform(wlo, whi, p.size))
+    return from_edges(n, np.concatenate(eu), np.concatenate(ev), np.concatenate(ew))
+
+
 def _inverse_cdf(cdf, u):
     """searchsorted(cdf, u, side="right"), with the queries sorted first so
     that the binary searches walk the table in order (same result)."""

@@ -64,3 +64,13 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(aj.aj_csr) == 48
     assert ctypes.sizeof(aj.aj_info) == 88
     assert ctypes.sizeof(aj.aj_params) == 136
+
+
+def test_failure_hooks_validate_their_arguments_without_gpu_work():
+    L = aj.lib()
+    assert L.aj_test_barrier_stall(-2, 1.0) == aj.AJ_EINVAL
+    assert L.aj_test_barrier_stall(0, 0.0) == aj.AJ_EINVAL
+    assert L.aj_test_barrier_stall(0, 5000.0) == aj.AJ_EINVAL
+    assert L.aj_test_barrier_stall(-1, 1.0) == aj.AJ_OK   # disarm
+    assert L.aj_test_alloc_fail(-2) == aj.AJ_EINVAL
+    assert L.aj_test_alloc_fail(-1) == aj.AJ_OK          # disarm

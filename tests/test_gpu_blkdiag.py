@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import schedule
 import synth
 
 torch = pytest.importorskip("torch")
@@ -41,10 +42,7 @@ def _parity(Q, B, bs, T=200, tol_rel=REL, x0=None, **kw):
     Jb = oracle.j_blkdiag(Q, bs)
     for r in range(nrhs):
         xr0 = None if x0 is None else x0.reshape(nrhs, Q["n"])[r]
-        ref = oracle.solve(Q, B[:, r], Jblk=Jb, maxit=T, stop=oracle.STOP_NONE, x0=xr0)
-        if np.linalg.norm(X[r] - ref["x"]) > tol_rel * np.linalg.norm(ref["x"]):
-            ref = oracle.solve(Q, B[:, r], Jblk=Jb, maxit=T, stop=oracle.STOP_NONE, x0=xr0,
-                               forced=ctx.restart_log(r))
+        ref = schedule.replay(Q, B[:, r], ctx.restart_log(r), T, Jblk=Jb, x0=xr0)
         err = np.linalg.norm(X[r] - ref["x"]) / np.linalg.norm(ref["x"])
         assert err <= tol_rel, (r, err)
     return ctx, X

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import schedule
 import synth
 
 torch = pytest.importorskip("torch")
@@ -65,9 +66,7 @@ def test_sdd_comparison_matches_oracle(method):
     assert abs(info["iters"] - ref["iters"]) <= 1
     # the iterates: the oracle run for the GPU's iteration count
     T = info["iters"]
-    ref = oracle.solve(Q, b, J, maxit=T, stop=oracle.STOP_NONE, **okw)
-    if okw["restart"] and np.linalg.norm(x - ref["x"]) > 1e-10 * np.linalg.norm(ref["x"]):
-        ref = oracle.solve(Q, b, J, maxit=T, stop=oracle.STOP_NONE, forced=c.restart_log(), **okw)
+    ref = schedule.replay(Q, b, c.restart_log(), T, J=J, **okw)
     assert np.linalg.norm(x - ref["x"]) <= 1e-10 * np.linalg.norm(ref["x"])
     # the reported gap is the returned x's, against the closed form
     g = _exact_gap(x, n)

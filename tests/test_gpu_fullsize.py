@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import synth
+from stepcheck import one_step, state_parts
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -25,21 +26,6 @@ def workload():
     return _W["w"]
 
 
-def _state_parts(blob, n):
-    # header: magic, n, nrhs, pol, state_bytes, pad, sb[4]; then RhsState; then 3 buffers
-    hdr = np.frombuffer(blob[:64], dtype=np.uint8)
-    nrhs = int(np.frombuffer(blob[16:20], np.int32)[0])
-    sbytes = int(np.frombuffer(blob[24:28], np.int32)[0])
-    assert nrhs == 1 and sbytes == 112 and len(hdr) == 64
-    st = blob[64:64 + sbytes]
-    beta = float(np.frombuffer(st[8:16], np.float64)[0])
-    t = int(np.frombuffer(st[48:56], np.int64)[0])
-    cur, prev = (int(v) for v in np.frombuffer(st[88:96], np.int32))
-    off = 64 + sbytes
-    bufs = [np.frombuffer(blob[off + k * 8 * n: off + (k + 1) * 8 * n], np.float64) for k in range(3)]
-    return t, beta, bufs[cur], bufs[prev]
-
-
 @pytest.mark.parametrize("fmt", ["csr", "stencil"])
 def test_fullsize_step_matches_oracle_step(fmt):
     # CSR is the benchmark's configuration; AUTO takes the stencil format here
@@ -51,19 +37,14 @@ def test_fullsize_step_matches_oracle_step(fmt):
     ctx.set(stop=aj.AJ_STOP_NONE, maxit=T, format=F)
     assert ctx.format()[0] == F
     ctx.solve(out=torch.empty(n, dtype=torch.float64, device="cuda"))
-    t, beta, xT, xTm1 = _state_parts(ctx.get_state(), n)
-    assert t == T
+    st = state_parts(ctx.get_state(), n)
+    assert st["t"] == T
     ctx2 = aj.from_csr(Q, b, device="cuda")
     ctx2.set(stop=aj.AJ_STOP_NONE, maxit=T + 1, format=F)
     ctx2.set_state(ctx.get_state())
     x_next, info = ctx2.solve()
     assert info["iters"] == T + 1
-    y = xT + beta * (xT - xTm1)
-    if (T + 1) in ctx2.restart_log():
-        ref = xT  # a restart at T+1 keeps x^{T+1} = x^T
-    else:
-        ref = oracle.solve(Q, b, oracle.j_absrowsum(Q), restart=False, maxit=1,
-                           stop=oracle.STOP_NONE, x0=y)["x"]
+    ref = one_step(Q, b, oracle.j_absrowsum(Q), st, (T + 1) in ctx2.restart_log())
     err = np.linalg.norm(x_next - ref) / np.linalg.norm(ref)
     assert err <= 1e-12, err
 

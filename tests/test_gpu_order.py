@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import schedule
 import synth
 
 torch = pytest.importorskip("torch")
@@ -29,10 +30,7 @@ def _fixed_parity(Q, B, T=200, x0=None, tol_rel=REL, **kw):
     J = oracle.j_absrowsum(Q)
     for r in range(nrhs):
         xr0 = None if x0 is None else x0.reshape(nrhs, Q["n"])[r]
-        ref = oracle.solve(Q, B[:, r], J, maxit=T, stop=oracle.STOP_NONE, x0=xr0)
-        if np.linalg.norm(X[r] - ref["x"]) > tol_rel * np.linalg.norm(ref["x"]):
-            ref = oracle.solve(Q, B[:, r], J, maxit=T, stop=oracle.STOP_NONE, x0=xr0,
-                               forced=ctx.restart_log(r))
+        ref = schedule.replay(Q, B[:, r], ctx.restart_log(r), T, J=J, x0=xr0)
         err = np.linalg.norm(X[r] - ref["x"]) / np.linalg.norm(ref["x"])
         assert err <= tol_rel, (r, err)
     return ctx

@@ -2,10 +2,14 @@
 
 Tolerances: after a fixed number of iterations the iterates agree to relative
 ||x_gpu - x_oracle|| <= 1e-10 (FP64 and the double-float policy); every solve
-to tolerance reaches an FP64-verified relative residual <= tol.  If a restart
-decision differs between the two (the test quantity <Q y - b, x^t - x^{t-1}>
-is summed in different orders), the oracle is replayed with the GPU's restart
-schedule and must then agree to the same tolerance.
+to tolerance reaches an FP64-verified relative residual <= tol.  The oracle
+always runs with the GPU's restart schedule forced, and oracle.schedule checks
+that schedule against the rule of Algorithm alg-apg-re: the spacing
+t > K_re + K_ell exactly, and the decision on d = <Q y - b, x^t - x^{t-1}>
+(summed in different orders on the two sides) the oracle's own except at a
+rounding-level tie, |d| <= 1e-12 ||Q y - b|| ||x^t - x^{t-1}||.  Three tests
+require the oracle's own schedule outright: a solve with six restarts and no
+near tie, the strict spacing at K_0 = 64, and ties (d = 0) that restart.
 """
 import math
 
@@ -14,6 +18,7 @@ import pytest
 
 import oracle
 from oracle import dense
+from oracle import schedule
 import synth
 
 torch = pytest.importorskip("torch")
@@ -53,13 +58,10 @@ def _compare_fixed(Q, b, T, precision="fp64", restart=True, momentum=True, j_pol
                         x0=x0, sweep_form=FORMS.get(form, aj.AJ_SWEEP_AUTO))
     assert info["iters"] == T and info["status"] == aj.AJ_EMAXIT
     J = _oracle_J(Q, j_policy, L if L else info["L_used"])
-    ref = oracle.solve(Q, b, J, restart=restart, momentum=momentum, maxit=T,
-                       stop=oracle.STOP_NONE, x0=x0)
     sched = ctx.restart_log()
-    if info["restarts"] != ref["restarts"] or np.linalg.norm(x - ref["x"]) > tol_rel * np.linalg.norm(ref["x"]):
-        # replay the GPU's restart decisions in the oracle
-        ref = oracle.solve(Q, b, J, restart=restart, momentum=momentum, maxit=T,
-                           stop=oracle.STOP_NONE, x0=x0, forced=sched)
+    assert len(sched) == info["restarts"]
+    # the GPU's restart decisions, each the rule's own up to a rounding-level tie
+    ref = schedule.replay(Q, b, sched, T, J=J, restart=restart, momentum=momentum, x0=x0)
     err = np.linalg.norm(x - ref["x"]) / max(np.linalg.norm(ref["x"]), 1e-300)
     assert err <= tol_rel, (err, sched)
     return ctx, x, info, ref
@@ -171,8 +173,7 @@ def test_x0_and_device_pointers():
     ctx.set(stop=aj.AJ_STOP_NONE, maxit=90, x0=x0d)
     out = torch.empty(Q["n"], dtype=torch.float64, device="cuda")
     _, info = ctx.solve(out=out)
-    ref = oracle.solve(Q, b, oracle.j_absrowsum(Q), maxit=90, stop=oracle.STOP_NONE, x0=x0,
-                       forced=ctx.restart_log())
+    ref = schedule.replay(Q, b, ctx.restart_log(), 90, J=oracle.j_absrowsum(Q), x0=x0)
     xg = out.cpu().numpy()
     assert np.linalg.norm(xg - ref["x"]) <= REL * np.linalg.norm(ref["x"])
 
@@ -265,9 +266,7 @@ def test_multi_rhs_200_iterations_match_oracle(nrhs, case):
     J = oracle.j_absrowsum(Q)
     for r in range(nrhs):
         assert infos[r]["iters"] == T
-        ref = oracle.solve(Q, B[:, r], J, maxit=T, stop=oracle.STOP_NONE)
-        if np.linalg.norm(X[r] - ref["x"]) > REL * np.linalg.norm(ref["x"]):
-            ref = oracle.solve(Q, B[:, r], J, maxit=T, stop=oracle.STOP_NONE, forced=ctx.restart_log(r))
+        ref = schedule.replay(Q, B[:, r], ctx.restart_log(r), T, J=J)
         err = np.linalg.norm(X[r] - ref["x"]) / np.linalg.norm(ref["x"])
         assert err <= REL, (r, err)
     if case == "long_rows":
@@ -319,3 +318,61 @@ def test_invalid_matrices_rejected():
     ctx = aj.from_csr(good, np.ones(36))
     with pytest.raises(aj.AJError):
         ctx.set(K0=1)
+
+
+# ---------------------------------------------------------------- the restart rule itself
+def _stop_is_clear(tr_relres, iters, tol):
+    # the residual near tol carries a relative rounding error of about eps / tol
+    # on either side; the stop iteration is fixed when it is clear of that
+    return all(abs(tr_relres[t] / tol - 1.0) > 1e-2 for t in (iters - 1, iters))
+
+
+@pytest.mark.parametrize("precision,form", [("fp64", "auto"), ("fp64", "lazy"), ("fp64", "stored"),
+                                            ("fp64", "delta"), ("df64", "auto")])
+@pytest.mark.parametrize("fmt", ["csr", "auto"])
+def test_restart_schedule_equals_the_oracles(precision, form, fmt):
+    """2-D Poisson 64 x 64 to relative residual 1e-12: six restarts, and every
+    d_t is at least 1e-4 of its scale ||g|| ||x^t - x^{t-1}||, so no decision is
+    near a tie.  The GPU must take exactly the oracle's restart iterations
+    (Algorithm alg-apg-re) and stop at the oracle's iteration."""
+    Q, b, _ = synth.workload("poisson2d_64")
+    J = oracle.j_absrowsum(Q)
+    tol = 1e-12
+    ref = oracle.solve(Q, b, J, tol=tol, maxit=20000, trace=True)
+    nat = [int(t) for t in np.nonzero(ref["trace"]["restart"])[0]]
+    assert len(nat) >= 3
+    F = aj.AJ_FMT_CSR if fmt == "csr" else aj.AJ_FMT_AUTO
+    ctx, x, info = _gpu(Q, b, precision=precision, tol=tol, maxit=20000, format=F,
+                        sweep_form=FORMS.get(form, aj.AJ_SWEEP_AUTO))
+    assert ctx.restart_log() == nat
+    assert info["restarts"] == len(nat)
+    if _stop_is_clear(ref["trace"]["relres"], ref["iters"], tol):
+        assert info["iters"] == ref["iters"]
+    else:
+        assert abs(info["iters"] - ref["iters"]) <= 1
+
+
+def test_restart_spacing_is_strict():
+    """K_0 = 64 on 2-D Poisson 32 x 32: the oracle's d is already >= 0 (at 6 %
+    of its scale) at t = 64 = K_re + K_0, so the strict t > K_re + K_ell
+    restarts at 65, where t >= K_re + K_ell would restart at 64."""
+    Q, b, _ = synth.workload("poisson2d_32")
+    J = oracle.j_absrowsum(Q)
+    nat, _ = schedule.natural(Q, b, 200, J=J, K0=64)
+    assert nat == [65, 200]
+    for F in (aj.AJ_FMT_CSR, aj.AJ_FMT_AUTO):
+        ctx, x, info = _gpu(Q, b, stop=aj.AJ_STOP_NONE, maxit=200, K0=64, format=F)
+        assert ctx.restart_log() == nat
+
+
+def test_tie_restarts():
+    """b = 0 from x^0 = 0: g = 0 and x^t - x^{t-1} = 0 exactly, so d = 0, and
+    the non-strict d >= 0 restarts as soon as the spacing allows: t = 3, 8,
+    17, 34 for K_0 = 2."""
+    Q = synth.poisson2d(8)
+    z = np.zeros(Q["n"])
+    nat, _ = schedule.natural(Q, z, 40, J=oracle.j_absrowsum(Q))
+    assert nat == [3, 8, 17, 34]
+    for form in FORMS.values():
+        ctx, x, info = _gpu(Q, z, stop=aj.AJ_STOP_NONE, maxit=40, sweep_form=form)
+        assert ctx.restart_log() == nat and np.all(x == 0.0)
