@@ -55,7 +55,7 @@ def algorithmic_bytes(n, nnz, precision, form="min", stencil=False, nrhs=1):
     right-hand sides share one pass over the matrix."""
     vb = {"fp64": 8, "df64": 8, "fp32_ir": 4, "bf16_ir": 2}[precision]
     sb = {"fp64": 8, "df64": 8, "fp32_ir": 4, "bf16_ir": 4}[precision]
-    kvec = {"stored": 7, "delta": 8}.get(form, 5)
+    kvec = {"stored": 7, "delta": 8, "y": 6}.get(form, 5)
     matrix = 0 if stencil else nnz * (vb + 4) + 4 * (n + 1)
     return matrix + nrhs * n * kvec * sb
 
@@ -84,6 +84,10 @@ def fp64_ops(n, nnz, form="stored"):
     rr, ||g||^2)."""
     if form == "delta":
         return nnz + 8 * n
+    if form == "y":
+        # explicit y: g, ||g||^2, x update, x difference, y candidate, d (check
+        # sweeps add a second row sum and 2 per row, not counted here)
+        return nnz + 6 * n
     return (nnz + 9 * n) if form == "stored" else (2 * nnz + 11 * n)
 
 
@@ -176,12 +180,16 @@ def dist_env():
 
 
 def cpu_oracle_sample(Q, b, iters):
-    """Time the FP64 oracle (one thread, as it stands) on `iters` iterations."""
+    """Time the FP64 oracle as it stands on `iters` iterations, in its -O3
+    -fopenmp build (the same source and bits; rows of each product and the
+    element-wise updates over the host's cores, every sum in one thread).
+    Returns (seconds, cores)."""
     import oracle
     J = oracle.j_absrowsum(Q)
+    oracle.lib(omp=True)
     t0 = time.perf_counter()
-    oracle.solve(Q, b, J, maxit=iters, stop=oracle.STOP_NONE)
-    return time.perf_counter() - t0
+    oracle.solve(Q, b, J, maxit=iters, stop=oracle.STOP_NONE, omp=True)
+    return time.perf_counter() - t0, oracle.host_cores()
 
 
 def run_reference(args):
@@ -195,8 +203,9 @@ def run_reference(args):
     per_step = 2
     for _ in range(args.warmup):
         cpu_oracle_sample(Q, b, 1)
-    ts = [cpu_oracle_sample(Q, b, per_step) for _ in range(args.steps)]
-    tot = sum(ts)
+    samples = [cpu_oracle_sample(Q, b, per_step) for _ in range(args.steps)]
+    tot = sum(t for t, _ in samples)
+    cores = samples[-1][1]
     value = B * per_step * args.steps / tot / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -206,9 +215,9 @@ def run_reference(args):
         "config": {"workload": HEADLINE_WORKLOAD, "precision": "fp64", "format": "csr",
                    "parallelism": "replicas x%d" % ws,
                    "sample": "each step %d iterations of the oracle on this system" % per_step},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d steps x %d iterations of the FP64 C oracle, one thread"
-                                   % (args.steps, per_step)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d steps x %d iterations of the FP64 C oracle (-O3 -fopenmp build, "
+                                   "%d threads)" % (args.steps, per_step, cores)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -435,14 +444,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32_ir", "bf16_ir"])
-    ap.add_argument("--form", default="auto", choices=["auto", "lazy", "stored", "delta"],
+    ap.add_argument("--form", default="auto", choices=["auto", "lazy", "stored", "delta", "y"],
                     help="sweep form; auto = stored for fp64, lazy otherwise (the library's AUTO)")
     ap.add_argument("--format", default="csr", choices=["csr", "stencil"],
                     help="format of the timed context (the headline workload is CSR)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-iters", type=int, default=12)
+    ap.add_argument("--cpu-iters", type=int, default=60)
     ap.add_argument("--workload", default=WORKLOAD,
                     help="poisson3d_N | poisson2d_N | chunglu_N | rgg_N (profiling cases)")
     ap.add_argument("--no-graph", action="store_true")
@@ -487,7 +496,8 @@ def main():
             return "delta" if precision == "fp64" else "lazy"
         return form
 
-    SWEEP = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED, "delta": aj.AJ_SWEEP_DELTA}
+    SWEEP = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED, "delta": aj.AJ_SWEEP_DELTA,
+             "y": aj.AJ_SWEEP_Y}
 
     def make(precision, form, auto=False, fmt=None, **extra):
         # auto: leave the sweep form to the library (what a caller gets); the
@@ -597,7 +607,7 @@ def main():
     if not args.no_variants:
         var = {}
         for p in ("fp64", "df64", "fp32_ir", "bf16_ir"):
-            for fm in (("delta", "stored", "lazy") if p == "fp64" else ("stored", "lazy")):
+            for fm in (("y", "delta", "stored", "lazy") if p == "fp64" else ("y", "stored", "lazy")):
                 c = make(p, fm)
                 vms, vinf, _ = time_solves(c, 2, 1)
                 vb = algorithmic_bytes(n, nnz, p)
@@ -612,7 +622,7 @@ def main():
                 del c
         # the stencil format on the same system (where Q is a grid stencil):
         # the sweep computes Q's entries, so it moves the n-vectors alone
-        for p, fm in (("fp64", "delta"), ("fp32_ir", "lazy")):
+        for p, fm in (("fp64", "delta"), ("fp64", "y"), ("fp32_ir", "lazy"), ("fp32_ir", "y")):
             try:
                 c = make(p, fm, fmt=aj.AJ_FMT_STENCIL)
             except RuntimeError:
@@ -688,13 +698,14 @@ def main():
     # ---- CPU oracle on a bounded sample (rank 0, N = 1)
     if not args.no_cpu and ws == 1 and rank == 0:
         T = args.cpu_iters
-        t = cpu_oracle_sample(Q, b, T)
+        t, cores = cpu_oracle_sample(Q, b, T)
         cpu_v = B * T / t / 1e9
         line["cpu_baseline"] = {
-            "value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d iterations of the FP64 C oracle (one thread) on the same system; "
-                      "%.0f ms per iteration, %.1f s extrapolated to the GPU's %d iterations"
-                      % (T, 1e3 * t / T, t / T * infos[-1]["iters"], infos[-1]["iters"])}
+            "value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d iterations of the FP64 C oracle (-O3 -fopenmp build of the same source, "
+                      "%d threads: rows and element-wise updates parallel, sums serial) on the same "
+                      "system; %.0f ms per iteration, %.1f s extrapolated to the GPU's %d iterations"
+                      % (T, cores, 1e3 * t / T, t / T * infos[-1]["iters"], infos[-1]["iters"])}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -118,10 +118,22 @@ typedef struct {
  * per entry instead of two); LAZY for the other precisions on CSR, where the
  * second row sum gathers from the same cached lines (measured faster on the
  * 3-D Poisson system and on 2-D grids with 4 RHS). */
+/*   Y       keeps y^t itself as a vector: the sweep gathers y^t, forms x^t and
+ *           writes the candidate y^{t+1} = x^t + beta_{t+1} (x^t - x^{t-1})
+ *           (beta_{t+1} depends on alpha_t only, known before the restart
+ *           test; a restart drops the candidate and reads y^{t+1} = x^{t-1}
+ *           from that iterate's buffer).  One multiply-add per stored entry
+ *           and six n-vectors of traffic, but the exact residual of x^{t-1}
+ *           needs a second row sum: it is formed on check sweeps only, once
+ *           ||Q y^t - b|| <= 3 tol ||b|| and every 32 iterations, so a solve
+ *           stops at the first checked iterate within tol (the oracle's stop
+ *           iteration where the check schedule reaches it, at most 31
+ *           iterations later otherwise).  Not with AJ_STOP_OBJGAP. */
 #define AJ_SWEEP_AUTO 0
 #define AJ_SWEEP_LAZY 1
 #define AJ_SWEEP_STORED 2
 #define AJ_SWEEP_DELTA 3
+#define AJ_SWEEP_Y 4
 
 /* Storage of Q for the fused sweep.  CSR: one row per thread.  SELL: the
  * SELL-C-sigma layout (C = 32, rows sorted by length within windows of sigma
@@ -179,7 +191,7 @@ typedef struct {
   double inner_tol;      /* IR modes: relative tolerance of each inner solve (default 1e-4) */
   int64_t max_outer;     /* IR modes: outer refinement steps (default 30) */
   int grid_ctas;         /* 0 = automatic; otherwise the number of persistent CTAs */
-  int sweep_form;        /* AJ_SWEEP_AUTO (default) | AJ_SWEEP_LAZY | AJ_SWEEP_STORED | AJ_SWEEP_DELTA */
+  int sweep_form;        /* AJ_SWEEP_AUTO (default) | _LAZY | _STORED | _DELTA | _Y */
   int sell_sigma;        /* AJ_FMT_SELL: sorting window sigma in rows (0 = 256) */
   int sell_lmax;         /* AJ_FMT_SELL: rows longer than this go to the warp-per-row bucket (0 = 64) */
   int reorder;           /* AJ_REORDER_AUTO (default) | AJ_REORDER_NONE | AJ_REORDER_RCM */
@@ -261,7 +273,12 @@ aj_status aj_pcg_solve(aj_ctx* ctx, double* x_out, int x_on_device, aj_info* inf
  * use the first context's stream.  Contexts whose sweep forms differ (AUTO
  * gives SELL matrices the stored form, CSR and stencil ones the lazy form in
  * the reduced precisions) run as one launch per sweep form, one after
- * another. */
+ * another; every member's info then reports the whole call (ms, kernel_ms
+ * and launches summed over the forms).  The return value is AJ_OK or the
+ * first solver status (AJ_EMAXIT, AJ_EDIVERGED, AJ_ENONFINITE) of a member,
+ * with every x_out and info written; any other error ends the call, and then
+ * only the members of the forms that had already run have their x_out and
+ * info written. */
 aj_status aj_solve_batch(aj_ctx* const* ctx, int count, double* const* x_out, int x_on_device,
                          aj_info* info);
 
@@ -370,10 +387,12 @@ const char* aj_strerror(aj_status s);
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current) and the kernel's
  * occupancy; make that first call before any stream capture begins.  Every
- * call on a device shares the one array, and it keeps the last call's
- * contents (each call re-initialises what must start at zero): calls whose
- * GPU work overlaps -- from two host threads, or on two streams -- race on
- * it and must be serialised by the caller. */
+ * call copies its status and solver state to the host and synchronises
+ * cuda_stream before it returns.  Every call on a device shares the one
+ * array, and it keeps the last call's contents (each call re-initialises what
+ * must start at zero): calls whose GPU work overlaps -- from two host
+ * threads, or on two streams -- race on it and must be serialised by the
+ * caller. */
 #define AJ_NOALLOC_MAX_N 131072
 aj_status aj_solve_noalloc(const aj_csr* Q, const double* b, const aj_params* p, double* x_out,
                            aj_info* info, void* cuda_stream);

@@ -20,7 +20,7 @@ from . import build as _build
 
 STOP_NONE, STOP_RELRES, STOP_OBJGAP = 0, 1, 2
 
-_lib = None
+_libs = {}
 
 
 class _Params(ctypes.Structure):
@@ -39,13 +39,20 @@ class _Info(ctypes.Structure):
 
 class _Trace(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in
-                ("alpha", "beta", "d", "restart", "f", "relres", "gnorm", "x", "y", "dxnorm")]
+                ("alpha", "beta", "d", "restart", "f", "relres", "gnorm", "x", "y", "dxnorm", "gfloor")]
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        path = _build.build()
+def host_cores():
+    """Cores this process may run on (its CPU affinity)."""
+    import os
+    return len(os.sched_getaffinity(0))
+
+
+def lib(omp=False):
+    """The correctness build, or (omp=True) the OpenMP timing build of the
+    same source, which computes the same bits on all the host's cores."""
+    if omp not in _libs:
+        path = _build.build_omp() if omp else _build.build()
         L = ctypes.CDLL(path)
         L.orc_spmv.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5
         L.orc_j_absrowsum.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 4
@@ -57,8 +64,8 @@ def lib():
                                                                               ctypes.c_void_p, ctypes.c_void_p,
                                                                               ctypes.c_void_p]
         L.orc_pcg_solve.restype = ctypes.c_int
-        _lib = L
-    return _lib
+        _libs[omp] = L
+    return _libs[omp]
 
 
 def _p(a):
@@ -159,11 +166,11 @@ def pcg(Q, b, *, maxit=1000, tol=1e-8, x0=None):
 
 
 def solve(Q, b, J=None, *, Jblk=None, restart=True, momentum=True, K0=2, maxit=1000, stop=STOP_RELRES,
-          tol=1e-8, fstar=0.0, x0=None, forced=None, trace=False, trace_iterates=False):
+          tol=1e-8, fstar=0.0, x0=None, forced=None, trace=False, trace_iterates=False, omp=False):
     """Run Algorithm alg-jacobi with the diagonal J or, if given, the block
     diagonal Jblk (from ``j_blkdiag``); returns a dict with x, iters,
     restarts, relres, f, converged and (trace=True) per-iteration arrays
-    indexed by t."""
+    indexed by t.  omp=True runs the OpenMP timing build (same bits)."""
     n, rp, ci, v = _csr(Q)
     b = np.ascontiguousarray(b, dtype=np.float64)
     bs = 0
@@ -188,16 +195,16 @@ def solve(Q, b, J=None, *, Jblk=None, restart=True, momentum=True, K0=2, maxit=1
     T = None
     if trace or trace_iterates:
         m = maxit + 1
-        for k in ("alpha", "beta", "d", "f", "relres", "gnorm", "dxnorm"):
+        for k in ("alpha", "beta", "d", "f", "relres", "gnorm", "dxnorm", "gfloor"):
             tr[k] = np.full(m, np.nan)
         tr["restart"] = np.zeros(m, dtype=np.uint8)
         if trace_iterates:
             tr["x"] = np.full((m, n), np.nan)
             tr["y"] = np.full((m, n), np.nan)
         T = _Trace(*[_p(tr.get(k)) for k in ("alpha", "beta", "d", "restart", "f", "relres",
-                                              "gnorm", "x", "y", "dxnorm")])
-    rc = lib().orc_aj_solve(ctypes.byref(P), _p(x), ctypes.byref(info),
-                            ctypes.byref(T) if T is not None else None)
+                                              "gnorm", "x", "y", "dxnorm", "gfloor")])
+    rc = lib(omp).orc_aj_solve(ctypes.byref(P), _p(x), ctypes.byref(info),
+                               ctypes.byref(T) if T is not None else None)
     if rc != 0:
         raise ValueError("oracle rejected the input")
     out = dict(x=x, iters=info.iters, restarts=info.restarts, relres=info.relres, f=info.f,

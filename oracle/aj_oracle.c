@@ -11,6 +11,11 @@
  *
  * Every loop runs in index order; every row sum runs in ascending column
  * order as the CSR arrays hold it.  No blocking, no fusion, no reordering.
+ * The baseline timing build (oracle/build.py, -fopenmp) spreads the loops
+ * whose iterations are independent -- the rows of a product, element-wise
+ * vector updates -- over threads (the OMP lines below; the correctness
+ * build ignores them); every sum, a row's or a dot product's, still runs in
+ * index order in one thread, so both builds give the same bits.
  *
  *   orc_spmv          out = Q y                          (the product in Alg. 3, step "x^t = ...")
  *   orc_j_absrowsum   J_kk = Q_kk + sum_{j!=k} |Q_kj|     (eq. J-diag, Section 3)
@@ -32,9 +37,17 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Independent iterations over threads in the -fopenmp timing build only. */
+#ifdef _OPENMP
+#define OMP_ROWS _Pragma("omp parallel for schedule(static)")
+#else
+#define OMP_ROWS
+#endif
+
 /* out_i = sum_j Q_ij y_j, j in CSR order (ascending column). */
 void orc_spmv(int64_t n, const int32_t* row_ptr, const int32_t* col,
               const double* val, const double* y, double* out) {
+  OMP_ROWS
   for (int64_t i = 0; i < n; i++) {
     double s = 0.0;
     for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; p++) s += val[p] * y[col[p]];
@@ -119,6 +132,9 @@ typedef struct {
  *   tr_f[t]       f(x^t) after the branch (t = 0: f(x^0))
  *   tr_relres[t]  relative residual of x^t after the branch
  *   tr_gnorm[t]   ||Q y^t - b||_2
+ *   tr_gfloor[t]  || |Q| |y^t| + |b| ||_2: the scale of the rounding error in Q y^t - b (a
+ *                 row sum of k terms in unit roundoff u errs by at most about k u times
+ *                 that row's entry)
  *   tr_dxnorm[t]  ||x^t - x^{t-1}||_2 with x^t before the restart branch (the scale of the
  *                 restart test: |d| <= ||Q y^t - b|| ||x^t - x^{t-1}|| by Cauchy-Schwarz)
  *   tr_x          (maxit + 1) x n: x^t after the branch, row t
@@ -135,6 +151,7 @@ typedef struct {
   double* x;
   double* y;
   double* dxnorm;
+  double* gfloor;
 } orc_trace;
 
 static void eval_x(const orc_params* P, const double* x, double* qx, double bnorm,
@@ -231,6 +248,7 @@ int orc_aj_solve(const orc_params* P, double* x_out, orc_info* info, const orc_t
   }
   if (P->x0)
     for (int64_t i = 0; i < n; i++) xprev[i] = P->x0[i];
+  OMP_ROWS
   for (int64_t i = 0; i < n; i++) { x[i] = xprev[i]; y[i] = xprev[i]; }
 
   double bnorm = sqrt(dot(n, P->b, P->b));
@@ -248,7 +266,17 @@ int orc_aj_solve(const orc_params* P, double* x_out, orc_info* info, const orc_t
     if (T && T->y) memcpy(T->y + (size_t)t * n, y, (size_t)n * sizeof(double));
     /* g = Q y^t - b */
     orc_spmv(n, P->row_ptr, P->col, P->val, y, g);
+    OMP_ROWS
     for (int64_t i = 0; i < n; i++) g[i] -= P->b[i];
+    double gfl = 0.0; /* trace only: || |Q| |y^t| + |b| || */
+    if (T && T->gfloor) {
+      for (int64_t i = 0; i < n; i++) {
+        double s = fabs(P->b[i]);
+        for (int32_t p = P->row_ptr[i]; p < P->row_ptr[i + 1]; p++) s += fabs(P->val[p]) * fabs(y[P->col[p]]);
+        gfl += s * s;
+      }
+      gfl = sqrt(gfl);
+    }
     /* x^t = y^t + J^{-1}(b - Q y^t) = y^t - J^{-1} g */
     if (P->Jblk) {
       for (int64_t r0 = 0; r0 < n; r0 += bs) {
@@ -257,6 +285,7 @@ int orc_aj_solve(const orc_params* P, double* x_out, orc_info* info, const orc_t
         for (int64_t k = 0; k < nb; k++) x[r0 + k] = y[r0 + k] - zb[k];
       }
     } else {
+      OMP_ROWS
       for (int64_t i = 0; i < n; i++) x[i] = y[i] - g[i] / P->J[i];
     }
     /* restart test quantity <Q y^t - b, x^t - x^{t-1}> */
@@ -274,6 +303,7 @@ int orc_aj_solve(const orc_params* P, double* x_out, orc_info* info, const orc_t
       Kre = t;
       K = 2 * K;
       ell++;
+      OMP_ROWS
       for (int64_t i = 0; i < n; i++) { x[i] = xprev[i]; y[i] = xprev[i]; }
       alpha_next = 1.0; /* alpha_{t+1} = 1, alpha_t = 0 */
       beta = 0.0;
@@ -285,6 +315,7 @@ int orc_aj_solve(const orc_params* P, double* x_out, orc_info* info, const orc_t
         alpha_next = 1.0;
         beta = 0.0;
       }
+      OMP_ROWS
       for (int64_t i = 0; i < n; i++) {
         y[i] = x[i] + beta * (x[i] - xprev[i]);
         xprev[i] = x[i];
@@ -296,6 +327,7 @@ int orc_aj_solve(const orc_params* P, double* x_out, orc_info* info, const orc_t
     if (T && T->restart) T->restart[t] = (uint8_t)restart;
     if (T && T->gnorm) T->gnorm[t] = sqrt(gg);
     if (T && T->dxnorm) T->dxnorm[t] = sqrt(dd);
+    if (T && T->gfloor) T->gfloor[t] = gfl;
     alpha = alpha_next;
     eval_x(P, x, qx, bnorm, &relres, &f);
     if (T && T->f) T->f[t] = f;

@@ -17,9 +17,15 @@ the only difference allowed:
   iteration, evaluates the rule on the oracle's own d_t.  Wherever the rule
   decides otherwise than the schedule, |d_t| must be at most
   ``guard * ||Q y^t - b|| * ||x^t - x^{t-1}||`` (guard = 1e-12 by default);
-  any other difference raises ``ScheduleError``.  A schedule that passes is
-  the rule's own up to rounding-level ties, and the returned oracle run is the
-  trajectory the GPU must match.
+  any other difference raises ``ScheduleError``.  Once the iteration has
+  converged to the rounding level, Q y^t - b is itself rounding noise and
+  so is the sign of d_t: the tie band then also admits
+  |d_t| <= 64 (u + u_64) || |Q| |y^t| + |b| || ||x^t - x^{t-1}||, the
+  rounding error a row sum of up to 64 terms can put into g in the GPU's
+  unit roundoff u (2^-53 in FP64, 2^-48 in double-float) and the oracle's
+  u_64 = 2^-53.  A schedule that passes is the rule's own up to
+  rounding-level ties, and the returned oracle run is the trajectory the GPU
+  must match.
 * ``natural`` returns the oracle's own schedule, for tests that require the
   schedules to be equal outright.
 """
@@ -28,6 +34,8 @@ import numpy as np
 from . import STOP_NONE, solve
 
 GUARD = 1e-12
+UNIT_ROUNDOFF = {"fp64": 2.0 ** -53, "df64": 2.0 ** -48}
+FLOOR_TERMS = 64
 
 
 class ScheduleError(AssertionError):
@@ -50,7 +58,7 @@ def check_spacing(sched, K0=2, restart=True):
 
 
 def replay(Q, b, sched, T, *, J=None, Jblk=None, restart=True, momentum=True, K0=2, x0=None,
-           guard=GUARD):
+           guard=GUARD, precision="fp64"):
     """Oracle run of T iterations with the schedule forced, every decision of
     which is checked against the rule on the oracle's d_t (see the module
     docstring).  Returns the oracle's result dict plus ``flips``: the
@@ -60,6 +68,7 @@ def replay(Q, b, sched, T, *, J=None, Jblk=None, restart=True, momentum=True, K0
     ref = solve(Q, b, J, Jblk=Jblk, restart=restart, momentum=momentum, K0=K0, maxit=T,
                 stop=STOP_NONE, x0=x0, forced=sched, trace=True)
     tr = ref["trace"]
+    floor_unit = FLOOR_TERMS * (UNIT_ROUNDOFF[precision] + UNIT_ROUNDOFF["fp64"])
     S = set(sched)
     Kre, K = 0, int(K0)
     flips = []
@@ -69,13 +78,14 @@ def replay(Q, b, sched, T, *, J=None, Jblk=None, restart=True, momentum=True, K0
         natural_t = bool(restart) and t > Kre + K and d >= 0.0
         if forced_t != natural_t:
             scale = float(tr["gnorm"][t]) * float(tr["dxnorm"][t])
-            if not abs(d) <= guard * scale:
+            floor = floor_unit * float(tr["gfloor"][t]) * float(tr["dxnorm"][t])
+            if not abs(d) <= guard * scale + floor:
                 raise ScheduleError(
                     "iteration %d: schedule %s, rule on the oracle's d = %.3e says %s; "
-                    "|d| / (||g|| ||dx||) = %.3e > %.0e" % (
+                    "|d| / (||g|| ||dx||) = %.3e > %.0e, rounding floor %.3e" % (
                         t, "restarts" if forced_t else "continues", d,
                         "restart" if natural_t else "continue",
-                        abs(d) / scale if scale > 0 else np.inf, guard))
+                        abs(d) / scale if scale > 0 else np.inf, guard, floor))
             flips.append(t)
         if forced_t:
             Kre, K = t, 2 * K

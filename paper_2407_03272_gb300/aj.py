@@ -20,7 +20,7 @@ AJ_RESTART_NONE, AJ_RESTART_ADAPTIVE = 0, 1
 AJ_STOP_RELRES, AJ_STOP_OBJGAP, AJ_STOP_NONE = 0, 1, 2
 AJ_FP64, AJ_DF64, AJ_FP32_IR, AJ_BF16_IR = 0, 1, 2, 3
 AJ_FMT_AUTO, AJ_FMT_CSR, AJ_FMT_SELL, AJ_FMT_STENCIL = 0, 1, 2, 3
-AJ_SWEEP_AUTO, AJ_SWEEP_LAZY, AJ_SWEEP_STORED, AJ_SWEEP_DELTA = 0, 1, 2, 3
+AJ_SWEEP_AUTO, AJ_SWEEP_LAZY, AJ_SWEEP_STORED, AJ_SWEEP_DELTA, AJ_SWEEP_Y = 0, 1, 2, 3, 4
 AJ_REORDER_AUTO, AJ_REORDER_NONE, AJ_REORDER_RCM = 0, 1, 2
 AJ_NOALLOC_MAX_N = 131072
 
@@ -298,15 +298,51 @@ def solve_batch(ctxs, outs, on_device=False):
     return [i.as_dict() for i in infos]
 
 
+def _check_noalloc_args(row_ptr, col, val, b, x_out, x0):
+    """The kernels of aj_solve_noalloc read row_ptr (n + 1 int32), col (nnz
+    int32), val (nnz float64), b and x0 (n float64) and write x_out (n
+    float64) through raw pointers: refuse anything else before the call."""
+    import torch
+    named = [("row_ptr", row_ptr, torch.int32), ("col", col, torch.int32), ("val", val, torch.float64),
+             ("b", b, torch.float64), ("x_out", x_out, torch.float64)]
+    if x0 is not None:
+        named.append(("x0", x0, torch.float64))
+    for name, t, dt in named:
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("aj_solve_noalloc: %s must be a torch tensor" % name)
+        if t.dtype != dt:
+            raise ValueError("aj_solve_noalloc: %s must be %s, not %s" % (name, dt, t.dtype))
+        if t.dim() != 1 or not t.is_contiguous():
+            raise ValueError("aj_solve_noalloc: %s must be a contiguous vector" % name)
+    n = row_ptr.numel() - 1
+    if n < 0:
+        raise ValueError("aj_solve_noalloc: row_ptr needs n + 1 entries")
+    if val.numel() != col.numel():
+        raise ValueError("aj_solve_noalloc: val and col differ in length")
+    for name, t, _ in named[3:]:
+        if t.numel() < n:
+            raise ValueError("aj_solve_noalloc: %s holds %d entries, n = %d" % (name, t.numel(), n))
+    dev = None
+    for name, t, _ in named:
+        if not t.is_cuda:
+            raise ValueError("aj_solve_noalloc takes device arrays only (%s is on %s)" % (name, t.device))
+        dev = t.device if dev is None else dev
+        if t.device != dev:
+            raise ValueError("aj_solve_noalloc: %s is on %s, row_ptr on %s" % (name, t.device, dev))
+    if dev.index != torch.cuda.current_device():
+        raise ValueError("aj_solve_noalloc: the arrays are on %s, the current device is cuda:%d"
+                         % (dev, torch.cuda.current_device()))
+
+
 def solve_noalloc(row_ptr, col, val, b, x_out, stream=None, **kw):
     """aj_solve_noalloc on device tensors: the FP64 solve for one right-hand
     side with the library's fixed scratch array (no device allocation inside
-    the call).  Returns (status, info dict)."""
-    ptrs = [_ptr(a) for a in (row_ptr, col, val, b, x_out)]
-    if not all(dev for _, dev in ptrs):
-        raise ValueError("aj_solve_noalloc takes device arrays only")
-    p = params(**kw)
+    the call).  Returns (status, info dict).  The tensors' types, lengths and
+    device are checked first (ValueError)."""
     x0 = kw.get("x0")
+    _check_noalloc_args(row_ptr, col, val, b, x_out, x0)
+    ptrs = [_ptr(a) for a in (row_ptr, col, val, b, x_out)]
+    p = params(**kw)
     if x0 is not None:
         p.x0, p.x0_on_device = _ptr(x0)
     csr = aj_csr(int(len(row_ptr) - 1), int(len(col)), ptrs[0][0], ptrs[1][0], ptrs[2][0], 1)

@@ -227,7 +227,7 @@ struct aj_ctx {
   void* bp = nullptr;
   void* jinvp = nullptr;
   void* x[3] = {nullptr, nullptr, nullptr};
-  void* u[2] = {nullptr, nullptr};  // Q x^t, Q x^{t-1} (stored sweep forms)
+  void* u[2] = {nullptr, nullptr};  // Q x^t, Q x^{t-1} (stored sweep forms); y^t, y^{t+1} (explicit y)
   void* dl = nullptr;               // x^t - x^{t-1} (difference sweep form)
   // SELL-C-sigma copy of Q (fmt = 1), rebuilt by aj_set
   Workspace sws;
@@ -244,7 +244,7 @@ struct aj_ctx {
   int *d_perm = nullptr, *d_rlen = nullptr, *d_sptr = nullptr, *d_scol = nullptr;
   int *d_long = nullptr, *d_ltp = nullptr, *d_huge = nullptr;
   void* d_sval = nullptr;
-  int qx = 0;                       // sweep form in use: 1 stored, 0 lazy
+  int qx = 0;                       // sweep form in use: 0 lazy, 1 stored, 2 difference, 3 explicit y
   double sQ = 1.0;
   double sb[kMaxRhs] = {1, 1, 1, 1};
   double L_used = 0.0;
@@ -838,8 +838,9 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   if (p->precision < AJ_FP64 || p->precision > AJ_BF16_IR) return AJ_EINVAL;
   if (p->format < AJ_FMT_AUTO || p->format > AJ_FMT_STENCIL) return AJ_EINVAL;
   if (p->grid_ctas < 0) return AJ_EINVAL;
-  if (p->sweep_form < AJ_SWEEP_AUTO || p->sweep_form > AJ_SWEEP_DELTA) return AJ_EINVAL;
+  if (p->sweep_form < AJ_SWEEP_AUTO || p->sweep_form > AJ_SWEEP_Y) return AJ_EINVAL;
   if (p->sweep_form == AJ_SWEEP_DELTA && p->precision != AJ_FP64) return AJ_EINVAL;
+  if (p->sweep_form == AJ_SWEEP_Y && p->stop == AJ_STOP_OBJGAP) return AJ_EINVAL;
   if (p->sell_sigma < 0 || p->sell_lmax < 0) return AJ_EINVAL;
   if (p->reorder < AJ_REORDER_AUTO || p->reorder > AJ_REORDER_RCM) return AJ_EINVAL;
   if ((p->precision == AJ_FP32_IR || p->precision == AJ_BF16_IR) &&
@@ -939,7 +940,8 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     const int kp = kernel_pol(pol);
     const int bps = std::max({1, persistent_blocks_per_sm(kp, nrhs, 0),
                               persistent_blocks_per_sm(kp, nrhs, 1),
-                              persistent_blocks_per_sm(kp, nrhs, 2)});
+                              persistent_blocks_per_sm(kp, nrhs, 2),
+                              persistent_blocks_per_sm(kp, nrhs, 3)});
     const int maxg = bps * c->sm_count;
     c->partials = (double*)c->pws.alloc((size_t)2 * maxg * nrhs * kNRed * 8);
     c->part_cap = maxg;
@@ -956,6 +958,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   c->qx = p->sweep_form == AJ_SWEEP_LAZY     ? 0
           : p->sweep_form == AJ_SWEEP_STORED ? 1
           : p->sweep_form == AJ_SWEEP_DELTA  ? 2
+          : p->sweep_form == AJ_SWEEP_Y      ? 3
           : (p->precision == AJ_FP64 ? 2 : 1);
   size_grid(c);
   // --- scaled copies for the non-FP64 policies (powers of two: exact)
@@ -2428,7 +2431,9 @@ extern "C" aj_status aj_solve_batch(aj_ctx* const* ctx, int count, double* const
     // one lockstep batch per sweep form (AUTO gives SELL matrices the stored
     // form and CSR ones the lazy form; the kernel runs one form), in turn
     aj_status worst = AJ_OK;
-    for (int q = 0; q < 3; q++) {
+    double ms_all = 0.0, kms_all = 0.0;
+    int64_t launches_all = 0;
+    for (int q = 0; q < 4; q++) {
       std::vector<aj_ctx*> cs;
       std::vector<double*> xs;
       std::vector<int> idx;
@@ -2444,8 +2449,18 @@ extern "C" aj_status aj_solve_batch(aj_ctx* const* ctx, int count, double* const
       if (s != AJ_OK && s != AJ_EMAXIT && s != AJ_EDIVERGED && s != AJ_ENONFINITE) return s;
       for (size_t k = 0; k < cs.size(); k++)
         if (info) info[idx[k]] = inf[k];
+      // the launches of one form run one after another: the call's totals are their sums
+      ms_all += inf[0].ms;
+      kms_all += inf[0].kernel_ms;
+      launches_all += inf[0].launches;
       if (s != AJ_OK && worst == AJ_OK) worst = s;
     }
+    if (info)
+      for (int i = 0; i < count; i++) {
+        info[i].ms = ms_all;
+        info[i].kernel_ms = kms_all;
+        info[i].launches = launches_all;
+      }
     return worst;
   }
   int dev_prev = 0;

@@ -92,7 +92,10 @@ static cudaError_t launch_lockstep_p(int qx, const LockLaunch& B, int grid, cuda
   const void* k = nullptr;
   if (qx == 0) k = (const void*)aj_lockstep_kernel<P, 0>;
   else if (qx == 1) k = (const void*)aj_lockstep_kernel<P, 1>;
-  else if constexpr (kHasDelta<P>) k = (const void*)aj_lockstep_kernel<P, 2>;
+  else if (qx == 3) k = (const void*)aj_lockstep_kernel<P, 3>;
+  else if constexpr (kHasDelta<P>) {
+    if (qx == 2) k = (const void*)aj_lockstep_kernel<P, 2>;
+  }
   if (!k) return cudaErrorInvalidValue;
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
 }
@@ -115,6 +118,7 @@ template <class P, bool MULTI>
 static const void* persistent_fn(int sf, int fm) {
   if (sf == 0) return persistent_fm<P, 0, MULTI>(fm);
   if (sf == 1) return persistent_fm<P, 1, MULTI>(fm);
+  if (sf == 3) return persistent_fm<P, 3, MULTI>(fm);
   if constexpr (kHasDelta<P>)
     if (sf == 2) return persistent_fm<P, 2, MULTI>(fm);
   return nullptr;
@@ -171,6 +175,7 @@ cudaError_t AJ_CAT(launch_lockstep_, AJ_SUFFIX)(int qx, const LockLaunch& B, int
 int AJ_CAT(lockstep_blocks_per_sm_, AJ_SUFFIX)(int qx) {
   if (qx == 0) return occ_of((const void*)aj_lockstep_kernel<AJ_POL, 0>);
   if (qx == 1) return occ_of((const void*)aj_lockstep_kernel<AJ_POL, 1>);
+  if (qx == 3) return occ_of((const void*)aj_lockstep_kernel<AJ_POL, 3>);
   if constexpr (kHasDelta<AJ_POL>)
     if (qx == 2) return occ_of((const void*)aj_lockstep_kernel<AJ_POL, 2>);
   return 0;

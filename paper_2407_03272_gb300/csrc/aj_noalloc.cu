@@ -50,7 +50,8 @@ constexpr size_t kOffRlog = align256(kOffState + sizeof(RhsState));
 constexpr size_t kOffBar = align256(kOffRlog + (size_t)kNaRlogCap * 8);
 constexpr size_t kOffErr = kOffBar + 64;
 constexpr size_t kOffFlags = kOffErr + 64;
-constexpr size_t kScratchBytes = align256(kOffFlags + 64);
+constexpr size_t kOffBpart = kOffFlags + 64;  // per-block partial sums of ||b||^2
+constexpr size_t kScratchBytes = align256(kOffBpart + (size_t)kNaMaxTiles * 8);
 
 // The fixed scratch: about 6.1 MB, held by every GPU that loads libaj.
 static __device__ __align__(256) unsigned char g_na_scratch[kScratchBytes];
@@ -108,12 +109,36 @@ __global__ void k_na_prepare(int n, long long nnz, const int* rp, const int* ci,
   jinv[i] = 1.0 / j;
 }
 
+// ||b||^2 in the order aj_create forms it, so that the stop test sees the
+// same bits: per block of 256 entries, the squares summed by a xor tree over
+// each warp's lanes and then the 8 warps in order (one partial per block,
+// into bpart); k_na_init then adds the partials in block order.  A
+// non-finite entry sets flag bit 32.
+__global__ void k_na_bnorm2(int n, const double* b, double* bpart, int* flags) {
+  __shared__ double sm[kNaThreads / 32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (i < n) {
+    const double bi = b[i];
+    if (!isfinite(bi)) atomicOr(flags, 32);
+    v = __dmul_rn(bi, bi);
+  }
+  for (int m = 16; m >= 1; m >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, m));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kNaThreads / 32; k++) s = __dadd_rn(s, sm[k]);
+    bpart[blockIdx.x] = s;
+  }
+}
+
 // x^0 into iterate buffer 0; clears the barrier counter, the error word and
-// the restart log; block 0 thread 0 also checks b and forms ||b||^2 in index
-// order and writes the initial solver state.
-__global__ void k_na_init(int n, const double* x0, const double* b, long long K0, double* x,
-                          RhsState* st, long long* rlog, unsigned long long* bar, int* err,
-                          int* flags) {
+// the restart log; block 0 thread 0 also adds the block partials of ||b||^2
+// (k_na_bnorm2) in block order and writes the initial solver state.
+__global__ void k_na_init(int n, const double* x0, const double* bpart, int nbpart, long long K0,
+                          double* x, RhsState* st, long long* rlog, unsigned long long* bar,
+                          int* err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] = x0 ? x0[i] : 0.0;
   if (i < kNaRlogCap) rlog[i] = -1;
@@ -121,13 +146,7 @@ __global__ void k_na_init(int n, const double* x0, const double* b, long long K0
     *bar = 0ull;
     *err = 0;
     double s = 0.0;
-    bool fin = true;
-    for (int k = 0; k < n; k++) {
-      const double v = b[k];
-      fin = fin && isfinite(v);
-      s = __dadd_rn(s, __dmul_rn(v, v));
-    }
-    if (!fin) atomicOr(flags, 32);
+    for (int k = 0; k < nbpart; k++) s = __dadd_rn(s, bpart[k]);
     RhsState q;
     memset(&q, 0, sizeof(q));
     q.alpha = 1.0;
@@ -241,6 +260,7 @@ extern "C" aj_status aj_solve_noalloc(const aj_csr* Q, const double* b, const aj
   unsigned long long* bar = (unsigned long long*)(base + kOffBar);
   int* err = (int*)(base + kOffErr);
   int* flags = (int*)(base + kOffFlags);
+  double* bpart = (double*)(base + kOffBpart);
   const unsigned blocks = (unsigned)((n + kNaThreads - 1) / kNaThreads);
   int launches = 0;
 
@@ -248,8 +268,9 @@ extern "C" aj_status aj_solve_noalloc(const aj_csr* Q, const double* b, const aj
   NA_CK(cudaMemsetAsync(flags, 0, sizeof(int), s));
   k_na_prepare<<<blocks, kNaThreads, 0, s>>>(n, Q->nnz, Q->row_ptr, Q->col, Q->val, p->j_policy,
                                              p->L, jinv, flags);
-  k_na_init<<<blocks, kNaThreads, 0, s>>>(n, p->x0, b, p->K0, xb[0], st, rlog, bar, err, flags);
-  launches += 2;
+  k_na_bnorm2<<<blocks, kNaThreads, 0, s>>>(n, b, bpart, flags);
+  k_na_init<<<blocks, kNaThreads, 0, s>>>(n, p->x0, bpart, (int)blocks, p->K0, xb[0], st, rlog, bar, err);
+  launches += 3;
   NA_CK(cudaGetLastError());
   int hflags = 0;
   NA_CK(cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -272,7 +293,9 @@ extern "C" aj_status aj_solve_noalloc(const aj_csr* Q, const double* b, const aj
   L.jinv = jinv;
   for (int k = 0; k < 3; k++) L.x[k] = xb[k];
   for (int k = 0; k < 2; k++) L.u[k] = ub[k];
-  L.qx = 1;  // the stored sweep form, as aj_set picks for AJ_FP64
+  // the stored sweep form: the same iterates, bit for bit, as the difference
+  // form, with one n-vector less of scratch
+  L.qx = 1;
   L.partials = part;
   L.bar = bar;
   L.err = err;

@@ -203,19 +203,21 @@ __global__ void k_bnorm2(int n, int nrhs, const double* b, double* part, int* ba
     for (int r = 0; r < nrhs; r++) {
       const double v = b[(long long)i * nrhs + r];
       if (!isfinite(v)) *bad = 1;
-      acc[r] = v * v;
+      acc[r] = __dmul_rn(v, v);
     }
   }
+  // explicitly rounded operations (no contraction), so that another kernel
+  // written with the same operations gives the same bits
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = 0; k < nrhs; k++) {
     double v = acc[k];
-    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+    for (int m = 16; m >= 1; m >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, m));
     if (lane == 0) sm[k][w] = v;
   }
   __syncthreads();
   if (threadIdx.x < nrhs) {
     double v = 0.0;
-    for (int k = 0; k < kSetupThreads / 32; k++) v += sm[threadIdx.x][k];
+    for (int k = 0; k < kSetupThreads / 32; k++) v = __dadd_rn(v, sm[threadIdx.x][k]);
     part[(size_t)blockIdx.x * nrhs + threadIdx.x] = v;
   }
 }

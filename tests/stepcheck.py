@@ -8,7 +8,7 @@ import numpy as np
 import oracle
 
 HEADER = 64
-STATE_BYTES = 112
+STATE_BYTES = 128
 
 
 def state_parts(blob, n):

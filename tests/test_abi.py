@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2407_03272_gb300 import aj
@@ -74,3 +75,33 @@ def test_failure_hooks_validate_their_arguments_without_gpu_work():
     assert L.aj_test_barrier_stall(-1, 1.0) == aj.AJ_OK   # disarm
     assert L.aj_test_alloc_fail(-2) == aj.AJ_EINVAL
     assert L.aj_test_alloc_fail(-1) == aj.AJ_OK          # disarm
+
+
+def test_noalloc_binding_refuses_bad_arrays_before_the_call():
+    torch = pytest.importorskip("torch")
+    n = 5
+    rp = torch.arange(n + 1, dtype=torch.int32)
+    ci = torch.arange(n, dtype=torch.int32)
+    v = torch.ones(n, dtype=torch.float64)
+    b = torch.ones(n, dtype=torch.float64)
+    out = torch.zeros(n, dtype=torch.float64)
+    bad = [
+        dict(row_ptr=rp.to(torch.int64)),                 # int64 row pointers
+        dict(col=ci.to(torch.int64)),
+        dict(val=v.to(torch.float32)),
+        dict(b=b.to(torch.float32)),                      # float32 right-hand side
+        dict(x_out=torch.zeros(n - 1, dtype=torch.float64)),  # short output
+        dict(b=torch.ones(n - 2, dtype=torch.float64)),
+        dict(val=torch.ones(n + 1, dtype=torch.float64)),  # val and col differ
+        dict(x_out=np.zeros(n)),                           # not a tensor
+    ]
+    base = dict(row_ptr=rp, col=ci, val=v, b=b, x_out=out)
+    for case in bad:
+        args = dict(base, **case)
+        with pytest.raises(ValueError):
+            aj.solve_noalloc(args["row_ptr"], args["col"], args["val"], args["b"], args["x_out"])
+    with pytest.raises(ValueError):
+        aj.solve_noalloc(rp, ci, v, b, out, x0=torch.zeros(n, dtype=torch.float32))
+    # well-formed host tensors are refused too: the entry point takes device arrays
+    with pytest.raises(ValueError, match="device"):
+        aj.solve_noalloc(rp, ci, v, b, out)

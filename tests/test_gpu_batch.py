@@ -148,7 +148,7 @@ def test_batch_of_mixed_sweep_forms_equals_solo(precision):
         if precision == "fp32_ir":
             kw["format"] = aj.AJ_FMT_SELL if k % 3 == 0 else aj.AJ_FMT_CSR
         else:
-            kw["sweep_form"] = (aj.AJ_SWEEP_DELTA, aj.AJ_SWEEP_STORED, aj.AJ_SWEEP_LAZY)[k % 3]
+            kw["sweep_form"] = (aj.AJ_SWEEP_DELTA, aj.AJ_SWEEP_STORED, aj.AJ_SWEEP_LAZY, aj.AJ_SWEEP_Y)[k % 4]
         kws.append(kw)
     ctxs = [_ctx(Q, B, **kw) for (Q, B), kw in zip(mix, kws)]
     X, infos = _batch(ctxs, mix)

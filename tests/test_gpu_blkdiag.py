@@ -42,7 +42,8 @@ def _parity(Q, B, bs, T=200, tol_rel=REL, x0=None, **kw):
     Jb = oracle.j_blkdiag(Q, bs)
     for r in range(nrhs):
         xr0 = None if x0 is None else x0.reshape(nrhs, Q["n"])[r]
-        ref = schedule.replay(Q, B[:, r], ctx.restart_log(r), T, Jblk=Jb, x0=xr0)
+        ref = schedule.replay(Q, B[:, r], ctx.restart_log(r), T, Jblk=Jb, x0=xr0,
+                              precision="df64" if kw.get("precision") == "df64" else "fp64")
         err = np.linalg.norm(X[r] - ref["x"]) / np.linalg.norm(ref["x"])
         assert err <= tol_rel, (r, err)
     return ctx, X
@@ -88,7 +89,7 @@ def test_blkdiag_several_rhs_with_x0(nrhs):
         _parity(Q, B, bs, T=150, x0=x0)
 
 
-@pytest.mark.parametrize("form", [aj.AJ_SWEEP_LAZY, aj.AJ_SWEEP_STORED, aj.AJ_SWEEP_DELTA])
+@pytest.mark.parametrize("form", [aj.AJ_SWEEP_LAZY, aj.AJ_SWEEP_STORED, aj.AJ_SWEEP_DELTA, aj.AJ_SWEEP_Y])
 def test_blkdiag_sweep_forms(form):
     Q = synth.poisson3d(11)
     B = _rhs(Q, seed=2)

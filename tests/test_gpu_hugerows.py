@@ -54,7 +54,8 @@ def test_hub_rows_200_iterations_match_oracle(nrhs, fmt):
     B = np.stack([synth.rhs(Q, synth.uniform(Q["n"], 93 + r)) for r in range(nrhs)], axis=1)
     kw = dict(format=aj.AJ_FMT_SELL) if fmt == "sell" else {}
     ctx = _parity(Q, B, 200, **kw)
-    assert ctx.format()[0] == aj.AJ_FMT_SELL
+    if fmt == "sell":
+        assert ctx.format()[0] == aj.AJ_FMT_SELL  # AUTO may time CSR (warp-summed hubs) faster
 
 
 @pytest.mark.parametrize("precision", ["fp64", "df64"])
@@ -68,7 +69,7 @@ def test_dense_rows_of_the_section_4_1_system(precision):
     ctx.set(precision=precision, stop=aj.AJ_STOP_NONE, maxit=T)
     assert ctx.format()[0] == aj.AJ_FMT_SELL
     x, info = ctx.solve()
-    ref = schedule.replay(Q, b, ctx.restart_log(), T, J=oracle.j_absrowsum(Q))
+    ref = schedule.replay(Q, b, ctx.restart_log(), T, J=oracle.j_absrowsum(Q), precision=precision)
     assert np.linalg.norm(x - ref["x"]) <= REL * np.linalg.norm(ref["x"])
 
 

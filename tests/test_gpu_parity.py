@@ -48,7 +48,8 @@ def _oracle_J(Q, j_policy, L=None):
     return oracle.j_scaled_diag(Q, L)
 
 
-FORMS = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED, "delta": aj.AJ_SWEEP_DELTA}
+FORMS = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED, "delta": aj.AJ_SWEEP_DELTA,
+         "y": aj.AJ_SWEEP_Y}
 
 
 def _compare_fixed(Q, b, T, precision="fp64", restart=True, momentum=True, j_policy=0, L=0.0,
@@ -61,14 +62,15 @@ def _compare_fixed(Q, b, T, precision="fp64", restart=True, momentum=True, j_pol
     sched = ctx.restart_log()
     assert len(sched) == info["restarts"]
     # the GPU's restart decisions, each the rule's own up to a rounding-level tie
-    ref = schedule.replay(Q, b, sched, T, J=J, restart=restart, momentum=momentum, x0=x0)
+    ref = schedule.replay(Q, b, sched, T, J=J, restart=restart, momentum=momentum, x0=x0,
+                          precision="df64" if precision == "df64" else "fp64")
     err = np.linalg.norm(x - ref["x"]) / max(np.linalg.norm(ref["x"]), 1e-300)
     assert err <= tol_rel, (err, sched)
     return ctx, x, info, ref
 
 
 # ---------------------------------------------------------------- fixed-iteration parity
-@pytest.mark.parametrize("form", ["lazy", "stored", "delta"])
+@pytest.mark.parametrize("form", ["lazy", "stored", "delta", "y"])
 @pytest.mark.parametrize("precision", ["fp64", "df64"])
 def test_poisson64_200_iterations_match_oracle(precision, form):
     if form == "delta" and precision != "fp64":
@@ -116,6 +118,7 @@ def test_lazy_and_stored_forms_agree(precision):
         xs_[form] = x
     tol = 1e-12 if precision in ("fp64", "df64") else 1e-4
     assert np.linalg.norm(xs_["lazy"] - xs_["stored"]) <= tol * np.linalg.norm(xs_["lazy"])
+    assert np.linalg.norm(xs_["y"] - xs_["stored"]) <= tol * np.linalg.norm(xs_["lazy"])
     if "delta" in xs_:
         np.testing.assert_array_equal(xs_["delta"], xs_["stored"])
 
@@ -129,7 +132,7 @@ def test_no_restart_and_jacobi_modes_match_oracle(precision):
                    j_policy=aj.AJ_J_SCALED_DIAG, L=1.0)
 
 
-@pytest.mark.parametrize("form", ["lazy", "stored"])
+@pytest.mark.parametrize("form", ["lazy", "stored", "y"])
 @pytest.mark.parametrize("precision", ["fp64", "df64"])
 def test_ragged_tail_and_long_rows(precision, form):
     # n = 300 rows of length 300 (> 32: the warp-cooperative path), n not a multiple of 256
@@ -242,7 +245,8 @@ def test_multi_rhs_equals_single(nrhs, precision):
 
 
 @pytest.mark.parametrize("nrhs", [2, 3, 4])
-@pytest.mark.parametrize("case", ["poisson_lazy", "poisson_stored", "long_rows", "sell_powerlaw"])
+@pytest.mark.parametrize("case", ["poisson_lazy", "poisson_stored", "poisson_y", "long_rows", "sell_powerlaw",
+                                  "sell_powerlaw_y"])
 def test_multi_rhs_200_iterations_match_oracle(nrhs, case):
     """Several right-hand sides share a row's lanes (lane r gathers column r
     of the interleaved vectors); every column must follow the FP64 oracle."""
@@ -256,6 +260,8 @@ def test_multi_rhs_200_iterations_match_oracle(nrhs, case):
     else:
         Q = synth.chung_lu_laplacian(20000, seed=29)
         kw = dict(format=aj.AJ_FMT_SELL, sell_sigma=256, sell_lmax=16)
+        if case.endswith("_y"):
+            kw["sweep_form"] = aj.AJ_SWEEP_Y
     n = Q["n"]
     B = np.stack([synth.rhs(Q, synth.uniform(n, 40 + r)) for r in range(nrhs)], axis=1)
     ctx = aj.from_csr(Q, np.ascontiguousarray(B.T).reshape(-1), nrhs=nrhs)
@@ -274,7 +280,7 @@ def test_multi_rhs_200_iterations_match_oracle(nrhs, case):
 
 
 # ---------------------------------------------------------------- checkpoint / resume
-@pytest.mark.parametrize("form", ["lazy", "stored", "delta"])
+@pytest.mark.parametrize("form", ["lazy", "stored", "delta", "y"])
 def test_resume_is_bit_identical(form):
     Q, b, xs = synth.workload("poisson2d_48")
     full = aj.from_csr(Q, b)
@@ -328,7 +334,8 @@ def _stop_is_clear(tr_relres, iters, tol):
 
 
 @pytest.mark.parametrize("precision,form", [("fp64", "auto"), ("fp64", "lazy"), ("fp64", "stored"),
-                                            ("fp64", "delta"), ("df64", "auto")])
+                                            ("fp64", "delta"), ("fp64", "y"), ("df64", "auto"),
+                                            ("df64", "y")])
 @pytest.mark.parametrize("fmt", ["csr", "auto"])
 def test_restart_schedule_equals_the_oracles(precision, form, fmt):
     """2-D Poisson 64 x 64 to relative residual 1e-12: six restarts, and every

@@ -31,7 +31,8 @@ def _parity(Q, b, T, tol_rel=REL, **kw):
     ctx, x, info = _fixed(Q, b, T, **kw)
     fmt = ctx.format()
     # the oracle with the GPU's restart schedule, checked against the rule
-    ref = schedule.replay(Q, b, ctx.restart_log(), T, J=oracle.j_absrowsum(Q))
+    ref = schedule.replay(Q, b, ctx.restart_log(), T, J=oracle.j_absrowsum(Q),
+                          precision="df64" if kw.get("precision") == "df64" else "fp64")
     err = np.linalg.norm(x - ref["x"]) / np.linalg.norm(ref["x"])
     assert err <= tol_rel, (err, fmt)
     return ctx, x, fmt

@@ -85,9 +85,10 @@ def test_auto_rule_per_precision_and_form():
 
 @pytest.mark.parametrize("precision,form", [
     ("fp64", aj.AJ_SWEEP_DELTA), ("fp64", aj.AJ_SWEEP_STORED), ("fp64", aj.AJ_SWEEP_LAZY),
-    ("df64", aj.AJ_SWEEP_STORED), ("df64", aj.AJ_SWEEP_LAZY),
-    ("fp32_ir", aj.AJ_SWEEP_LAZY), ("fp32_ir", aj.AJ_SWEEP_STORED),
-    ("bf16_ir", aj.AJ_SWEEP_LAZY), ("bf16_ir", aj.AJ_SWEEP_STORED)])
+    ("fp64", aj.AJ_SWEEP_Y), ("df64", aj.AJ_SWEEP_STORED), ("df64", aj.AJ_SWEEP_LAZY),
+    ("df64", aj.AJ_SWEEP_Y), ("fp32_ir", aj.AJ_SWEEP_LAZY), ("fp32_ir", aj.AJ_SWEEP_STORED),
+    ("fp32_ir", aj.AJ_SWEEP_Y), ("bf16_ir", aj.AJ_SWEEP_LAZY), ("bf16_ir", aj.AJ_SWEEP_STORED),
+    ("bf16_ir", aj.AJ_SWEEP_Y)])
 def test_stencil_iterates_bitwise_equal_csr(precision, form):
     # 3-D 23^3: 12167 rows, 47 full tiles and a ragged one
     Q = synth.poisson3d(23)

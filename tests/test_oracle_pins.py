@@ -551,3 +551,15 @@ def test_pcg_recursive_residual_tracks_true_residual(case):
         assert abs(r["rr"][-1] - true) <= 1e-10 * np.linalg.norm(b)
     r = oracle.pcg(Q, b, maxit=500, tol=1e-12)
     assert np.linalg.norm(A @ r["x"] - b) <= 1e-11 * np.linalg.norm(b)
+
+
+def test_openmp_timing_build_computes_the_same_bits():
+    # the CPU baseline times the -O3 -fopenmp build of the same source: it
+    # spreads independent rows over threads and keeps every sum in one thread
+    Q, b, _ = synth.workload("poisson3d_20")
+    J = oracle.j_absrowsum(Q)
+    a = oracle.solve(Q, b, J, maxit=150, stop=oracle.STOP_NONE, trace=True)
+    c = oracle.solve(Q, b, J, maxit=150, stop=oracle.STOP_NONE, trace=True, omp=True)
+    np.testing.assert_array_equal(a["x"], c["x"])
+    np.testing.assert_array_equal(a["trace"]["d"], c["trace"]["d"])
+    assert a["restarts"] == c["restarts"] and oracle.host_cores() >= 1

@@ -23,6 +23,7 @@ pytestmark = pytest.mark.gpu
 from paper_2407_03272_gb300 import aj  # noqa: E402
 
 REL = 1e-10
+GRID = 16  # the 64 x 64 system has 16 tiles of 256 rows
 
 
 def _device_system(name):
@@ -34,8 +35,11 @@ def _device_system(name):
 
 
 def _reference(Q, b, **kw):
+    # the ordinary entry point in the configuration the allocation-free one
+    # runs: CSR rows, the stored sweep form, the same grid (so the FP64
+    # reductions are summed in the same order)
     ctx = aj.from_csr(Q, b, device="cuda:0")
-    ctx.set(**kw)
+    ctx.set(format=aj.AJ_FMT_CSR, sweep_form=aj.AJ_SWEEP_STORED, grid_ctas=GRID, **kw)
     x, info = ctx.solve()
     ctx.close()
     return x, info
@@ -43,7 +47,7 @@ def _reference(Q, b, **kw):
 
 def _noalloc(t, n, **kw):
     out = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda:0")
-    st, info = aj.solve_noalloc(*t, out, stream=torch.cuda.current_stream(), **kw)
+    st, info = aj.solve_noalloc(*t, out, stream=torch.cuda.current_stream(), grid_ctas=GRID, **kw)
     torch.cuda.synchronize()
     return st, out.cpu().numpy(), info
 
@@ -74,6 +78,7 @@ def test_noalloc_matches_solve_to_tolerance_twice():
         assert st == aj.AJ_OK and info["status"] == aj.AJ_OK
         assert info["iters"] == rinfo["iters"]
         assert info["relres"] <= 1e-8
+        assert info["relres"] == rinfo["relres"] or abs(info["relres"] - rinfo["relres"]) <= 1e-3 * rinfo["relres"]
         assert _rel(x, ref) <= REL
 
 
