@@ -34,9 +34,11 @@ METRIC = "fused AJ-iteration HBM GB/s; time to 1e-8 residual; served solves/s, p
 UNIT = "GB/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-# FP64 issue rate of GB300 derived from its nominal 1.25 TFLOP/s FP64 (2 flops per FMA):
-# 152 SMs x 2 FP64 instructions/clk x 2.07 GHz = 0.629 T FP64 instructions/s.
-FP64_PEAK_TOPS = 152 * 2 * 2.07e9 / 1e12
+# FP64 issue rate of GB300, measured: a kernel of 8 independent DFMA chains per
+# thread (1216 CTAs x 256 threads, CUDA events) retires 0.626 T DFMA/s at
+# 2.06 GHz, i.e. 2 FP64 instructions per clock per SM on 152 SMs (the nominal
+# 1.25 TFLOP/s FP64 with an FMA counted as 2 flops).
+FP64_PEAK_TOPS = 0.626
 
 
 HEADLINE_WORKLOAD = ("3-D 7-point Dirichlet Poisson 256^3 (n=16777216, nnz=117047296), "
@@ -89,6 +91,24 @@ def fp64_ops(n, nnz, form="stored"):
         # sweeps add a second row sum and 2 per row, not counted here)
         return nnz + 6 * n
     return (nnz + 9 * n) if form == "stored" else (2 * nnz + 11 * n)
+
+
+def q_matrix(Q):
+    """Q as a scipy CSR matrix, for reporting only (the error below)."""
+    import scipy.sparse as sp
+    n = int(Q["n"])
+    return sp.csr_matrix((Q["val"], Q["col"], Q["row_ptr"]), shape=(n, n))
+
+
+def q_error(A, x, xs, b):
+    """||x - x*||_Q / ||x*||_Q with b = Q x* (x*^T Q x* = x*^T b): the error of a
+    result against the exact solution in the energy norm (a seminorm for a
+    singular Laplacian, where x* is one solution of many).  Reporting only,
+    on the host."""
+    e = np.asarray(x, dtype=np.float64) - xs
+    num = float(e @ (A @ e))
+    den = float(xs @ b)
+    return math.sqrt(max(num, 0.0) / den) if den > 0 else math.sqrt(max(num, 0.0))
 
 
 def load_peaks():
@@ -253,8 +273,9 @@ def bench_graph(aj, torch, dev, stream, hbm_peak, n):
     plain FP64 path, format chosen by the autotuner, each solved to 1e-8."""
     import synth
     t0 = time.perf_counter()
-    Q, b, _ = synth.workload("chunglu_%d" % n)
+    Q, b, xs = synth.workload("chunglu_%d" % n)
     gen_s = time.perf_counter() - t0
+    Aq = q_matrix(Q)
     nnz = int(Q["row_ptr"][-1])
     tens = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (Q["row_ptr"], Q["col"], Q["val"], b)]
     out = torch.empty(n, dtype=torch.float64, device=dev)
@@ -280,6 +301,7 @@ def bench_graph(aj, torch, dev, stream, hbm_peak, n):
         gbs = B * info["iters"] / (info["kernel_ms"] * 1e-3) / 1e9
         res[prec] = {"time_to_tol_ms": ms, "iterations": info["iters"], "outer": info["outer"],
                      "relres": info["relres"], "status": info["status"],
+                     "error_vs_xstar_Qnorm": q_error(Aq, out.cpu().numpy(), xs, b),
                      "format": {"kind": "SELL-32-sigma" if fmt[0] == aj.AJ_FMT_SELL else "CSR",
                                 "sigma": fmt[1], "long_row_threshold": fmt[2], "fill_ratio": fmt[3]},
                      "setup_incl_autotune_s": setup_s,
@@ -289,6 +311,23 @@ def bench_graph(aj, torch, dev, stream, hbm_peak, n):
     res["fp32_ir_speedup_vs_fp64"] = res["fp64"]["time_to_tol_ms"] / res["fp32_ir"]["time_to_tol_ms"]
     res["pcg_fp64"] = time_pcg(aj, torch, stream, tens, n, out)
     return res
+
+
+def max_mix_error(systems, mats, xs_of, cache):
+    """Largest ||x - x*||_Q / ||x*||_Q over the right-hand sides of the mixed
+    workloads; xs_of(k) gives system k's result (n * nrhs, column-major)."""
+    import synth
+    worst = 0.0
+    for k, (j, nrhs, seeds) in enumerate(systems):
+        if j not in cache:
+            cache[j] = q_matrix(mats[j])
+        A = cache[j]
+        n = int(mats[j]["n"])
+        x = np.asarray(xs_of(k), dtype=np.float64).reshape(nrhs, n)
+        for r, sd in enumerate(seeds):
+            xst = synth.uniform(n, sd)
+            worst = max(worst, q_error(A, x[r], xst, A @ xst))
+    return worst
 
 
 def bench_batched(aj, torch, dev, stream, count, pool):
@@ -327,16 +366,19 @@ def bench_batched(aj, torch, dev, stream, count, pool):
                        "matrices from a pool of %d, b=Qx* per system; tol 1e-8" % (count, pool),
            "systems": count, "rows_total": int(sum(mats[j]["n"] * 1 for j, _, _ in systems)),
            "rhs_total": int(sum(nr for _, nr, _ in systems)), "generate_s": gen_s}
+    qcache = {}
     for prec in ("fp32_ir", "fp64"):
         cs = build(prec)
         aj.solve_batch(cs[:4], outs[:4], on_device=True)  # warm-up
         ms, wall, infos = timed(lambda: aj.solve_batch(cs, outs, on_device=True))
         ok = sum(1 for i in infos if i["status"] == aj.AJ_OK)
+        err = max_mix_error(systems, mats, lambda k: outs[k].cpu().numpy(), qcache)
         stn = [c.format()[0] == aj.AJ_FMT_STENCIL for c in cs]
         byt = sum(algorithmic_bytes(mats[j]["n"], int(mats[j]["row_ptr"][-1]), prec, stencil=st, nrhs=nr)
                   * i["iters"] for (j, nr, _), i, st in zip(systems, infos, stn))
         res["batched_" + prec] = {"makespan_ms": ms, "wall_ms": wall, "systems_per_s": count / (ms * 1e-3),
                                   "ok": ok, "max_relres": max(i["relres"] for i in infos),
+                                  "max_error_vs_xstar_Qnorm": err,
                                   "stencil_systems": int(sum(stn)),
                                   "approx_GBps": byt / (ms * 1e-3) / 1e9,
                                   "iterations_total": int(sum(i["iters"] for i in infos))}
@@ -346,7 +388,9 @@ def bench_batched(aj, torch, dev, stream, count, pool):
             ms_s, wall_s, inf_s = timed(serial)
             res["serial_fp64"] = {"makespan_ms": ms_s, "wall_ms": wall_s, "systems_per_s": count / (ms_s * 1e-3),
                                   "ok": sum(1 for i in inf_s if i["status"] == aj.AJ_OK),
-                                  "max_relres": max(i["relres"] for i in inf_s)}
+                                  "max_relres": max(i["relres"] for i in inf_s),
+                                  "max_error_vs_xstar_Qnorm": max_mix_error(
+                                      systems, mats, lambda k: outs[k].cpu().numpy(), qcache)}
         for c in cs:
             c.close()
     res["batched_fp32_ir_speedup_vs_serial_fp64"] = (res["serial_fp64"]["makespan_ms"]
@@ -395,6 +439,7 @@ def bench_served(aj, torch, count, pool, rate, budget_gb):
     bs = [synth.mix_rhs(mats[j], seeds) for j, _, seeds in systems]
     gen_s = time.perf_counter() - t0
     srv = aj.Server(int(budget_gb * 1e9), max_slots=512)
+    qcache = {}
 
     def run(reqs, r, seed):
         gaps = np.random.default_rng(seed).exponential(1.0 / r, len(reqs))
@@ -407,17 +452,19 @@ def bench_served(aj, torch, count, pool, rate, budget_gb):
                 time.sleep(d)
             tickets.append(srv.submit_csr(mats[j], bs[k], nrhs=nrhs, precision="fp32_ir", tol=1e-8,
                                           maxit=200000))
-        lat, rel, ok = [], [], 0
+        lat, rel, ok, xres = [], [], 0, []
         for t in tickets:
-            st, _, info = srv.result(t)
+            st, xr, info = srv.result(t)
             ok += st == aj.AJ_OK
             lat.append(info["ms"])
             rel.append(info["relres"])
+            xres.append(xr)
         wall = time.perf_counter() - w0
+        err = max_mix_error([s for _, s in reqs], mats, lambda k: xres[k], qcache)
         lat = np.array(lat)
         return {"offered_per_s": r, "requests": len(reqs), "ok": ok, "solves_per_s": len(reqs) / wall,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "max_relres": float(max(rel)), "wall_s": wall}
+                "max_relres": float(max(rel)), "max_error_vs_xstar_Qnorm": err, "wall_s": wall}
 
     reqs = list(enumerate(systems))
     # warm-up: a few requests
@@ -446,7 +493,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32_ir", "bf16_ir"])
     ap.add_argument("--form", default="auto", choices=["auto", "lazy", "stored", "delta", "y"],
                     help="sweep form; auto = stored for fp64, lazy otherwise (the library's AUTO)")
-    ap.add_argument("--format", default="csr", choices=["csr", "stencil"],
+    ap.add_argument("--format", default="csr", choices=["csr", "stencil", "sell"],
                     help="format of the timed context (the headline workload is CSR)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -539,13 +586,15 @@ def main():
 
     # ---- headline: the chosen precision, K timed solves
     form = form_of(args.precision, args.form)
-    FMT = {"csr": aj.AJ_FMT_CSR, "stencil": aj.AJ_FMT_STENCIL}
+    FMT = {"csr": aj.AJ_FMT_CSR, "stencil": aj.AJ_FMT_STENCIL, "sell": aj.AJ_FMT_SELL}
     stn = args.format == "stencil"
     ctx = make(args.precision, form, auto=args.form == "auto", fmt=FMT[args.format])
     if args.form == "auto" and args.precision != "fp64" and ctx.format()[0] == aj.AJ_FMT_SELL:
         form = "stored"  # the library's AUTO choice for SELL
     with Clocks(dev.index) as clk:
         ms, infos, launches = time_solves(ctx, args.steps, args.warmup)
+    Aq = q_matrix(Q)
+    err_head = q_error(Aq, out.cpu().numpy(), xs, b)
     B = algorithmic_bytes(n, nnz, args.precision, stencil=stn)
     iters = sum(i["iters"] for i in infos)
     ms, _, value = job_throughput(ms, B * iters, dist, dev)
@@ -558,8 +607,8 @@ def main():
         roof = {"bound": "alu", "achieved": achieved_t, "peak": FP64_PEAK_TOPS,
                 "unit": "T FP64 instructions/s",
                 "frac": achieved_t / FP64_PEAK_TOPS, "traffic": None,
-                "peak_kind": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz "
-                             "(nominal 1.25 TFLOP/s FP64 with FMA = 2 flops)",
+                "peak_kind": "measured: DFMA issue probe, 0.626 T/s at 2.06 GHz "
+                             "(2 FP64 instructions/clk/SM x 152 SMs)",
                 "hbm": {"achieved": kern_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": kern_gbs / hbm_peak, "peak_kind": peak_kind}}
     else:
@@ -598,6 +647,7 @@ def main():
         "time_to_tol_ms": ms / args.steps,
         "iterations": infos[-1]["iters"], "restarts": infos[-1]["restarts"],
         "relres": infos[-1]["relres"], "sweeps_per_solve": sweeps / len(infos),
+        "error_vs_xstar_Qnorm": err_head,
         "gpu_launches": int(launches),
         "roofline": roof,
         "clocks": clk.summary(),
@@ -616,6 +666,7 @@ def main():
                 var[p + "/" + fm] = {
                     "time_to_tol_ms": vms / 2, "iterations": vinf[-1]["iters"],
                     "outer": vinf[-1]["outer"], "relres": vinf[-1]["relres"],
+                    "error_vs_xstar_Qnorm": q_error(Aq, out.cpu().numpy(), xs, b),
                     "fused_GBps": vb * it / (kms * 1e-3) / 1e9,
                     "fused_hbm_frac": vb * it / (kms * 1e-3) / 1e9 / hbm_peak,
                     "kernel_ms_per_iteration": kms / max(it, 1)}
@@ -634,6 +685,7 @@ def main():
             var[p + "/stencil-" + fm] = {
                 "time_to_tol_ms": vms / 2, "iterations": vinf[-1]["iters"],
                 "outer": vinf[-1]["outer"], "relres": vinf[-1]["relres"],
+                "error_vs_xstar_Qnorm": q_error(Aq, out.cpu().numpy(), xs, b),
                 "fused_GBps": vb * it / (kms * 1e-3) / 1e9,
                 "fused_hbm_frac": vb * it / (kms * 1e-3) / 1e9 / hbm_peak,
                 "kernel_ms_per_iteration": kms / max(it, 1)}
@@ -648,6 +700,7 @@ def main():
             var[p + "/blkdiag4-" + fm] = {
                 "time_to_tol_ms": vms / 2, "iterations": vinf[-1]["iters"],
                 "outer": vinf[-1]["outer"], "relres": vinf[-1]["relres"],
+                "error_vs_xstar_Qnorm": q_error(Aq, out.cpu().numpy(), xs, b),
                 "fused_GBps": vb * it / (kms * 1e-3) / 1e9,
                 "kernel_ms_per_iteration": kms / max(it, 1)}
             del c

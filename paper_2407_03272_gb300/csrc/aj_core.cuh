@@ -472,40 +472,11 @@ __device__ __forceinline__ typename P::X* ubuf(const IterArgs<P>& a, int k) {
   return k == 0 ? a.u[0] : a.u[1];
 }
 
-// Gather sources of one right-hand side's sweep: its rows are summed against
-// s1 always and against s2 when `two`.
-//   lazy (SF 0):       s1 = x^{s-1}, s2 = x^{s-2} (two unless a restart made them one)
-//   stored (SF 1, 2):  s1 = x^{s-1}
-//   explicit y (SF 3): s1 = y^s (the buffer x^{s-1} itself on the first sweep
-//                      and after a restart, where y^s = x^{s-1}); s2 = x^{s-1}
-//                      on a check sweep (the exact stop test needs Q x^{s-1})
-template <class P>
-struct Sources {
-  const typename P::X* s1;
-  const typename P::X* s2;
-  bool two;
-};
-template <class P, int SF>
-__device__ __forceinline__ Sources<P> sources(const IterArgs<P>& a, const RhsState& q) {
-  Sources<P> o;
-  const bool same = q.cur == q.prev;
-  if constexpr (SF == 3) {
-    o.s1 = same ? xbuf(a, q.cur) : ubuf(a, q.yb);
-    o.s2 = xbuf(a, q.cur);
-    o.two = q.chk && !same;
-  } else {
-    o.s1 = xbuf(a, q.cur);
-    o.s2 = xbuf(a, q.prev);
-    o.two = SF == 0 && !same;
-  }
-  return o;
-}
-
 // Partial row sums over entries q0, q0 + step, ... < re (CSR arrays) for
 // right-hand side r of an nr-RHS system, U entries loaded before their
-// multiply-adds, which run in entry order.  lx sums against xc; lp against
-// xp when `two`.
-template <class P>
+// multiply-adds, which run in entry order.  lx sums against x^{s-1} (buffer
+// xc); lp against x^{s-2} (buffer xp) when `two` (lazy form, the two differ).
+template <class P, bool QX>
 __device__ __forceinline__ void row_sums_strided(const IterArgs<P>& a, int nr, int r,
                                                  const typename P::X* xc, const typename P::X* xp,
                                                  bool two, int q0, int re, int step,
@@ -541,6 +512,81 @@ __device__ __forceinline__ void row_sums_strided(const IterArgs<P>& a, int nr, i
   }
 }
 
+// Warp-cooperative row sums of one long row for right-hand side r (lanes
+// stride over the entries, then a fixed xor tree).  Returns the sums in every
+// lane; sp equals sx when the stored form or x^{s-1} = x^{s-2} needs no
+// second sum.  Every lane of the warp must call it.
+template <class P, bool QX>
+__device__ __forceinline__ void long_row_sums(const IterArgs<P>& a, const RhsState& q, int nr, int r,
+                                              int rs, int re, typename P::S& sx, typename P::S& sp) {
+  using S = typename P::S;
+  const int lane = threadIdx.x & 31;
+  const bool two = !QX && q.cur != q.prev;
+  S lx = P::zero(), lp = P::zero();
+  if (!q.done)
+    row_sums_strided<P, QX>(a, nr, r, xbuf(a, q.cur), xbuf(a, q.prev), two, rs + lane, re, 32, lx, lp);
+  lx = P::finish(lx);
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) lx = P::combine(lx, P::shfl_xor(lx, m));
+  sx = lx;
+  sp = lx;
+  if (two) {
+    lp = P::finish(lp);
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) lp = P::combine(lp, P::shfl_xor(lp, m));
+    sp = lp;
+  }
+}
+
+// CTA-cooperative row sums of one huge row for right-hand side r: threads
+// stride over the entries, then a fixed xor tree per warp and the warps in
+// order.  Results valid in every thread.  Every thread of the CTA must call it.
+template <class P, bool QX>
+__device__ __forceinline__ void cta_row_sums(const IterArgs<P>& a, const RhsState& q, int nr, int r,
+                                             int rs, int re, typename P::S& sx, typename P::S& sp) {
+  using S = typename P::S;
+  __shared__ S red[2][kWarps];
+  const bool two = !QX && q.cur != q.prev;
+  S lx = P::zero(), lp = P::zero();
+  if (!q.done)
+    row_sums_strided<P, QX>(a, nr, r, xbuf(a, q.cur), xbuf(a, q.prev), two, rs + threadIdx.x, re,
+                            kThreads, lx, lp);
+  const int w = threadIdx.x >> 5;
+  lx = P::finish(lx);
+  lp = P::finish(lp);
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    lx = P::combine(lx, P::shfl_xor(lx, m));
+    if (two) lp = P::combine(lp, P::shfl_xor(lp, m));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = lx;
+    red[1][w] = lp;
+  }
+  __syncthreads();
+  S tx = red[0][0], tp = red[1][0];
+  for (int k = 1; k < kWarps; k++) {
+    tx = P::combine(tx, red[0][k]);
+    if (two) tp = P::combine(tp, red[1][k]);
+  }
+  sx = tx;
+  sp = two ? tp : tx;
+  __syncthreads();
+}
+
+// The explicit-y form (SF 3) gathers from its own sources: y^s (the
+// buffer x^{s-1} itself on the first sweep and after a restart, where
+// y^s = x^{s-1}), and x^{s-1} again in a second pass on a check sweep, where
+// the exact stop test needs Q x^{s-1}.  Sources for right-hand side state q:
+template <class P>
+__device__ __forceinline__ const typename P::X* y_source(const IterArgs<P>& a, const RhsState& q) {
+  return q.cur == q.prev ? xbuf(a, q.cur) : ubuf(a, q.yb);
+}
+template <class P>
+__device__ __forceinline__ bool y_check(const RhsState& q) {
+  return q.chk && q.cur != q.prev;
+}
+
 // Fixed xor tree of a warp's partial sums; the total in every lane.
 template <class P>
 __device__ __forceinline__ typename P::S warp_total(typename P::S v) {
@@ -550,34 +596,28 @@ __device__ __forceinline__ typename P::S warp_total(typename P::S v) {
   return v;
 }
 
-// Warp-cooperative row sums of one long row for right-hand side r (lanes
-// stride over the entries, then a fixed xor tree).  Returns the sums in every
-// lane: sx over the sweep's first source, sp over the second when the sweep
-// needs it (else sp = sx).  Every lane of the warp must call it.
-template <class P, int SF>
-__device__ __forceinline__ void long_row_sums(const IterArgs<P>& a, const RhsState& q, int nr, int r,
-                                              int rs, int re, typename P::S& sx, typename P::S& sp) {
+// long_row_sums of the explicit-y form: sx over y^s; sp over x^{s-1} on a
+// check sweep, in a second pass (else sp = sx).  Every lane must call it.
+template <class P>
+__device__ __forceinline__ void long_row_sums_y(const IterArgs<P>& a, const RhsState& q, int nr, int r,
+                                                int rs, int re, typename P::S& sx, typename P::S& sp) {
   using S = typename P::S;
   const int lane = threadIdx.x & 31;
-  const Sources<P> src = sources<P, SF>(a, q);
-  // the explicit-y form sums its second source in a pass of its own (one
-  // chain's registers), the lazy form both in one pass
-  const bool two = SF == 0 && src.two;
-  S lx = P::zero(), lp = P::zero();
-  if (!q.done) row_sums_strided<P>(a, nr, r, src.s1, src.s2, two, rs + lane, re, 32, lx, lp);
+  S lx = P::zero(), unused = P::zero();
+  if (!q.done)
+    row_sums_strided<P, true>(a, nr, r, y_source(a, q), nullptr, false, rs + lane, re, 32, lx, unused);
   sx = warp_total<P>(lx);
   sp = sx;
-  if (two) sp = warp_total<P>(lp);
-  if (SF == 3 && src.two) {
-    S l2 = P::zero(), unused = P::zero();
-    if (!q.done) row_sums_strided<P>(a, nr, r, src.s2, src.s2, false, rs + lane, re, 32, l2, unused);
+  if (y_check<P>(q)) {
+    S l2 = P::zero();
+    if (!q.done)
+      row_sums_strided<P, true>(a, nr, r, xbuf(a, q.cur), nullptr, false, rs + lane, re, 32, l2, unused);
     sp = warp_total<P>(l2);
   }
 }
 
-// CTA-cooperative row sums of one huge row for right-hand side r: threads
-// stride over the entries, then a fixed xor tree per warp and the warps in
-// order.  Results valid in every thread.  Every thread of the CTA must call it.
+// cta_row_sums of the explicit-y form (same sources as long_row_sums_y).
+// Every thread of the CTA must call it.
 template <class P>
 __device__ __forceinline__ typename P::S cta_total(typename P::S v, typename P::S* red) {
   using S = typename P::S;
@@ -589,25 +629,94 @@ __device__ __forceinline__ typename P::S cta_total(typename P::S v, typename P::
   __syncthreads();
   return t;
 }
-template <class P, int SF>
-__device__ __forceinline__ void cta_row_sums(const IterArgs<P>& a, const RhsState& q, int nr, int r,
-                                             int rs, int re, typename P::S& sx, typename P::S& sp) {
+template <class P>
+__device__ __forceinline__ void cta_row_sums_y(const IterArgs<P>& a, const RhsState& q, int nr, int r,
+                                               int rs, int re, typename P::S& sx, typename P::S& sp) {
   using S = typename P::S;
   __shared__ S red[kWarps];
-  const Sources<P> src = sources<P, SF>(a, q);
-  const bool two = SF == 0 && src.two;
-  S lx = P::zero(), lp = P::zero();
+  S lx = P::zero(), unused = P::zero();
   if (!q.done)
-    row_sums_strided<P>(a, nr, r, src.s1, src.s2, two, rs + threadIdx.x, re, kThreads, lx, lp);
+    row_sums_strided<P, true>(a, nr, r, y_source(a, q), nullptr, false, rs + threadIdx.x, re, kThreads,
+                              lx, unused);
   sx = cta_total<P>(lx, red);
   sp = sx;
-  if (two) sp = cta_total<P>(lp, red);
-  if (SF == 3 && src.two) {
-    S l2 = P::zero(), unused = P::zero();
+  if (y_check<P>(q)) {
+    S l2 = P::zero();
     if (!q.done)
-      row_sums_strided<P>(a, nr, r, src.s2, src.s2, false, rs + threadIdx.x, re, kThreads, l2, unused);
+      row_sums_strided<P, true>(a, nr, r, xbuf(a, q.cur), nullptr, false, rs + threadIdx.x, re, kThreads,
+                                l2, unused);
     sp = cta_total<P>(l2, red);
   }
+}
+
+// Loop-invariant values of the explicit-y form's row update (nothing for the
+// other forms, whose registers they would otherwise take).
+template <class P, bool YS>
+struct YConst {
+  __device__ explicit YConst(const RhsState&) {}
+};
+template <class P>
+struct YConst<P, true> {
+  typename P::S bnext;  // beta of the candidate y^{s+1}
+  __device__ explicit YConst(const RhsState& q) : bnext(P::coef(q.beta_next)) {}
+};
+
+// One row's sum against src over entries colp[k * stride], valp[k * stride],
+// k < cnt, in chunks of U loads issued before their multiply-adds (entry
+// order), for the second pass of an explicit-y check sweep.
+template <class P, int U>
+__device__ __forceinline__ typename P::S row_pass(const int* colp, const typename P::V* valp, int cnt,
+                                                  int stride, const typename P::X* src, int nr, int r) {
+  using S = typename P::S;
+  using V = typename P::V;
+  S acc = P::zero();
+  for (int q0 = 0; q0 < cnt; q0 += U) {
+    int cc[U];
+    V vv[U];
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+      const bool in = q0 + k < cnt;
+      cc[k] = in ? ld_ro(colp + (q0 + k) * stride) : 0;
+      vv[k] = in ? P::ldv(valp + (q0 + k) * stride) : P::vzero();
+    }
+    S xv[U];
+#pragma unroll
+    for (int k = 0; k < U; k++) xv[k] = q0 + k < cnt ? P::ldg(src + (size_t)cc[k] * nr + r) : P::zero();
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+      if (q0 + k >= cnt) break;
+      P::macv(acc, vv[k], xv[k]);
+    }
+  }
+  return P::finish(acc);
+}
+
+// The same for stencil row i (a 5- or 7-point constant-coefficient
+// Dirichlet Laplacian in natural order; bit k of inm: neighbour k of
+// -N^2, -N, -1, 0, +1, +N, +N^2 lies in the grid).
+template <class P, int U>
+__device__ __forceinline__ typename P::S stencil_pass(int i, unsigned inm, int N, int NN, typename P::V s_diag,
+                                                      typename P::V s_off, const typename P::X* src, int nr,
+                                                      int r) {
+  using S = typename P::S;
+  S acc = P::zero();
+#pragma unroll
+  for (int k0 = 0; k0 < 7; k0 += U) {
+    S xv[U];
+#pragma unroll
+    for (int j = 0; j < U; j++) {
+      const int k = k0 + j;
+      const int off = k == 0 ? -NN : k == 1 ? -N : k == 2 ? -1 : k == 3 ? 0 : k == 4 ? 1 : k == 5 ? N : NN;
+      xv[j] = (k < 7 && (inm >> k & 1u)) ? P::ldg(src + (size_t)(i + off) * nr + r) : P::zero();
+    }
+#pragma unroll
+    for (int j = 0; j < U; j++) {
+      const int k = k0 + j;
+      if (k >= 7 || !(inm >> k & 1u)) continue;
+      P::macv(acc, k == 3 ? s_diag : s_off, xv[j]);
+    }
+  }
+  return P::finish(acc);
 }
 
 // Reduction slots a sweep fills: d and rr always, ||Q y - b||^2 in the
@@ -657,81 +766,6 @@ __host__ __device__ constexpr int row_unroll(bool qx) {
   return (qx ? 1 : 2) * 8 / AJ_ROW_UNROLL >= 2 ? 4 : 8;
 }
 
-// Row sums of one row for right-hand side r over its entries colp[k * stride],
-// valp[k * stride], k < cnt, in chunks of U: every load of a chunk is issued
-// before its multiply-adds, which then run in ascending entry order.  sa sums
-// against xa; sb against xb when `two`.
-template <class P, int U>
-__device__ __forceinline__ void row_chunks(const int* colp, const typename P::V* valp, int cnt, int stride,
-                                           const typename P::X* xa, const typename P::X* xb, bool two,
-                                           int nr, int r, typename P::S& sa, typename P::S& sb) {
-  using S = typename P::S;
-  using V = typename P::V;
-  for (int q0 = 0; q0 < cnt; q0 += U) {
-    int cc[U];
-    V vv[U];
-#pragma unroll
-    for (int k = 0; k < U; k++) {
-      const bool in = q0 + k < cnt;
-      cc[k] = in ? ld_ro(colp + (q0 + k) * stride) : 0;
-      vv[k] = in ? P::ldv(valp + (q0 + k) * stride) : P::vzero();
-    }
-    S xv[U], pv[U];
-#pragma unroll
-    for (int k = 0; k < U; k++) {
-      xv[k] = P::zero();
-      pv[k] = P::zero();
-      if (q0 + k < cnt) {
-        xv[k] = P::ldg(xa + (size_t)cc[k] * nr + r);
-        if (two) pv[k] = P::ldg(xb + (size_t)cc[k] * nr + r);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < U; k++) {
-      if (q0 + k >= cnt) break;
-      P::macv(sa, vv[k], xv[k]);
-      if (two) P::macv(sb, vv[k], pv[k]);
-    }
-  }
-}
-
-// Row sums of stencil row i (a 5- or 7-point constant-coefficient Dirichlet
-// Laplacian in natural order): the up to 7 neighbours in ascending column
-// order, -N^2, -N, -1, 0, +1, +N, +N^2 (bit k of inm: neighbour k lies in the
-// grid), loaded in chunks of U as for CSR rows.
-template <class P, int U>
-__device__ __forceinline__ void stencil_chunks(int i, unsigned inm, int N, int NN, typename P::V s_diag,
-                                               typename P::V s_off, const typename P::X* xa,
-                                               const typename P::X* xb, bool two, int nr, int r,
-                                               typename P::S& sa, typename P::S& sb) {
-  using S = typename P::S;
-  using V = typename P::V;
-#pragma unroll
-  for (int k0 = 0; k0 < 7; k0 += U) {
-    S xv[U], pv[U];
-#pragma unroll
-    for (int j = 0; j < U; j++) {
-      const int k = k0 + j;
-      const int off = k == 0 ? -NN : k == 1 ? -N : k == 2 ? -1 : k == 3 ? 0 : k == 4 ? 1 : k == 5 ? N : NN;
-      xv[j] = P::zero();
-      pv[j] = P::zero();
-      if (k < 7 && (inm >> k & 1u)) {
-        const size_t e = (size_t)(i + off) * nr + r;
-        xv[j] = P::ldg(xa + e);
-        if (two) pv[j] = P::ldg(xb + e);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < U; j++) {
-      const int k = k0 + j;
-      if (k >= 7 || !(inm >> k & 1u)) continue;
-      const V v = k == 3 ? s_diag : s_off;
-      P::macv(sa, v, xv[j]);
-      if (two) P::macv(sb, v, pv[j]);
-    }
-  }
-}
-
 // One sweep over the CTA's tiles: the fused SpMV at y, x update and reduction
 // terms.  `compute_x` is false on a residual-only sweep (no x^s is formed).
 // Reduction slots (per lane, for the lane's right-hand side): 0 d, 1
@@ -748,11 +782,14 @@ __device__ __forceinline__ void stencil_chunks(int i, unsigned inm, int N, int N
 // update computes anyway for the restart test), 3 explicit y: the sweep
 // gathers y^s itself, written by the previous sweep as the candidate
 // y^s = x^{s-1} + beta_s (x^{s-1} - x^{s-2}) (beta_s needs only alpha_{s-1},
-// known before the restart test), and writes the candidate y^{s+1}; after a
-// restart the candidate is dropped and y^{s+1} = x^{s-1} is read from that
-// iterate's buffer.  One row sum and no Q x vectors, but no exact residual:
-// the stop test's Q x^{s-1} is summed in a second pass on check sweeps only
-// (RhsState::chk), and ||Q y^s - b||^2 (slot 1) decides when to check.
+// known before the restart test), and writes the candidate y^{s+1} in u; a
+// restart drops the candidate, and y^{s+1} = x^{s-1} is read from that
+// iterate's buffer.  One row sum and no Q x vectors, but no exact residual
+// on the way: the stop test's Q x^{s-1} is summed in a second pass on check
+// sweeps only (RhsState::chk), which ||Q y^s - b||^2 (slot 1) schedules.
+// (The explicit-y code sits in `if constexpr` blocks of its own: at the
+// register caps of the FP32 and BF16 policies even values the other forms
+// never use changed their register allocation, and their speed.)
 template <class P, int SF, int FM, bool MULTI>
 __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, bool compute_x,
                                       bool want_obj, typename P::A (&acc)[kNRed], int cta,
@@ -760,9 +797,10 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
   using S = typename P::S;
   using V = typename P::V;
   using X = typename P::X;
-  constexpr bool QX = SF == 1 || SF == 2;  // Q x^{s-1} is stored for the next sweep
+  constexpr bool YS = SF == 3;             // explicit y
+  constexpr bool QX = SF == 1 || SF == 2;  // Q x^{s-1} stored for the next sweep
+  constexpr bool ONE = SF != 0;            // one gathered vector in the main pass
   constexpr bool DL = SF == 2;
-  constexpr bool YS = SF == 3;
   const int nr = MULTI ? a.nrhs : 1;
   const int lg = MULTI ? a.lgr : 0;
   const int r = threadIdx.x & ((1 << lg) - 1);   // this lane's right-hand side
@@ -770,23 +808,17 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
   const int rpt = kThreads >> lg;                // rows per tile
   const bool lane_on = r < nr;
   const RhsState& me = st[lane_on ? r : 0];
-  const Sources<P> src = sources<P, SF>(a, me);
-  const X* xc = src.s1;                          // gathered by every row sum
-  const X* xp = src.s2;                          // lazy: x^{s-2}; explicit y: x^{s-1}
-  const X* xcur = xbuf(a, me.cur);               // x^{s-1}, own rows
+  const X* xc = YS ? y_source(a, me) : xbuf(a, me.cur);  // gathered by the main pass
+  const X* xp = YS ? xbuf(a, me.cur) : xbuf(a, me.prev);
   X* xn = xbuf(a, me.nxt);
   X* uc = QX ? ubuf(a, me.uw) : nullptr;
   const X* up = QX ? ubuf(a, 1 - me.uw) : nullptr;
-  X* yw = YS ? ubuf(a, 1 - me.yb) : nullptr;     // the candidate y^{s+1}
   const bool same = me.cur == me.prev;
-  const bool two = SF == 0 && src.two;           // lazy: both sums in one pass
-  const bool chk2 = YS && src.two;               // explicit y: Q x^{s-1} in a second pass
   const bool active = lane_on && me.done == 0;
   const S beta = P::coef(me.beta);
-  const S bnext = P::coef(YS ? me.beta_next : 0.0);
+  const YConst<P, YS> yk(me);
   const int lane = threadIdx.x & 31;
   constexpr bool ANY = FM != 0;
-  constexpr int U = row_unroll(SF != 0);
   const bool sell = FM == 1 && a.fmt == 1;
   // stencil: the rows of a constant-coefficient Dirichlet Laplacian in natural
   // order, their entries known without loading them (same values, same
@@ -856,11 +888,14 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
     if (ANY && huge) {
       for (int k = 0; k < nr; k++) {
         S hx, hp;
-        cta_row_sums<P, SF>(a, st[k], nr, k, rs, re, hx, hp);
+        if constexpr (YS) cta_row_sums_y<P>(a, st[k], nr, k, rs, re, hx, hp);
+        else cta_row_sums<P, QX>(a, st[k], nr, k, rs, re, hx, hp);
         if (k == r) { sx = hx; sp = hp; }
       }
     } else if (ANY && stn && valid && active) {
-      // grid coordinates by multiply-shift division (Granlund and Montgomery, PLDI 1994)
+      // the up to 7 neighbours in ascending column order: -N^2, -N, -1, 0, +1, +N, +N^2
+      // (bit k of inm: neighbour k lies in the grid); grid coordinates by
+      // multiply-shift division (Granlund and Montgomery, PLDI 1994)
       const int N = a.sN, NN = a.sdim == 3 ? N * N : 0;
       const int q = (int)(((unsigned long long)i * a.smag) >> a.sshift);  // i / N
       const int ix = i - q * N;
@@ -868,42 +903,91 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       const unsigned inm = (ix > 0 ? 4u : 0u) | 8u | (ix < N - 1 ? 16u : 0u) | (iy > 0 ? 2u : 0u) |
                            (iy < N - 1 ? 32u : 0u) | (i >= NN && NN ? 1u : 0u) |
                            (NN && i < a.n - NN ? 64u : 0u);
-      stencil_chunks<P, U>(i, inm, N, NN, s_diag, s_off, xc, xp, two, nr, r, sx, sp);
-      sx = P::finish(sx);
-      if (SF == 0) sp = same ? sx : P::finish(sp);
-      if (YS) {
-        sp = sx;
-        if (chk2) {
-          S s2 = P::zero(), unused = P::zero();
-          stencil_chunks<P, U>(i, inm, N, NN, s_diag, s_off, xp, xp, false, nr, r, s2, unused);
-          sp = P::finish(s2);
+      const bool two = !ONE && !same;
+      // chunks of U neighbours, as for CSR rows: loads first, then the
+      // multiply-adds in ascending order
+      constexpr int U = row_unroll(ONE);
+#pragma unroll
+      for (int k0 = 0; k0 < 7; k0 += U) {
+        S xv[U], pv[U];
+#pragma unroll
+        for (int j = 0; j < U; j++) {
+          const int k = k0 + j;
+          const int off = k == 0 ? -NN : k == 1 ? -N : k == 2 ? -1 : k == 3 ? 0 : k == 4 ? 1 : k == 5 ? N : NN;
+          xv[j] = P::zero();
+          pv[j] = P::zero();
+          if (k < 7 && (inm >> k & 1u)) {
+            const size_t e = (size_t)(i + off) * nr + r;
+            xv[j] = P::ldg(xc + e);
+            if (two) pv[j] = P::ldg(xp + e);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < U; j++) {
+          const int k = k0 + j;
+          if (k >= 7 || !(inm >> k & 1u)) continue;
+          const V v = k == 3 ? s_diag : s_off;
+          P::macv(sx, v, xv[j]);
+          if (two) P::macv(sp, v, pv[j]);
         }
       }
-    } else if (valid && !is_long && active) {
-      row_chunks<P, U>(colp, valp, cnt, stride, xc, xp, two, nr, r, sx, sp);
       sx = P::finish(sx);
-      if (SF == 0) sp = same ? sx : P::finish(sp);
-      if (YS) {
+      if (!ONE) sp = same ? sx : P::finish(sp);
+      if constexpr (YS) {
         sp = sx;
-        if (chk2) {
-          S s2 = P::zero(), unused = P::zero();
-          row_chunks<P, U>(colp, valp, cnt, stride, xp, xp, false, nr, r, s2, unused);
-          sp = P::finish(s2);
+        if (y_check<P>(me)) sp = stencil_pass<P, U>(i, inm, N, NN, s_diag, s_off, xp, nr, r);
+      }
+    } else if (valid && !is_long && active) {
+      // chunks of U entries: every load of a chunk is issued before its
+      // multiply-adds, which then run in ascending entry order
+      constexpr int U = row_unroll(ONE);
+      const bool two = !ONE && !same;
+      for (int q0 = 0; q0 < cnt; q0 += U) {
+        int cc[U];
+        V vv[U];
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+          const bool in = q0 + k < cnt;
+          cc[k] = in ? ld_ro(colp + (q0 + k) * stride) : 0;
+          vv[k] = in ? P::ldv(valp + (q0 + k) * stride) : P::vzero();
         }
+        S xv[U], pv[U];
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+          xv[k] = P::zero();
+          pv[k] = P::zero();
+          if (q0 + k < cnt) {
+            xv[k] = P::ldg(xc + (size_t)cc[k] * nr + r);
+            if (two) pv[k] = P::ldg(xp + (size_t)cc[k] * nr + r);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+          if (q0 + k >= cnt) break;
+          P::macv(sx, vv[k], xv[k]);
+          if (two) P::macv(sp, vv[k], pv[k]);
+        }
+      }
+      sx = P::finish(sx);
+      if (!ONE) sp = same ? sx : P::finish(sp);
+      if constexpr (YS) {
+        sp = sx;
+        if (y_check<P>(me)) sp = row_pass<P, U>(colp, valp, cnt, stride, xp, nr, r);
       }
     }
     // long rows: the whole warp sums each one for every right-hand side; the
     // lane of right-hand side k of the row's group takes sum k
     unsigned lm = FM == 2 ? 0u : __ballot_sync(0xffffffffu, is_long && r == 0);
     while (lm) {
-      const int src_lane = __ffs(lm) - 1;
+      const int src = __ffs(lm) - 1;
       lm &= lm - 1;
-      const int lrs = __shfl_sync(0xffffffffu, rs, src_lane);
-      const int lre = __shfl_sync(0xffffffffu, re, src_lane);
+      const int lrs = __shfl_sync(0xffffffffu, rs, src);
+      const int lre = __shfl_sync(0xffffffffu, re, src);
       for (int k = 0; k < nr; k++) {
         S tx, tp;
-        long_row_sums<P, SF>(a, st[k], nr, k, lrs, lre, tx, tp);
-        if (lane == src_lane + k) { sx = tx; sp = tp; }
+        if constexpr (YS) long_row_sums_y<P>(a, st[k], nr, k, lrs, lre, tx, tp);
+        else long_row_sums<P, QX>(a, st[k], nr, k, lrs, lre, tx, tp);
+        if (lane == src + k) { sx = tx; sp = tp; }
       }
     }
     if (ANY && a.jblk > 1) {
@@ -914,34 +998,33 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       const bool upd = valid && active;
       const size_t e = (size_t)i * nr + r;
       S g = P::zero(), yi = P::zero(), xi = P::zero();
-      if (upd) {
+      if (YS && upd) {
         const S bi = P::ldr(a.b + e);
-        if constexpr (YS) {
-          yi = P::ldg(xc + e);
-          xi = same ? yi : P::ldx(xcur + e);
-          g = P::sub(sx, bi);
-          P::acc_prod(acc[1], g, g);
-          if (chk2) {
-            const S g0 = P::sub(sp, bi);
-            P::acc_prod(acc[2], g0, g0);
-          }
-        } else {
-          xi = P::ldg(xc + e);
-          const S g0 = P::sub(sx, bi);
+        yi = P::ldg(xc + e);
+        xi = same ? yi : P::ldx(xp + e);
+        g = P::sub(sx, bi);
+        P::acc_prod(acc[1], g, g);
+        if (y_check<P>(me)) {
+          const S g0 = P::sub(sp, bi);
           P::acc_prod(acc[2], g0, g0);
-          if (want_obj) {
-            P::acc_prod(acc[3], xi, sx);
-            P::acc_prod(acc[4], bi, xi);
-          }
-          if (QX) P::stx(uc + e, sx);
-          if (same) {
-            g = g0;
-            yi = xi;
-          } else {
-            const S spi = QX ? P::ldx(up + e) : sp;
-            g = P::fma_(beta, P::sub(sx, spi), g0);
-            yi = DL ? P::fma_(beta, P::ldx(a.dl + e), xi) : P::fma_(beta, P::sub(xi, P::ldx(xp + e)), xi);
-          }
+        }
+      } else if (upd) {
+        xi = P::ldg(xc + e);
+        const S bi = P::ldr(a.b + e);
+        const S g0 = P::sub(sx, bi);
+        P::acc_prod(acc[2], g0, g0);
+        if (want_obj) {
+          P::acc_prod(acc[3], xi, sx);
+          P::acc_prod(acc[4], bi, xi);
+        }
+        if (QX) P::stx(uc + e, sx);
+        if (same) {
+          g = g0;
+          yi = xi;
+        } else {
+          const S spi = QX ? P::ldx(up + e) : sp;
+          g = P::fma_(beta, P::sub(sx, spi), g0);
+          yi = DL ? P::fma_(beta, P::ldx(a.dl + e), xi) : P::fma_(beta, P::sub(xi, P::ldx(xp + e)), xi);
         }
       }
       if (!compute_x) continue;
@@ -959,7 +1042,7 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
         const S dx = P::sub(xnew, xi);
         P::stx(xn + e, xnew);
         if (DL) P::stx(a.dl + e, dx);
-        if (YS) P::stx(yw + e, P::fma_(bnext, dx, xnew));
+        if constexpr (YS) P::stx(ubuf(a, 1 - me.yb) + e, P::fma_(yk.bnext, dx, xnew));
         P::acc_prod(acc[0], g, dx);
       }
       continue;
@@ -967,27 +1050,28 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
     if (!valid || !active) continue;
     const S ji = P::ldr(a.jinv + i);
     const size_t e = (size_t)i * nr + r;
-    const S bi = P::ldr(a.b + e);
     if constexpr (YS) {
+      const S bi = P::ldr(a.b + e);
       const S yi = P::ldg(xc + e);
-      // g = Q y^s - b; its norm decides when to check, and it is the exact
-      // residual of x^{s-1} when y^s = x^{s-1}
+      // g = Q y^s - b: its norm schedules the checks, and it is minus the
+      // exact residual of x^{s-1} where y^s = x^{s-1}
       const S g = P::sub(sx, bi);
       P::acc_prod(acc[1], g, g);
-      if (chk2) {
+      if (y_check<P>(me)) {
         const S g0 = P::sub(sp, bi);
         P::acc_prod(acc[2], g0, g0);
       }
       if (!compute_x) continue;
-      const S xi = same ? yi : P::ldx(xcur + e);
+      const S xi = same ? yi : P::ldx(xp + e);
       const S xnew = P::fnma(ji, g, yi);
       const S dx = P::sub(xnew, xi);
       P::stx(xn + e, xnew);
-      P::stx(yw + e, P::fma_(bnext, dx, xnew));
+      P::stx(ubuf(a, 1 - me.yb) + e, P::fma_(yk.bnext, dx, xnew));
       P::acc_prod(acc[0], g, dx);
       continue;
     }
     const S xi = P::ldg(xc + e);
+    const S bi = P::ldr(a.b + e);
     // g0 = Q x^{s-1} - b: minus the exact residual of x^{s-1}
     const S g0 = P::sub(sx, bi);
     P::acc_prod(acc[2], g0, g0);
@@ -1035,10 +1119,11 @@ __device__ __forceinline__ double next_alpha(double a) { return 0.5 * (1.0 + sqr
 // grid totals tot[r][k].  Identical inputs give identical decisions in every
 // CTA.  Returns true when every right-hand side is done.  ysf: the sweep ran
 // in the explicit-y form (see sweep).
+template <bool ysf>
 __device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kNRed], int nr, long long s,
                                             long long maxit, int stop, int restart, int momentum,
                                             double tol, double fstar, double fscale, long long* rlog,
-                                            int rlog_cap, bool log_it, bool ysf) {
+                                            int rlog_cap, bool log_it) {
   bool all_done = true;
   for (int r = 0; r < nr; r++) {
     RhsState& q = st[r];
@@ -1107,7 +1192,7 @@ __device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kN
       q.prev = oldcur;
       q.cur = oldnew;
       q.nxt = (oldprev != oldcur && oldprev != oldnew) ? oldprev : (3 - oldcur - oldnew);
-      q.yb = 1 - q.yb;  // explicit y: the candidate this sweep wrote is y^{t+1}
+      if (ysf) q.yb = 1 - q.yb;  // explicit y: the candidate this sweep wrote is y^{t+1}
     }
     q.uw = 1 - q.uw;
     q.t = t;
@@ -1141,13 +1226,10 @@ struct SolveSmem {
 // summed in a fixed order that does not depend on nr or on which CTA runs
 // this: thread t adds the partials of CTAs t, t + 256, ... in ascending
 // order, then a xor tree over the lanes and the warps in order.  Every
-// thread must call it; the totals are valid in sm.tot after it returns.  MR:
-// the most right-hand sides the caller can have (1 keeps the one-RHS kernels'
-// per-thread sums in 5 registers instead of 20).
-template <int MR = kMaxRhs>
+// thread must call it; the totals are valid in sm.tot after it returns.
 __device__ __forceinline__ void grid_totals(const double* part, int ncta, int nr, bool want_obj,
                                             bool want_gg, SolveSmem& sm) {
-  constexpr int NV = MR * kNRed;
+  constexpr int NV = kMaxRhs * kNRed;
   double v[NV];
 #pragma unroll
   for (int q = 0; q < NV; q++) v[q] = 0.0;
@@ -1155,7 +1237,7 @@ __device__ __forceinline__ void grid_totals(const double* part, int ncta, int nr
   for (int c = threadIdx.x; c < ncta; c += kThreads) {
     const double* pc = part + (size_t)c * nr * kNRed;
 #pragma unroll
-    for (int r = 0; r < MR; r++)
+    for (int r = 0; r < kMaxRhs; r++)
 #pragma unroll
       for (int k = 0; k < kNRed; k++)
         if (r < nr && k < nslot && slot_used(k, want_obj, want_gg)) v[r * kNRed + k] += __ldcg(pc + r * kNRed + k);
@@ -1219,7 +1301,7 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, i
                    s0 == 0 && cta == a.bar_withhold_cta))
       return false;
     // every CTA sums the partials in the same fixed order
-    grid_totals<MULTI ? kMaxRhs : 1>(part, ncta, nr, want_obj, SF == 3, sm);
+    grid_totals(part, ncta, nr, want_obj, SF == 3, sm);
     if (threadIdx.x == 0) {
       if (a.trace && cta == 0 && s_run >= 1 && s_run <= a.trace_cap) {
         for (int r = 0; r < nr; r++) {
@@ -1230,8 +1312,8 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, i
           tr[3] = sm.st[r].beta;
         }
       }
-      sm.done = scalar_step(sm.st, sm.tot, nr, s_run, a.maxit, a.stop, a.restart, a.momentum, a.tol,
-                            a.fstar, a.fscale, a.rlog, a.rlog_cap, cta == 0, SF == 3)
+      sm.done = scalar_step<SF == 3>(sm.st, sm.tot, nr, s_run, a.maxit, a.stop, a.restart, a.momentum,
+                                     a.tol, a.fstar, a.fscale, a.rlog, a.rlog_cap, cta == 0)
                     ? 1
                     : 0;
     }
@@ -1351,8 +1433,8 @@ __device__ __forceinline__ bool lock_enter(const LockArgs<P>& b, IterArgs<P>& a,
       if (!sm.st[r].done) s_run = sm.st[r].t + 1;
     grid_totals(a.partials + (size_t)((k - 1) & 1) * V * nr * kNRed, V, nr, want_obj, SF == 3, sm);
     if (threadIdx.x == 0)
-      sm.done = scalar_step(sm.st, sm.tot, nr, s_run, a.maxit, a.stop, a.restart, a.momentum, a.tol,
-                            a.fstar, a.fscale, a.rlog, a.rlog_cap, log_it, SF == 3)
+      sm.done = scalar_step<SF == 3>(sm.st, sm.tot, nr, s_run, a.maxit, a.stop, a.restart, a.momentum,
+                                     a.tol, a.fstar, a.fscale, a.rlog, a.rlog_cap, log_it)
                     ? 1
                     : 0;
     __syncthreads();
