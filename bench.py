@@ -64,12 +64,14 @@ def algorithmic_bytes(n, nnz, precision, form="min", stencil=False, nrhs=1):
 
 # DRAM bytes (read + written) per fused sweep over the bytes the sweep form
 # moves in that sweep, from the ncu captures of the kernel on the 128^3
-# Poisson system (50 iterations, 51 sweeps per launch): FP64 difference form
+# Poisson system (50 iterations, 51 sweeps per launch): FP64 explicit-y form
+# 14.924 GB / 51 / 284.0 MB, FP64 difference form
 # 16.687 GB / 51 / 317.6 MB, FP64 stored 15.968 GB / 51 / 300.8 MB, FP32
 # values stored 9.382 GB / 51 / 183.8 MB, FP32 values lazy 9.157 GB / 51 /
 # 167.0 MB.  The bench scales it to a full launch by the sweeps it runs;
 # traffic grows in proportion to the rows.
-TRAFFIC_PER_FORM_BYTES = {("fp64", "delta"): 16.687168e9 / 51 / 317587460.0,
+TRAFFIC_PER_FORM_BYTES = {("fp64", "y"): 14.924282e9 / 51 / 284033028.0,
+                          ("fp64", "delta"): 16.687168e9 / 51 / 317587460.0,
                           ("fp64", "stored"): 15.967641e9 / 51 / 300810244.0,
                           ("fp32_ir", "stored"): 9.382468e9 / 51 / 183762948.0,
                           ("fp32_ir", "lazy"): 9.157071e9 / 51 / 166985732.0}
@@ -87,9 +89,10 @@ def fp64_ops(n, nnz, form="stored"):
     if form == "delta":
         return nnz + 8 * n
     if form == "y":
-        # explicit y: g, ||g||^2, x update, x difference, y candidate, d (check
-        # sweeps add a second row sum and 2 per row, not counted here)
-        return nnz + 6 * n
+        # explicit y: the row sum starts at -b, then the x update, the x
+        # difference, the y candidate and d, plus ||g||^2 on every 4th sweep
+        # (check sweeps add a second row sum, not counted here)
+        return nnz + 4 * n + n / 4
     return (nnz + 9 * n) if form == "stored" else (2 * nnz + 11 * n)
 
 
@@ -498,7 +501,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-iters", type=int, default=60)
+    ap.add_argument("--cpu-iters", type=int, default=160)
     ap.add_argument("--workload", default=WORKLOAD,
                     help="poisson3d_N | poisson2d_N | chunglu_N | rgg_N (profiling cases)")
     ap.add_argument("--no-graph", action="store_true")
@@ -537,10 +540,10 @@ def main():
     stream = torch.cuda.current_stream()
 
     def form_of(precision, form):
-        # the library's AUTO choice on this (CSR) workload: the difference form
-        # for FP64, lazy otherwise
+        # the library's AUTO choice on this (CSR) workload: the explicit-y form
+        # for FP64 (one right-hand side), lazy otherwise
         if form == "auto":
-            return "delta" if precision == "fp64" else "lazy"
+            return "y" if precision == "fp64" else "lazy"
         return form
 
     SWEEP = {"lazy": aj.AJ_SWEEP_LAZY, "stored": aj.AJ_SWEEP_STORED, "delta": aj.AJ_SWEEP_DELTA,

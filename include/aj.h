@@ -113,22 +113,28 @@ typedef struct {
  *           instruction instead of two (the kept difference is the one the
  *           update computes anyway for the restart test); AJ_FP64 only, one
  *           more n-vector written per sweep.
- * AUTO picks DELTA for AJ_FP64, whose FP64 issue rate binds on GB300; STORED
- * for matrices stored as SELL (irregular rows, whose gathers are random: one
- * per entry instead of two); LAZY for the other precisions on CSR, where the
- * second row sum gathers from the same cached lines (measured faster on the
- * 3-D Poisson system and on 2-D grids with 4 RHS). */
-/*   Y       keeps y^t itself as a vector: the sweep gathers y^t, forms x^t and
+ *   Y       keeps y^t itself as a vector: the sweep gathers y^t, forms x^t and
  *           writes the candidate y^{t+1} = x^t + beta_{t+1} (x^t - x^{t-1})
  *           (beta_{t+1} depends on alpha_t only, known before the restart
  *           test; a restart drops the candidate and reads y^{t+1} = x^{t-1}
- *           from that iterate's buffer).  One multiply-add per stored entry
- *           and six n-vectors of traffic, but the exact residual of x^{t-1}
- *           needs a second row sum: it is formed on check sweeps only, once
- *           ||Q y^t - b|| <= 3 tol ||b|| and every 32 iterations, so a solve
- *           stops at the first checked iterate within tol (the oracle's stop
- *           iteration where the check schedule reaches it, at most 31
- *           iterations later otherwise).  Not with AJ_STOP_OBJGAP. */
+ *           from that iterate's buffer).  One multiply-add per stored entry,
+ *           the row sum starting at -b, and six n-vectors of traffic; but the
+ *           exact residual of x^{t-1} needs a second row sum.  It is formed
+ *           on check sweeps only: once ||Q y^t - b|| (summed every 4th sweep,
+ *           and every sweep within 10x of the stop) falls to 1.5 tol ||b||
+ *           (widened by the largest residual-to-monitor ratio the checks have
+ *           met), and every 32 iterations.  A solve so stops at the first
+ *           checked iterate within tol: the oracle's stop iteration where the
+ *           checks reach it, at most 31 iterations later otherwise.  The
+ *           divergence guard reads ||Q y^t - b|| on the sweeps that sum it.
+ *           Not with AJ_STOP_OBJGAP.
+ * AUTO picks Y for AJ_FP64 with one right-hand side (its FP64 issue rate
+ * binds on GB300, and Y runs the fewest FP64 instructions per row), DELTA for
+ * AJ_FP64 with several or with AJ_STOP_OBJGAP; STORED for matrices stored as
+ * SELL (irregular rows, whose gathers are random: one per entry instead of
+ * two); LAZY for the other precisions on CSR, where the second row sum
+ * gathers from the same cached lines (measured faster on the 3-D Poisson
+ * system and on 2-D grids with 4 RHS). */
 #define AJ_SWEEP_AUTO 0
 #define AJ_SWEEP_LAZY 1
 #define AJ_SWEEP_STORED 2
@@ -196,6 +202,8 @@ typedef struct {
   int sell_lmax;         /* AJ_FMT_SELL: rows longer than this go to the warp-per-row bucket (0 = 64) */
   int reorder;           /* AJ_REORDER_AUTO (default) | AJ_REORDER_NONE | AJ_REORDER_RCM */
   int j_block;           /* AJ_J_BLKDIAG: rows per block, 1, 2, 4 or 8 (0 = 4) */
+  int sell_c;            /* AJ_FMT_SELL: slice height C, 32, 16 or 8 (0 = 32): C rows per
+                            warp step, 32 / C lanes share a row (one right-hand side) */
 } aj_params;
 
 /* Per-solve report. */
@@ -212,6 +220,30 @@ typedef struct {
   int64_t launches; /* kernels this solve launched (fused, setup and conversion kernels) */
   aj_status status; /* AJ_OK, AJ_EMAXIT, AJ_EDIVERGED, AJ_ENONFINITE or AJ_ETIMEOUT */
 } aj_info;
+
+/* What aj_set chose for the fused sweep (the autotuner's tuple under
+ * AJ_FMT_AUTO).  The autotuner runs when the rows are long-tailed and the
+ * system is large (n >= 65536): it times CSR and SELL with sigma in {256,
+ * 4096} and sell_lmax in {64, 256}, then SELL's slice height C in {16, 8}
+ * for the best of these, then 1-2 CTAs per SM below the kernel's occupancy,
+ * 8 sweeps each, and caches the choice per matrix shape, precision, RHS
+ * count, sweep form and order. */
+typedef struct {
+  int format;          /* AJ_FMT_CSR, AJ_FMT_SELL or AJ_FMT_STENCIL */
+  int sell_c;          /* SELL slice height C: rows per warp step (0 unless SELL) */
+  int sell_sigma;      /* SELL sorting window (0 unless SELL) */
+  int sell_lmax;       /* SELL long-row threshold (0 unless SELL) */
+  int lanes_per_row;   /* lanes that share a row: 32 / C for SELL with one RHS; with
+                          several RHS one lane per RHS (2 or 4); else 1 */
+  int rows_per_cta;    /* rows one CTA sweeps per tile */
+  int threads_per_cta; /* 256 */
+  int ctas_per_sm;     /* persistent CTAs per SM of the solve's launch */
+  int grid;            /* persistent CTAs in all */
+  int sweep_form;      /* the form in use: AJ_SWEEP_LAZY, _STORED, _DELTA or _Y */
+  int tuned;           /* 1: chosen by timing candidates (or from the autotuner's cache) */
+  int pad_;
+  double fill_ratio;   /* stored entries over nnz (SELL padding); 1 for CSR, 0 for STENCIL */
+} aj_tuning;
 
 /* Fill *p with the defaults above. */
 void aj_params_default(aj_params* p);
@@ -230,6 +262,10 @@ aj_status aj_create(const aj_csr* Q, const double* b, int nrhs, aj_ctx** out);
  * fails, after which the context counts as never set: its next solve first
  * applies the default parameters, as on a fresh context. */
 aj_status aj_set(aj_ctx* ctx, const aj_params* p);
+
+/* The tuple of aj_tuning for the context's last successful aj_set.
+ * AJ_EINVAL if ctx or out is NULL or aj_set has not succeeded yet. */
+aj_status aj_get_tuning(aj_ctx* ctx, aj_tuning* out);
 
 /* The format aj_set chose (AJ_FMT_CSR, AJ_FMT_SELL or AJ_FMT_STENCIL), its
  * sigma and long-row threshold (0 unless SELL), and the entries the sweep
@@ -371,7 +407,8 @@ const char* aj_strerror(aj_status s);
  *   b       n device doubles; read only.
  *   p       parameters as for aj_set; precision must be AJ_FP64 (the sweep
  *           form is always AJ_SWEEP_STORED, which computes the same iterates
- *           bit for bit as the AJ_SWEEP_DELTA form AUTO picks for FP64;
+ *           as the other FP64 forms up to rounding and, bit for bit, as
+ *           AJ_SWEEP_DELTA;
  *           p->reorder is ignored: rows keep the caller's order), and
  *           AJ_J_SCALED_DIAG needs p->L > 0 (no power-iteration estimate);
  *           p->x0, if given, must be a device pointer (x0_on_device = 1).

@@ -41,7 +41,16 @@ class aj_params(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int64),
                 ("grid_ctas", ctypes.c_int), ("sweep_form", ctypes.c_int),
                 ("sell_sigma", ctypes.c_int), ("sell_lmax", ctypes.c_int), ("reorder", ctypes.c_int),
-                ("j_block", ctypes.c_int)]
+                ("j_block", ctypes.c_int), ("sell_c", ctypes.c_int)]
+
+
+class aj_tuning(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int) for k in ("format", "sell_c", "sell_sigma", "sell_lmax", "lanes_per_row",
+                                            "rows_per_cta", "threads_per_cta", "ctas_per_sm", "grid",
+                                            "sweep_form", "tuned", "pad_")] + [("fill_ratio", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
 class aj_info(ctypes.Structure):
@@ -79,6 +88,7 @@ SIGNATURES = [
     ("aj_create", ctypes.c_int, [ctypes.POINTER(aj_csr), ctypes.c_void_p, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_void_p)]),
     ("aj_set", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(aj_params)]),
+    ("aj_get_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(aj_tuning)]),
     ("aj_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("aj_get_order", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double)]),
@@ -202,6 +212,12 @@ class Context:
         _check(lib().aj_get_format(self._h, ctypes.byref(f), ctypes.byref(sg), ctypes.byref(lm),
                                    ctypes.byref(fr)), "aj_get_format")
         return f.value, sg.value, lm.value, fr.value
+
+    def tuning(self):
+        """The fused sweep's configuration aj_set chose (aj_get_tuning), as a dict."""
+        t = aj_tuning()
+        _check(lib().aj_get_tuning(self._h, ctypes.byref(t)), "aj_get_tuning")
+        return t.as_dict()
 
     def order(self):
         """(reordered, span_before, span_after) decided by aj_set."""

@@ -194,12 +194,12 @@ int lockstep_blocks_per_sm(int pol, int qx) {
   }
   return 0;
 }
-int persistent_blocks_per_sm(int pol, int nrhs, int qx) {
+int persistent_blocks_per_sm(int pol, int nrhs, int qx, int fm) {
   switch (pol) {
-    case 0: return blocks_per_sm_f64(nrhs, qx);
-    case 1: return blocks_per_sm_df64(nrhs, qx);
-    case 2: return blocks_per_sm_f32(nrhs, qx);
-    case 3: return blocks_per_sm_b16(nrhs, qx);
+    case 0: return blocks_per_sm_f64(nrhs, qx, fm);
+    case 1: return blocks_per_sm_df64(nrhs, qx, fm);
+    case 2: return blocks_per_sm_f32(nrhs, qx, fm);
+    case 3: return blocks_per_sm_b16(nrhs, qx, fm);
   }
   return 0;
 }
@@ -231,7 +231,9 @@ struct aj_ctx {
   void* dl = nullptr;               // x^t - x^{t-1} (difference sweep form)
   // SELL-C-sigma copy of Q (fmt = 1), rebuilt by aj_set
   Workspace sws;
-  int fmt = 0, sell_sigma = 0, sell_lmax = 0;
+  int fmt = 0, sell_sigma = 0, sell_lmax = 0, sell_cl = 5;
+  int ctas_cap = 0;   // CTAs per SM the autotuner chose (0: the kernel's occupancy)
+  int tuned = 0;      // 1 when the format and grid came from timing (or its cache)
   int sdim = 0, sN = 0;  // stencil format (fmt = 2): dimensions and grid side
   // block-diagonal J (eq. J-blkdiag, jblk > 1 rows per block): row k of each
   // block's inverse in FP64 and in the iteration precision, rebuilt by aj_set
@@ -242,7 +244,7 @@ struct aj_ctx {
   double fill = 1.0;
   int nsell = 0, ntiles_sell = 0, nltiles = 0, nhuge = 0;
   int *d_perm = nullptr, *d_rlen = nullptr, *d_sptr = nullptr, *d_scol = nullptr;
-  int *d_long = nullptr, *d_ltp = nullptr, *d_huge = nullptr;
+  int *d_long = nullptr, *d_ltp = nullptr, *d_huge = nullptr, *d_tdesc = nullptr;
   void* d_sval = nullptr;
   int qx = 0;                       // sweep form in use: 0 lazy, 1 stored, 2 difference, 3 explicit y
   double sQ = 1.0;
@@ -814,7 +816,10 @@ static aj_status choose_format(aj_ctx* c, const aj_params* p);
 // tile up to the co-resident limit (SELL counts its sliced, long-row and
 // huge-row tiles), or the caller's grid_ctas.
 static void size_grid(aj_ctx* c) {
-  const int bps = std::max(1, persistent_blocks_per_sm(kernel_pol(c->pol), c->nrhs, c->qx));
+  // the instantiation the launch takes: the stencil rows alone, CSR alone, or any
+  const int fm = c->fmt == 2 ? 2 : (c->fmt == 1 || c->jblk > 1) ? 1 : 0;
+  int bps = std::max(1, persistent_blocks_per_sm(kernel_pol(c->pol), c->nrhs, c->qx, fm));
+  if (c->ctas_cap > 0) bps = std::min(bps, c->ctas_cap);
   const long long rpt = kThreads >> lanes_log2(c->nrhs);
   const long long ntiles = c->fmt == 1 ? (long long)c->ntiles_sell + c->nltiles + c->nhuge
                                        : (c->n + rpt - 1) / rpt;
@@ -842,6 +847,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   if (p->sweep_form == AJ_SWEEP_DELTA && p->precision != AJ_FP64) return AJ_EINVAL;
   if (p->sweep_form == AJ_SWEEP_Y && p->stop == AJ_STOP_OBJGAP) return AJ_EINVAL;
   if (p->sell_sigma < 0 || p->sell_lmax < 0) return AJ_EINVAL;
+  if (p->sell_c != 0 && p->sell_c != 8 && p->sell_c != 16 && p->sell_c != 32) return AJ_EINVAL;
   if (p->reorder < AJ_REORDER_AUTO || p->reorder > AJ_REORDER_RCM) return AJ_EINVAL;
   if ((p->precision == AJ_FP32_IR || p->precision == AJ_BF16_IR) &&
       (!(p->inner_tol > 0.0) || p->max_outer < 1))
@@ -938,10 +944,9 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     c->r64 = (double*)c->pws.alloc((size_t)(m + 1) * 8);
     if (!c->x64 || !c->r64) return AJ_ENOMEM;
     const int kp = kernel_pol(pol);
-    const int bps = std::max({1, persistent_blocks_per_sm(kp, nrhs, 0),
-                              persistent_blocks_per_sm(kp, nrhs, 1),
-                              persistent_blocks_per_sm(kp, nrhs, 2),
-                              persistent_blocks_per_sm(kp, nrhs, 3)});
+    int bps = 1;  // the largest grid any sweep form and format may take
+    for (int q = 0; q < 4; q++)
+      for (int f = 0; f < 3; f++) bps = std::max(bps, persistent_blocks_per_sm(kp, nrhs, q, f));
     const int maxg = bps * c->sm_count;
     c->partials = (double*)c->pws.alloc((size_t)2 * maxg * nrhs * kNRed * 8);
     c->part_cap = maxg;
@@ -952,14 +957,17 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     c->pol = pol;
   }
   // --- sweep form and grid: a multiple of the SM count when the problem is large enough
-  // AUTO: the difference form for FP64; for the other precisions the stored
-  // form while the format is chosen, then the lazy form on CSR (see the end
-  // of aj_set)
+  // AUTO: for FP64 the explicit-y form with one right-hand side (the fewest
+  // FP64 instructions per row: 256^3 Poisson 0.480 ms per sweep against 0.553
+  // in the difference form), the difference form with several or with the
+  // objective-gap stop; for the other precisions the stored form while the
+  // format is chosen, then the lazy form on CSR (see the end of aj_set)
+  const bool auto_y = p->precision == AJ_FP64 && p->stop != AJ_STOP_OBJGAP && nrhs == 1;
   c->qx = p->sweep_form == AJ_SWEEP_LAZY     ? 0
           : p->sweep_form == AJ_SWEEP_STORED ? 1
           : p->sweep_form == AJ_SWEEP_DELTA  ? 2
           : p->sweep_form == AJ_SWEEP_Y      ? 3
-          : (p->precision == AJ_FP64 ? 2 : 1);
+          : (p->precision == AJ_FP64 ? (auto_y ? 3 : 2) : 1);
   size_grid(c);
   // --- scaled copies for the non-FP64 policies (powers of two: exact)
   if (pol != AJ_FP64) {
@@ -1136,6 +1144,7 @@ static IterLaunch make_launch(aj_ctx* c, const void* bvec, long long maxit, int 
   }
   if (c->fmt == 1) {
     L.nsell = c->nsell;
+    L.sell_cl = c->sell_cl;
     L.ntiles_sell = c->ntiles_sell;
     L.nltiles = c->nltiles;
     L.perm = c->d_perm;
@@ -1147,6 +1156,7 @@ static IterLaunch make_launch(aj_ctx* c, const void* bvec, long long maxit, int 
     L.ltp = c->d_ltp;
     L.nhuge = c->nhuge;
     L.huge_rows = c->d_huge;
+    L.tile_desc = c->d_tdesc;
   }
   L.b = bvec;
   L.jinv = c->pol == AJ_FP64 ? (const void*)c->jinv64 : c->jinvp;
@@ -1225,16 +1235,20 @@ static const int kHugeRow = 4096;
 template <class T>
 static void sell_fill(aj_ctx* c, const void* val) {
   k_sell_fill<T><<<grid1d(c->nsell), kSetupThreads, 0, c->stream>>>(
-      c->nsell, c->d_perm, c->d_rlen, c->d_sptr, c->rp, c->ci, (const T*)val, c->d_scol, (T*)c->d_sval);
+      c->nsell, c->sell_cl, c->d_perm, c->d_rlen, c->d_sptr, c->rp, c->ci, (const T*)val, c->d_scol,
+      (T*)c->d_sval);
   counted();
 }
 
-static aj_status build_sell(aj_ctx* c, int sigma, int lmax) {
+static aj_status build_sell(aj_ctx* c, int sigma, int lmax, int cl = 5) {
   c->sws.release();
   c->fmt = 0;
   c->fill = 1.0;
+  if (c->nrhs > 1) cl = 5;  // several right-hand sides take the lanes of a row
   const int n = (int)c->n;
   const int rpt = kThreads >> lanes_log2(c->nrhs);  // rows per tile
+  const int C = 1 << cl;                            // slice height
+  const int rpt_sell = cl < 5 ? (kWarps << cl) : rpt;  // rows per sliced tile
   cudaStream_t s = c->stream;
   std::vector<int> rp((size_t)n + 1);
   CK(cudaMemcpyAsync(rp.data(), c->rp, rp.size() * 4, cudaMemcpyDeviceToHost, s));
@@ -1252,17 +1266,17 @@ static aj_status build_sell(aj_ctx* c, int sigma, int lmax) {
     std::stable_sort(b, e, [&](int x, int y) { return len(x) > len(y); });
   }
   const int nsell = (int)rows.size();
-  const int nslices = (nsell + 31) / 32;
+  const int nslices = (nsell + C - 1) / C;
   std::vector<int> rlen(nsell), sptr((size_t)nslices + 1);
   long long tot = 0;
   for (int sl = 0; sl < nslices; sl++) {
     int w = 0;
-    for (int p = sl * 32; p < std::min(nsell, sl * 32 + 32); p++) {
+    for (int p = sl * C; p < std::min(nsell, sl * C + C); p++) {
       rlen[p] = len(rows[p]);
       w = std::max(w, rlen[p]);
     }
     sptr[sl] = (int)tot;
-    tot += 32ll * w;
+    tot += (long long)C * w;
     if (tot > (1ll << 31) - 64) return AJ_ENOMEM;
   }
   sptr[nslices] = (int)tot;
@@ -1289,6 +1303,29 @@ static aj_status build_sell(aj_ctx* c, int sigma, int lmax) {
     long_entries += l;
   }
   if (!lng.empty()) ltp.push_back((int)lng.size());
+  // the sweep's tile order: every tile (sliced, long-row, huge-row) by its
+  // estimated work, heaviest first -- stored entries (with the slices'
+  // padding) plus a per-row cost for the update -- so that the round-robin
+  // deal over the CTAs leaves none more than one tile's work behind
+  const int ntsell = (nsell + rpt_sell - 1) / rpt_sell;
+  std::vector<std::pair<long long, int>> order;
+  order.reserve((size_t)ntsell + ltp.size() + hug.size());
+  const long long kRowCost = 8;
+  for (int k = 0; k < ntsell; k++) {
+    const int p0 = k * rpt_sell, p1 = std::min(nsell, p0 + rpt_sell);
+    const long long ent = (long long)sptr[(p1 + C - 1) / C] - sptr[p0 / C];
+    order.push_back({ent + kRowCost * (p1 - p0), k});
+  }
+  for (int lt = 0; lt + 1 < (int)ltp.size(); lt++) {
+    long long ent = 0;
+    for (int j = ltp[lt]; j < ltp[lt + 1]; j++) ent += len(lng[j]);
+    order.push_back({ent + kRowCost * (ltp[lt + 1] - ltp[lt]), (1 << 29) | lt});
+  }
+  for (int h = 0; h < (int)hug.size(); h++) order.push_back({(long long)len(hug[h]) + kRowCost * kThreads, (2 << 29) | h});
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<long long, int>& x, const std::pair<long long, int>& y) { return x.first > y.first; });
+  std::vector<int> tdesc(order.size());
+  for (size_t k = 0; k < order.size(); k++) tdesc[k] = order[k].second;
   const size_t vb = velem_bytes(c->pol);
   c->d_perm = (int*)c->sws.alloc(((size_t)nsell + 1) * 4);
   c->d_rlen = (int*)c->sws.alloc(((size_t)nsell + 1) * 4);
@@ -1298,8 +1335,9 @@ static aj_status build_sell(aj_ctx* c, int sigma, int lmax) {
   c->d_long = (int*)c->sws.alloc((lng.size() + 1) * 4);
   c->d_ltp = (int*)c->sws.alloc(ltp.size() * 4);
   c->d_huge = (int*)c->sws.alloc((hug.size() + 1) * 4);
+  c->d_tdesc = (int*)c->sws.alloc((tdesc.size() + 1) * 4);
   if (!c->d_perm || !c->d_rlen || !c->d_sptr || !c->d_scol || !c->d_sval || !c->d_long || !c->d_ltp ||
-      !c->d_huge) {
+      !c->d_huge || !c->d_tdesc) {
     c->sws.release();
     return AJ_ENOMEM;
   }
@@ -1311,11 +1349,14 @@ static aj_status build_sell(aj_ctx* c, int sigma, int lmax) {
   if (!lng.empty()) CK(cudaMemcpyAsync(c->d_long, lng.data(), lng.size() * 4, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->d_ltp, ltp.data(), ltp.size() * 4, cudaMemcpyHostToDevice, s));
   if (!hug.empty()) CK(cudaMemcpyAsync(c->d_huge, hug.data(), hug.size() * 4, cudaMemcpyHostToDevice, s));
+  if (!tdesc.empty())
+    CK(cudaMemcpyAsync(c->d_tdesc, tdesc.data(), tdesc.size() * 4, cudaMemcpyHostToDevice, s));
   for (int h : hug) long_entries += len(h);
   CK(cudaMemsetAsync(c->d_scol, 0, ((size_t)tot + 32) * 4, s));
   CK(cudaMemsetAsync(c->d_sval, 0, ((size_t)tot + 32) * vb, s));
   c->nsell = nsell;
-  c->ntiles_sell = (nsell + rpt - 1) / rpt;
+  c->sell_cl = cl;
+  c->ntiles_sell = ntsell;
   c->nltiles = (int)ltp.size() - 1;
   c->nhuge = (int)hug.size();
   if (nsell) {
@@ -1368,7 +1409,12 @@ struct TuneKey {
            std::tie(o.n, o.nnz, o.sumsq, o.maxlen, o.pol, o.nrhs, o.qx, o.ordered);
   }
 };
-static std::map<TuneKey, std::array<int, 3>> g_tune;  // -> {fmt, sigma, lmax}
+// the autotuner's choice: format (0 CSR, 1 SELL), sigma, lmax, log2 of the
+// SELL slice height, CTAs per SM
+struct TuneVal {
+  int fmt, sigma, lmax, cl, ctas;
+};
+static std::map<TuneKey, TuneVal> g_tune;
 static std::mutex g_tune_mu;
 
 // The constant-coefficient stencil format: Q in natural row order is the
@@ -1414,10 +1460,20 @@ static aj_status detect_stencil(aj_ctx* c, bool* is) {
   return AJ_OK;
 }
 
+static int log2_slice(int C) { return C == 8 ? 3 : C == 16 ? 4 : 5; }
+
+// Times the sweep with at most `ctas` CTAs per SM (0: the kernel's occupancy).
+static aj_status time_grid(aj_ctx* c, int ctas, double* ms) {
+  c->ctas_cap = ctas;
+  return time_sweeps(c, ms);
+}
+
 static aj_status choose_format(aj_ctx* c, const aj_params* p) {
   const int sig = p->sell_sigma > 0 ? p->sell_sigma : 256;
   const int lmx = p->sell_lmax > 0 ? p->sell_lmax : 64;
-  if (p->format == AJ_FMT_SELL) return build_sell(c, sig, lmx);
+  c->ctas_cap = 0;
+  c->tuned = 0;
+  if (p->format == AJ_FMT_SELL) return build_sell(c, sig, lmx, log2_slice(p->sell_c));
   c->sws.release();
   c->fmt = 0;
   c->fill = 1.0;
@@ -1464,35 +1520,94 @@ static aj_status choose_format(aj_ctx* c, const aj_params* p) {
   }
   const double mean = (double)c->nnz / n;
   if (maxlen <= 2.0 * mean + 8.0) return AJ_OK;
+  // the autotuner (long-tailed rows): format and SELL's sorting window sigma
+  // and long-row threshold, then SELL's slice height C in {32, 16, 8} (rows
+  // per warp step; 32 / C lanes share a row), then the CTAs per SM; every
+  // candidate timed over 8 sweeps, the choice cached per matrix shape
   const TuneKey key{c->n, c->nnz, sumsq, maxlen, c->pol, c->nrhs, c->qx, c->ordered};
+  auto apply = [&](const TuneVal& v) -> aj_status {
+    aj_status e = AJ_OK;
+    if (v.fmt == 1) {
+      e = build_sell(c, v.sigma, v.lmax, v.cl);
+    } else {
+      c->sws.release();
+      c->fmt = 0;
+      c->fill = 1.0;
+    }
+    c->ctas_cap = v.ctas;
+    c->tuned = 1;
+    return e;
+  };
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      if (it->second[0] == 1) return build_sell(c, it->second[1], it->second[2]);
-      return AJ_OK;
+      const TuneVal v = it->second;
+      return apply(v);
     }
   }
-  const std::array<int, 3> cand[] = {{0, 0, 0}, {1, 256, 64}, {1, 4096, 64}, {1, 256, 256}};
-  std::array<int, 3> best = cand[0];
+  const TuneVal cand[] = {{0, 0, 0, 5, 0}, {1, 256, 64, 5, 0}, {1, 4096, 64, 5, 0}, {1, 256, 256, 5, 0}};
+  TuneVal best = cand[0];
   double best_ms = 1e300;
-  for (const auto& k : cand) {
-    aj_status e = k[0] ? build_sell(c, k[1], k[2]) : AJ_OK;
-    if (k[0] == 0) { c->sws.release(); c->fmt = 0; c->fill = 1.0; }
-    if (e != AJ_OK) continue;
-    double ms = 0.0;
-    e = time_sweeps(c, &ms);
+  auto consider = [&](const TuneVal& v) -> aj_status {
+    aj_status e = apply(v);
+    if (e == AJ_ENOMEM) return AJ_OK;  // a candidate that does not fit is skipped
     if (e != AJ_OK) return e;
-    if (ms < best_ms) { best_ms = ms; best = k; }
+    double ms = 0.0;
+    e = time_grid(c, v.ctas, &ms);
+    if (e != AJ_OK) return e;
+    if (ms < best_ms) { best_ms = ms; best = v; }
+    return AJ_OK;
+  };
+  for (const auto& v : cand) {
+    aj_status e = consider(v);
+    if (e != AJ_OK) return e;
+  }
+  if (best.fmt == 1 && c->nrhs == 1) {
+    for (int cl : {4, 3}) {
+      TuneVal v = best;
+      v.cl = cl;
+      aj_status e = consider(v);
+      if (e != AJ_OK) return e;
+    }
+  }
+  {
+    // CTAs per SM below the kernel's occupancy (fewer CTAs, less imbalance at
+    // each grid barrier, more L1 per CTA)
+    const int fm = best.fmt == 1 ? 1 : 0;
+    const int occ = std::max(1, persistent_blocks_per_sm(kernel_pol(c->pol), c->nrhs, c->qx, fm));
+    for (int k = occ - 1; k >= std::max(2, occ - 2); k--) {
+      TuneVal v = best;
+      v.ctas = k;
+      aj_status e = consider(v);
+      if (e != AJ_OK) return e;
+    }
   }
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key] = best;
   }
-  if (best[0] == 1) return build_sell(c, best[1], best[2]);
-  c->sws.release();
-  c->fmt = 0;
-  c->fill = 1.0;
+  return apply(best);
+}
+
+extern "C" aj_status aj_get_tuning(aj_ctx* c, aj_tuning* out) {
+  if (!c || !out || !c->have_prm) return AJ_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->format = c->fmt == 1 ? AJ_FMT_SELL : c->fmt == 2 ? AJ_FMT_STENCIL : AJ_FMT_CSR;
+  const bool sell = c->fmt == 1;
+  const int lg = lanes_log2(c->nrhs);
+  out->sell_c = sell ? 1 << c->sell_cl : 0;
+  out->sell_sigma = sell ? c->sell_sigma : 0;
+  out->sell_lmax = sell ? c->sell_lmax : 0;
+  out->lanes_per_row = sell && c->sell_cl < 5 ? 32 >> c->sell_cl : 1 << lg;
+  out->rows_per_cta = sell && c->sell_cl < 5 ? kWarps << c->sell_cl : kThreads >> lg;
+  out->threads_per_cta = kThreads;
+  out->grid = c->grid;
+  out->ctas_per_sm = (c->grid + c->sm_count - 1) / std::max(1, c->sm_count);
+  out->sweep_form = c->qx == 0 ? AJ_SWEEP_LAZY : c->qx == 1 ? AJ_SWEEP_STORED : c->qx == 2 ? AJ_SWEEP_DELTA
+                                                                                         : AJ_SWEEP_Y;
+  out->tuned = c->tuned;
+  out->fill_ratio = c->fill;
   return AJ_OK;
 }
 

@@ -41,6 +41,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace aj {
 
 constexpr int kThreads = 256;  // threads per CTA = rows per tile (one row per thread)
@@ -78,9 +80,13 @@ struct RhsState {
   int yb;             // u buffer holding y^{t+1} for the next sweep (unless cur == prev:
                       // then y^{t+1} = x^t is the buffer cur itself)
   int chk;            // the next sweep also sums Q x^t for the exact stop test
+  int near;           // the monitor is within kNearFactor of the stop: sum it every sweep
+  int pad_;
   double beta_next;   // beta_{t+2} = (alpha_{t+1} - 1) / alpha_{t+2}: the next sweep writes
                       // y^{t+2} = x^{t+1} + beta_next (x^{t+1} - x^t), the point iteration
                       // t+2 uses unless iteration t+1 restarts
+  double gmon;        // the last ||Q y - b||^2 summed (the monitor of the check schedule)
+  double gcal;        // the largest ||b - Q x||^2 / monitor seen on check sweeps (>= 1 used)
 };
 
 // ----------------------------------------------------------------------------
@@ -274,6 +280,7 @@ struct PolF64 {
   __device__ static void macv(S& acc, V v, S x) { acc = fma(v, x, acc); }
   __device__ static void mac(S& acc, const V* v, S x) { macv(acc, ldv(v), x); }
   __device__ static S finish(S a) { return a; }
+  __device__ static S neg(S a) { return -a; }
   __device__ static S add(S a, S b) { return a + b; }
   __device__ static S sub(S a, S b) { return a - b; }
   __device__ static S mul(S a, S b) { return a * b; }
@@ -315,6 +322,7 @@ struct PolDF64 {
   }
   __device__ static S finish(S a) { return fast_two_sum_ordered(a); }
   __device__ static S fast_two_sum_ordered(S a) { return two_sum(a.hi, a.lo); }
+  __device__ static S neg(S a) { return dw_neg(a); }
   __device__ static S add(S a, S b) { return dw_add(a, b); }
   __device__ static S sub(S a, S b) { return dw_sub(a, b); }
   __device__ static S mul(S a, S b) { return dw_mul(a, b); }
@@ -355,6 +363,7 @@ struct PolF32 {
   __device__ static void macv(S& acc, V v, S x) { acc = __fmaf_rn(v, x, acc); }
   __device__ static void mac(S& acc, const V* v, S x) { macv(acc, ldv(v), x); }
   __device__ static S finish(S a) { return a; }
+  __device__ static S neg(S a) { return -a; }
   __device__ static S add(S a, S b) { return __fadd_rn(a, b); }
   __device__ static S sub(S a, S b) { return __fsub_rn(a, b); }
   __device__ static S mul(S a, S b) { return __fmul_rn(a, b); }
@@ -421,6 +430,8 @@ struct IterArgs {
   int jblk;                   // rows per block of J (1: diagonal J; 2, 4, 8: eq. J-blkdiag,
                               // jinv then holds row k of each block's inverse at jinv[k * jblk])
   int nsell;                  // SELL: rows in the sliced part
+  int sell_cl;                // SELL: log2 of the slice height C (5: 32 rows; 4, 3: 16, 8 rows,
+                              // one right-hand side only, 32 / C lanes per row)
   int ntiles_sell;            // SELL: tiles of the sliced part
   int nltiles;                // SELL: tiles of long rows
   const int* perm;            // SELL: [nsell] row at each position
@@ -432,6 +443,8 @@ struct IterArgs {
   const int* ltp;             // SELL: [nltiles + 1] long tile k = long_rows[ltp[k] .. ltp[k+1])
   int nhuge;                  // SELL: rows summed by a whole CTA, one per tile
   const int* huge_rows;       // SELL: [nhuge]
+  const int* tile_desc;       // SELL: [ntiles_sell + nltiles + nhuge] the tiles in sweep order:
+                              // kind << 29 | index, kind 0 sliced, 1 long rows, 2 a huge row
   const typename P::X* b;     // [n * nrhs]
   const typename P::X* jinv;  // [n]
   typename P::X* x[3];        // three iterate buffers, [n * nrhs] each
@@ -662,14 +675,15 @@ struct YConst<P, true> {
 };
 
 // One row's sum against src over entries colp[k * stride], valp[k * stride],
-// k < cnt, in chunks of U loads issued before their multiply-adds (entry
-// order), for the second pass of an explicit-y check sweep.
+// k < cnt, added to acc in chunks of U loads issued before their
+// multiply-adds (entry order), for the second pass of an explicit-y check
+// sweep.
 template <class P, int U>
 __device__ __forceinline__ typename P::S row_pass(const int* colp, const typename P::V* valp, int cnt,
-                                                  int stride, const typename P::X* src, int nr, int r) {
+                                                  int stride, const typename P::X* src, int nr, int r,
+                                                  typename P::S acc) {
   using S = typename P::S;
   using V = typename P::V;
-  S acc = P::zero();
   for (int q0 = 0; q0 < cnt; q0 += U) {
     int cc[U];
     V vv[U];
@@ -697,9 +711,8 @@ __device__ __forceinline__ typename P::S row_pass(const int* colp, const typenam
 template <class P, int U>
 __device__ __forceinline__ typename P::S stencil_pass(int i, unsigned inm, int N, int NN, typename P::V s_diag,
                                                       typename P::V s_off, const typename P::X* src, int nr,
-                                                      int r) {
+                                                      int r, typename P::S acc) {
   using S = typename P::S;
-  S acc = P::zero();
 #pragma unroll
   for (int k0 = 0; k0 < 7; k0 += U) {
     S xv[U];
@@ -766,6 +779,27 @@ __host__ __device__ constexpr int row_unroll(bool qx) {
   return (qx ? 1 : 2) * 8 / AJ_ROW_UNROLL >= 2 ? 4 : 8;
 }
 
+// The FP64 explicit-y sweep on CSR rows (one RHS) runs 5 CTAs per SM with
+// chunks of 4 entries: at 48 registers its gathers stay in flight and the FP64
+// pipe busy (256^3 Poisson: 0.480 against 0.522 ms per sweep at 4 CTAs and
+// chunks of 8).  Its stencil-only twin keeps 4 CTAs and chunks of 8 (0.427
+// against 0.468 ms).  Every other kernel: the policy's CTAs per SM.
+#ifndef AJ_Y_CSR_MINB
+#define AJ_Y_CSR_MINB 5
+#endif
+template <class P, int SF, int FM, bool MULTI>
+__host__ __device__ constexpr bool y_csr_f64() {
+  return std::is_same<P, PolF64>::value && SF == 3 && FM == 0 && !MULTI;
+}
+template <class P, int SF, int FM, bool MULTI>
+__host__ __device__ constexpr int kernel_min_blocks() {
+  return y_csr_f64<P, SF, FM, MULTI>() ? AJ_Y_CSR_MINB : MULTI ? P::kMinBlocksMulti : P::kMinBlocks;
+}
+template <class P, int SF, int FM, bool MULTI>
+__host__ __device__ constexpr int kernel_row_unroll() {
+  return y_csr_f64<P, SF, FM, MULTI>() ? 4 : row_unroll(SF != 0);
+}
+
 // One sweep over the CTA's tiles: the fused SpMV at y, x update and reduction
 // terms.  `compute_x` is false on a residual-only sweep (no x^s is formed).
 // Reduction slots (per lane, for the lane's right-hand side): 0 d, 1
@@ -790,7 +824,7 @@ __host__ __device__ constexpr int row_unroll(bool qx) {
 // (The explicit-y code sits in `if constexpr` blocks of its own: at the
 // register caps of the FP32 and BF16 policies even values the other forms
 // never use changed their register allocation, and their speed.)
-template <class P, int SF, int FM, bool MULTI>
+template <class P, int SF, int FM, bool MULTI, bool MON = true>
 __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, bool compute_x,
                                       bool want_obj, typename P::A (&acc)[kNRed], int cta,
                                       int ncta) {
@@ -839,6 +873,8 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
     // (k < cnt) and, for long rows, its CSR range rs .. re
     int i, rs = 0, re = 0, cnt = 0, stride = 1;
     bool valid, is_long, huge = false;
+    int sub = 0;         // SELL with C < 32: this lane's share of its row's entries
+    bool split = false;  //   (warp-uniform: the whole CTA sweeps the same tile)
     const int* colp = a.col;
     const V* valp = a.val;
     if (!sell) {
@@ -852,37 +888,58 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       cnt = re - rs;
       colp += rs;
       valp += rs;
-    } else if (tile < a.ntiles_sell) {
-      const int pos = tile * rpt + slot;
-      valid = pos < a.nsell;
-      i = valid ? ld_ro(a.perm + pos) : 0;
-      if (valid) {
-        cnt = ld_ro(a.rlen + pos);
-        const int base = ld_ro(a.sptr + (pos >> 5)) + (pos & 31);
-        colp = a.scol + base;
-        valp = a.sval + base;
-        stride = 32;
-      }
-      is_long = false;
-    } else if (tile < a.ntiles_sell + a.nltiles) {
-      // long rows dealt round-robin over the warps: row j of the tile goes to
-      // warp j % 8, row slot j / 8 of that warp
-      const int lt = tile - a.ntiles_sell;
-      const int pos = ld_ro(a.ltp + lt) + (lane >> lg) * kWarps + (threadIdx.x >> 5);
-      valid = pos < ld_ro(a.ltp + lt + 1);
-      i = valid ? ld_ro(a.long_rows + pos) : 0;
-      if (valid) {
+    } else {
+      // SELL: tile k of the sweep is the one tile_desc[k] names (kind in bits
+      // 29-30, index below), heaviest first, so that dealing them round-robin
+      // to the CTAs leaves no CTA more than one tile's work behind the others
+      const int dsc = ld_ro(a.tile_desc + tile);
+      const int kind = dsc >> 29, ix = dsc & 0x1fffffff;
+      if (kind == 0) {
+        // slices of C = 2^cl rows, entry k of a slice's row p at
+        // sptr[slice] + C k + p.  With C < 32 (one right-hand side) the
+        // L = 32 / C lanes of a row take its entries k = sub, sub + L, ... and
+        // a warp reads 32 consecutive stored words per load; a tile is then
+        // 8 C rows, one slice per warp
+        const int cl = a.sell_cl;
+        int pos;
+        if (cl < 5) {
+          split = true;
+          sub = lane >> cl;
+          pos = ix * (kWarps << cl) + ((threadIdx.x >> 5) << cl) + (lane & ((1 << cl) - 1));
+        } else {
+          pos = ix * rpt + slot;
+        }
+        valid = pos < a.nsell;
+        i = valid ? ld_ro(a.perm + pos) : 0;
+        if (valid) {
+          const int len = ld_ro(a.rlen + pos);
+          const int lsh = 5 - cl;  // log2 L
+          cnt = split ? (len > sub ? (len - sub + (1 << lsh) - 1) >> lsh : 0) : len;
+          const int base = ld_ro(a.sptr + (pos >> cl)) + (pos & ((1 << cl) - 1)) + (sub << cl);
+          colp = a.scol + base;
+          valp = a.sval + base;
+          stride = 32;
+        }
+        is_long = false;
+      } else if (kind == 1) {
+        // long rows dealt round-robin over the warps: row j of the tile goes to
+        // warp j % 8, row slot j / 8 of that warp
+        const int pos = ld_ro(a.ltp + ix) + (lane >> lg) * kWarps + (threadIdx.x >> 5);
+        valid = pos < ld_ro(a.ltp + ix + 1);
+        i = valid ? ld_ro(a.long_rows + pos) : 0;
+        if (valid) {
+          rs = ld_ro(a.row_ptr + i);
+          re = ld_ro(a.row_ptr + i + 1);
+        }
+        is_long = valid;
+      } else {
+        i = ld_ro(a.huge_rows + ix);
         rs = ld_ro(a.row_ptr + i);
         re = ld_ro(a.row_ptr + i + 1);
+        huge = true;
+        is_long = false;
+        valid = slot == 0;  // the first lane group owns the row's update
       }
-      is_long = valid;
-    } else {
-      i = ld_ro(a.huge_rows + (tile - a.ntiles_sell - a.nltiles));
-      rs = ld_ro(a.row_ptr + i);
-      re = ld_ro(a.row_ptr + i + 1);
-      huge = true;
-      is_long = false;
-      valid = slot == 0;  // the first lane group owns the row's update
     }
     S sx = P::zero(), sp = P::zero();
     if (ANY && huge) {
@@ -891,6 +948,13 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
         if constexpr (YS) cta_row_sums_y<P>(a, st[k], nr, k, rs, re, hx, hp);
         else cta_row_sums<P, QX>(a, st[k], nr, k, rs, re, hx, hp);
         if (k == r) { sx = hx; sp = hp; }
+      }
+      if constexpr (YS) {
+        if (valid && active) {  // the explicit-y sums carry -b (see below)
+          const S bi = P::ldr(a.b + (size_t)i * nr + r);
+          sx = P::sub(sx, bi);
+          sp = P::sub(sp, bi);
+        }
       }
     } else if (ANY && stn && valid && active) {
       // the up to 7 neighbours in ascending column order: -N^2, -N, -1, 0, +1, +N, +N^2
@@ -906,7 +970,9 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       const bool two = !ONE && !same;
       // chunks of U neighbours, as for CSR rows: loads first, then the
       // multiply-adds in ascending order
-      constexpr int U = row_unroll(ONE);
+      constexpr int U = kernel_row_unroll<P, SF, FM, MULTI>();
+      // explicit y: the row sum starts at -b and yields g = Q y - b itself
+      if constexpr (YS) sx = P::neg(P::ldr(a.b + (size_t)i * nr + r));
 #pragma unroll
       for (int k0 = 0; k0 < 7; k0 += U) {
         S xv[U], pv[U];
@@ -935,13 +1001,16 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       if (!ONE) sp = same ? sx : P::finish(sp);
       if constexpr (YS) {
         sp = sx;
-        if (y_check<P>(me)) sp = stencil_pass<P, U>(i, inm, N, NN, s_diag, s_off, xp, nr, r);
+        if (y_check<P>(me))
+          sp = stencil_pass<P, U>(i, inm, N, NN, s_diag, s_off, xp, nr, r, P::neg(P::ldr(a.b + (size_t)i * nr + r)));
       }
     } else if (valid && !is_long && active) {
       // chunks of U entries: every load of a chunk is issued before its
       // multiply-adds, which then run in ascending entry order
-      constexpr int U = row_unroll(ONE);
+      constexpr int U = kernel_row_unroll<P, SF, FM, MULTI>();
       const bool two = !ONE && !same;
+      if constexpr (YS)  // g = Q y - b itself (-b in the row's first lane only)
+        sx = sub == 0 ? P::neg(P::ldr(a.b + (size_t)i * nr + r)) : P::zero();
       for (int q0 = 0; q0 < cnt; q0 += U) {
         int cc[U];
         V vv[U];
@@ -972,7 +1041,20 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       if (!ONE) sp = same ? sx : P::finish(sp);
       if constexpr (YS) {
         sp = sx;
-        if (y_check<P>(me)) sp = row_pass<P, U>(colp, valp, cnt, stride, xp, nr, r);
+        if (y_check<P>(me))
+          sp = row_pass<P, U>(colp, valp, cnt, stride, xp, nr, r,
+                              sub == 0 ? P::neg(P::ldr(a.b + (size_t)i * nr + r)) : P::zero());
+      }
+    }
+    if constexpr (FM == 1) {
+      if (split) {
+        // the lanes of a row add their shares (xor over the lane bits above
+        // log2 C, all within the row's lanes); its first lane updates it
+        for (int m = 1 << a.sell_cl; m < 32; m <<= 1) {
+          sx = P::combine(sx, P::shfl_xor(sx, m));
+          sp = P::combine(sp, P::shfl_xor(sp, m));
+        }
+        valid = valid && sub == 0;
       }
     }
     // long rows: the whole warp sums each one for every right-hand side; the
@@ -987,7 +1069,15 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
         S tx, tp;
         if constexpr (YS) long_row_sums_y<P>(a, st[k], nr, k, lrs, lre, tx, tp);
         else long_row_sums<P, QX>(a, st[k], nr, k, lrs, lre, tx, tp);
-        if (lane == src + k) { sx = tx; sp = tp; }
+        if (lane == src + k) {
+          sx = tx;
+          sp = tp;
+          if constexpr (YS) {  // -b, as the other explicit-y row sums carry it
+            const S bi = P::ldr(a.b + (size_t)i * nr + r);
+            sx = P::sub(sx, bi);
+            sp = P::sub(sp, bi);
+          }
+        }
       }
     }
     if (ANY && a.jblk > 1) {
@@ -999,15 +1089,11 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       const size_t e = (size_t)i * nr + r;
       S g = P::zero(), yi = P::zero(), xi = P::zero();
       if (YS && upd) {
-        const S bi = P::ldr(a.b + e);
         yi = P::ldg(xc + e);
         xi = same ? yi : P::ldx(xp + e);
-        g = P::sub(sx, bi);
-        P::acc_prod(acc[1], g, g);
-        if (y_check<P>(me)) {
-          const S g0 = P::sub(sp, bi);
-          P::acc_prod(acc[2], g0, g0);
-        }
+        g = sx;  // Q y - b: the explicit-y row sums carry -b
+        if (MON) P::acc_prod(acc[1], g, g);
+        if (y_check<P>(me)) P::acc_prod(acc[2], sp, sp);
       } else if (upd) {
         xi = P::ldg(xc + e);
         const S bi = P::ldr(a.b + e);
@@ -1051,16 +1137,13 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
     const S ji = P::ldr(a.jinv + i);
     const size_t e = (size_t)i * nr + r;
     if constexpr (YS) {
-      const S bi = P::ldr(a.b + e);
       const S yi = P::ldg(xc + e);
-      // g = Q y^s - b: its norm schedules the checks, and it is minus the
-      // exact residual of x^{s-1} where y^s = x^{s-1}
-      const S g = P::sub(sx, bi);
-      P::acc_prod(acc[1], g, g);
-      if (y_check<P>(me)) {
-        const S g0 = P::sub(sp, bi);
-        P::acc_prod(acc[2], g0, g0);
-      }
+      // g = Q y^s - b (the row sums start at -b): its norm schedules the
+      // checks, and it is minus the exact residual of x^{s-1} where
+      // y^s = x^{s-1}; sp = Q x^{s-1} - b on a check sweep
+      const S g = sx;
+      if (MON) P::acc_prod(acc[1], g, g);
+      if (y_check<P>(me)) P::acc_prod(acc[2], sp, sp);
       if (!compute_x) continue;
       const S xi = same ? yi : P::ldx(xp + e);
       const S xnew = P::fnma(ji, g, yi);
@@ -1104,13 +1187,34 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
 }
 
 // Explicit-y form: the next sweep also sums Q x^t (a check sweep) once
-// ||Q y^t - b|| <= kChkFactor * tol * ||b|| (y^t extrapolates towards x^t, so
-// this norm tracks the residual of x^t: measured ratios 0.6-2.3 at the stop
-// on grid and graph Laplacians), and in any case every kChkEvery iterations,
-// so that a solve stops at most that many iterations after its first
-// iterate within tol.
-constexpr double kChkFactor = 3.0;
-constexpr long long kChkEvery = 32;
+// ||Q y^t - b|| <= kChkFactor * tol * ||b|| / sqrt(gcal) (y^t extrapolates
+// towards x^t, so this norm tracks the residual of x^t: measured ratios
+// 0.6-2.3 at the stop on grid and graph Laplacians; gcal, the largest
+// squared ratio of residual to monitor the check sweeps have seen, widens
+// the trigger where it runs high), and in any case every kChkEvery
+// iterations, so that a solve stops at most that many iterations after its
+// first iterate within tol.
+#ifndef AJ_CHK_FACTOR
+#define AJ_CHK_FACTOR 1.5
+#endif
+#ifndef AJ_CHK_EVERY
+#define AJ_CHK_EVERY 32
+#endif
+#ifndef AJ_MON_EVERY
+#define AJ_MON_EVERY 4
+#endif
+constexpr double kChkFactor = AJ_CHK_FACTOR;
+constexpr long long kChkEvery = AJ_CHK_EVERY;
+// ||Q y - b||^2 is summed on every kMonEvery-th sweep only (one FP64
+// instruction per row the other sweeps save), on every sweep once it is
+// within kNearFactor of the stop (so that the checks start on a fresh
+// value), and on the sweeps where y^s = x^{s-1}, whose exact residual it
+// then is.
+constexpr long long kMonEvery = AJ_MON_EVERY;
+constexpr double kNearFactor = 10.0;
+__device__ __forceinline__ bool monitor_sweep(const RhsState& q) {
+  return q.cur == q.prev || q.near || q.t % kMonEvery == 0;
+}
 
 // alpha_{t+1} = (1 + sqrt(1 + 4 alpha_t^2)) / 2 (Algorithm alg-apg-re).
 __device__ __forceinline__ double next_alpha(double a) { return 0.5 * (1.0 + sqrt(1.0 + 4.0 * a * a)); }
@@ -1128,8 +1232,14 @@ __device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kN
   for (int r = 0; r < nr; r++) {
     RhsState& q = st[r];
     if (q.done) continue;
+    // explicit y: whether this right-hand side's own schedule summed the
+    // monitor in the sweep (the sweep sums it for all when one needs it, but
+    // each uses it on its own schedule, as it would alone)
+    const bool mon = !ysf || monitor_sweep(q);
     const double d = tot[r][0];
-    const double gg = tot[r][1];
+    const double gg = tot[r][1];  // explicit y: valid where mon
+    const double gmon_before = q.gmon;
+    if (ysf && mon) q.gmon = gg;
     // the exact squared residual of x^{s-1}: summed by every sweep of the
     // lazy and stored forms; in the explicit-y form by check sweeps, and equal
     // to ||Q y^s - b||^2 where y^s = x^{s-1} (first sweep, after a restart)
@@ -1144,13 +1254,15 @@ __device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kN
       q.fval = fscale * (0.5 * tot[r][3] - tot[r][4]);
     }
     if (s == 1) q.rr0 = rr;
+    if (ysf && q.chk && !same && gmon_before > 0.0) q.gcal = fmax(q.gcal, rr / gmon_before);
     bool stop_now = false;
     if (have_rr) {
       if (stop == kStopRelres) stop_now = q.relres <= tol;
       else if (stop == kStopObjgap) stop_now = fabs(q.fval - fstar) / (1.0 + fabs(fstar)) <= tol;
     }
-    // divergence guard: the residual (at y^s in the explicit-y form) against that of x^0
-    const double grow = ysf ? gg : rr;
+    // divergence guard: the residual (at y^s in the explicit-y form, on its
+    // monitor sweeps) against that of x^0
+    const double grow = ysf ? (mon ? gg : 0.0) : rr;
     if (!isfinite(grow) || !isfinite(rr) || !isfinite(d)) {
       q.done = 1; q.status = kENonfinite; q.t_final = q.t;
       continue;
@@ -1199,8 +1311,10 @@ __device__ __forceinline__ bool scalar_step(RhsState* st, const double (*tot)[kN
     if (ysf) {
       q.beta_next = momentum ? (q.alpha - 1.0) / next_alpha(q.alpha) : 0.0;
       const double bn2 = q.bnorm2 > 0.0 ? q.bnorm2 : 1.0;
+      const double est = q.gmon * fmax(1.0, q.gcal);  // the residual it stands for, squared
       q.chk = stop == kStopRelres &&
-              (gg <= kChkFactor * kChkFactor * tol * tol * bn2 || t % kChkEvery == 0 || t >= maxit);
+              (est <= kChkFactor * kChkFactor * tol * tol * bn2 || t % kChkEvery == 0 || t >= maxit);
+      q.near = stop == kStopRelres && est <= kNearFactor * kNearFactor * tol * tol * bn2;
     }
     all_done = false;
   }
@@ -1278,16 +1392,23 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, i
     // sweep number in the run's own numbering: x^{s-1} is checked, x^s formed
     long long s_run = 0;
     bool compute_x = false;
+    bool mon = SF != 3;  // explicit y: is ||Q y - b||^2 summed this sweep?
     for (int r = 0; r < nr; r++) {
       if (!sm.st[r].done) {
         s_run = sm.st[r].t + 1;
         compute_x = compute_x || (sm.st[r].t < a.maxit);
+        mon = mon || monitor_sweep(sm.st[r]);
       }
     }
     A acc[kNRed];
 #pragma unroll
     for (int k = 0; k < kNRed; k++) acc_zero(acc[k]);
-    sweep<P, SF, FM, MULTI>(a, sm.st, compute_x, want_obj, acc, cta, ncta);
+    if constexpr (SF == 3) {
+      if (mon) sweep<P, SF, FM, MULTI, true>(a, sm.st, compute_x, want_obj, acc, cta, ncta);
+      else sweep<P, SF, FM, MULTI, false>(a, sm.st, compute_x, want_obj, acc, cta, ncta);
+    } else {
+      sweep<P, SF, FM, MULTI>(a, sm.st, compute_x, want_obj, acc, cta, ncta);
+    }
     // CTA partials -> global (parity-buffered by sweep)
     double* part = a.partials + (size_t)(sw & 1) * ncta * nr * kNRed;
 #pragma unroll
@@ -1331,7 +1452,7 @@ __device__ __forceinline__ bool run_solve(const IterArgs<P>& a, SolveSmem& sm, i
 // selects the formats the instantiation reads (see sweep), MULTI the one for
 // several right-hand sides.
 template <class P, int SF, int FM, bool MULTI>
-__global__ void __launch_bounds__(kThreads, MULTI ? P::kMinBlocksMulti : P::kMinBlocks) aj_persistent_kernel(IterArgs<P> a) {
+__global__ void __launch_bounds__(kThreads, (kernel_min_blocks<P, SF, FM, MULTI>())) aj_persistent_kernel(IterArgs<P> a) {
   __shared__ SolveSmem sm;
   const int nr = MULTI ? a.nrhs : 1;
   if ((int)threadIdx.x < nr) sm.st[threadIdx.x] = a.state[threadIdx.x];
@@ -1466,12 +1587,21 @@ __global__ void __launch_bounds__(kThreads, P::kMinBlocksMulti) aj_lockstep_kern
       const bool want_obj = a.stop == kStopObjgap;
       const int V = __ldg(b.sys_nu + s);
       bool compute_x = false;
+      bool mon = SF != 3;  // the monitor schedule of a solo run, from the same state
       for (int r = 0; r < nr; r++)
-        if (!sm.st[r].done) compute_x = compute_x || (sm.st[r].t < a.maxit);
+        if (!sm.st[r].done) {
+          compute_x = compute_x || (sm.st[r].t < a.maxit);
+          mon = mon || monitor_sweep(sm.st[r]);
+        }
       A acc[kNRed];
 #pragma unroll
       for (int q = 0; q < kNRed; q++) acc_zero(acc[q]);
-      sweep<P, SF, 1, true>(a, sm.st, compute_x, want_obj, acc, v, V);
+      if constexpr (SF == 3) {
+        if (mon) sweep<P, SF, 1, true, true>(a, sm.st, compute_x, want_obj, acc, v, V);
+        else sweep<P, SF, 1, true, false>(a, sm.st, compute_x, want_obj, acc, v, V);
+      } else {
+        sweep<P, SF, 1, true>(a, sm.st, compute_x, want_obj, acc, v, V);
+      }
       double* part = a.partials + (size_t)(k & 1) * V * nr * kNRed;
 #pragma unroll
       for (int q = 0; q < kNRed; q++) {

@@ -32,6 +32,7 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
   a.sshift = L.sshift;
   a.jblk = L.jblk < 1 ? 1 : L.jblk;
   a.nsell = L.nsell;
+  a.sell_cl = L.sell_cl ? L.sell_cl : 5;
   a.ntiles_sell = L.ntiles_sell;
   a.nltiles = L.nltiles;
   a.perm = L.perm;
@@ -43,6 +44,7 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
   a.ltp = L.ltp;
   a.nhuge = L.nhuge;
   a.huge_rows = L.huge_rows;
+  a.tile_desc = L.tile_desc;
   a.b = static_cast<const typename P::X*>(L.b);
   a.jinv = static_cast<const typename P::X*>(L.jinv);
   for (int k = 0; k < 3; k++) a.x[k] = static_cast<typename P::X*>(L.x[k]);
@@ -138,13 +140,18 @@ static cudaError_t launch_m(const IterLaunch& L, int grid, cudaStream_t s) {
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
 }
 
-// Co-resident CTAs of the persistent kernel: the smallest over its format
-// instantiations, so that a grid sized by it fits any of them.
+// Co-resident CTAs of the persistent kernel for formats fm (0 CSR only, 1
+// any, 2 stencil only), or with fm < 0 the smallest over the three, so that
+// a grid sized by it fits any of them.
 template <class P, bool MULTI>
-static int occ_m(int qx) {
-  int occ = 1 << 30;
-  for (int fm = 0; fm < 3; fm++) {
+static int occ_m(int qx, int fm) {
+  if (fm >= 0) {
     const void* k = persistent_fn<P, MULTI>(qx, fm);
+    return k ? occ_of(k) : 0;
+  }
+  int occ = 1 << 30;
+  for (int f = 0; f < 3; f++) {
+    const void* k = persistent_fn<P, MULTI>(qx, f);
     if (!k) return 0;
     occ = std::min(occ, occ_of(k));
   }
@@ -157,9 +164,9 @@ cudaError_t AJ_CAT(launch_persistent_, AJ_SUFFIX)(int nrhs, const IterLaunch& L,
   return nrhs == 1 ? launch_m<AJ_POL, false>(L, grid, s) : launch_m<AJ_POL, true>(L, grid, s);
 }
 
-int AJ_CAT(blocks_per_sm_, AJ_SUFFIX)(int nrhs, int qx) {
+int AJ_CAT(blocks_per_sm_, AJ_SUFFIX)(int nrhs, int qx, int fm) {
   if (nrhs < 1 || nrhs > kMaxRhs) return 0;
-  return nrhs == 1 ? occ_m<AJ_POL, false>(qx) : occ_m<AJ_POL, true>(qx);
+  return nrhs == 1 ? occ_m<AJ_POL, false>(qx, fm) : occ_m<AJ_POL, true>(qx, fm);
 }
 
 void AJ_CAT(pack_iter_args_, AJ_SUFFIX)(const IterLaunch& L, void* dst) {

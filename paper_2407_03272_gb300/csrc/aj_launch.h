@@ -21,6 +21,7 @@ struct IterLaunch {
   int sshift;
   int jblk;                         // rows per block of J (1: diagonal)
   int nsell;
+  int sell_cl;  // log2 of the SELL slice height
   int ntiles_sell;
   int nltiles;
   const int* perm;
@@ -32,6 +33,7 @@ struct IterLaunch {
   const int* ltp;
   int nhuge;
   const int* huge_rows;
+  const int* tile_desc;  // SELL: tiles in sweep order (see IterArgs)
   const void* b;
   const void* jinv;
   void* x[3];
@@ -87,17 +89,18 @@ int lockstep_blocks_per_sm(int pol, int qx);
 // Cooperative launch of the persistent kernel for precision `pol`
 // (0 F64, 1 DF64, 2 F32, 3 BF16), nrhs in [1, 4] and the sweep form L.qx.
 cudaError_t launch_persistent(int pol, int nrhs, const IterLaunch& L, int grid, cudaStream_t s);
-// Co-resident CTAs per SM of that kernel (0 on error).
-int persistent_blocks_per_sm(int pol, int nrhs, int qx);
+// Co-resident CTAs per SM of that kernel for formats fm (0 CSR only, 1 any,
+// 2 stencil only; fm < 0: the smallest over the three), 0 on error.
+int persistent_blocks_per_sm(int pol, int nrhs, int qx, int fm = -1);
 
 cudaError_t launch_persistent_f64(int nrhs, const IterLaunch& L, int grid, cudaStream_t s);
 cudaError_t launch_persistent_df64(int nrhs, const IterLaunch& L, int grid, cudaStream_t s);
 cudaError_t launch_persistent_f32(int nrhs, const IterLaunch& L, int grid, cudaStream_t s);
 cudaError_t launch_persistent_b16(int nrhs, const IterLaunch& L, int grid, cudaStream_t s);
-int blocks_per_sm_f64(int nrhs, int qx);
-int blocks_per_sm_df64(int nrhs, int qx);
-int blocks_per_sm_f32(int nrhs, int qx);
-int blocks_per_sm_b16(int nrhs, int qx);
+int blocks_per_sm_f64(int nrhs, int qx, int fm = -1);
+int blocks_per_sm_df64(int nrhs, int qx, int fm = -1);
+int blocks_per_sm_f32(int nrhs, int qx, int fm = -1);
+int blocks_per_sm_b16(int nrhs, int qx, int fm = -1);
 
 #define AJ_DECLARE_BATCHED(suf)                                                              \
   void pack_iter_args_##suf(const IterLaunch& L, void* dst);                                 \

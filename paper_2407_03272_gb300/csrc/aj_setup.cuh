@@ -291,15 +291,16 @@ __global__ void k_scale(int n, double* x, double s) {
 // entries of row perm[p] in CSR order; entry k goes to sptr[p / 32] + 32 k +
 // p % 32.  T is the stored value type of the iteration precision.
 template <class T>
-__global__ void k_sell_fill(int nsell, const int* perm, const int* rlen, const int* sptr,
+__global__ void k_sell_fill(int nsell, int cl, const int* perm, const int* rlen, const int* sptr,
                             const int* rp, const int* ci, const T* val, int* scol, T* sval) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nsell) return;
   const int i = perm[p], len = rlen[p], r0 = rp[i];
-  const long long base = (long long)sptr[p >> 5] + (p & 31);
+  const long long C = 1ll << cl;  // slice height
+  const long long base = (long long)sptr[p >> cl] + (p & (C - 1));
   for (int k = 0; k < len; k++) {
-    scol[base + 32ll * k] = ci[r0 + k];
-    sval[base + 32ll * k] = val[r0 + k];
+    scol[base + C * k] = ci[r0 + k];
+    sval[base + C * k] = val[r0 + k];
   }
 }
 

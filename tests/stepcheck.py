@@ -8,7 +8,7 @@ import numpy as np
 import oracle
 
 HEADER = 64
-STATE_BYTES = 128
+STATE_BYTES = 152
 
 
 def state_parts(blob, n):

@@ -64,7 +64,8 @@ def test_struct_layouts_match_header():
     # sizes a C compiler gives the three public structs on LP64
     assert ctypes.sizeof(aj.aj_csr) == 48
     assert ctypes.sizeof(aj.aj_info) == 88
-    assert ctypes.sizeof(aj.aj_params) == 136
+    assert ctypes.sizeof(aj.aj_params) == 144
+    assert ctypes.sizeof(aj.aj_tuning) == 56
 
 
 def test_failure_hooks_validate_their_arguments_without_gpu_work():

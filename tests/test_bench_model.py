@@ -51,5 +51,6 @@ def test_fp64_instruction_model():
     assert b.fp64_ops(n, nnz, "delta") == nnz + 8 * n
     assert b.fp64_ops(n, nnz, "stored") == nnz + 9 * n
     assert b.fp64_ops(n, nnz, "lazy") == 2 * nnz + 11 * n
-    # the derived FP64 issue peak: 152 SMs x 2 instructions per clock x 2.07 GHz
-    assert abs(b.FP64_PEAK_TOPS - 152 * 2 * 2.07e9 / 1e12) < 1e-12
+    assert b.fp64_ops(n, nnz, "y") == nnz + 4.25 * n
+    # the measured FP64 issue peak: 2 instructions per clock on 152 SMs at 2.06 GHz
+    assert abs(b.FP64_PEAK_TOPS - 152 * 2 * 2.06e9 / 1e12) < 1e-3

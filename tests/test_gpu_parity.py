@@ -225,20 +225,25 @@ def test_zero_rhs_and_tiny_systems():
 
 
 # ---------------------------------------------------------------- several right-hand sides
+@pytest.mark.parametrize("form", ["auto", "y"])
 @pytest.mark.parametrize("nrhs", [2, 3, 4])
 @pytest.mark.parametrize("precision", ["fp64", "df64", "fp32_ir"])
-def test_multi_rhs_equals_single(nrhs, precision):
+def test_multi_rhs_equals_single(nrhs, precision, form):
     Q = synth.poisson2d(30)
     n = Q["n"]
     B = np.stack([synth.rhs(Q, synth.uniform(n, 20 + r)) for r in range(nrhs)], axis=1)
     bc = np.ascontiguousarray(B.T).reshape(-1)  # column-major n x nrhs
     ctx = aj.from_csr(Q, bc, nrhs=nrhs)
-    # the same grid for both runs, so the FP64 reductions are summed in the same order
-    ctx.set(precision=precision, tol=1e-9, maxit=10000, grid_ctas=8)
+    # the same sweep form for both runs (AUTO gives FP64 with one right-hand
+    # side the explicit-y form, with several the difference form), and the
+    # same grid, so the FP64 reductions are summed in the same order
+    sf = aj.AJ_SWEEP_Y if form == "y" else (aj.AJ_SWEEP_DELTA if precision == "fp64" else aj.AJ_SWEEP_AUTO)
+    ctx.set(precision=precision, tol=1e-9, maxit=10000, grid_ctas=8, sweep_form=sf)
     X, infos = ctx.solve(per_rhs=True)
     X = X.reshape(nrhs, n)
     for r in range(nrhs):
-        c1, x1, i1 = _gpu(Q, B[:, r], precision=precision, tol=1e-9, maxit=10000, grid_ctas=8)
+        c1, x1, i1 = _gpu(Q, B[:, r], precision=precision, tol=1e-9, maxit=10000, grid_ctas=8,
+                          sweep_form=sf)
         assert infos[r]["iters"] == i1["iters"]
         np.testing.assert_array_equal(X[r], x1)
         assert _relres(Q, B[:, r], X[r]) <= 1e-9
