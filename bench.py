@@ -293,6 +293,7 @@ def bench_graph(aj, torch, dev, stream, hbm_peak, n):
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t1
         fmt = ctx.format()
+        tuning = ctx.tuning()
         ctx.solve(out=out)
         e0, e1 = _events(torch, stream)
         e0.record(stream)
@@ -305,8 +306,9 @@ def bench_graph(aj, torch, dev, stream, hbm_peak, n):
         res[prec] = {"time_to_tol_ms": ms, "iterations": info["iters"], "outer": info["outer"],
                      "relres": info["relres"], "status": info["status"],
                      "error_vs_xstar_Qnorm": q_error(Aq, out.cpu().numpy(), xs, b),
-                     "format": {"kind": "SELL-32-sigma" if fmt[0] == aj.AJ_FMT_SELL else "CSR",
+                     "format": {"kind": "SELL-C-sigma" if fmt[0] == aj.AJ_FMT_SELL else "CSR",
                                 "sigma": fmt[1], "long_row_threshold": fmt[2], "fill_ratio": fmt[3]},
+                     "tuning": tuning,
                      "setup_incl_autotune_s": setup_s,
                      "fused_GBps": gbs, "fused_hbm_frac": gbs / hbm_peak,
                      "kernel_ms_per_iteration": info["kernel_ms"] / max(info["iters"], 1)}
@@ -333,7 +335,7 @@ def max_mix_error(systems, mats, xs_of, cache):
     return worst
 
 
-def bench_batched(aj, torch, dev, stream, count, pool):
+def bench_batched(aj, torch, dev, stream, count, pool, lockstep_fp64=False):
     """Independent systems in one persistent launch per right-hand-side count
     (aj_solve_batch), against the same systems solved one after another."""
     import synth
@@ -370,8 +372,23 @@ def bench_batched(aj, torch, dev, stream, count, pool):
            "systems": count, "rows_total": int(sum(mats[j]["n"] * 1 for j, _, _ in systems)),
            "rhs_total": int(sum(nr for _, nr, _ in systems)), "generate_s": gen_s}
     qcache = {}
+    c0 = aj.cache_stats()
     for prec in ("fp32_ir", "fp64"):
         cs = build(prec)
+        if prec == "fp64" and not lockstep_fp64:
+            # the plain FP64 path the mixed-precision batch is compared with:
+            # the same systems solved one after another
+            def serial():
+                return [c.solve(out=o)[1] for c, o in zip(cs, outs)]
+            ms_s, wall_s, inf_s = timed(serial)
+            res["serial_fp64"] = {"makespan_ms": ms_s, "wall_ms": wall_s, "systems_per_s": count / (ms_s * 1e-3),
+                                  "ok": sum(1 for i in inf_s if i["status"] == aj.AJ_OK),
+                                  "max_relres": max(i["relres"] for i in inf_s),
+                                  "max_error_vs_xstar_Qnorm": max_mix_error(
+                                      systems, mats, lambda k: outs[k].cpu().numpy(), qcache)}
+            for c in cs:
+                c.close()
+            break
         aj.solve_batch(cs[:4], outs[:4], on_device=True)  # warm-up
         ms, wall, infos = timed(lambda: aj.solve_batch(cs, outs, on_device=True))
         ok = sum(1 for i in infos if i["status"] == aj.AJ_OK)
@@ -398,6 +415,8 @@ def bench_batched(aj, torch, dev, stream, count, pool):
             c.close()
     res["batched_fp32_ir_speedup_vs_serial_fp64"] = (res["serial_fp64"]["makespan_ms"]
                                                      / res["batched_fp32_ir"]["makespan_ms"])
+    c1 = aj.cache_stats()
+    res["cache_lookups"] = {k: c1[k] - c0[k] for k in c1}
     return res
 
 
@@ -470,6 +489,7 @@ def bench_served(aj, torch, count, pool, rate, budget_gb):
                 "max_relres": float(max(rel)), "max_error_vs_xstar_Qnorm": err, "wall_s": wall}
 
     reqs = list(enumerate(systems))
+    c0 = aj.cache_stats()
     # warm-up: a few requests
     for t in [srv.submit_csr(mats[j], bs[k], nrhs=nr, precision="fp32_ir", tol=1e-8) for k, (j, nr, _) in reqs[:4]]:
         srv.result(t)
@@ -478,13 +498,15 @@ def bench_served(aj, torch, count, pool, rate, budget_gb):
     sub = run(reqs[count:], sub_rate, 52)
     st = srv.stats()
     srv.close()
+    c1 = aj.cache_stats()
     return {"workload": "Poisson arrivals; requests: 80%% the batched mix, 20%% 3-D Poisson (side 64..192), "
                         "1-4 RHS, FP32 values + FP64 refinement to 1e-8, %.0f GB budget, matrices from a "
                         "pool of %d" % (budget_gb, pool),
             "generate_s": gen_s, "at_offered_rate": sat, "at_0.8x_capacity": sub,
             "overloaded_at_offered_rate": sat["solves_per_s"] < 0.95 * rate,
             "server": {"rounds": st["rounds"], "peak_active": st["peak_active"],
-                       "peak_GB": st["peak_bytes"] / 1e9, "kernel_ms": st["kernel_ms"]}}
+                       "peak_GB": st["peak_bytes"] / 1e9, "kernel_ms": st["kernel_ms"]},
+            "cache_lookups": {k: c1[k] - c0[k] for k in c1}}
 
 
 def main():
@@ -509,8 +531,10 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-sdd", action="store_true")
     ap.add_argument("--graph-n", type=int, default=8388608)
-    ap.add_argument("--batch-count", type=int, default=512)
-    ap.add_argument("--served-count", type=int, default=300)
+    ap.add_argument("--batch-count", type=int, default=2048)
+    ap.add_argument("--batched-fp64", action="store_true",
+                    help="also time the batch in one lockstep launch in FP64 (beside one after another)")
+    ap.add_argument("--served-count", type=int, default=500)
     ap.add_argument("--served-rate", type=float, default=2000.0)
     ap.add_argument("--fixed-iters", type=int, default=0,
                     help="run exactly this many iterations per step instead of solving to 1e-8")
@@ -746,7 +770,7 @@ def main():
         if not args.no_graph:
             line["graph"] = bench_graph(aj, torch, dev, stream, hbm_peak, args.graph_n)
         if not args.no_batched:
-            line["batched"] = bench_batched(aj, torch, dev, stream, args.batch_count, 48)
+            line["batched"] = bench_batched(aj, torch, dev, stream, args.batch_count, 48, args.batched_fp64)
         if not args.no_served:
             line["served"] = bench_served(aj, torch, args.served_count, 48, args.served_rate, 120.0)
         if not args.no_sdd:

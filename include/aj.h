@@ -437,6 +437,13 @@ aj_status aj_solve_noalloc(const aj_csr* Q, const double* b, const aj_params* p,
 /* Diagnostics: number of CUDA kernels libaj has launched in this process. */
 uint64_t aj_kernel_launches(void);
 
+/* Diagnostics: lookups in this process of aj_set's two caches, keyed by the
+ * matrix, whose hits skip host work: the locality ordering (RCM test, keyed
+ * by the sparsity pattern's hash) and the autotuner's choice (keyed by n,
+ * nnz, the row-length moments, precision, RHS count, sweep form and order).
+ * Any pointer may be NULL. */
+void aj_cache_stats(uint64_t* order_hits, uint64_t* order_misses, uint64_t* tune_hits, uint64_t* tune_misses);
+
 /* ---- Failure-detection test hooks.  The paper has no counterpart: they let
  * a test drive the library's error paths without faulting a GPU.
  *

@@ -115,6 +115,7 @@ SIGNATURES = [
     ("aj_destroy", None, [ctypes.c_void_p]),
     ("aj_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("aj_kernel_launches", ctypes.c_uint64, []),
+    ("aj_cache_stats", None, [ctypes.POINTER(ctypes.c_uint64)] * 4),
     ("aj_solve_noalloc", ctypes.c_int, [ctypes.POINTER(aj_csr), ctypes.c_void_p, ctypes.POINTER(aj_params),
                                         ctypes.c_void_p, ctypes.POINTER(aj_info), ctypes.c_void_p]),
     ("aj_test_barrier_stall", ctypes.c_int, [ctypes.c_int, ctypes.c_double]),
@@ -367,6 +368,13 @@ def solve_noalloc(row_ptr, col, val, b, x_out, stream=None, **kw):
     st = lib().aj_solve_noalloc(ctypes.byref(csr), ptrs[3][0], ctypes.byref(p), ptrs[4][0],
                                 ctypes.byref(inf), ctypes.c_void_p(s))
     return st, inf.as_dict()
+
+
+def cache_stats():
+    """Hits and misses of aj_set's ordering and autotuner caches (aj_cache_stats)."""
+    v = [ctypes.c_uint64() for _ in range(4)]
+    lib().aj_cache_stats(*[ctypes.byref(x) for x in v])
+    return dict(zip(("order_hits", "order_misses", "tune_hits", "tune_misses"), (x.value for x in v)))
 
 
 def inject_barrier_stall(cta, timeout_ms):

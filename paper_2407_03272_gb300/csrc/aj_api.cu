@@ -53,6 +53,10 @@ std::atomic<int> g_stall_cta{-1};
 std::atomic<long long> g_stall_timeout_ns{0};
 std::atomic<long long> g_alloc_fail_after{-1};
 
+// Hits and misses of the process-wide caches (aj_cache_stats): the ordering
+// cache of aj_set's locality test and the autotuner's choices.
+std::atomic<unsigned long long> g_order_hits{0}, g_order_misses{0}, g_tune_hits{0}, g_tune_misses{0};
+
 bool alloc_hook_fails() {
   long long v = g_alloc_fail_after.load();
   while (v >= 0) {
@@ -244,7 +248,7 @@ struct aj_ctx {
   double fill = 1.0;
   int nsell = 0, ntiles_sell = 0, nltiles = 0, nhuge = 0;
   int *d_perm = nullptr, *d_rlen = nullptr, *d_sptr = nullptr, *d_scol = nullptr;
-  int *d_long = nullptr, *d_ltp = nullptr, *d_huge = nullptr, *d_tdesc = nullptr;
+  int *d_long = nullptr, *d_ltp = nullptr, *d_huge = nullptr;
   void* d_sval = nullptr;
   int qx = 0;                       // sweep form in use: 0 lazy, 1 stored, 2 difference, 3 explicit y
   double sQ = 1.0;
@@ -776,6 +780,7 @@ static aj_status choose_order(aj_ctx* c, int mode) {
       hit = true;
     }
   }
+  (hit ? g_order_hits : g_order_misses).fetch_add(1);
   if (!hit) {
     const std::vector<int> none;
     ent.span0 = ent.span1 = row_spans(n, rp, ci, none);
@@ -817,7 +822,7 @@ static aj_status choose_format(aj_ctx* c, const aj_params* p);
 // huge-row tiles), or the caller's grid_ctas.
 static void size_grid(aj_ctx* c) {
   // the instantiation the launch takes: the stencil rows alone, CSR alone, or any
-  const int fm = c->fmt == 2 ? 2 : (c->fmt == 1 || c->jblk > 1) ? 1 : 0;
+  const int fm = c->fmt == 2 ? 2 : c->jblk > 1 ? 1 : c->fmt == 1 ? (c->sell_cl < 5 ? 4 : AJ_SELL_FM) : 0;
   int bps = std::max(1, persistent_blocks_per_sm(kernel_pol(c->pol), c->nrhs, c->qx, fm));
   if (c->ctas_cap > 0) bps = std::min(bps, c->ctas_cap);
   const long long rpt = kThreads >> lanes_log2(c->nrhs);
@@ -946,7 +951,7 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
     const int kp = kernel_pol(pol);
     int bps = 1;  // the largest grid any sweep form and format may take
     for (int q = 0; q < 4; q++)
-      for (int f = 0; f < 3; f++) bps = std::max(bps, persistent_blocks_per_sm(kp, nrhs, q, f));
+      for (int f = 0; f < 5; f++) bps = std::max(bps, persistent_blocks_per_sm(kp, nrhs, q, f));
     const int maxg = bps * c->sm_count;
     c->partials = (double*)c->pws.alloc((size_t)2 * maxg * nrhs * kNRed * 8);
     c->part_cap = maxg;
@@ -1042,7 +1047,10 @@ extern "C" aj_status aj_set(aj_ctx* c, const aj_params* p) {
   // (irregular rows: one random gather per entry instead of two), lazy for
   // the other precisions on CSR, where the second row sum gathers from the
   // same cached lines and saves two n-vectors of traffic
-  if (p->sweep_form == AJ_SWEEP_AUTO && p->precision != AJ_FP64 && c->fmt != 1) c->qx = 0;
+  // (FP32 values in the stencil format: the explicit-y form, 0.187 against
+  // 0.213 ms per 256^3 sweep lazy; it gathers one vector instead of two)
+  if (p->sweep_form == AJ_SWEEP_AUTO && p->precision != AJ_FP64 && c->fmt != 1)
+    c->qx = (c->fmt == 2 && p->precision == AJ_FP32_IR && c->nrhs == 1 && p->stop != AJ_STOP_OBJGAP) ? 3 : 0;
   size_grid(c);
   c->have_prm = true;
   return AJ_OK;
@@ -1156,7 +1164,6 @@ static IterLaunch make_launch(aj_ctx* c, const void* bvec, long long maxit, int 
     L.ltp = c->d_ltp;
     L.nhuge = c->nhuge;
     L.huge_rows = c->d_huge;
-    L.tile_desc = c->d_tdesc;
   }
   L.b = bvec;
   L.jinv = c->pol == AJ_FP64 ? (const void*)c->jinv64 : c->jinvp;
@@ -1303,29 +1310,10 @@ static aj_status build_sell(aj_ctx* c, int sigma, int lmax, int cl = 5) {
     long_entries += l;
   }
   if (!lng.empty()) ltp.push_back((int)lng.size());
-  // the sweep's tile order: every tile (sliced, long-row, huge-row) by its
-  // estimated work, heaviest first -- stored entries (with the slices'
-  // padding) plus a per-row cost for the update -- so that the round-robin
-  // deal over the CTAs leaves none more than one tile's work behind
+  // the huge rows sorted longest first (one tile each); the long rows are
+  // sorted longest first already
+  std::stable_sort(hug.begin(), hug.end(), [&](int x, int y) { return len(x) > len(y); });
   const int ntsell = (nsell + rpt_sell - 1) / rpt_sell;
-  std::vector<std::pair<long long, int>> order;
-  order.reserve((size_t)ntsell + ltp.size() + hug.size());
-  const long long kRowCost = 8;
-  for (int k = 0; k < ntsell; k++) {
-    const int p0 = k * rpt_sell, p1 = std::min(nsell, p0 + rpt_sell);
-    const long long ent = (long long)sptr[(p1 + C - 1) / C] - sptr[p0 / C];
-    order.push_back({ent + kRowCost * (p1 - p0), k});
-  }
-  for (int lt = 0; lt + 1 < (int)ltp.size(); lt++) {
-    long long ent = 0;
-    for (int j = ltp[lt]; j < ltp[lt + 1]; j++) ent += len(lng[j]);
-    order.push_back({ent + kRowCost * (ltp[lt + 1] - ltp[lt]), (1 << 29) | lt});
-  }
-  for (int h = 0; h < (int)hug.size(); h++) order.push_back({(long long)len(hug[h]) + kRowCost * kThreads, (2 << 29) | h});
-  std::stable_sort(order.begin(), order.end(),
-                   [](const std::pair<long long, int>& x, const std::pair<long long, int>& y) { return x.first > y.first; });
-  std::vector<int> tdesc(order.size());
-  for (size_t k = 0; k < order.size(); k++) tdesc[k] = order[k].second;
   const size_t vb = velem_bytes(c->pol);
   c->d_perm = (int*)c->sws.alloc(((size_t)nsell + 1) * 4);
   c->d_rlen = (int*)c->sws.alloc(((size_t)nsell + 1) * 4);
@@ -1335,9 +1323,8 @@ static aj_status build_sell(aj_ctx* c, int sigma, int lmax, int cl = 5) {
   c->d_long = (int*)c->sws.alloc((lng.size() + 1) * 4);
   c->d_ltp = (int*)c->sws.alloc(ltp.size() * 4);
   c->d_huge = (int*)c->sws.alloc((hug.size() + 1) * 4);
-  c->d_tdesc = (int*)c->sws.alloc((tdesc.size() + 1) * 4);
   if (!c->d_perm || !c->d_rlen || !c->d_sptr || !c->d_scol || !c->d_sval || !c->d_long || !c->d_ltp ||
-      !c->d_huge || !c->d_tdesc) {
+      !c->d_huge) {
     c->sws.release();
     return AJ_ENOMEM;
   }
@@ -1349,8 +1336,6 @@ static aj_status build_sell(aj_ctx* c, int sigma, int lmax, int cl = 5) {
   if (!lng.empty()) CK(cudaMemcpyAsync(c->d_long, lng.data(), lng.size() * 4, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->d_ltp, ltp.data(), ltp.size() * 4, cudaMemcpyHostToDevice, s));
   if (!hug.empty()) CK(cudaMemcpyAsync(c->d_huge, hug.data(), hug.size() * 4, cudaMemcpyHostToDevice, s));
-  if (!tdesc.empty())
-    CK(cudaMemcpyAsync(c->d_tdesc, tdesc.data(), tdesc.size() * 4, cudaMemcpyHostToDevice, s));
   for (int h : hug) long_entries += len(h);
   CK(cudaMemsetAsync(c->d_scol, 0, ((size_t)tot + 32) * 4, s));
   CK(cudaMemsetAsync(c->d_sval, 0, ((size_t)tot + 32) * vb, s));
@@ -1543,9 +1528,11 @@ static aj_status choose_format(aj_ctx* c, const aj_params* p) {
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
       const TuneVal v = it->second;
+      g_tune_hits.fetch_add(1);
       return apply(v);
     }
   }
+  g_tune_misses.fetch_add(1);
   const TuneVal cand[] = {{0, 0, 0, 5, 0}, {1, 256, 64, 5, 0}, {1, 4096, 64, 5, 0}, {1, 256, 256, 5, 0}};
   TuneVal best = cand[0];
   double best_ms = 1e300;
@@ -1571,10 +1558,13 @@ static aj_status choose_format(aj_ctx* c, const aj_params* p) {
       if (e != AJ_OK) return e;
     }
   }
-  {
+#ifndef AJ_TUNE_CTAS
+#define AJ_TUNE_CTAS 1
+#endif
+  if (AJ_TUNE_CTAS) {
     // CTAs per SM below the kernel's occupancy (fewer CTAs, less imbalance at
     // each grid barrier, more L1 per CTA)
-    const int fm = best.fmt == 1 ? 1 : 0;
+    const int fm = best.fmt == 1 ? (best.cl < 5 ? 4 : AJ_SELL_FM) : 0;
     const int occ = std::max(1, persistent_blocks_per_sm(kernel_pol(c->pol), c->nrhs, c->qx, fm));
     for (int k = occ - 1; k >= std::max(2, occ - 2); k--) {
       TuneVal v = best;
@@ -1656,6 +1646,12 @@ static int batch_units(const aj_ctx* c, long long active_tiles, int grid) {
   const long long v = (long long)std::ceil(want);
   return (int)std::max<long long>(1, std::min<long long>({v, nt, (long long)cap}));
 }
+
+// 1: every lockstep launch prints its systems, units, grid, sweeps and device
+// time to stderr (a diagnostic build)
+#ifndef AJ_TRACE_LOCKSTEP
+#define AJ_TRACE_LOCKSTEP 0
+#endif
 
 // Device buffers of lockstep launches, kept between launches and grown on
 // demand (a server keeps one for its lifetime).
@@ -1829,6 +1825,17 @@ static aj_status run_batched(std::vector<BatchItem>& items, bool log_restarts, d
     float kms = 0.f;
     cudaEventElapsedTime(&kms, ws.e0, ws.e1);
     if (kernel_ms) *kernel_ms += kms;
+#if AJ_TRACE_LOCKSTEP
+    {
+      long long rows = 0, nnz = 0;
+      for (int i : act) {
+        rows += items[i].c->n * items[i].c->nrhs;
+        nnz += items[i].c->nnz * items[i].c->nrhs;
+      }
+      fprintf(stderr, "lockstep systems %d units %zu grid %d sweeps %lld ms %.3f rowrhs %lld nnzrhs %lld\n", m,
+              unit.size(), grid, sweeps, kms, rows, nnz);
+    }
+#endif
     if (err != 0) return err == kETimeout ? AJ_ETIMEOUT : AJ_ECUDA;
     for (int j = 0; j < m; j++) {
       const int i = act[j];
@@ -3077,6 +3084,14 @@ extern "C" void aj_server_destroy(aj_server* s) {
 }
 
 extern "C" uint64_t aj_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" void aj_cache_stats(uint64_t* order_hits, uint64_t* order_misses, uint64_t* tune_hits,
+                               uint64_t* tune_misses) {
+  if (order_hits) *order_hits = g_order_hits.load();
+  if (order_misses) *order_misses = g_order_misses.load();
+  if (tune_hits) *tune_hits = g_tune_hits.load();
+  if (tune_misses) *tune_misses = g_tune_misses.load();
+}
 
 extern "C" aj_status aj_test_barrier_stall(int cta, double timeout_ms) {
   if (cta < -1 || !(timeout_ms > 0.0) || timeout_ms > 4000.0) return AJ_EINVAL;

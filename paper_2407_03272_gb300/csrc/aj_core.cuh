@@ -43,6 +43,22 @@
 
 #include <type_traits>
 
+// SELL sweeps: the instantiation (3: SELL alone, 1: the any-format one) and
+// the tile order (0: sliced tiles, then long-row tiles, then huge rows;
+// 1: huge rows and long-row tiles first -- measured slower on the 8.4M-vertex
+// Chung-Lu graph, 0.87 against 0.79 ms per FP32 sweep)
+#ifndef AJ_SELL_FM
+#define AJ_SELL_FM 3
+#endif
+#ifndef AJ_SELL_HEAVY_FIRST
+#define AJ_SELL_HEAVY_FIRST 0
+#endif
+// SELL: 1 rotates the slices of a tile over the warps from tile to tile
+// (0: warp w always takes slice w; 1.04 against 0.87 ms per FP32 sweep of that graph)
+#ifndef AJ_SELL_ROTATE
+#define AJ_SELL_ROTATE 1
+#endif
+
 namespace aj {
 
 constexpr int kThreads = 256;  // threads per CTA = rows per tile (one row per thread)
@@ -443,8 +459,6 @@ struct IterArgs {
   const int* ltp;             // SELL: [nltiles + 1] long tile k = long_rows[ltp[k] .. ltp[k+1])
   int nhuge;                  // SELL: rows summed by a whole CTA, one per tile
   const int* huge_rows;       // SELL: [nhuge]
-  const int* tile_desc;       // SELL: [ntiles_sell + nltiles + nhuge] the tiles in sweep order:
-                              // kind << 29 | index, kind 0 sliced, 1 long rows, 2 a huge row
   const typename P::X* b;     // [n * nrhs]
   const typename P::X* jinv;  // [n]
   typename P::X* x[3];        // three iterate buffers, [n * nrhs] each
@@ -791,9 +805,16 @@ template <class P, int SF, int FM, bool MULTI>
 __host__ __device__ constexpr bool y_csr_f64() {
   return std::is_same<P, PolF64>::value && SF == 3 && FM == 0 && !MULTI;
 }
+// CTAs per SM of the one-RHS SELL-only kernels of the FP32 and BF16 policies
+// (0: the policy's own)
+#ifndef AJ_SELL_MINB
+#define AJ_SELL_MINB 0
+#endif
 template <class P, int SF, int FM, bool MULTI>
 __host__ __device__ constexpr int kernel_min_blocks() {
-  return y_csr_f64<P, SF, FM, MULTI>() ? AJ_Y_CSR_MINB : MULTI ? P::kMinBlocksMulti : P::kMinBlocks;
+  return y_csr_f64<P, SF, FM, MULTI>() ? AJ_Y_CSR_MINB
+         : (FM >= 3 && !MULTI && P::kId >= 2 && AJ_SELL_MINB > 0) ? AJ_SELL_MINB
+         : MULTI ? P::kMinBlocksMulti : P::kMinBlocks;
 }
 template <class P, int SF, int FM, bool MULTI>
 __host__ __device__ constexpr int kernel_row_unroll() {
@@ -808,7 +829,9 @@ __host__ __device__ constexpr int kernel_row_unroll() {
 // FM: the formats the instantiation reads -- 0 CSR only, which keeps the
 // other formats' code and registers out of the CSR kernel; 1 any (runtime
 // a.fmt: CSR, SELL or stencil; needed by the block-diagonal J on CSR and by
-// the batched kernel); 2 the stencil rows alone.  MULTI:
+// the batched kernel); 2 the stencil rows alone; 3 SELL alone with slices
+// of 32 rows (the graph sweeps, without the CSR, stencil and block-J code);
+// 4 SELL alone with slices of 8 or 16 rows (split rows).  MULTI:
 // nrhs and the lanes per row come from the arguments; otherwise one.
 // SF: sweep form -- 0 lazy, 1 stored, 2 stored with the difference
 // delta = x^{s-1} - x^{s-2} kept in a.dl (y = x + beta delta costs one
@@ -853,7 +876,7 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
   const YConst<P, YS> yk(me);
   const int lane = threadIdx.x & 31;
   constexpr bool ANY = FM != 0;
-  const bool sell = FM == 1 && a.fmt == 1;
+  const bool sell = FM >= 3 || (FM == 1 && a.fmt == 1);
   // stencil: the rows of a constant-coefficient Dirichlet Laplacian in natural
   // order, their entries known without loading them (same values, same
   // ascending column order as in CSR, so the sums are the CSR sums bit for bit)
@@ -868,7 +891,12 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
     }
   }
   const int ntiles = sell ? a.ntiles_sell + a.nltiles + a.nhuge : (a.n + rpt - 1) / rpt;
-  for (int tile = cta; tile < ntiles; tile += ncta) {
+  // SELL: the rows of a sorting window run longest first, so slice w of a
+  // tile is longer than slice w + 1; warp w takes slice (w + kt) mod 8 of the
+  // CTA's kt-th tile, so that no warp takes the longest slice of every tile
+  // and waits on the others at the grid barrier the least
+  int kt = 0;
+  for (int tile = cta; tile < ntiles; tile += ncta, kt++) {
     // this lane group's row i, its entries colp[k * stride], valp[k * stride]
     // (k < cnt) and, for long rows, its CSR range rs .. re
     int i, rs = 0, re = 0, cnt = 0, stride = 1;
@@ -889,25 +917,33 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       colp += rs;
       valp += rs;
     } else {
-      // SELL: tile k of the sweep is the one tile_desc[k] names (kind in bits
-      // 29-30, index below), heaviest first, so that dealing them round-robin
-      // to the CTAs leaves no CTA more than one tile's work behind the others
-      const int dsc = ld_ro(a.tile_desc + tile);
-      const int kind = dsc >> 29, ix = dsc & 0x1fffffff;
+      // SELL: the sliced tiles in row order (neighbouring tiles gather from
+      // nearby rows), then the tiles of long rows (longest first), then the
+      // huge rows (one per tile, longest first); AJ_SELL_HEAVY_FIRST puts the
+      // last two kinds first
+#if AJ_SELL_HEAVY_FIRST
+      const int kind = tile < a.nhuge ? 2 : tile < a.nhuge + a.nltiles ? 1 : 0;
+      const int ix = kind == 2 ? tile : kind == 1 ? tile - a.nhuge : tile - a.nhuge - a.nltiles;
+#else
+      const int kind = tile < a.ntiles_sell ? 0 : tile < a.ntiles_sell + a.nltiles ? 1 : 2;
+      const int ix = kind == 0 ? tile : kind == 1 ? tile - a.ntiles_sell : tile - a.ntiles_sell - a.nltiles;
+#endif
       if (kind == 0) {
         // slices of C = 2^cl rows, entry k of a slice's row p at
         // sptr[slice] + C k + p.  With C < 32 (one right-hand side) the
         // L = 32 / C lanes of a row take its entries k = sub, sub + L, ... and
         // a warp reads 32 consecutive stored words per load; a tile is then
         // 8 C rows, one slice per warp
-        const int cl = a.sell_cl;
+        // (the SELL-32-only kernel, FM 3, never meets split slices)
+        const int cl = (FM == 4 || FM == 1) ? a.sell_cl : 5;
+        const int wv = ((threadIdx.x >> 5) + AJ_SELL_ROTATE * kt) & (kWarps - 1);  // the slice this warp takes
         int pos;
-        if (cl < 5) {
+        if ((FM == 4 || FM == 1) && cl < 5) {
           split = true;
           sub = lane >> cl;
-          pos = ix * (kWarps << cl) + ((threadIdx.x >> 5) << cl) + (lane & ((1 << cl) - 1));
+          pos = ix * (kWarps << cl) + (wv << cl) + (lane & ((1 << cl) - 1));
         } else {
-          pos = ix * rpt + slot;
+          pos = ix * rpt + (wv << (5 - lg)) + (lane >> lg);
         }
         valid = pos < a.nsell;
         i = valid ? ld_ro(a.perm + pos) : 0;
@@ -1046,7 +1082,7 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
                               sub == 0 ? P::neg(P::ldr(a.b + (size_t)i * nr + r)) : P::zero());
       }
     }
-    if constexpr (FM == 1) {
+    if constexpr (FM == 4 || FM == 1) {
       if (split) {
         // the lanes of a row add their shares (xor over the lane bits above
         // log2 C, all within the row's lanes); its first lane updates it
@@ -1080,7 +1116,7 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
         }
       }
     }
-    if (ANY && a.jblk > 1) {
+    if ((FM == 1 || FM == 2) && a.jblk > 1) {  // (the SELL-only kernels never meet a block J)
       // eq. J-blkdiag: x^t_i = y^t_i - sum_m (J^{bb})^{-1}_{im} g_m over the rows m
       // of i's block, which sit in lanes of this warp (blocks align with tiles
       // and jblk << lg <= 32); every lane takes part in the exchange

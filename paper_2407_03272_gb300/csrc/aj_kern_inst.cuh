@@ -44,7 +44,6 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
   a.ltp = L.ltp;
   a.nhuge = L.nhuge;
   a.huge_rows = L.huge_rows;
-  a.tile_desc = L.tile_desc;
   a.b = static_cast<const typename P::X*>(L.b);
   a.jinv = static_cast<const typename P::X*>(L.jinv);
   for (int k = 0; k < 3; k++) a.x[k] = static_cast<typename P::X*>(L.x[k]);
@@ -108,12 +107,14 @@ static int occ_of(const void* k) {
 }
 
 // The persistent kernel for sweep form sf and formats fm (0 CSR only, 1
-// any, 2 stencil only).
+// any, 2 stencil only, 3 SELL-32 only, 4 SELL-16/8 only).
 template <class P, int SF, bool MULTI>
 static const void* persistent_fm(int fm) {
-  return fm == 0 ? (const void*)aj_persistent_kernel<P, SF, 0, MULTI>
+  return fm == 0   ? (const void*)aj_persistent_kernel<P, SF, 0, MULTI>
          : fm == 1 ? (const void*)aj_persistent_kernel<P, SF, 1, MULTI>
-                   : (const void*)aj_persistent_kernel<P, SF, 2, MULTI>;
+         : fm == 2 ? (const void*)aj_persistent_kernel<P, SF, 2, MULTI>
+         : fm == 3 ? (const void*)aj_persistent_kernel<P, SF, 3, MULTI>
+                   : (const void*)aj_persistent_kernel<P, SF, 4, MULTI>;
 }
 
 template <class P, bool MULTI>
@@ -126,9 +127,11 @@ static const void* persistent_fn(int sf, int fm) {
   return nullptr;
 }
 
-// The instantiation a launch needs: the stencil rows alone, CSR alone, or any.
+// The instantiation a launch needs: the stencil rows alone, SELL alone, CSR
+// alone, or any (the block-diagonal J).
 static int launch_fm(const IterLaunch& L) {
-  return L.fmt == 2 ? 2 : (L.fmt == 1 || L.jblk > 1) ? 1 : 0;
+  return L.fmt == 2 ? 2 : L.jblk > 1 ? 1
+         : L.fmt == 1 ? (L.sell_cl && L.sell_cl < 5 ? 4 : AJ_SELL_FM) : 0;
 }
 
 template <class P, bool MULTI>
@@ -141,7 +144,7 @@ static cudaError_t launch_m(const IterLaunch& L, int grid, cudaStream_t s) {
 }
 
 // Co-resident CTAs of the persistent kernel for formats fm (0 CSR only, 1
-// any, 2 stencil only), or with fm < 0 the smallest over the three, so that
+// any, 2 stencil only, 3 and 4 SELL only), or with fm < 0 the smallest over them, so that
 // a grid sized by it fits any of them.
 template <class P, bool MULTI>
 static int occ_m(int qx, int fm) {
@@ -150,7 +153,7 @@ static int occ_m(int qx, int fm) {
     return k ? occ_of(k) : 0;
   }
   int occ = 1 << 30;
-  for (int f = 0; f < 3; f++) {
+  for (int f = 0; f < 5; f++) {
     const void* k = persistent_fn<P, MULTI>(qx, f);
     if (!k) return 0;
     occ = std::min(occ, occ_of(k));

@@ -33,7 +33,6 @@ struct IterLaunch {
   const int* ltp;
   int nhuge;
   const int* huge_rows;
-  const int* tile_desc;  // SELL: tiles in sweep order (see IterArgs)
   const void* b;
   const void* jinv;
   void* x[3];
@@ -90,7 +89,8 @@ int lockstep_blocks_per_sm(int pol, int qx);
 // (0 F64, 1 DF64, 2 F32, 3 BF16), nrhs in [1, 4] and the sweep form L.qx.
 cudaError_t launch_persistent(int pol, int nrhs, const IterLaunch& L, int grid, cudaStream_t s);
 // Co-resident CTAs per SM of that kernel for formats fm (0 CSR only, 1 any,
-// 2 stencil only; fm < 0: the smallest over the three), 0 on error.
+// 2 stencil only, 3 SELL-32 only, 4 SELL-16/8 only; fm < 0: the smallest over
+// them), 0 on error.
 int persistent_blocks_per_sm(int pol, int nrhs, int qx, int fm = -1);
 
 cudaError_t launch_persistent_f64(int nrhs, const IterLaunch& L, int grid, cudaStream_t s);

@@ -106,3 +106,9 @@ def test_noalloc_binding_refuses_bad_arrays_before_the_call():
     # well-formed host tensors are refused too: the entry point takes device arrays
     with pytest.raises(ValueError, match="device"):
         aj.solve_noalloc(rp, ci, v, b, out)
+
+
+def test_cache_stats_without_gpu_work():
+    s = aj.cache_stats()
+    assert set(s) == {"order_hits", "order_misses", "tune_hits", "tune_misses"}
+    assert all(v >= 0 for v in s.values())

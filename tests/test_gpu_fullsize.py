@@ -65,15 +65,19 @@ def test_fullsize_solve_reaches_1e8(precision, kw):
     assert abs(rr - info["relres"]) <= 1e-3 * rr
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_ir", "bf16_ir"])
-def test_fullsize_stencil_equals_csr_bitwise(precision):
-    # the stencil rows are the CSR rows' sums bit for bit, at the full size too
+@pytest.mark.parametrize("precision,form", [("fp64", "auto"), ("fp32_ir", "lazy"), ("fp32_ir", "y"),
+                                            ("bf16_ir", "auto")])
+def test_fullsize_stencil_equals_csr_bitwise(precision, form):
+    # the stencil rows are the CSR rows' sums bit for bit, at the full size
+    # too, in the same sweep form (AUTO gives FP32 values in the stencil
+    # format the explicit-y form, on CSR the lazy one)
     Q, b, xs = workload()
     n = Q["n"]
+    sf = {"auto": aj.AJ_SWEEP_AUTO, "lazy": aj.AJ_SWEEP_LAZY, "y": aj.AJ_SWEEP_Y}[form]
     out = {}
     for F in (aj.AJ_FMT_CSR, aj.AJ_FMT_STENCIL):
         c = aj.from_csr(Q, b, device="cuda")
-        c.set(precision=precision, stop=aj.AJ_STOP_NONE, maxit=60, inner_tol=1e-30, format=F)
+        c.set(precision=precision, stop=aj.AJ_STOP_NONE, maxit=60, inner_tol=1e-30, format=F, sweep_form=sf)
         x = torch.empty(n, dtype=torch.float64, device="cuda")
         _, info = c.solve(out=x)
         out[F] = (x.cpu().numpy(), info["iters"])

@@ -234,10 +234,11 @@ def test_multi_rhs_equals_single(nrhs, precision, form):
     B = np.stack([synth.rhs(Q, synth.uniform(n, 20 + r)) for r in range(nrhs)], axis=1)
     bc = np.ascontiguousarray(B.T).reshape(-1)  # column-major n x nrhs
     ctx = aj.from_csr(Q, bc, nrhs=nrhs)
-    # the same sweep form for both runs (AUTO gives FP64 with one right-hand
-    # side the explicit-y form, with several the difference form), and the
-    # same grid, so the FP64 reductions are summed in the same order
-    sf = aj.AJ_SWEEP_Y if form == "y" else (aj.AJ_SWEEP_DELTA if precision == "fp64" else aj.AJ_SWEEP_AUTO)
+    # the same sweep form for both runs (AUTO gives FP64, and FP32 values in
+    # the stencil format, with one right-hand side the explicit-y form, with
+    # several the difference or lazy form), and the same grid, so the FP64
+    # reductions are summed in the same order
+    sf = aj.AJ_SWEEP_Y if form == "y" else (aj.AJ_SWEEP_DELTA if precision == "fp64" else aj.AJ_SWEEP_LAZY)
     ctx.set(precision=precision, tol=1e-9, maxit=10000, grid_ctas=8, sweep_form=sf)
     X, infos = ctx.solve(per_rhs=True)
     X = X.reshape(nrhs, n)

@@ -178,8 +178,11 @@ def test_explicit_stencil_with_renumbering_is_refused():
     assert c.order()[0] == 1 and c.format()[0] == aj.AJ_FMT_CSR
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_ir"])
-def test_batched_stencil_members_equal_csr(precision):
+@pytest.mark.parametrize("precision,form", [("fp64", "auto"), ("fp32_ir", "lazy"), ("fp32_ir", "y")])
+def test_batched_stencil_members_equal_csr(precision, form):
+    # both formats in the same sweep form (AUTO gives one-RHS FP32 members in
+    # the stencil format the explicit-y form, on CSR the lazy one)
+    sf = {"auto": aj.AJ_SWEEP_AUTO, "lazy": aj.AJ_SWEEP_LAZY, "y": aj.AJ_SWEEP_Y}[form]
     rng = np.random.default_rng(5)
     mix = []
     for k in range(10):
@@ -187,7 +190,8 @@ def test_batched_stencil_members_equal_csr(precision):
         mix.append((Q, _rhs(Q, nrhs=int(rng.integers(1, 5)), seed=50 * k)))
     out = {}
     for fmt in (aj.AJ_FMT_STENCIL, aj.AJ_FMT_CSR):
-        ctxs = [_ctx(Q, B, format=fmt, precision=precision, tol=1e-8, maxit=40000, grid_ctas=1 + k % 3)
+        ctxs = [_ctx(Q, B, format=fmt, precision=precision, tol=1e-8, maxit=40000, grid_ctas=1 + k % 3,
+                     sweep_form=sf)
                 for k, (Q, B) in enumerate(mix)]
         outs = [np.empty(Q["n"] * B.shape[1]) for Q, B in mix]
         infos = aj.solve_batch(ctxs, outs)
