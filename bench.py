@@ -253,6 +253,24 @@ def _events(torch, stream):
     return e0, e1
 
 
+class _nvtx:
+    """An NVTX range around a timed section, so that a profiler can select
+    its launches (ncu --nvtx --nvtx-include NAME/)."""
+
+    def __init__(self, torch, name):
+        self.nv = getattr(torch.cuda, "nvtx", None)
+        self.name = name
+
+    def __enter__(self):
+        if self.nv is not None:
+            self.nv.range_push(self.name)
+
+    def __exit__(self, *exc):
+        if self.nv is not None:
+            self.nv.range_pop()
+        return False
+
+
 def time_pcg(aj, torch, stream, tens, n, out):
     """Sec. 4.2's comparator on the same system: diagonally preconditioned CG
     in FP64 to relative residual 1e-8 (one warm-up solve, one timed)."""
@@ -296,10 +314,11 @@ def bench_graph(aj, torch, dev, stream, hbm_peak, n):
         tuning = ctx.tuning()
         ctx.solve(out=out)
         e0, e1 = _events(torch, stream)
-        e0.record(stream)
-        _, info = ctx.solve(out=out)
-        e1.record(stream)
-        torch.cuda.synchronize()
+        with _nvtx(torch, "graph_" + prec):
+            e0.record(stream)
+            _, info = ctx.solve(out=out)
+            e1.record(stream)
+            torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         B = algorithmic_bytes(n, nnz, prec)
         gbs = B * info["iters"] / (info["kernel_ms"] * 1e-3) / 1e9
@@ -390,7 +409,8 @@ def bench_batched(aj, torch, dev, stream, count, pool, lockstep_fp64=False):
                 c.close()
             break
         aj.solve_batch(cs[:4], outs[:4], on_device=True)  # warm-up
-        ms, wall, infos = timed(lambda: aj.solve_batch(cs, outs, on_device=True))
+        with _nvtx(torch, "batched_" + prec):
+            ms, wall, infos = timed(lambda: aj.solve_batch(cs, outs, on_device=True))
         ok = sum(1 for i in infos if i["status"] == aj.AJ_OK)
         err = max_mix_error(systems, mats, lambda k: outs[k].cpu().numpy(), qcache)
         stn = [c.format()[0] == aj.AJ_FMT_STENCIL for c in cs]

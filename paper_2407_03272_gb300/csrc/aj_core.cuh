@@ -806,9 +806,9 @@ __host__ __device__ constexpr bool y_csr_f64() {
   return std::is_same<P, PolF64>::value && SF == 3 && FM == 0 && !MULTI;
 }
 // CTAs per SM of the one-RHS SELL-only kernels of the FP32 and BF16 policies
-// (0: the policy's own)
+// (0: the policy's own); see AJ_SELL_PIPE
 #ifndef AJ_SELL_MINB
-#define AJ_SELL_MINB 0
+#define AJ_SELL_MINB 4
 #endif
 template <class P, int SF, int FM, bool MULTI>
 __host__ __device__ constexpr int kernel_min_blocks() {
@@ -816,9 +816,31 @@ __host__ __device__ constexpr int kernel_min_blocks() {
          : (FM >= 3 && !MULTI && P::kId >= 2 && AJ_SELL_MINB > 0) ? AJ_SELL_MINB
          : MULTI ? P::kMinBlocksMulti : P::kMinBlocks;
 }
+// The SELL-only kernels (FM 3, 4).  FP32 and BF16 values: chunks of
+// AJ_SELL_UNROLL entries, and (AJ_SELL_PIPE) chunk q + 1's columns and values
+// loaded while chunk q's gathers are in flight, at AJ_SELL_MINB CTAs per SM.
+// FP64 and double-float values: chunks of AJ_SELL_UNROLL_F64, no pipeline.
+// Chung-Lu graph, n = 8.4M, per sweep: FP32 0.80 -> 0.71 ms (pipelined
+// chunks of 8 at 4 CTAs/SM; at the 40-register cap of 6 CTAs/SM the pipeline
+// spilled, 1.03 ms), FP64 1.13 -> 1.10 ms (chunks of 4).
+#ifndef AJ_SELL_UNROLL
+#define AJ_SELL_UNROLL 8
+#endif
+#ifndef AJ_SELL_UNROLL_F64
+#define AJ_SELL_UNROLL_F64 4
+#endif
+#ifndef AJ_SELL_PIPE
+#define AJ_SELL_PIPE 1
+#endif
+template <class P>
+__host__ __device__ constexpr bool sell_pipe() {
+  return P::kId >= 2 && AJ_SELL_PIPE;
+}
 template <class P, int SF, int FM, bool MULTI>
 __host__ __device__ constexpr int kernel_row_unroll() {
-  return y_csr_f64<P, SF, FM, MULTI>() ? 4 : row_unroll(SF != 0);
+  return y_csr_f64<P, SF, FM, MULTI>() ? 4
+         : FM >= 3 ? (P::kId >= 2 ? AJ_SELL_UNROLL : AJ_SELL_UNROLL_F64)
+                   : row_unroll(SF != 0);
 }
 
 // One sweep over the CTA's tiles: the fused SpMV at y, x update and reduction
@@ -1047,30 +1069,75 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
       const bool two = !ONE && !same;
       if constexpr (YS)  // g = Q y - b itself (-b in the row's first lane only)
         sx = sub == 0 ? P::neg(P::ldr(a.b + (size_t)i * nr + r)) : P::zero();
-      for (int q0 = 0; q0 < cnt; q0 += U) {
+      if constexpr (FM >= 3 && sell_pipe<P>()) {
+        // the same chunks and multiply-adds in the same order; the columns
+        // and values of the next chunk are loaded before this chunk's gathers
+        // are used
         int cc[U];
         V vv[U];
 #pragma unroll
         for (int k = 0; k < U; k++) {
-          const bool in = q0 + k < cnt;
-          cc[k] = in ? ld_ro(colp + (q0 + k) * stride) : 0;
-          vv[k] = in ? P::ldv(valp + (q0 + k) * stride) : P::vzero();
+          const bool in = k < cnt;
+          cc[k] = in ? ld_ro(colp + k * stride) : 0;
+          vv[k] = in ? P::ldv(valp + k * stride) : P::vzero();
         }
-        S xv[U], pv[U];
+        for (int q0 = 0; q0 < cnt; q0 += U) {
+          S xv[U], pv[U];
 #pragma unroll
-        for (int k = 0; k < U; k++) {
-          xv[k] = P::zero();
-          pv[k] = P::zero();
-          if (q0 + k < cnt) {
-            xv[k] = P::ldg(xc + (size_t)cc[k] * nr + r);
-            if (two) pv[k] = P::ldg(xp + (size_t)cc[k] * nr + r);
+          for (int k = 0; k < U; k++) {
+            xv[k] = P::zero();
+            pv[k] = P::zero();
+            if (q0 + k < cnt) {
+              xv[k] = P::ldg(xc + (size_t)cc[k] * nr + r);
+              if (two) pv[k] = P::ldg(xp + (size_t)cc[k] * nr + r);
+            }
+          }
+          int cn[U];
+          V vn[U];
+#pragma unroll
+          for (int k = 0; k < U; k++) {
+            const bool in = q0 + U + k < cnt;
+            cn[k] = in ? ld_ro(colp + (q0 + U + k) * stride) : 0;
+            vn[k] = in ? P::ldv(valp + (q0 + U + k) * stride) : P::vzero();
+          }
+#pragma unroll
+          for (int k = 0; k < U; k++) {
+            if (q0 + k >= cnt) break;
+            P::macv(sx, vv[k], xv[k]);
+            if (two) P::macv(sp, vv[k], pv[k]);
+          }
+#pragma unroll
+          for (int k = 0; k < U; k++) {
+            cc[k] = cn[k];
+            vv[k] = vn[k];
           }
         }
+      } else {
+        for (int q0 = 0; q0 < cnt; q0 += U) {
+          int cc[U];
+          V vv[U];
 #pragma unroll
-        for (int k = 0; k < U; k++) {
-          if (q0 + k >= cnt) break;
-          P::macv(sx, vv[k], xv[k]);
-          if (two) P::macv(sp, vv[k], pv[k]);
+          for (int k = 0; k < U; k++) {
+            const bool in = q0 + k < cnt;
+            cc[k] = in ? ld_ro(colp + (q0 + k) * stride) : 0;
+            vv[k] = in ? P::ldv(valp + (q0 + k) * stride) : P::vzero();
+          }
+          S xv[U], pv[U];
+#pragma unroll
+          for (int k = 0; k < U; k++) {
+            xv[k] = P::zero();
+            pv[k] = P::zero();
+            if (q0 + k < cnt) {
+              xv[k] = P::ldg(xc + (size_t)cc[k] * nr + r);
+              if (two) pv[k] = P::ldg(xp + (size_t)cc[k] * nr + r);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < U; k++) {
+            if (q0 + k >= cnt) break;
+            P::macv(sx, vv[k], xv[k]);
+            if (two) P::macv(sp, vv[k], pv[k]);
+          }
         }
       }
       sx = P::finish(sx);
@@ -1600,6 +1667,23 @@ __device__ __forceinline__ bool lock_enter(const LockArgs<P>& b, IterArgs<P>& a,
   return sm.done != 0 || k >= kmax;
 }
 
+// One unit's sweep in the instantiation of its system's format (as a solo
+// run of the same system launches it): the stencil rows alone, SELL alone
+// (slices of 32 rows, or of 8 or 16 with split rows), CSR alone, or any
+// format for the block-diagonal J.
+#ifndef AJ_LOCK_BY_FORMAT
+#define AJ_LOCK_BY_FORMAT 1
+#endif
+template <class P, int SF, bool MON>
+__device__ __forceinline__ void lock_sweep(const IterArgs<P>& a, const RhsState* st, bool compute_x,
+                                           bool want_obj, typename P::A (&acc)[kNRed], int v, int V) {
+  if (!AJ_LOCK_BY_FORMAT || a.jblk > 1) sweep<P, SF, 1, true, MON>(a, st, compute_x, want_obj, acc, v, V);
+  else if (a.fmt == 2) sweep<P, SF, 2, true, MON>(a, st, compute_x, want_obj, acc, v, V);
+  else if (a.fmt == 1 && a.sell_cl < 5) sweep<P, SF, 4, true, MON>(a, st, compute_x, want_obj, acc, v, V);
+  else if (a.fmt == 1) sweep<P, SF, 3, true, MON>(a, st, compute_x, want_obj, acc, v, V);
+  else sweep<P, SF, 0, true, MON>(a, st, compute_x, want_obj, acc, v, V);
+}
+
 template <class P, int SF>
 __global__ void __launch_bounds__(kThreads, P::kMinBlocksMulti) aj_lockstep_kernel(LockArgs<P> b) {
   __shared__ SolveSmem sm;
@@ -1633,10 +1717,10 @@ __global__ void __launch_bounds__(kThreads, P::kMinBlocksMulti) aj_lockstep_kern
 #pragma unroll
       for (int q = 0; q < kNRed; q++) acc_zero(acc[q]);
       if constexpr (SF == 3) {
-        if (mon) sweep<P, SF, 1, true, true>(a, sm.st, compute_x, want_obj, acc, v, V);
-        else sweep<P, SF, 1, true, false>(a, sm.st, compute_x, want_obj, acc, v, V);
+        if (mon) lock_sweep<P, SF, true>(a, sm.st, compute_x, want_obj, acc, v, V);
+        else lock_sweep<P, SF, false>(a, sm.st, compute_x, want_obj, acc, v, V);
       } else {
-        sweep<P, SF, 1, true>(a, sm.st, compute_x, want_obj, acc, v, V);
+        lock_sweep<P, SF, true>(a, sm.st, compute_x, want_obj, acc, v, V);
       }
       double* part = a.partials + (size_t)(k & 1) * V * nr * kNRed;
 #pragma unroll
