@@ -537,7 +537,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32_ir", "bf16_ir"])
     ap.add_argument("--form", default="auto", choices=["auto", "lazy", "stored", "delta", "y"],
-                    help="sweep form; auto = stored for fp64, lazy otherwise (the library's AUTO)")
+                    help="sweep form; auto = the library's AUTO choice (explicit y for fp64 with one RHS)")
     ap.add_argument("--format", default="csr", choices=["csr", "stencil", "sell"],
                     help="format of the timed context (the headline workload is CSR)")
     ap.add_argument("--no-variants", action="store_true")

@@ -135,6 +135,21 @@ __device__ __forceinline__ T ld_gather(const T* p) {
 template <class T>
 __device__ __forceinline__ void st_l2(T* p, T v) { __stcg(p, v); }
 
+// Asynchronous 16-byte copies global -> shared (cp.async, read at L2 like
+// ld_l2), src_bytes <= 16 of them read and the rest of the 16 zero-filled;
+// both addresses 16-byte aligned.  A thread's copies form groups
+// (commit); wait<N> returns when all but the newest N of its groups have
+// landed.  The waits are the hardware's own: no spin in this code.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -287,6 +302,7 @@ struct PolF64 {
   static constexpr int kMinBlocks = AJ_MINB_F64;
   static constexpr int kMinBlocksMulti = AJ_MINB_MULTI;
   __device__ static S zero() { return 0.0; }
+  __device__ static S from_x(X v) { return v; }
   __device__ static S ldx(const X* p) { return ld_l2(p); }
   __device__ static S ldg(const X* p) { return ld_gather(p); }
   __device__ static S ldr(const X* p) { return ld_ro(p); }
@@ -319,6 +335,7 @@ struct PolDF64 {
   static constexpr int kMinBlocks = AJ_MINB_DF64;
   static constexpr int kMinBlocksMulti = AJ_MINB_MULTI;
   __device__ static S zero() { return {0.f, 0.f}; }
+  __device__ static S from_x(X v) { return {v.x, v.y}; }
   __device__ static S ldx(const X* p) { float2 v = ld_l2(p); return {v.x, v.y}; }
   __device__ static S ldg(const X* p) { float2 v = ld_gather(p); return {v.x, v.y}; }
   __device__ static S ldr(const X* p) { float2 v = ld_ro(p); return {v.x, v.y}; }
@@ -370,6 +387,7 @@ struct PolF32 {
   static constexpr int kMinBlocks = AJ_MINB_F32;
   static constexpr int kMinBlocksMulti = AJ_MINB_MULTI;
   __device__ static S zero() { return 0.f; }
+  __device__ static S from_x(X v) { return v; }
   __device__ static S ldx(const X* p) { return ld_l2(p); }
   __device__ static S ldg(const X* p) { return ld_gather(p); }
   __device__ static S ldr(const X* p) { return ld_ro(p); }
@@ -869,10 +887,209 @@ __host__ __device__ constexpr int kernel_row_unroll() {
 // (The explicit-y code sits in `if constexpr` blocks of its own: at the
 // register caps of the FP32 and BF16 policies even values the other forms
 // never use changed their register allocation, and their speed.)
+// ----------------------------------------------------------------------------
+// The stencil sweep of the explicit-y form with one right-hand side, its
+// gathers staged in shared memory.  A tile of 256 rows i0 .. i0 + 255 gathers
+// y only from five contiguous segments -- rows i0 + off .. i0 + 255 + off for
+// off = -N^2, -N, +N, +N^2, and i0 - 1 .. i0 + 256 for the row itself and its
+// +-1 neighbours -- and reads its own rows of x^{s-1}, b and J^{-1}.  Those
+// eight pieces are copied to shared memory by cp.async, STAGES - 1 tiles
+// ahead of the tile being summed, so the sweep waits on memory once per
+// launch instead of once per tile.  Every row sums the same neighbours in the
+// same order with the same operations as the unstaged stencil rows (and so
+// as CSR rows), and the reduction terms accumulate in the same tile order:
+// the iterates are the unstaged sweep's bit for bit.
+// AJ_STENCIL_STAGE: the policies that stage, bit P::kId (1 FP64, 2
+// double-float, 4 FP32, 8 BF16); AJ_STAGE_ST64 / AJ_STAGE_ST32: the stages
+// of the 8-byte and 4-byte vector policies.  Measured per 256^3 sweep,
+// staged against unstaged: FP64 0.418 / 0.426 ms, BF16 values 0.179 / 0.194
+// (4 stages; 2 and 3: 0.190, 0.188), FP32 values 0.204 / 0.181 and
+// double-float 0.333 / 0.275 -- so FP64 and BF16 stage, the other two do not.
+// The staged sweep issues fewer loads but more index arithmetic and a CTA
+// barrier per tile, which the FP32 and double-float sweeps, already issue
+// bound, pay for.
+#ifndef AJ_STENCIL_STAGE
+#define AJ_STENCIL_STAGE 9
+#endif
+#ifndef AJ_STAGE_ST64
+#define AJ_STAGE_ST64 2
+#endif
+#ifndef AJ_STAGE_ST32
+#define AJ_STAGE_ST32 4
+#endif
+template <class P>
+struct StencilStage {
+  using X = typename P::X;
+  static constexpr int kE = 16 / (int)sizeof(X);        // elements per 16-byte copy
+  static constexpr int kL = kThreads + 2 * kE;           // elements of a y segment
+  static constexpr int kStages = P::kId >= 2 ? AJ_STAGE_ST32 : AJ_STAGE_ST64;  // tiles in flight + 1
+  static constexpr int kCH = kL / kE;                    // copies per y segment
+  static constexpr int kCO = kThreads / kE;              // copies per own-row piece
+  static constexpr int kCopies = 5 * kCH + 3 * kCO;      // copies per tile
+  static constexpr int kPer = (kCopies + kThreads - 1) / kThreads;  // per thread
+  __align__(16) X seg[kStages][5][kL];                   // y^s around the tile
+  __align__(16) X own[kStages][3][kThreads];             // x^{s-1}, b, J^{-1} of its rows
+};
+
+// The stage buffers: one block of shared memory per kernel, whichever
+// monitor variant of the sweep uses it.
+template <class P>
+__device__ __forceinline__ StencilStage<P>& stencil_stage_smem() {
+  __shared__ StencilStage<P> sg;
+  return sg;
+}
+
+// First element of y segment j (0..4: -N^2, -N, the row and its +-1, +N,
+// +N^2) of the tile at row i0, rounded down to a whole 16-byte copy (a
+// multiple of E elements; for a negative start too, by the two's-complement
+// mask).
+template <class P>
+__device__ __forceinline__ int stage_seg_start(int i0, int j, int N, int NN) {
+  constexpr int E = StencilStage<P>::kE;
+  const int base = i0 + (j == 0 ? -NN : j == 1 ? -N : j == 2 ? -1 : j == 3 ? N : NN);
+  return base & ~(E - 1);
+}
+
+template <class P, bool MON>
+__device__ __forceinline__ void sweep_stencil_y_staged(const IterArgs<P>& a, const RhsState& me,
+                                                       bool compute_x, typename P::A (&acc)[kNRed],
+                                                       int cta, int ncta) {
+  using S = typename P::S;
+  using V = typename P::V;
+  using X = typename P::X;
+  using SG = StencilStage<P>;
+  constexpr int ST = SG::kStages;
+  constexpr int E = SG::kE;
+  constexpr int U = kernel_row_unroll<P, 3, 2, false>();
+  SG& sg = stencil_stage_smem<P>();
+  const X* yc = y_source(a, me);
+  const X* xp = xbuf(a, me.cur);
+  X* xn = xbuf(a, me.nxt);
+  X* yn = ubuf(a, 1 - me.yb);
+  const bool same = me.cur == me.prev;
+  const bool active = me.done == 0;
+  const bool check = y_check<P>(me);
+  const YConst<P, true> yk(me);
+  const V s_diag = P::ldv(a.val + a.sdiag_at);
+  const V s_off = P::ldv(a.val + a.soff_at);
+  const int n = a.n;
+  const int N = a.sN, NN = a.sdim == 3 ? N * N : 0;
+  const int ntiles = (n + kThreads - 1) / kThreads;
+  // the copies of tile t into stage slot k, the parts inside the vectors:
+  // copy c = threadIdx.x + p * 256 is chunk q of piece j (y segments 0..4,
+  // then x^{s-1}, b, J^{-1})
+  auto issue = [&](int t, int k) {
+    const int i0 = t * kThreads;
+#pragma unroll
+    for (int p = 0; p < SG::kPer; p++) {
+      const int c = (int)threadIdx.x + p * kThreads;
+      if (c >= SG::kCopies) continue;
+      const X* src;
+      X* dst;
+      int g;
+      if (c < 5 * SG::kCH) {
+        const int j = c / SG::kCH, q = c - j * SG::kCH;
+        if ((j == 0 || j == 4) && NN == 0) continue;  // 2-D grid: no +-N^2 neighbours
+        g = stage_seg_start<P>(i0, j, N, NN) + q * E;
+        src = yc;
+        dst = &sg.seg[k][j][q * E];
+      } else {
+        const int j = (c - 5 * SG::kCH) / SG::kCO, q = c - 5 * SG::kCH - j * SG::kCO;
+        if (j == 0 && same) continue;  // x^{s-1} = y^s: not read
+        g = i0 + q * E;
+        src = j == 0 ? xp : j == 1 ? a.b : a.jinv;
+        dst = &sg.own[k][j][q * E];
+      }
+      if (g < 0 || g >= n) continue;
+      const int left = n - g;
+      cp_async16(dst, src + g, (left < E ? left : E) * (int)sizeof(X));
+    }
+  };
+  __syncthreads();  // the previous sweep's reads of the stage slots are done
+#pragma unroll
+  for (int p = 0; p < ST - 1; p++) {
+    const int t = cta + p * ncta;
+    if (t < ntiles) issue(t, p);
+    cp_async_commit();
+  }
+  int k = 0;
+  for (int tile = cta; tile < ntiles; tile += ncta, k = k + 1 == ST ? 0 : k + 1) {
+    // tile's copies have landed (the newest ST - 2 groups may still fly), and
+    // every thread is done with the previous tile's slot, refilled next
+    cp_async_wait<ST - 2>();
+    __syncthreads();
+    {
+      const int t = tile + (ST - 1) * ncta;
+      if (t < ntiles) issue(t, k == 0 ? ST - 1 : k - 1);
+      cp_async_commit();
+    }
+    const int i0 = tile * kThreads;
+    const int i = i0 + (int)threadIdx.x;
+    if (i < n && active) {
+      const int q = (int)(((unsigned long long)i * a.smag) >> a.sshift);  // i / N
+      const int ix = i - q * N;
+      const int iy = a.sdim == 3 ? q - (int)(((unsigned long long)q * a.smag) >> a.sshift) * N : q;
+      const unsigned inm = (ix > 0 ? 4u : 0u) | 8u | (ix < N - 1 ? 16u : 0u) | (iy > 0 ? 2u : 0u) |
+                           (iy < N - 1 ? 32u : 0u) | (i >= NN && NN ? 1u : 0u) |
+                           (NN && i < n - NN ? 64u : 0u);
+      const S bi = P::from_x(sg.own[k][1][threadIdx.x]);
+      S sx = P::neg(bi);
+      // neighbour kn at offset off lies in segment j at (i + off) - start_j;
+      // the row's own segment (j = 2) holds -1, 0, +1
+      const int r2 = i - stage_seg_start<P>(i0, 2, N, NN);  // the row itself in segment 2
+#pragma unroll
+      for (int kn = 0; kn < 7; kn++) {
+        if (!(inm >> kn & 1u)) continue;
+        X v;
+        if (kn == 0) v = sg.seg[k][0][i - NN - stage_seg_start<P>(i0, 0, N, NN)];
+        else if (kn == 1) v = sg.seg[k][1][i - N - stage_seg_start<P>(i0, 1, N, NN)];
+        else if (kn <= 4) v = sg.seg[k][2][r2 + kn - 3];
+        else if (kn == 5) v = sg.seg[k][3][i + N - stage_seg_start<P>(i0, 3, N, NN)];
+        else v = sg.seg[k][4][i + NN - stage_seg_start<P>(i0, 4, N, NN)];
+        P::macv(sx, kn == 3 ? s_diag : s_off, P::from_x(v));
+      }
+      sx = P::finish(sx);
+      const S yi = P::from_x(sg.seg[k][2][r2]);
+      const S g = sx;  // Q y^s - b
+      if (MON) P::acc_prod(acc[1], g, g);
+      if (check) {
+        const S sp = stencil_pass<P, U>(i, inm, N, NN, s_diag, s_off, xp, 1, 0, P::neg(bi));
+        P::acc_prod(acc[2], sp, sp);
+      }
+      if (compute_x) {
+        const S ji = P::from_x(sg.own[k][2][threadIdx.x]);
+        const S xi = same ? yi : P::from_x(sg.own[k][0][threadIdx.x]);
+        const S xnew = P::fnma(ji, g, yi);
+        const S dx = P::sub(xnew, xi);
+        P::stx(xn + i, xnew);
+        P::stx(yn + i, P::fma_(yk.bnext, dx, xnew));
+        P::acc_prod(acc[0], g, dx);
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// Whether the staged stencil sweep can run: a diagonal J, and 16-byte aligned
+// vectors for the copies (the iterate buffers, b and J^{-1} are separate
+// allocations).
+template <class P>
+__device__ __forceinline__ bool stencil_stage_ok(const IterArgs<P>& a, const RhsState& me) {
+  const unsigned long long m = (unsigned long long)y_source(a, me) | (unsigned long long)xbuf(a, me.cur) |
+                               (unsigned long long)a.b | (unsigned long long)a.jinv;
+  return ((AJ_STENCIL_STAGE >> P::kId) & 1) && a.jblk == 1 && (m & 15ull) == 0;
+}
+
 template <class P, int SF, int FM, bool MULTI, bool MON = true>
 __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, bool compute_x,
                                       bool want_obj, typename P::A (&acc)[kNRed], int cta,
                                       int ncta) {
+  if constexpr (FM == 2 && !MULTI && SF == 3) {
+    if (stencil_stage_ok<P>(a, st[0])) {
+      sweep_stencil_y_staged<P, MON>(a, st[0], compute_x, acc, cta, ncta);
+      return;
+    }
+  }
   using S = typename P::S;
   using V = typename P::V;
   using X = typename P::X;
@@ -1674,6 +1891,17 @@ __device__ __forceinline__ bool lock_enter(const LockArgs<P>& b, IterArgs<P>& a,
 #ifndef AJ_LOCK_BY_FORMAT
 #define AJ_LOCK_BY_FORMAT 1
 #endif
+// CTAs per SM of the lockstep kernel: 5 for FP32 and BF16 values (256
+// systems of the batched mix in FP32-IR: 7.03 s, against 8.0 s at 4, 8.2 s
+// at 6 where it spills and 9.5 s at 3), the policy's multi-RHS count for
+// FP64 and double-float values; AJ_LOCK_MINB > 0 overrides both
+#ifndef AJ_LOCK_MINB
+#define AJ_LOCK_MINB 0
+#endif
+template <class P>
+__host__ __device__ constexpr int lock_min_blocks() {
+  return AJ_LOCK_MINB > 0 ? AJ_LOCK_MINB : P::kId >= 2 ? 5 : P::kMinBlocksMulti;
+}
 template <class P, int SF, bool MON>
 __device__ __forceinline__ void lock_sweep(const IterArgs<P>& a, const RhsState* st, bool compute_x,
                                            bool want_obj, typename P::A (&acc)[kNRed], int v, int V) {
@@ -1685,7 +1913,7 @@ __device__ __forceinline__ void lock_sweep(const IterArgs<P>& a, const RhsState*
 }
 
 template <class P, int SF>
-__global__ void __launch_bounds__(kThreads, P::kMinBlocksMulti) aj_lockstep_kernel(LockArgs<P> b) {
+__global__ void __launch_bounds__(kThreads, lock_min_blocks<P>()) aj_lockstep_kernel(LockArgs<P> b) {
   __shared__ SolveSmem sm;
   __shared__ IterArgs<P> a;
   using A = typename P::A;

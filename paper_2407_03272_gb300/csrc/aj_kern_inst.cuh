@@ -101,7 +101,16 @@ static cudaError_t launch_lockstep_p(int qx, const LockLaunch& B, int grid, cuda
   return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, 0, s);
 }
 
+// Co-resident CTAs per SM of kernel k.  Kernels with stage buffers in shared
+// memory (the staged stencil sweep) ask for the largest shared-memory
+// carveout first, so that their CTAs per SM are limited by registers, not by
+// the L1 / shared split; the others keep the default split (their gathers
+// use L1).
 static int occ_of(const void* k) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k) == cudaSuccess && fa.sharedSizeBytes > 8192)
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  cudaGetLastError();
   int nb = 0;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, 0) == cudaSuccess ? nb : 0;
 }
