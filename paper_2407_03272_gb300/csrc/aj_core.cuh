@@ -917,6 +917,29 @@ __host__ __device__ constexpr int kernel_row_unroll() {
 #ifndef AJ_STAGE_ST32
 #define AJ_STAGE_ST32 4
 #endif
+// The row tiles (CSR and stencil) a CTA sweeps, cta of ncta: round-robin
+// (tiles cta, cta + ncta, ...) or, with AJ_TILE_CONTIG, one contiguous block
+// (a 3-D grid's +-N neighbours of a 256-row tile are then the CTA's previous
+// and next tiles).  first, step and end of the CTA's tile sequence.
+#ifndef AJ_TILE_CONTIG
+#define AJ_TILE_CONTIG 0
+#endif
+struct TileRange {
+  int first, step, end;
+  __device__ TileRange(int ntiles, int cta, int ncta, bool contig) {
+    if (contig) {
+      const int per = ntiles / ncta, rem = ntiles - per * ncta;
+      first = cta * per + (cta < rem ? cta : rem);
+      end = first + per + (cta < rem ? 1 : 0);
+      step = 1;
+    } else {
+      first = cta;
+      end = ntiles;
+      step = ncta;
+    }
+  }
+};
+
 template <class P>
 struct StencilStage {
   using X = typename P::X;
@@ -975,6 +998,7 @@ __device__ __forceinline__ void sweep_stencil_y_staged(const IterArgs<P>& a, con
   const int n = a.n;
   const int N = a.sN, NN = a.sdim == 3 ? N * N : 0;
   const int ntiles = (n + kThreads - 1) / kThreads;
+  const TileRange tr(ntiles, cta, ncta, AJ_TILE_CONTIG);
   // the copies of tile t into stage slot k, the parts inside the vectors:
   // copy c = threadIdx.x + p * 256 is chunk q of piece j (y segments 0..4,
   // then x^{s-1}, b, J^{-1})
@@ -1008,19 +1032,19 @@ __device__ __forceinline__ void sweep_stencil_y_staged(const IterArgs<P>& a, con
   __syncthreads();  // the previous sweep's reads of the stage slots are done
 #pragma unroll
   for (int p = 0; p < ST - 1; p++) {
-    const int t = cta + p * ncta;
-    if (t < ntiles) issue(t, p);
+    const int t = tr.first + p * tr.step;
+    if (t < tr.end) issue(t, p);
     cp_async_commit();
   }
   int k = 0;
-  for (int tile = cta; tile < ntiles; tile += ncta, k = k + 1 == ST ? 0 : k + 1) {
+  for (int tile = tr.first; tile < tr.end; tile += tr.step, k = k + 1 == ST ? 0 : k + 1) {
     // tile's copies have landed (the newest ST - 2 groups may still fly), and
     // every thread is done with the previous tile's slot, refilled next
     cp_async_wait<ST - 2>();
     __syncthreads();
     {
-      const int t = tile + (ST - 1) * ncta;
-      if (t < ntiles) issue(t, k == 0 ? ST - 1 : k - 1);
+      const int t = tile + (ST - 1) * tr.step;
+      if (t < tr.end) issue(t, k == 0 ? ST - 1 : k - 1);
       cp_async_commit();
     }
     const int i0 = tile * kThreads;
@@ -1135,7 +1159,8 @@ __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, 
   // CTA's kt-th tile, so that no warp takes the longest slice of every tile
   // and waits on the others at the grid barrier the least
   int kt = 0;
-  for (int tile = cta; tile < ntiles; tile += ncta, kt++) {
+  const TileRange tr(ntiles, cta, ncta, AJ_TILE_CONTIG && !sell);
+  for (int tile = tr.first; tile < tr.end; tile += tr.step, kt++) {
     // this lane group's row i, its entries colp[k * stride], valp[k * stride]
     // (k < cnt) and, for long rows, its CSR range rs .. re
     int i, rs = 0, re = 0, cnt = 0, stride = 1;
