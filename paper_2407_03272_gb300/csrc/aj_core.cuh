@@ -920,7 +920,11 @@ __host__ __device__ constexpr int kernel_row_unroll() {
 // The row tiles (CSR and stencil) a CTA sweeps, cta of ncta: round-robin
 // (tiles cta, cta + ncta, ...) or, with AJ_TILE_CONTIG, one contiguous block
 // (a 3-D grid's +-N neighbours of a 256-row tile are then the CTA's previous
-// and next tiles).  first, step and end of the CTA's tile sequence.
+// and next tiles).  first, step and end of the CTA's tile sequence.  Measured
+// on the 256^3 Poisson system, contiguous against round-robin: FP64
+// explicit y 0.514 / 0.486 ms per sweep, FP32 lazy 0.356 / 0.317, FP32
+// stencil 0.195 / 0.181 -- round-robin keeps the whole grid's gather window
+// (and its +-N^2 planes) in L2, which outweighs the L1 hits.
 #ifndef AJ_TILE_CONTIG
 #define AJ_TILE_CONTIG 0
 #endif
