@@ -366,6 +366,12 @@ extern "C" void aj_destroy(aj_ctx* c) {
   c->ows.release();
   c->rws.release();
   c->base.release();
+  // the frees above are stream-ordered: wait for them, so that the pool can
+  // hand the memory to the next allocation on any stream at once instead of
+  // mapping new memory (aj_create of a 256^3 system took 41-51 ms instead of
+  // 9 ms when it followed a context freed on the legacy stream)
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->kev0) cudaEventDestroy(c->kev0);

@@ -1973,9 +1973,10 @@ __global__ void __launch_bounds__(kThreads, lock_min_blocks<P>()) aj_lockstep_ke
       A acc[kNRed];
 #pragma unroll
       for (int q = 0; q < kNRed; q++) acc_zero(acc[q]);
+      // (the objective-gap stop never takes the explicit-y form)
       if constexpr (SF == 3) {
-        if (mon) lock_sweep<P, SF, true>(a, sm.st, compute_x, want_obj, acc, v, V);
-        else lock_sweep<P, SF, false>(a, sm.st, compute_x, want_obj, acc, v, V);
+        if (mon) lock_sweep<P, SF, true>(a, sm.st, compute_x, false, acc, v, V);
+        else lock_sweep<P, SF, false>(a, sm.st, compute_x, false, acc, v, V);
       } else {
         lock_sweep<P, SF, true>(a, sm.st, compute_x, want_obj, acc, v, V);
       }
