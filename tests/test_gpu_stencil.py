@@ -99,6 +99,22 @@ def test_stencil_iterates_bitwise_equal_csr(precision, form):
         assert a[2][0]["status"] == aj.AJ_OK and a[2][0]["relres"] <= 1e-8
 
 
+@pytest.mark.parametrize("precision", ["fp64", "bf16_ir", "df64", "fp32_ir"])
+@pytest.mark.parametrize("N,dim", [(37, 2), (5, 3), (3, 2)])
+def test_staged_stencil_grids_bitwise_equal_csr(precision, N, dim):
+    # the explicit-y stencil sweep whose gathers are staged in shared memory
+    # (FP64 and BF16 values; the other two run unstaged): odd sides, so the
+    # +-N segments start off a 16-byte boundary; a 2-D grid (no +-N^2
+    # segments); ragged last tiles; and a grid smaller than one tile
+    Q = synth.poisson2d(N) if dim == 2 else synth.poisson3d(N)
+    B = _rhs(Q, seed=13)
+    for grid in (3, 0):
+        a, b = _pair(Q, B, precision=precision, sweep_form=aj.AJ_SWEEP_Y, tol=1e-8, maxit=40000,
+                     grid_ctas=grid)
+        _assert_same(a, b)
+        assert a[2][0]["status"] == aj.AJ_OK and a[2][0]["relres"] <= 1e-8
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32_ir"])
 def test_stencil_multi_rhs_and_x0_bitwise_equal_csr(precision):
     Q = synth.poisson2d(53)
