@@ -70,7 +70,7 @@ def algorithmic_bytes(n, nnz, precision, form="min", stencil=False, nrhs=1):
 # values stored 9.382 GB / 51 / 183.8 MB, FP32 values lazy 9.157 GB / 51 /
 # 167.0 MB.  The bench scales it to a full launch by the sweeps it runs;
 # traffic grows in proportion to the rows.
-TRAFFIC_PER_FORM_BYTES = {("fp64", "y"): 14.924282e9 / 51 / 284033028.0,
+TRAFFIC_PER_FORM_BYTES = {("fp64", "y"): 15.089756e9 / 51 / 284033028.0,
                           ("fp64", "delta"): 16.687168e9 / 51 / 317587460.0,
                           ("fp64", "stored"): 15.967641e9 / 51 / 300810244.0,
                           ("fp32_ir", "stored"): 9.382468e9 / 51 / 183762948.0,

@@ -1212,6 +1212,7 @@ static IterLaunch make_launch(aj_ctx* c, const void* bvec, long long maxit, int 
   L.jinv = c->pol == AJ_FP64 ? (const void*)c->jinv64 : c->jinvp;
   if (c->jblk > 1) L.jinv = c->pol == AJ_FP64 ? (const void*)c->jb64 : c->jbp;
   L.jblk = c->jblk;
+  L.short_rows = c->maxlen <= kLongRow ? 1 : 0;
   for (int k = 0; k < 3; k++) L.x[k] = c->x[k];
   for (int k = 0; k < 2; k++) L.u[k] = c->u[k];
   L.dl = c->dl;

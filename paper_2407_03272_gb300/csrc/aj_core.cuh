@@ -461,6 +461,7 @@ struct IterArgs {
   int sdiag_at, soff_at;      // stencil: entries of val holding the diagonal and the off-diagonal value
   unsigned long long smag;    // stencil: q / N = (q * smag) >> sshift for 0 <= q < 2^31
   int sshift;
+  int short_rows;             // 1: no row has more than kLongRow entries
   int jblk;                   // rows per block of J (1: diagonal J; 2, 4, 8: eq. J-blkdiag,
                               // jinv then holds row k of each block's inverse at jinv[k * jblk])
   int nsell;                  // SELL: rows in the sliced part
@@ -828,9 +829,22 @@ __host__ __device__ constexpr bool y_csr_f64() {
 #ifndef AJ_SELL_MINB
 #define AJ_SELL_MINB 4
 #endif
+// AJ_Y_CSR_TWO: the FP64 explicit-y CSR sweep keeps two rows per thread in
+// flight (tiles t and t + ncta), at AJ_Y_CSR_TWO_MINB CTAs/SM with chunks of
+// AJ_Y_CSR_TWO_U entries (256^3 Poisson: 0.464 ms per sweep at 4 CTAs/SM and
+// chunks of 4, against 0.486 ms with one row per thread at 5 CTAs/SM)
+#ifndef AJ_Y_CSR_TWO
+#define AJ_Y_CSR_TWO 1
+#endif
+#ifndef AJ_Y_CSR_TWO_MINB
+#define AJ_Y_CSR_TWO_MINB 4
+#endif
+#ifndef AJ_Y_CSR_TWO_U
+#define AJ_Y_CSR_TWO_U 4
+#endif
 template <class P, int SF, int FM, bool MULTI>
 __host__ __device__ constexpr int kernel_min_blocks() {
-  return y_csr_f64<P, SF, FM, MULTI>() ? AJ_Y_CSR_MINB
+  return y_csr_f64<P, SF, FM, MULTI>() ? (AJ_Y_CSR_TWO ? AJ_Y_CSR_TWO_MINB : AJ_Y_CSR_MINB)
          : (FM >= 3 && !MULTI && P::kId >= 2 && AJ_SELL_MINB > 0) ? AJ_SELL_MINB
          : MULTI ? P::kMinBlocksMulti : P::kMinBlocks;
 }
@@ -1108,10 +1122,100 @@ __device__ __forceinline__ bool stencil_stage_ok(const IterArgs<P>& a, const Rhs
   return ((AJ_STENCIL_STAGE >> P::kId) & 1) && a.jblk == 1 && (m & 15ull) == 0;
 }
 
+// The FP64 explicit-y CSR sweep with two rows per thread in flight: the
+// thread's row of tile t and of tile t + ncta (the next tile it would sweep)
+// load their chunks together, then each row sums and updates exactly as in
+// the one-row sweep, the first row first, so the iterates and the reduction
+// terms are the one-row sweep's bit for bit.  Only for matrices without
+// long rows (a.short_rows) and on sweeps without the check pass.
+template <class P, bool MON>
+__device__ __forceinline__ void sweep_csr_y_two(const IterArgs<P>& a, const RhsState& me, bool compute_x,
+                                                typename P::A (&acc)[kNRed], int cta, int ncta) {
+  using S = typename P::S;
+  using V = typename P::V;
+  using X = typename P::X;
+  constexpr int U = AJ_Y_CSR_TWO_U;
+  const X* yc = y_source(a, me);
+  const X* xp = xbuf(a, me.cur);
+  X* xn = xbuf(a, me.nxt);
+  X* yn = ubuf(a, 1 - me.yb);
+  const bool same = me.cur == me.prev;
+  const bool active = me.done == 0;
+  const YConst<P, true> yk(me);
+  const int n = a.n;
+  const int ntiles = (n + kThreads - 1) / kThreads;
+  for (int t1 = cta; t1 < ntiles; t1 += 2 * ncta) {
+    const int t2 = t1 + ncta;
+    const int i1 = t1 * kThreads + (int)threadIdx.x;
+    const int i2 = t2 * kThreads + (int)threadIdx.x;
+    const bool v1 = i1 < n && active;
+    const bool v2 = t2 < ntiles && i2 < n && active;
+    int rs1 = 0, c1 = 0, rs2 = 0, c2 = 0;
+    if (v1) {
+      rs1 = ld_ro(a.row_ptr + i1);
+      c1 = ld_ro(a.row_ptr + i1 + 1) - rs1;
+    }
+    if (v2) {
+      rs2 = ld_ro(a.row_ptr + i2);
+      c2 = ld_ro(a.row_ptr + i2 + 1) - rs2;
+    }
+    S s1 = v1 ? P::neg(P::ldr(a.b + i1)) : P::zero();
+    S s2 = v2 ? P::neg(P::ldr(a.b + i2)) : P::zero();
+    const int cm = c1 > c2 ? c1 : c2;
+    for (int q0 = 0; q0 < cm; q0 += U) {
+      int ca[U], cb[U];
+      V va[U], vb[U];
+#pragma unroll
+      for (int k = 0; k < U; k++) {
+        const bool ia = q0 + k < c1, ib = q0 + k < c2;
+        ca[k] = ia ? ld_ro(a.col + rs1 + q0 + k) : 0;
+        va[k] = ia ? P::ldv(a.val + rs1 + q0 + k) : P::vzero();
+        cb[k] = ib ? ld_ro(a.col + rs2 + q0 + k) : 0;
+        vb[k] = ib ? P::ldv(a.val + rs2 + q0 + k) : P::vzero();
+      }
+      S ya[U], yb[U];
+#pragma unroll
+      for (int k = 0; k < U; k++) {
+        ya[k] = q0 + k < c1 ? P::ldg(yc + ca[k]) : P::zero();
+        yb[k] = q0 + k < c2 ? P::ldg(yc + cb[k]) : P::zero();
+      }
+#pragma unroll
+      for (int k = 0; k < U; k++)
+        if (q0 + k < c1) P::macv(s1, va[k], ya[k]);
+#pragma unroll
+      for (int k = 0; k < U; k++)
+        if (q0 + k < c2) P::macv(s2, vb[k], yb[k]);
+    }
+#pragma unroll
+    for (int w = 0; w < 2; w++) {
+      const bool v = w == 0 ? v1 : v2;
+      if (!v) continue;
+      const int i = w == 0 ? i1 : i2;
+      const S g = P::finish(w == 0 ? s1 : s2);  // Q y^s - b
+      const S yi = P::ldg(yc + i);
+      if (MON) P::acc_prod(acc[1], g, g);
+      if (!compute_x) continue;
+      const S ji = P::ldr(a.jinv + i);
+      const S xi = same ? yi : P::ldx(xp + i);
+      const S xnew = P::fnma(ji, g, yi);
+      const S dx = P::sub(xnew, xi);
+      P::stx(xn + i, xnew);
+      P::stx(yn + i, P::fma_(yk.bnext, dx, xnew));
+      P::acc_prod(acc[0], g, dx);
+    }
+  }
+}
+
 template <class P, int SF, int FM, bool MULTI, bool MON = true>
 __device__ __forceinline__ void sweep(const IterArgs<P>& a, const RhsState* st, bool compute_x,
                                       bool want_obj, typename P::A (&acc)[kNRed], int cta,
                                       int ncta) {
+  if constexpr (y_csr_f64<P, SF, FM, MULTI>() && AJ_Y_CSR_TWO) {
+    if (a.short_rows && !y_check<P>(st[0])) {
+      sweep_csr_y_two<P, MON>(a, st[0], compute_x, acc, cta, ncta);
+      return;
+    }
+  }
   if constexpr (FM == 2 && !MULTI && SF == 3) {
     if (stencil_stage_ok<P>(a, st[0])) {
       sweep_stencil_y_staged<P, MON>(a, st[0], compute_x, acc, cta, ncta);

@@ -31,6 +31,7 @@ static IterArgs<P> typed_args(const IterLaunch& L) {
   a.smag = L.smag;
   a.sshift = L.sshift;
   a.jblk = L.jblk < 1 ? 1 : L.jblk;
+  a.short_rows = L.short_rows;
   a.nsell = L.nsell;
   a.sell_cl = L.sell_cl ? L.sell_cl : 5;
   a.ntiles_sell = L.ntiles_sell;

@@ -20,6 +20,7 @@ struct IterLaunch {
   unsigned long long smag;          // stencil: q / N = (q * smag) >> sshift for 0 <= q < 2^31
   int sshift;
   int jblk;                         // rows per block of J (1: diagonal)
+  int short_rows;                   // 1: no row has more than 32 entries (zero: not known)
   int nsell;
   int sell_cl;  // log2 of the SELL slice height
   int ntiles_sell;
