@@ -842,6 +842,12 @@ __host__ __device__ constexpr bool y_csr_f64() {
 #ifndef AJ_Y_CSR_TWO_U
 #define AJ_Y_CSR_TWO_U 4
 #endif
+// AJ_Y_CSR_TWO_EARLY: 0 loads J^-1_i and x^{t-1}_i after the row sums; 1 loads
+// them before the chunk loop; 2 prefetches their lines into L2 before it.
+// Measured per 256^3 sweep: 0.457 ms, 0.515 ms (spills), 0.464 ms.
+#ifndef AJ_Y_CSR_TWO_EARLY
+#define AJ_Y_CSR_TWO_EARLY 0
+#endif
 template <class P, int SF, int FM, bool MULTI>
 __host__ __device__ constexpr int kernel_min_blocks() {
   return y_csr_f64<P, SF, FM, MULTI>() ? (AJ_Y_CSR_TWO ? AJ_Y_CSR_TWO_MINB : AJ_Y_CSR_MINB)
@@ -1161,6 +1167,26 @@ __device__ __forceinline__ void sweep_csr_y_two(const IterArgs<P>& a, const RhsS
     }
     S s1 = v1 ? P::neg(P::ldr(a.b + i1)) : P::zero();
     S s2 = v2 ? P::neg(P::ldr(a.b + i2)) : P::zero();
+    S e_j1 = P::zero(), e_j2 = P::zero(), e_x1 = P::zero(), e_x2 = P::zero();
+    if constexpr (AJ_Y_CSR_TWO_EARLY == 1) {
+      if (v1 && compute_x) {
+        e_j1 = P::ldr(a.jinv + i1);
+        if (!same) e_x1 = P::ldx(xp + i1);
+      }
+      if (v2 && compute_x) {
+        e_j2 = P::ldr(a.jinv + i2);
+        if (!same) e_x2 = P::ldx(xp + i2);
+      }
+    } else if constexpr (AJ_Y_CSR_TWO_EARLY == 2) {
+      if (v1 && compute_x) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.jinv + i1));
+        if (!same) asm volatile("prefetch.global.L2 [%0];" ::"l"(xp + i1));
+      }
+      if (v2 && compute_x) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.jinv + i2));
+        if (!same) asm volatile("prefetch.global.L2 [%0];" ::"l"(xp + i2));
+      }
+    }
     const int cm = c1 > c2 ? c1 : c2;
     for (int q0 = 0; q0 < cm; q0 += U) {
       int ca[U], cb[U];
@@ -1195,8 +1221,14 @@ __device__ __forceinline__ void sweep_csr_y_two(const IterArgs<P>& a, const RhsS
       const S yi = P::ldg(yc + i);
       if (MON) P::acc_prod(acc[1], g, g);
       if (!compute_x) continue;
-      const S ji = P::ldr(a.jinv + i);
-      const S xi = same ? yi : P::ldx(xp + i);
+      S ji, xi;
+      if constexpr (AJ_Y_CSR_TWO_EARLY == 1) {
+        ji = w == 0 ? e_j1 : e_j2;
+        xi = same ? yi : (w == 0 ? e_x1 : e_x2);
+      } else {
+        ji = P::ldr(a.jinv + i);
+        xi = same ? yi : P::ldx(xp + i);
+      }
       const S xnew = P::fnma(ji, g, yi);
       const S dx = P::sub(xnew, xi);
       P::stx(xn + i, xnew);
